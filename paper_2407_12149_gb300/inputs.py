@@ -1,0 +1,207 @@
+"""Seeded synthetic problem generators for the MGMC sampler.
+
+This module holds none of the sampler's arithmetic: it only produces the
+inputs that define a posterior problem (Sec. 5.1 of the paper) -- the
+coefficient field kappa^2(x), observation locations and values, the noise
+covariance Gamma, the rows of the observation operator B (point evaluation
+of the piecewise multilinear grid function, Eq. B_ell_definition) and the
+vector F_L of a box-average quantity of interest (Eq. F_matrix).  Both the
+CUDA library and the CPU oracle consume these arrays; neither is imported
+here.
+
+Grids: a level with n interior points per axis has vertices at (i + 1) h,
+i = 0 .. n-1, h = 1 / (n + 1); zero Dirichlet values sit at i = -1 and i = n.
+Site index s = i + n (j + n k) (x fastest).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import Optional
+
+import numpy as np
+
+
+def kappa2_field(n: int, dim: int, seed: int, base: float = 10.0, std: float = 0.5,
+                 length: float = 0.1, n_features: int = 512) -> np.ndarray:
+    """Non-stationary kappa^2(x) = base * exp(g(x)) on the interior vertices.
+
+    g is a random-Fourier-feature approximation (Rahimi & Recht 2007) of a
+    centred Gaussian field with squared-exponential covariance
+    std^2 exp(-|x-y|^2 / (2 length^2)):
+        g(x) = std sqrt(2/K) sum_k cos(w_k . x + b_k),
+        w_k ~ N(0, length^-2 I), b_k ~ U[0, 2 pi).
+    Evaluated separably through complex exponentials.  Returns float64 [n^dim].
+    """
+    rng = np.random.default_rng(seed)
+    w = rng.normal(0.0, 1.0 / length, size=(n_features, dim))
+    b = rng.uniform(0.0, 2.0 * np.pi, size=n_features)
+    h = 1.0 / (n + 1)
+    x = (np.arange(n) + 1.0) * h
+    ph = [np.exp(1j * np.outer(w[:, a], x)) for a in range(dim)]   # [K, n] per axis
+    c = np.exp(1j * b) * std * np.sqrt(2.0 / n_features)
+    if dim == 2:
+        g = np.real((ph[1].T * c) @ ph[0])                            # [y, x]
+    else:
+        g = np.empty((n, n, n))
+        for kz in range(n):
+            g[kz] = np.real((ph[1].T * (c * ph[2][:, kz])) @ ph[0])
+    return (base * np.exp(g)).ravel()
+
+
+def obs_locations(m: int, dim: int, seed: int) -> np.ndarray:
+    """m observation points, seeded uniform in (0, 1)^dim."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(0.0, 1.0, size=(m, dim))
+
+
+def obs_values(m: int, seed: int, lo: float = 1.0, hi: float = 4.0) -> np.ndarray:
+    """Observed values y_j in [1, 4] as in Sec. 5.1.2 of the paper."""
+    rng = np.random.default_rng(seed + 7919)
+    return rng.uniform(lo, hi, size=m)
+
+
+def point_obs_rows(n: int, dim: int, xyz: np.ndarray):
+    """Rows of B for point observations: multilinear interpolation weights.
+
+    For each point the 2^dim vertices of the enclosing cell get the product of
+    1D hat-function values; a boundary vertex (zero Dirichlet value) is
+    reported as site -1 with weight 0.  Returns (site int32 [m, 2^dim],
+    weight float64 [m, 2^dim]); corner order: bit a of the corner index
+    selects the upper vertex along axis a.
+    """
+    xyz = np.atleast_2d(np.asarray(xyz, dtype=np.float64))
+    m = xyz.shape[0]
+    h = 1.0 / (n + 1)
+    nc = 1 << dim
+    site = np.full((m, nc), -1, dtype=np.int32)
+    wts = np.zeros((m, nc), dtype=np.float64)
+    for k in range(m):
+        cell = np.minimum(np.floor(xyz[k] / h).astype(np.int64), n)   # vertex index of lower corner
+        t = xyz[k] / h - cell
+        for corner in range(nc):
+            w = 1.0
+            idx = []
+            for a in range(dim):
+                up = (corner >> a) & 1
+                v = cell[a] + up                 # vertex index 0 .. n+1
+                w *= t[a] if up else (1.0 - t[a])
+                idx.append(v - 1)                # interior index
+            if all(0 <= i < n for i in idx) and w != 0.0:
+                s = idx[0] + n * idx[1] + (n * n * idx[2] if dim == 3 else 0)
+                site[k, corner] = s
+                wts[k, corner] = w
+    return site, wts
+
+
+def qoi_box(n: int, dim: int, c0: int, c1: int):
+    """F_L for the average of the multilinear interpolant over the box
+    [c0 h, c1 h]^dim (c0 < c1 are vertex indices of grid lines).
+
+    Exact for piecewise multilinear functions: vertex weight = product of 1D
+    trapezoid weights (1/2 on the box faces, 1 inside) / (c1 - c0)^dim.
+    Returns (site int32, weight float64) over the interior vertices with
+    nonzero weight.
+    """
+    if not (0 <= c0 < c1 <= n + 1):
+        raise ValueError("box outside the grid")
+    w1 = np.zeros(n)
+    for v in range(c0, c1 + 1):
+        i = v - 1
+        if 0 <= i < n:
+            w1[i] = 0.5 if v in (c0, c1) else 1.0
+    w1 /= (c1 - c0)
+    if dim == 2:
+        W = np.outer(w1, w1)                       # [j, i]
+    else:
+        W = np.einsum("k,j,i->kji", w1, w1, w1)
+    flat = W.ravel()
+    sites = np.nonzero(flat)[0].astype(np.int32)
+    return sites, flat[sites].copy()
+
+
+def central_box(n: int, cells: int):
+    """Vertex-line indices of the central box of `cells` cells per axis."""
+    ncell = n + 1
+    c0 = (ncell - cells) // 2
+    return c0, c0 + cells
+
+
+@dataclass
+class Problem:
+    """A posterior problem N(A~^-1 f, A~^-1) on one grid (Sec. 5.1)."""
+    name: str
+    dim: int
+    n: int
+    n_levels: int
+    kappa2: Optional[np.ndarray]          # float64 [n^dim] or None
+    kappa2_const: float = 10.0
+    obs_site: Optional[np.ndarray] = None # int32 [m, 2^dim]
+    obs_w: Optional[np.ndarray] = None    # float64 [m, 2^dim]
+    Gamma: Optional[np.ndarray] = None    # float64 [m, m]
+    y: Optional[np.ndarray] = None        # float64 [m]
+    qoi_site: Optional[np.ndarray] = None
+    qoi_w: Optional[np.ndarray] = None
+    scale_hd: int = 1
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def m(self) -> int:
+        return 0 if self.obs_site is None else int(self.obs_site.shape[0])
+
+    @property
+    def N(self) -> int:
+        return self.n ** self.dim
+
+
+def levels_for(n: int, coarsest: int = 1) -> int:
+    """Number of grids n -> (n-1)/2 -> ... down to `coarsest` points per axis."""
+    L, nn = 1, n
+    while nn > coarsest:
+        if (nn - 1) % 2:
+            raise ValueError("n must be 2^k - 1")
+        nn = (nn - 1) // 2
+        L += 1
+    if nn != coarsest:
+        raise ValueError("coarsest size not reachable")
+    return L
+
+
+def make_problem(name: str, dim: int, n: int, *, n_levels: Optional[int] = None,
+                 coarsest: int = 1, kappa2_seed: Optional[int] = None, kappa2_const: float = 10.0,
+                 m: int = 0, obs_seed: int = 1, sigma2: float = 1e-4, qoi_cells: Optional[int] = None,
+                 scale_hd: int = 1) -> Problem:
+    """Assemble a seeded problem.  kappa2_seed=None gives constant kappa^2."""
+    if n_levels is None:
+        n_levels = levels_for(n, coarsest)
+    k2 = None if kappa2_seed is None else kappa2_field(n, dim, kappa2_seed)
+    p = Problem(name=name, dim=dim, n=n, n_levels=n_levels, kappa2=k2, kappa2_const=kappa2_const,
+                scale_hd=scale_hd)
+    if m > 0:
+        xyz = obs_locations(m, dim, obs_seed)
+        p.obs_site, p.obs_w = point_obs_rows(n, dim, xyz)
+        p.Gamma = sigma2 * np.eye(m)
+        p.y = obs_values(m, obs_seed)
+        p.meta["obs_xyz"] = xyz
+    if qoi_cells is not None:
+        c0, c1 = central_box(n, qoi_cells)
+        p.qoi_site, p.qoi_w = qoi_box(n, dim, c0, c1)
+        p.meta["qoi_box"] = (c0, c1)
+    return p
+
+
+def config1() -> Problem:
+    """Plain MGMC, 31^2, kappa^2 = 10, no observations, 4 grids, QoI central 8x8 cells."""
+    return make_problem("plain-2d-31", 2, 31, n_levels=4, kappa2_const=10.0, qoi_cells=8)
+
+
+def config2(n: int = 1023, n_levels: Optional[int] = None) -> Problem:
+    """Bayesian 2D, non-stationary kappa^2, 16 point observations, Gamma = 1e-4 I."""
+    return make_problem(f"bayes-2d-{n}", 2, n, n_levels=n_levels, kappa2_seed=2024, m=16, obs_seed=1,
+                        qoi_cells=max(2, (46 * (n + 1)) // 1024))
+
+
+def config3(n: int = 127, n_levels: Optional[int] = None) -> Problem:
+    """Bayesian 3D, kappa^2 = 25, 32 point observations, coarsest 3^3, QoI central 16^3 cells."""
+    return make_problem(f"bayes-3d-{n}", 3, n, n_levels=n_levels, coarsest=3 if n_levels is None else 1,
+                        kappa2_const=25.0, m=32, obs_seed=3,
+                        qoi_cells=max(2, (16 * (n + 1)) // 128))

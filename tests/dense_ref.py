@@ -1,0 +1,138 @@
+"""Dense-matrix constructions written from the definitions, used to pin the oracle.
+
+Everything here is built from the problem definition with dense linear
+algebra (numpy solves / Cholesky) rather than sweeps or stencils, so that it
+shares no code path with the oracle:
+  - A_L from the finite-difference formula s (kappa^2 I - Delta_h);
+  - P from the coarse hat functions evaluated at the fine vertices (Sec. 5.1.3);
+  - A_{l-1} = P^T A_l P and B_{l-1} = P^T B_l (Eq. A_ell_1_B_ell_1);
+  - the forward/backward low-rank Gibbs splittings M~ = D + L + B Gamma^-1 B^T
+    (Eq. M_lowrank_gibbs) with L the strictly lower part in colour order;
+  - the deterministic V-cycle iteration matrix X_L (Lemma MG-iteration-rep).
+"""
+import numpy as np
+
+
+def fd_operator(n, d, kappa2, scale_hd=1):
+    h = 1.0 / (n + 1)
+    N = n ** d
+    k2 = np.broadcast_to(np.asarray(kappa2, dtype=float), (N,)) if np.ndim(kappa2) == 0 else np.asarray(kappa2)
+    s = h ** d if scale_hd else 1.0
+    # 1D second-difference matrix and Kronecker sums: -Delta_h = sum_a I x T x I
+    T = (2.0 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)) / (h * h)
+    I = np.eye(n)
+    if d == 2:
+        lap = np.kron(I, T) + np.kron(T, I)
+    else:
+        lap = np.kron(np.kron(I, I), T) + np.kron(np.kron(I, T), I) + np.kron(np.kron(T, I), I)
+    return s * (lap + np.diag(k2))
+
+
+def prolongation_1d(nc):
+    """Coarse hat functions (width 2H, H = 2h) sampled at the fine interior vertices."""
+    nf = 2 * nc + 1
+    hf = 1.0 / (nf + 1)
+    H = 2.0 * hf
+    xf = (np.arange(nf) + 1.0) * hf
+    Xc = (np.arange(nc) + 1.0) * H
+    return np.maximum(0.0, 1.0 - np.abs(xf[:, None] - Xc[None, :]) / H)
+
+
+def prolongation(nc, d):
+    P1 = prolongation_1d(nc)
+    if d == 2:
+        return np.kron(P1, P1)
+    return np.kron(np.kron(P1, P1), P1)
+
+
+def colour_order(n, d):
+    """Sites in colour-major order (the parity-colour reading), lexicographic inside."""
+    if d == 2:
+        seq = [(0, 0), (1, 1), (0, 1), (1, 0)]
+    else:
+        seq = [(0, 0, 0), (0, 1, 1), (1, 0, 1), (1, 1, 0), (0, 0, 1), (0, 1, 0), (1, 0, 0), (1, 1, 1)]
+    idx = np.arange(n ** d)
+    coords = [idx % n, (idx // n) % n] + ([idx // (n * n)] if d == 3 else [])
+    perm = []
+    for c in seq:
+        mask = np.ones(n ** d, bool)
+        for a in range(d):
+            mask &= (coords[a] % 2) == c[a]
+        perm.extend(idx[mask].tolist())
+    return np.array(perm)
+
+
+def B_dense(N, obs_site, obs_w):
+    m = obs_site.shape[0]
+    B = np.zeros((N, m))
+    for k in range(m):
+        for s, w in zip(obs_site[k], obs_w[k]):
+            if s >= 0:
+                B[s, k] += w
+    return B
+
+
+class Hierarchy:
+    """Dense operators of every level, index 0 = coarsest."""
+
+    def __init__(self, n, d, n_levels, kappa2, B=None, Gamma=None, scale_hd=1):
+        self.d = d
+        self.A = [None] * n_levels
+        self.B = [None] * n_levels
+        self.P = [None] * n_levels     # P[l]: level l-1 -> l
+        self.n = [None] * n_levels
+        A = fd_operator(n, d, kappa2, scale_hd)
+        self.A[-1] = A
+        self.B[-1] = B if B is not None else np.zeros((n ** d, 0))
+        self.n[-1] = n
+        nn = n
+        for l in range(n_levels - 1, 0, -1):
+            nc = (nn - 1) // 2
+            P = prolongation(nc, d)
+            self.P[l] = P
+            self.A[l - 1] = P.T @ self.A[l] @ P
+            self.B[l - 1] = P.T @ self.B[l]
+            self.n[l - 1] = nc
+            nn = nc
+        m = self.B[-1].shape[1]
+        self.Gamma = Gamma if Gamma is not None else np.zeros((0, 0))
+        self.Gi = np.linalg.inv(self.Gamma) if m else np.zeros((0, 0))
+        self.m = m
+
+    def Atilde(self, l):
+        return self.A[l] + self.B[l] @ self.Gi @ self.B[l].T
+
+    def splitting(self, l, direction):
+        """M~ of Eq. M_lowrank_gibbs (omega = 1) in natural site order."""
+        A = self.A[l]
+        perm = colour_order(self.n[l], self.d)
+        Ap = A[np.ix_(perm, perm)]
+        Mp = np.tril(Ap) if direction == 0 else np.triu(Ap)
+        M = np.zeros_like(A)
+        M[np.ix_(perm, perm)] = Mp
+        return M + self.B[l] @ self.Gi @ self.B[l].T
+
+    def smoother_matrix(self, l, direction):
+        M = self.splitting(l, direction)
+        return np.eye(M.shape[0]) - np.linalg.solve(M, self.Atilde(l))
+
+    def iteration_matrix(self, l=None):
+        """X_l of the noise-free V(1,1)-cycle with exact coarsest solve."""
+        if l is None:
+            l = len(self.A) - 1
+        At = self.Atilde(l)
+        N = At.shape[0]
+        if l == 0:
+            return np.zeros((N, N))
+        P = self.P[l]
+        Ac = self.Atilde(l - 1)
+        Xc = self.iteration_matrix(l - 1)
+        cgc = np.eye(N) - P @ (np.eye(Ac.shape[0]) - Xc) @ np.linalg.solve(Ac, P.T @ At)
+        return self.smoother_matrix(l, 1) @ cgc @ self.smoother_matrix(l, 0)
+
+
+def a_norm(X, A):
+    w, V = np.linalg.eigh(A)
+    Ah = (V * np.sqrt(w)) @ V.T
+    Aih = (V / np.sqrt(w)) @ V.T
+    return np.linalg.norm(Ah @ X @ Aih, 2)
