@@ -60,7 +60,7 @@ def lib():
         L.oracle_level_G_support.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
         L.oracle_coarsest_dense.argtypes = [ctypes.c_void_p, _c_dbl_p]
         L.oracle_smoother_step_given.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
-                                                 _c_dbl_p, _c_dbl_p, _c_dbl_p, _c_dbl_p]
+                                                 _c_dbl_p, _c_dbl_p, _c_dbl_p, _c_dbl_p, _c_dbl_p]
         L.oracle_sample.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64,
                                     ctypes.c_uint32, ctypes.c_int, _c_dbl_p, _c_dbl_p]
         L.oracle_mean_solve.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, _c_dbl_p,
@@ -181,12 +181,14 @@ class Oracle:
         return lib().oracle_rel_residual(self._h, _dp(x))
 
     # -- method --------------------------------------------------------
-    def smoother_step_given(self, l, direction, x, f, zdiag, zlr):
+    def smoother_step_given(self, l, direction, x, fd, zdiag, zlr, d=None):
+        """Alg. 3 on level l for the right-hand side fd + B_l Gamma^-1 d."""
         x = np.array(x, dtype=np.float64, copy=True)
-        f = np.ascontiguousarray(f, dtype=np.float64)
+        fd = np.ascontiguousarray(fd, dtype=np.float64)
         zd = np.ascontiguousarray(zdiag, dtype=np.float64)
         zl = np.ascontiguousarray(zlr if zlr is not None else np.zeros(max(self.m, 1)), dtype=np.float64)
-        rc = lib().oracle_smoother_step_given(self._h, l, direction, _dp(x), _dp(f), _dp(zd), _dp(zl))
+        dv = np.ascontiguousarray(d if d is not None else np.zeros(max(self.m, 1)), dtype=np.float64)
+        rc = lib().oracle_smoother_step_given(self._h, l, direction, _dp(x), _dp(fd), _dp(dv), _dp(zd), _dp(zl))
         if rc:
             raise OracleError(rc)
         return x

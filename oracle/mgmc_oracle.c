@@ -18,16 +18,29 @@
  *  Eq. (f_ell_definition):  f_L = B Gamma^-1 y.
  *  Eq. (galerkin_triple_product): A~_l = A_l + B_l Gamma^-1 B_l^T.
  *  Alg. 3 + Eq. (lowrank_gibbs_two_steps), (Bellstar_definition):
- *    theta* = theta + (D + L)^-1 (f + xi - A theta) as a colour-ordered
- *    Gauss-Seidel sweep, xi = D^{1/2} z + B L_Gamma^-T z',
+ *    theta* = theta + (D + L)^-1 (f + xi - A theta),
+ *    xi = D^{1/2} z + B xi_LR, xi_LR = L_Gamma^-T z',
  *    theta' = theta* - G (B^T theta*),  G = C (Gamma + B^T C)^-1,
  *    C = (D + L)^-1 B; backward direction swaps L <-> L^T.
  *    (Alg. 3's triangular solve is read as the increment form of
  *    Eq. lowrank_gibbs_two_steps.)
+ *    Evaluation: every level's right-hand side is held as
+ *    f_l = fd_l + B_l Gamma^-1 d_l (dense fd_l, data vector d_l; on the
+ *    finest level fd_L = 0, d_L = y, Eq. f_ell_definition).  Splitting the
+ *    sweep's right-hand side into its dense part s and B u,
+ *    u = Gamma^-1 d + xi_LR, gives theta* = theta*_s + C u with theta*_s the
+ *    Gauss-Seidel sweep of the dense part alone, and since
+ *    C - G B^T C = G Gamma (from Eq. Bellstar_definition),
+ *        theta' = theta*_s - G (B^T theta*_s - d - L_Gamma z').
+ *    This is the same update; it avoids forming theta*, whose entries near
+ *    an observation reach |Gamma^-1 y| w / a_ii and cancel in theta'.
  *  Alg. 1 with gamma = 1 (V-cycle), nu1 forward / nu2 backward sweeps,
  *    f_{l-1} = P^T (f_l - A~_l theta), coarse start psi = 0, theta += P psi.
+ *    With the split: fd_{l-1} = P^T (fd_l - A_l theta) and
+ *    d_{l-1} = d_l - B_l^T theta (because P^T B_l = B_{l-1}).
  *  Sec. 3.4 / Sec. 5.1.3: exact coarsest sampler
- *    theta_0 = A~_0^-1 f_0 + L_0^-T z  with A~_0 = L_0 L_0^T.
+ *    theta_0 = A~_0^-1 f_0 + L_0^-T z  with A~_0 = L_0 L_0^T,
+ *    f_0 = fd_0 + B_0 Gamma^-1 d_0.
  *  Eq. (MGMC_estimator), Sec. 5.3.2: QoI series F^T theta, lagged
  *    autocovariance with divisor n - t, IACT with Wolff's automatic window.
  *
@@ -77,8 +90,9 @@ typedef struct {
     int g_nrows[2];
     int* g_site[2];
     double* g_val[2];
-    /* work vectors for the cycle */
+    /* work vectors for the cycle: dense right-hand side fd, data vector d */
     double* f;
+    double* dv;
     double* x;
     double* r;
     double* e;
@@ -406,9 +420,9 @@ static void gs_sweep(const oracle_problem* p, int l, const olevel* L, int dir, d
     }
 }
 
-/* Low-rank noise xi_LR = L_Gamma^-T z' (z' standard normal), Sec. 3.5. */
-static void lowrank_noise(const oracle_problem* p, int l, uint32_t slot, const double* zgiven,
-                          double* xi)
+/* Gamma xi_LR = L_Gamma z' (z' standard normal), the low-rank noise of Sec. 2.4
+ * in the units of the data vector. */
+static void lowrank_noise(const oracle_problem* p, int l, uint32_t slot, const double* zgiven, double* gxi)
 {
     int m = p->m;
     double* zp = malloc(sizeof(double) * (m > 0 ? m : 1));
@@ -416,38 +430,38 @@ static void lowrank_noise(const oracle_problem* p, int l, uint32_t slot, const d
         zp[k] = zgiven ? zgiven[k] : draw(p, 1u, l, slot, (uint32_t)(k >> 1), k & 1);
     for (int k = 0; k < m; ++k) {
         double acc = 0.0;
-        for (int t = 0; t < m; ++t) acc += p->LGinvT[k * m + t] * zp[t];
-        xi[k] = acc;
+        for (int t = 0; t <= k; ++t) acc += p->LG[k * m + t] * zp[t];
+        gxi[k] = acc;
     }
     free(zp);
 }
 
-/* Alg. 3: one Gibbs smoother step with low-rank correction on level l. */
-static void lowrank_gibbs(const oracle_problem* p, int l, int dir, double* x, const double* f,
+/* Alg. 3: one Gibbs smoother step with low-rank correction on level l,
+ * right-hand side fd + B Gamma^-1 d:
+ *   theta*_s = Gauss-Seidel sweep of fd + D^{1/2} z,
+ *   theta'   = theta*_s - G (B^T theta*_s - d - L_Gamma z'). */
+static void lowrank_gibbs(const oracle_problem* p, int l, int dir, double* x, const double* fd, const double* d,
                           uint32_t slot, const double* zdiag, const double* zlr, int use_noise)
 {
     olevel* L = &p->lev[l];
     int m = p->m;
-    double* e = NULL;
-    if (m > 0 && use_noise) {
-        double* xi = malloc(sizeof(double) * m);
-        lowrank_noise(p, l, slot, zlr, xi);
-        e = L->e;
-        apply_B(p, L, xi, e);
-        free(xi);
-    }
-    /* theta* = theta + (D + L)^-1 (f + xi - A theta) */
-    gs_sweep(p, l, L, dir, x, f, e, zdiag, slot, use_noise);
+    gs_sweep(p, l, L, dir, x, fd, NULL, zdiag, slot, use_noise);
     if (m == 0) return;
-    /* theta' = theta* - G (B^T theta*) */
-    double* z = malloc(sizeof(double) * m);
-    apply_Bt(p, L, x, z);
+    double* v = malloc(sizeof(double) * m * 2);
+    double* gxi = v + m;
+    apply_Bt(p, L, x, v);
+    if (use_noise) {
+        lowrank_noise(p, l, slot, zlr, gxi);
+        for (int k = 0; k < m; ++k) v[k] = v[k] - d[k] - gxi[k];
+    } else {
+        for (int k = 0; k < m; ++k) v[k] = v[k] - d[k];
+    }
     for (int r = 0; r < L->g_nrows[dir]; ++r) {
         double acc = 0.0;
-        for (int k = 0; k < m; ++k) acc += L->g_val[dir][(size_t)r * m + k] * z[k];
+        for (int k = 0; k < m; ++k) acc += L->g_val[dir][(size_t)r * m + k] * v[k];
         x[L->g_site[dir][r]] -= acc;
     }
-    free(z);
+    free(v);
 }
 
 /* ------------------------------------------------------------------ */
@@ -465,6 +479,7 @@ static void free_level(olevel* L)
         free(L->g_val[dir]);
     }
     free(L->f);
+    free(L->dv);
     free(L->x);
     free(L->r);
     free(L->e);
@@ -496,11 +511,12 @@ static int alloc_level(oracle_problem* p, olevel* L, int n)
     for (int a = 1; a < p->d; ++a) L->N *= n;
     L->a = calloc((size_t)L->N * p->NS, sizeof(double));
     L->f = calloc((size_t)L->N, sizeof(double));
+    L->dv = calloc((size_t)(p->m > 0 ? p->m : 1), sizeof(double));
     L->x = calloc((size_t)L->N, sizeof(double));
     L->r = calloc((size_t)L->N, sizeof(double));
     L->e = calloc((size_t)L->N, sizeof(double));
     L->b_ptr = calloc((size_t)p->m + 1, sizeof(int));
-    if (!L->a || !L->f || !L->x || !L->r || !L->e || !L->b_ptr) return ERR_OOM;
+    if (!L->a || !L->f || !L->dv || !L->x || !L->r || !L->e || !L->b_ptr) return ERR_OOM;
     return 0;
 }
 
@@ -903,13 +919,22 @@ fail:
 /* coarsest exact sampler and the V-cycle (Alg. 1)                     */
 /* ------------------------------------------------------------------ */
 
-static void coarsest_sample(oracle_problem* p, double* x, const double* f)
+static void coarsest_sample(oracle_problem* p, double* x, const double* fd, const double* d)
 {
-    int n0 = p->n0;
+    int n0 = p->n0, m = p->m;
+    olevel* L0 = &p->lev[0];
     double* yv = malloc(sizeof(double) * n0);
+    double* f0 = malloc(sizeof(double) * n0);
+    /* f_0 = fd_0 + B_0 Gamma^-1 d_0 */
+    memcpy(f0, fd, sizeof(double) * n0);
+    for (int k = 0; k < m; ++k) {
+        double gk = 0.0;
+        for (int t = 0; t < m; ++t) gk += p->Gamma_inv[k * m + t] * d[t];
+        for (int e = L0->b_ptr[k]; e < L0->b_ptr[k + 1]; ++e) f0[L0->b_site[e]] += L0->b_w[e] * gk;
+    }
     /* L y = f */
     for (int i = 0; i < n0; ++i) {
-        double acc = f[i];
+        double acc = f0[i];
         for (int t = 0; t < i; ++t) acc -= p->L0[(size_t)i * n0 + t] * yv[t];
         yv[i] = acc / p->L0[(size_t)i * n0 + i];
     }
@@ -922,6 +947,7 @@ static void coarsest_sample(oracle_problem* p, double* x, const double* f)
         x[i] = acc / p->L0[(size_t)i * n0 + i];
     }
     free(yv);
+    free(f0);
 }
 
 static void restrict_to(const oracle_problem* p, const olevel* F, const olevel* C,
@@ -972,23 +998,28 @@ static void prolong_add(const oracle_problem* p, const olevel* C, const olevel* 
     }
 }
 
-static void mgmc_level(oracle_problem* p, int l, double* x, const double* f)
+static void mgmc_level(oracle_problem* p, int l, double* x, const double* fd, const double* d)
 {
     if (l == 0) {
-        coarsest_sample(p, x, f);
+        coarsest_sample(p, x, fd, d);
         return;
     }
     olevel* L = &p->lev[l];
     olevel* C = &p->lev[l - 1];
-    for (int j = 0; j < p->nu1; ++j) lowrank_gibbs(p, l, 0, x, f, (uint32_t)(2 * j), NULL, NULL, p->noise);
-    /* f_{l-1} = P^T (f_l - A~_l theta) */
-    apply_Atilde(p, L, x, L->r);
-    for (int s = 0; s < L->N; ++s) L->r[s] = f[s] - L->r[s];
+    for (int j = 0; j < p->nu1; ++j) lowrank_gibbs(p, l, 0, x, fd, d, (uint32_t)(2 * j), NULL, NULL, p->noise);
+    /* f_{l-1} = P^T (f_l - A~_l theta):  fd_{l-1} = P^T (fd_l - A_l theta),
+       d_{l-1} = d_l - B_l^T theta */
+    apply_A(p, L, x, L->r);
+    for (int s = 0; s < L->N; ++s) L->r[s] = fd[s] - L->r[s];
     restrict_to(p, L, C, L->r, C->f);
+    if (p->m > 0) {
+        apply_Bt(p, L, x, C->dv);
+        for (int k = 0; k < p->m; ++k) C->dv[k] = d[k] - C->dv[k];
+    }
     memset(C->x, 0, sizeof(double) * C->N);
-    mgmc_level(p, l - 1, C->x, C->f);
+    mgmc_level(p, l - 1, C->x, C->f, C->dv);
     prolong_add(p, C, L, C->x, x);
-    for (int j = 0; j < p->nu2; ++j) lowrank_gibbs(p, l, 1, x, f, (uint32_t)(2 * j + 1), NULL, NULL, p->noise);
+    for (int j = 0; j < p->nu2; ++j) lowrank_gibbs(p, l, 1, x, fd, d, (uint32_t)(2 * j + 1), NULL, NULL, p->noise);
 }
 
 static double qoi_of(const oracle_problem* p, const double* x)
@@ -1007,7 +1038,10 @@ int oracle_sample(oracle_problem* p, int64_t n_steps, uint64_t seed, uint64_t st
     p->noise = noise ? 1 : 0;
     for (int64_t s = 0; s < n_steps; ++s) {
         p->cycle = step_offset + (uint64_t)s;
-        mgmc_level(p, p->n_levels - 1, x, p->fL);
+        olevel* Lf = &p->lev[p->n_levels - 1];
+        memset(Lf->f, 0, sizeof(double) * Lf->N);      /* fd_L = 0 */
+        if (p->m > 0) memcpy(Lf->dv, p->y, sizeof(double) * p->m);   /* d_L = y */
+        mgmc_level(p, p->n_levels - 1, x, Lf->f, Lf->dv);
         if (qoi_out) qoi_out[s] = qoi_of(p, x);
     }
     return 0;
@@ -1102,11 +1136,11 @@ int oracle_coarsest_dense(const oracle_problem* p, double* out)
     return 0;
 }
 
-int oracle_smoother_step_given(const oracle_problem* p, int l, int dir, double* x, const double* f,
-                               const double* zdiag, const double* zlr)
+int oracle_smoother_step_given(const oracle_problem* p, int l, int dir, double* x, const double* fd,
+                               const double* d, const double* zdiag, const double* zlr)
 {
-    if (!p || l < 1 || l >= p->n_levels || !x || !f || !zdiag || (p->m > 0 && !zlr)) return ERR_ARG;
-    lowrank_gibbs(p, l, dir, x, f, 0u, zdiag, zlr, 1);
+    if (!p || l < 1 || l >= p->n_levels || !x || !fd || !zdiag || (p->m > 0 && (!zlr || !d))) return ERR_ARG;
+    lowrank_gibbs(p, l, dir, x, fd, d, 0u, zdiag, zlr, 1);
     return 0;
 }
 

@@ -53,11 +53,12 @@ int oracle_level_G_support(const oracle_problem* p, int l, int dir);
 int oracle_coarsest_dense(const oracle_problem* p, double* out);
 
 /* One Alg. 3 step (Gibbs smoother with low-rank correction) on level l
- * with the random numbers supplied: zdiag[N] standard normals for
- * xi_diag = D^{1/2} zdiag and zlr[m] standard normals for
- * xi_LR = L_Gamma^{-T} zlr.  x (in/out) and f are dense level vectors. */
+ * for the right-hand side f = fd + B_l Gamma^-1 d, with the random numbers
+ * supplied: zdiag[N] standard normals for xi_diag = D^{1/2} zdiag and zlr[m]
+ * standard normals for xi_LR = L_Gamma^{-T} zlr.  x (in/out) and fd are
+ * dense level vectors, d has m entries. */
 int oracle_smoother_step_given(const oracle_problem* p, int l, int dir,
-                               double* x, const double* f,
+                               double* x, const double* fd, const double* d,
                                const double* zdiag, const double* zlr);
 
 /* Run n_steps MGMC V-cycles (Alg. 1, gamma = 1) on the finest level.

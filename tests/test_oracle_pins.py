@@ -111,7 +111,8 @@ def test_galerkin_equals_dense_PtAP(dim, n, levels, var_kappa):
 @pytest.mark.parametrize("dim,n,levels", [(2, 15, 3), (3, 7, 2)])
 @pytest.mark.parametrize("direction", [0, 1])
 def test_alg3_equals_generic_random_smoother(dim, n, levels, direction):
-    """theta' of Alg. 3 == theta + M~^-1 (f + xi - A~ theta), xi = D^1/2 z + B L_G^-T z'."""
+    """theta' of Alg. 3 == theta + M~^-1 (f + xi - A~ theta), xi = D^1/2 z + B L_G^-T z',
+    for f = fd + B Gamma^-1 d (the split the oracle evaluates)."""
     p = inputs.make_problem("t", dim, n, n_levels=levels, kappa2_seed=3, m=5, obs_seed=2)
     p.Gamma = np.diag(np.linspace(1e-4, 3e-4, 5)) + 2e-5  # non-diagonal SPD Gamma
     o = _oracle(p)
@@ -120,12 +121,14 @@ def test_alg3_equals_generic_random_smoother(dim, n, levels, direction):
     for l in range(1, levels):
         N = o.level_N(l)
         theta = rng.normal(size=N)
-        f = rng.normal(size=N)
+        fd = rng.normal(size=N)
+        d = rng.normal(size=5) * 3.0
         zd = rng.normal(size=N)
         zl = rng.normal(size=5)
-        got = o.smoother_step_given(l, direction, theta, f, zd, zl)
+        got = o.smoother_step_given(l, direction, theta, fd, zd, zl, d=d)
         D = np.diag(np.diag(H.A[l]))
         LG = np.linalg.cholesky(p.Gamma)
+        f = fd + H.B[l] @ np.linalg.solve(p.Gamma, d)
         xi = np.sqrt(D) @ zd + H.B[l] @ np.linalg.solve(LG.T, zl)
         M = H.splitting(l, direction)
         want = theta + np.linalg.solve(M, f + xi - H.Atilde(l) @ theta)
