@@ -1,0 +1,313 @@
+"""Benchmark of the GB300 MGMC sampler on the 1023^2 Bayesian workload.
+
+Workload: 2D unit square, 1023 x 1023 interior grid (h = 1/1024), non-stationary
+kappa^2 = 10 exp(g), 16 point observations, Gamma = 1e-4 I, 10-grid V-cycle with
+the paper's low-rank Gibbs smoother (nu1 = nu2 = 1), FP32 sweeps with FP64
+low-rank / coarsest / QoI arithmetic.  One step = one MGMC V-cycle (the whole
+hot path) of one chain.  The metric is QoI ESS/s = (V-cycles/s) / tau_int, with
+tau_int measured on the device (Wolff window) from an untimed 2000-cycle chain.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
+
+--impl reference times the plain FP64 CPU oracle on the host cores (the only
+baseline this method has: the paper's code is a sequential CPU program).
+Multi-GPU: replicas only -- every rank advances its own independent chain
+(Philox stream = rank) of the same problem; no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# DRAM bytes (read + write) per launch of the timed forward sweep of the
+# finest grid, from the ncu capture summarised in
+# profiles/fine_sweep_fp32_1023.md; None until captured for the current kernel.
+FINE_SWEEP_TRAFFIC_BYTES = None
+
+TAU_CALIBRATION = 2000     # untimed cycles used for tau_int on the device
+CPU_SAMPLE_CYCLES = 12     # bounded oracle sample for the CPU baseline
+REF_MAX_STEPS = 60         # cap on timed oracle cycles in the reference arm
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples taken during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", gpu_id], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_id_for_smi(torch, dev):
+    try:
+        u = torch.cuda.get_device_properties(dev).uuid
+        s = str(u)
+        return s if s.startswith("GPU-") else "GPU-" + s
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        return vis.split(",")[dev] if vis else str(dev)
+
+
+def cpu_baseline(problem, tau_ref):
+    """Time the FP64 CPU oracle on the same workload (bounded sample, one core)."""
+    import oracle
+    o = oracle.Oracle(problem.dim, problem.n, problem.n_levels, kappa2=problem.kappa2, obs_site=problem.obs_site,
+                      obs_w=problem.obs_w, Gamma=problem.Gamma, y=problem.y, qoi_site=problem.qoi_site,
+                      qoi_w=problem.qoi_w)
+    x = o.sample(1, 2024, qoi=False)
+    t = time.perf_counter()
+    o.sample(CPU_SAMPLE_CYCLES, 2024, x=x, step_offset=1, qoi=False)
+    dt = time.perf_counter() - t
+    cps = CPU_SAMPLE_CYCLES / dt
+    return {"value": cps / tau_ref, "unit": "QoI ESS/s", "cores": 1, "kind": "oracle",
+            "sample": f"{CPU_SAMPLE_CYCLES} V-cycles of the same 1023^2 problem after 1 untimed cycle, set-up "
+                      f"excluded; {cps:.3f} V-cycles/s divided by the oracle's own tau_int = {tau_ref:.4f} "
+                      f"(oracle/tau_bayes_2d_1023.json)"}
+
+
+def load_tau_ref():
+    path = os.path.join(ROOT, "oracle", "tau_bayes_2d_1023.json")
+    with open(path) as f:
+        d = json.load(f)
+    return float(d["tau"]), d
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2407_12149_gb300 import inputs
+    import oracle
+    p = inputs.config2()
+    tau_ref, _ = load_tau_ref()
+    o = oracle.Oracle(p.dim, p.n, p.n_levels, kappa2=p.kappa2, obs_site=p.obs_site, obs_w=p.obs_w, Gamma=p.Gamma,
+                      y=p.y, qoi_site=p.qoi_site, qoi_w=p.qoi_w)
+    x = None
+    for w in range(min(args.warmup, 3)):
+        x = o.sample(1, 2024, x=x, step_offset=w, qoi=False)
+    K = min(args.steps, REF_MAX_STEPS)
+    t = time.perf_counter()
+    for k in range(K):
+        x = o.sample(1, 2024, x=x, step_offset=args.warmup + k, qoi=False)
+    dt = time.perf_counter() - t
+    cps = K / dt
+    val = cps / tau_ref
+    line = {"metric": "QoI ESS/s", "value": val, "unit": "QoI ESS/s", "n_gpus": args.gpus, "steps": K,
+            "warmup": min(args.warmup, 3), "ms_per_step": 1e3 * dt / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "bayes-2d-1023: 1023^2, kappa^2 = 10 exp(g), 16 point obs, Gamma = 1e-4 I, "
+                                   "10-grid V(1,1)-cycle, low-rank Gibbs smoother", "v_cycles_per_s": cps,
+                       "tau_int": tau_ref},
+            "cpu_baseline": {"value": val, "unit": "QoI ESS/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{K} of {args.steps} requested V-cycles timed on one host core (FP64 "
+                                       f"CPU oracle, set-up excluded); tau_int from oracle/tau_bayes_2d_1023.json"},
+            "e2e": {"value": val, "unit": "QoI ESS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_mine(args):
+    import torch
+    ws, rank, local = dist_env()
+    from paper_2407_12149_gb300 import build, inputs
+    from paper_2407_12149_gb300 import mgmc as M
+    build.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    p = inputs.config2()
+    s = M.Sampler(p, precision="fp32", device=local)
+    stream = torch.cuda.current_stream()
+    chain = rank
+    N = p.N
+    launches = s.launches_per_cycle()
+
+    # --- untimed calibration chain: burn-in 100, then tau_int on the device ----
+    x = s.zeros()
+    qcal = torch.zeros(TAU_CALIBRATION + 100, dtype=torch.float64, device=dev)
+    s.sample(x, TAU_CALIBRATION + 100, 2024, step_offset=0, chain=chain, qoi=qcal)
+    st = M.mgmc_qoi_stats(qcal.data_ptr(), TAU_CALIBRATION + 100, 100, 1.5)
+    tau = st["tau_int"]
+    offset = TAU_CALIBRATION + 100
+
+    # --- CPU baseline (rank 0, one GPU only), before the GPU timing ------------
+    cpu = None
+    if rank == 0 and ws == 1:
+        try:
+            tau_ref, _ = load_tau_ref()
+            cpu = cpu_baseline(p, tau_ref)
+        except Exception as e:  # report, do not fail the GPU measurement
+            cpu = {"value": None, "unit": "QoI ESS/s", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+
+    # --- device-timed steps ----------------------------------------------------
+    M.mgmc_set_profiling(s.h, True)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)    # 256 MB > L2
+    qstep = torch.zeros(1, dtype=torch.float64, device=dev)
+    for w in range(args.warmup):
+        flush.fill_(float(w))
+        s.sample(x, 1, 2024, step_offset=offset, chain=chain, qoi=qstep)
+        offset += 1
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(gpu_id_for_smi(torch, local))
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    fwd_ms, bwd_ms = [], []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        s.sample(x, 1, 2024, step_offset=offset, chain=chain, qoi=qstep)
+        ev[k][1].record(stream)
+        offset += 1
+        f_ms, b_ms = M.mgmc_profile_times(s.h)   # synchronises the stream
+        fwd_ms.append(f_ms)
+        bwd_ms.append(b_ms)
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    clk = clocks.stop()
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    cps = ws * args.steps / (total_ms / 1e3)
+    value = cps / tau
+
+    # --- end-to-end through the public API with pinned host buffers -----------
+    M.mgmc_set_profiling(s.h, False)
+    xh = x.cpu().pin_memory()
+    qh = torch.zeros(1, dtype=torch.float64).pin_memory()
+    n_e2e = args.steps
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for k in range(n_e2e):
+        s.sample(xh, 1, 2024, step_offset=offset, chain=chain, qoi=qh)   # H2D x, cycle, D2H x + QoI
+        offset += 1
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = ws * n_e2e / e2e_s / tau
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peak, peak_kind = measured_peak()
+    sweep_bytes = 12 * N     # read x + read s*kappa^2 + write x, FP32, per forward sweep of the finest grid
+    fwd_avg = statistics.mean(fwd_ms)
+    achieved = sweep_bytes / (fwd_avg * 1e-3) / 1e9
+    line = {
+        "metric": "QoI ESS/s", "value": value, "unit": "QoI ESS/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "bayes-2d-1023: 1023^2, kappa^2 = 10 exp(g), 16 point obs, Gamma = 1e-4 I, "
+                               "10-grid V(1,1)-cycle, low-rank Gibbs smoother, FP32 sweeps / FP64 low-rank",
+                   "v_cycles_per_s": cps, "tau_int": tau, "tau_err": st["tau_err"],
+                   "tau_from": f"device Wolff estimate on an untimed {TAU_CALIBRATION}-cycle chain",
+                   "l2": "256 MB buffer written between timed steps (inputs are smaller than L2)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "kernel": "k_sweep_colour (finest grid, forward sweep, both colours)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": f"{peak_kind} HBM copy bandwidth",
+                     "traffic": FINE_SWEEP_TRAFFIC_BYTES,
+                     "algorithmic_bytes": sweep_bytes, "avg_ms": fwd_avg,
+                     "bwd_sweep_avg_ms": statistics.mean(bwd_ms)},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "QoI ESS/s", "h2d_bytes_per_step": 4 * N,
+                "d2h_bytes_per_step": 4 * N + 8},
+        "gpu_launches": args.steps * (launches + 3),
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_mine(args)
+
+
+if __name__ == "__main__":
+    main()

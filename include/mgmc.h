@@ -1,0 +1,176 @@
+/*
+ * mgmc.h -- C ABI of the GB300 Multigrid Monte Carlo (MGMC) sampler.
+ *
+ * The sampler draws from the Gaussian posterior N(mu, A~^-1),
+ *   A~ = A + B Gamma^-1 B^T,  mu = A~^-1 f,  f = B Gamma^-1 y,
+ * (Sec. 2.2, Eqs. post-mean / post-cov / f_ell_definition of Kazashi, Mueller,
+ * Scheichl, "Multigrid Monte Carlo Revisited", arXiv 2407.12149), where A is
+ * the finite-difference precision s (kappa^2(x) I - Delta_h) on the interior
+ * vertices of the unit square or cube with zero Dirichlet values and
+ * s = h^d (default, the bilinear-form scaling of Sec. 2.3) or s = 1.
+ * One call of mgmc_sample applies n_steps MGMC V-cycles (Alg. 1, gamma = 1)
+ * with the paper's Gibbs smoother with low-rank correction (Alg. 3: nu1
+ * forward sweeps before the coarse-grid correction, nu2 backward sweeps
+ * after it), Galerkin coarse operators (Eq. galerkin_triple_product),
+ * restriction = transpose of the multilinear prolongation, and an exact
+ * Cholesky sampler on the coarsest grid (Sec. 2.5).
+ *
+ * Conventions used by every entry point:
+ *   - Grids are cubes: n interior points per axis, n = 2^k - 1; level
+ *     l-1 has (n_l - 1)/2 points per axis.  A dense field of a grid holds
+ *     n^dim values, site s = i + n (j + n k), x fastest.
+ *   - Host arrays passed to mgmc_create are copied; the caller keeps
+ *     ownership.  Device buffers the handle needs are obtained from the
+ *     caller's allocator (or cudaMalloc when the allocator is NULL) and are
+ *     returned to it by mgmc_destroy.
+ *   - Work is ordered on the CUDA stream passed in (a cudaStream_t given as
+ *     void*; NULL = legacy default stream).  mgmc_sample returns once the
+ *     work is queued unless a host pointer was passed; mgmc_mean_solve and
+ *     mgmc_qoi_stats synchronise that stream.
+ *   - No exception crosses this boundary.  Every function returns a status;
+ *     mgmc_last_error() gives a message for the last failing call on the
+ *     calling thread.  There is no CPU fallback: without a usable CUDA
+ *     device the calls fail with MGMC_ERR_CUDA.
+ *   - A handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef MGMC_H
+#define MGMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MGMC_OK = 0,
+    MGMC_ERR_ARG = 1,      /* invalid argument (size not 2^k-1, NaN input, bad pointer, ...) */
+    MGMC_ERR_CUDA = 2,     /* CUDA runtime error or no device */
+    MGMC_ERR_OOM = 3,      /* allocator returned NULL */
+    MGMC_ERR_NOT_SPD = 4,  /* Gamma, a coarse operator or A~_0 is not symmetric positive definite */
+    MGMC_ERR_TIMEOUT = 5,  /* a bounded device-side wait gave up */
+    MGMC_ERR_STATE = 6,    /* handle in the wrong state for this call */
+    MGMC_ERR_NUMERIC = 7   /* non-finite value produced */
+} mgmc_status;
+
+enum { MGMC_FP64 = 0, MGMC_FP32 = 1 };
+
+/* Maximum number of observations (columns of B). */
+#define MGMC_MAX_OBS 64
+/* Maximum number of unknowns on the coarsest grid (dense Cholesky). */
+#define MGMC_MAX_COARSEST 1024
+
+typedef struct mgmc_ctx* mgmc_handle;
+
+/* Device-memory provider.  alloc(bytes, stream, ctx) returns device memory
+ * or NULL; free(ptr, stream, ctx) returns it.  Both are called only from
+ * mgmc_create / mgmc_destroy on the caller's thread. */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* stream, void* ctx);
+    void (*free)(void* ptr, void* stream, void* ctx);
+    void* ctx;
+} mgmc_allocator;
+
+typedef struct {
+    int dim;          /* 2 or 3 */
+    int n;            /* interior points per axis of the finest grid, 2^k - 1 */
+    int n_levels;     /* number of grids (>= 1); 0 = coarsen down to n = 1 */
+    int nu1, nu2;     /* forward / backward smoothing sweeps per level (paper: 1, 1) */
+    int precision;    /* MGMC_FP64 or MGMC_FP32: type of the smoother, transfer and
+                         state arithmetic; the low-rank update, coarsest Cholesky
+                         sample and QoI accumulation are FP64 in both */
+    int scale_hd;     /* 1: A = h^d (kappa^2 - Delta_h) (default); 0: kappa^2 - Delta_h */
+    int coarse_max_n; /* grids with n <= coarse_max_n run inside one single-CTA kernel;
+                         0 selects the default (63 in 2D, 15 in 3D) */
+} mgmc_config;
+
+/* Fill cfg with the paper's defaults for a dim-dimensional n^dim grid. */
+mgmc_status mgmc_config_default(mgmc_config* cfg, int dim, int n);
+
+/* Create a sampler for one posterior (Sec. 2.2 / 2.3).
+ *   kappa2:       host [n^dim] kappa^2 at the fine vertices, or NULL to use kappa2_const.
+ *   m:            number of observations beta (0 <= m <= MGMC_MAX_OBS).
+ *   obs_site/obs_w: host [m * nnz_per_obs]: row k of B^T as (fine site, weight);
+ *                 site -1 marks an unused entry (e.g. a Dirichlet boundary vertex).
+ *   Gamma:        host [m * m] row-major SPD observation-noise covariance.
+ *   y:            host [m] observed values.
+ *   n_qoi, qoi_site, qoi_w: host sparse F_L of the linear QoI F_L^T x (Eq. F_matrix).
+ * Errors: MGMC_ERR_ARG (sizes, non-finite values, sites out of range),
+ * MGMC_ERR_NOT_SPD, MGMC_ERR_OOM, MGMC_ERR_CUDA.  *out is NULL on error. */
+mgmc_status mgmc_create(const mgmc_config* cfg, const mgmc_allocator* alloc, void* stream,
+                        const double* kappa2, double kappa2_const,
+                        int m, const int32_t* obs_site, const double* obs_w, int nnz_per_obs,
+                        const double* Gamma, const double* y,
+                        int n_qoi, const int32_t* qoi_site, const double* qoi_w,
+                        mgmc_handle* out);
+
+/* Rows of B for point observations at xyz (host [m * dim], each in (0,1)^dim):
+ * the 2^dim multilinear interpolation weights of the enclosing cell
+ * (Eq. B_ell_definition for point evaluation).  obs_site / obs_w: host
+ * [m * 2^dim]; vertices on the boundary get site -1, weight 0.  Corner c's
+ * bit a selects the upper vertex along axis a. */
+mgmc_status mgmc_point_obs_rows(int dim, int n, int m, const double* xyz, int32_t* obs_site, double* obs_w);
+
+/* Apply n_steps MGMC V-cycles to x_inout (dense n^dim field in the handle's
+ * precision; device or host memory).  Cycle t uses the random numbers of
+ * cycle index step_offset + t, so runs split at any point reproduce a single
+ * run bit for bit.  chain (< 65536) selects an independent random stream.
+ * qoi_out: NULL or [n_steps] doubles (device or host) receiving F_L^T x
+ * after every cycle.  Host buffers are staged through device memory on the
+ * stream and the call synchronises it before returning. */
+mgmc_status mgmc_sample(mgmc_handle h, int64_t n_steps, uint64_t seed, uint64_t step_offset,
+                        uint32_t chain, void* x_inout, double* qoi_out, void* stream);
+
+/* Posterior mean by noise-free V-cycles (deterministic multigrid, Sec. 3.2):
+ * iterates from mean_out (dense n^dim field, handle precision, device or
+ * host) until ||f - A~ x||_2 <= rtol ||f||_2 or max_cycles.  Synchronous.
+ * cycles_done / rel_residual may be NULL. */
+mgmc_status mgmc_mean_solve(mgmc_handle h, double rtol, int max_cycles, void* mean_out,
+                            int* cycles_done, double* rel_residual, void* stream);
+
+typedef struct {
+    double mean;      /* sample mean of the kept series */
+    double var;       /* lag-0 autocovariance */
+    double tau_int;   /* IACT, tau = 1 + 2 sum_{t=1}^{W} rho(t) (Sec. 5.3.2) */
+    double tau_err;   /* its statistical error (Wolff 2004, Eq. 42) */
+    double ess;       /* effective sample size n_used / tau_int */
+    int64_t window;   /* Wolff's automatic window W */
+    int64_t n_used;   /* n - burn_in */
+} mgmc_stats;
+
+/* Chain statistics of a QoI series on the device (Sec. 5.3.2): lagged
+ * autocovariance with divisor n - t and Wolff's automatic window with
+ * parameter S (1.5 if S <= 0), computed by CUDA kernels.  qoi: device
+ * [n] doubles; the first burn_in entries are skipped.  Scratch of
+ * (n - burn_in)/2 + 1 doubles comes from cudaMallocAsync on the stream.
+ * Synchronous. */
+mgmc_status mgmc_qoi_stats(const double* qoi, int64_t n, int64_t burn_in, double S, mgmc_stats* out,
+                           void* stream);
+
+/* Number of grids, unknowns per axis of grid l (0 = coarsest) and the
+ * precision of a handle. */
+mgmc_status mgmc_info(mgmc_handle h, int* n_levels, int* precision, int* dim);
+mgmc_status mgmc_level_n(mgmc_handle h, int l, int* n);
+
+/* Kernels launched per V-cycle by mgmc_sample (for launch accounting). */
+mgmc_status mgmc_launches_per_cycle(mgmc_handle h, int* launches);
+
+/* Benchmark timing: with enable != 0 the captured cycle records CUDA events
+ * around the finest grid's forward sweep and its backward sweep (finest grid
+ * above coarse_max_n only).  mgmc_profile_times synchronises the stream given
+ * and writes ms[0] = forward sweep, ms[1] = backward sweep of the last cycle
+ * run (n >= 2).  MGMC_ERR_STATE when profiling is off or the finest grid runs
+ * inside the single-CTA kernel. */
+mgmc_status mgmc_set_profiling(mgmc_handle h, int enable);
+mgmc_status mgmc_profile_times(mgmc_handle h, float* ms, int n, void* stream);
+
+mgmc_status mgmc_destroy(mgmc_handle h);
+
+/* Message of the last failing call on this thread; valid until the next call. */
+const char* mgmc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,665 @@
+// api.cu -- the C ABI (include/mgmc.h): handle life cycle, device upload of
+// the hierarchy, CUDA-graph capture of one V-cycle and the sampling loop.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "setup.hpp"
+
+using namespace mgmc;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+mgmc_status fail(mgmc_status code, const std::string& msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                                         \
+    do {                                                                                                       \
+        cudaError_t _e = (expr);                                                                               \
+        if (_e != cudaSuccess)                                                                                 \
+            return fail(MGMC_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e));                     \
+    } while (0)
+
+long long padded_pitch(int n, int elem_bytes)
+{
+    int align = 128 / elem_bytes;
+    return ((long long)(n + 5) + align - 1) / align * align;
+}
+
+struct Buffers {
+    mgmc_allocator alloc{};
+    bool use_cuda_malloc = true;
+    cudaStream_t stream = nullptr;
+    std::vector<void*> list;
+    void* get(size_t bytes)
+    {
+        if (bytes == 0) bytes = 16;
+        bytes = (bytes + 255) / 256 * 256;
+        void* p = nullptr;
+        if (use_cuda_malloc) {
+            if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
+        } else {
+            p = alloc.alloc(bytes, (void*)stream, alloc.ctx);
+        }
+        if (p) list.push_back(p);
+        return p;
+    }
+    void release()
+    {
+        for (void* p : list) {
+            if (use_cuda_malloc)
+                cudaFree(p);
+            else
+                alloc.free(p, (void*)stream, alloc.ctx);
+        }
+        list.clear();
+    }
+};
+
+}  // namespace
+
+struct mgmc_ctx {
+    mgmc_config cfg{};
+    int L = 0;            // number of levels
+    int top = 0;          // highest level inside the coarse kernel
+    int m = 0;
+    int device = 0;
+    Buffers buf;
+    CycleState* cs = nullptr;
+    DevProblem P{};
+    std::vector<DevLevel<float>> lf;
+    std::vector<DevLevel<double>> ld;
+    void* levels_dev = nullptr;
+    double* chol = nullptr;
+    int n0 = 0;
+    int n_qoi = 0;
+    long long* q_site = nullptr;
+    double* q_w = nullptr;
+    void* x_stage = nullptr;
+    double* u = nullptr;
+    double* partial = nullptr;
+    double* rnorm = nullptr;
+    int max_partial = 0;
+    double f_norm = 0.0;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int launches = 0;
+    bool profile = false;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool fp32() const { return cfg.precision == MGMC_FP32; }
+};
+
+namespace {
+
+template <typename T>
+std::vector<DevLevel<T>>& levels_of(mgmc_ctx* h);
+template <>
+std::vector<DevLevel<float>>& levels_of<float>(mgmc_ctx* h) { return h->lf; }
+template <>
+std::vector<DevLevel<double>>& levels_of<double>(mgmc_ctx* h) { return h->ld; }
+
+template <typename V>
+V* upload(mgmc_ctx* h, const std::vector<V>& v, mgmc_status& st)
+{
+    V* p = (V*)h->buf.get(v.size() * sizeof(V));
+    if (!p) {
+        st = MGMC_ERR_OOM;
+        return nullptr;
+    }
+    if (!v.empty() && cudaMemcpyAsync(p, v.data(), v.size() * sizeof(V), cudaMemcpyHostToDevice, h->buf.stream) !=
+                          cudaSuccess)
+        st = MGMC_ERR_CUDA;
+    return p;
+}
+
+template <typename T>
+mgmc_status build_device_levels(mgmc_ctx* h, const HostProblem& hp)
+{
+    const int d = hp.dim;
+    auto& levels = levels_of<T>(h);
+    levels.assign(hp.n_levels, DevLevel<T>{});
+    mgmc_status st = MGMC_OK;
+    for (int l = 0; l < hp.n_levels; ++l) {
+        const HostLevel& HL = hp.lev[l];
+        DevLevel<T>& D = levels[l];
+        std::memset(&D, 0, sizeof(D));
+        D.level = l;
+        D.dim = d;
+        D.n = HL.n;
+        D.pitch = (int)padded_pitch(HL.n, sizeof(T));
+        D.plane = (long long)D.pitch * (HL.n + 2);
+        D.base = 4 + D.pitch + (d == 3 ? D.plane : 0);
+        D.alloc = d == 3 ? D.plane * (HL.n + 2) : D.plane;
+        auto off = [&](long long s) {
+            int i = (int)(s % HL.n), j = (int)((s / HL.n) % HL.n), k = d == 3 ? (int)(s / ((long long)HL.n * HL.n)) : 0;
+            return site_offset(d, D.pitch, D.plane, D.base, i, j, k);
+        };
+        size_t fbytes = (size_t)D.alloc * sizeof(T);
+        D.x = (T*)h->buf.get(fbytes);
+        if (!D.x) return fail(MGMC_ERR_OOM, "allocator returned NULL");
+        CUDA_TRY(cudaMemsetAsync(D.x, 0, fbytes, h->buf.stream));
+        const bool finest = l == hp.n_levels - 1;
+        if (!finest) {
+            D.f = (T*)h->buf.get(fbytes);
+            if (!D.f) return fail(MGMC_ERR_OOM, "allocator returned NULL");
+            CUDA_TRY(cudaMemsetAsync(D.f, 0, fbytes, h->buf.stream));
+        }
+        if (finest) {
+            D.fine = 1;
+            std::vector<T> diag((size_t)D.alloc, T(0));
+            for (long long s = 0; s < HL.N; ++s)
+                diag[(size_t)off(s)] = sizeof(T) == 4 ? (T)hp.kappa_part[(size_t)s] : (T)HL.st[(size_t)s * hp.NS + hp.C];
+            D.diag = upload(h, diag, st);
+            D.woff = (T)hp.woff_fine;
+        } else {
+            D.fine = 0;
+            D.ncoef = (hp.NS + 1) / 2;
+            std::vector<T> coef((size_t)D.alloc * D.ncoef, T(0));
+            std::vector<double> rs;
+            if (sizeof(T) == 4) rs = row_sums(hp, l);
+            for (long long s = 0; s < HL.N; ++s) {
+                long long e = off(s);
+                const double* a = &HL.st[(size_t)s * hp.NS];
+                coef[(size_t)e] = sizeof(T) == 4 ? (T)rs[(size_t)s] : (T)a[hp.C];
+                for (int t = 1; t < D.ncoef; ++t) coef[(size_t)t * D.alloc + e] = (T)a[hp.C + t];
+            }
+            D.coef = upload(h, coef, st);
+        }
+        if (hp.m > 0) {
+            // rows of B grouped by grid row, sorted by x index
+            long long nrows = d == 3 ? (long long)HL.n * HL.n : HL.n;
+            std::vector<std::vector<std::pair<int, std::pair<int, double>>>> rows((size_t)nrows);
+            for (int k = 0; k < hp.m; ++k)
+                for (int t = HL.bptr[k]; t < HL.bptr[k + 1]; ++t) {
+                    long long s = HL.bsite[t];
+                    int i = (int)(s % HL.n);
+                    long long r = s / HL.n;
+                    rows[(size_t)r].push_back({i, {k, HL.bw[t]}});
+                }
+            std::vector<int> rptr((size_t)nrows + 1, 0), ei, ek;
+            std::vector<double> ew;
+            for (long long r = 0; r < nrows; ++r) {
+                auto& v = rows[(size_t)r];
+                std::sort(v.begin(), v.end(), [](const auto& a, const auto& b) {
+                    return a.first != b.first ? a.first < b.first : a.second.first < b.second.first;
+                });
+                for (auto& e : v) {
+                    ei.push_back(e.first);
+                    ek.push_back(e.second.first);
+                    ew.push_back(e.second.second);
+                }
+                rptr[(size_t)r + 1] = (int)ei.size();
+            }
+            D.brow_ptr = upload(h, rptr, st);
+            D.bent_i = upload(h, ei, st);
+            D.bent_k = upload(h, ek, st);
+            D.bent_w = upload(h, ew, st);
+            std::vector<long long> cs;
+            for (long long s : HL.bsite) cs.push_back(off(s));
+            D.bcol_ptr = upload(h, HL.bptr, st);
+            D.bcol_site = upload(h, cs, st);
+            D.bcol_w = upload(h, HL.bw, st);
+            for (int dir = 0; dir < 2; ++dir) {
+                D.g_rows[dir] = (int)HL.gsite[dir].size();
+                std::vector<long long> gs;
+                for (long long s : HL.gsite[dir]) gs.push_back(off(s));
+                D.g_site[dir] = upload(h, gs, st);
+                D.g_val[dir] = upload(h, HL.gval[dir], st);
+            }
+            std::vector<double> dv(hp.m, 0.0);
+            if (finest) dv = hp.y;
+            D.d = upload(h, dv, st);
+        }
+        if (st != MGMC_OK) return fail(st, "device upload failed");
+    }
+    for (int l = 1; l < hp.n_levels; ++l) levels[l].dnext = levels[l - 1].d;
+    // descriptors of the levels handled by the single-CTA kernel
+    size_t dbytes = sizeof(DevLevel<T>) * (size_t)(h->top + 1);
+    h->levels_dev = h->buf.get(dbytes);
+    if (!h->levels_dev) return fail(MGMC_ERR_OOM, "allocator returned NULL");
+    CUDA_TRY(cudaMemcpyAsync(h->levels_dev, levels.data(), dbytes, cudaMemcpyHostToDevice, h->buf.stream));
+    return MGMC_OK;
+}
+
+template <typename T>
+void enqueue_cycle(mgmc_ctx* h, cudaStream_t s, int& launches)
+{
+    auto& lv = levels_of<T>(h);
+    const int Lf = h->L - 1;
+    const DevProblem& P = h->P;
+    const bool prof = h->profile && h->top < Lf;
+    for (int l = Lf; l > h->top; --l) {
+        const DevLevel<T>& D = lv[l];
+        if (l < Lf) cudaMemsetAsync(D.x, 0, (size_t)D.alloc * sizeof(T), s);
+        for (int j = 0; j < h->cfg.nu1; ++j) {
+            if (prof && l == Lf && j == 0) cudaEventRecordWithFlags(h->ev[0], s, cudaEventRecordExternal);
+            launch_sweep<T>(D, P, 0, (unsigned)(2 * j), s, launches);
+            if (prof && l == Lf && j == 0) cudaEventRecordWithFlags(h->ev[1], s, cudaEventRecordExternal);
+            launch_lowrank<T>(D, P, 0, (unsigned)(2 * j), j == h->cfg.nu1 - 1, s, launches);
+        }
+        if (h->cfg.nu1 == 0) launch_lowrank<T>(D, P, -1, 0u, true, s, launches);
+        launch_restrict<T>(D, lv[l - 1], s, launches);
+    }
+    launch_coarse<T>((const DevLevel<T>*)h->levels_dev, h->cfg.dim, h->top, h->top == Lf, P, h->chol, h->n0,
+                     h->cfg.nu1, h->cfg.nu2, s, launches);
+    for (int l = h->top + 1; l <= Lf; ++l) {
+        const DevLevel<T>& D = lv[l];
+        launch_prolong<T>(lv[l - 1], D, s, launches);
+        for (int j = 0; j < h->cfg.nu2; ++j) {
+            if (prof && l == Lf && j == 0) cudaEventRecordWithFlags(h->ev[2], s, cudaEventRecordExternal);
+            launch_sweep<T>(D, P, 1, (unsigned)(2 * j + 1), s, launches);
+            if (prof && l == Lf && j == 0) cudaEventRecordWithFlags(h->ev[3], s, cudaEventRecordExternal);
+            launch_lowrank<T>(D, P, 1, (unsigned)(2 * j + 1), false, s, launches);
+        }
+    }
+    launch_qoi<T>(lv[Lf], h->n_qoi, h->q_site, h->q_w, P, s, launches);
+}
+
+mgmc_status ensure_graph(mgmc_ctx* h)
+{
+    if (h->exec) return MGMC_OK;
+    cudaGraph_t graph = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int launches = 0;
+    if (h->fp32())
+        enqueue_cycle<float>(h, h->cap_stream, launches);
+    else
+        enqueue_cycle<double>(h, h->cap_stream, launches);
+    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
+    if (e != cudaSuccess) return fail(MGMC_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&h->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        h->exec = nullptr;
+        return fail(MGMC_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    h->launches = launches;
+    return MGMC_OK;
+}
+
+bool is_device_ptr(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+mgmc_status check_device()
+{
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess || count == 0) {
+        cudaGetLastError();
+        return fail(MGMC_ERR_CUDA, "no CUDA device available (the sampler has no CPU fallback)");
+    }
+    return MGMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mgmc_last_error(void) { return g_last_error.c_str(); }
+
+mgmc_status mgmc_config_default(mgmc_config* cfg, int dim, int n)
+{
+    if (!cfg) return fail(MGMC_ERR_ARG, "cfg is NULL");
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->dim = dim;
+    cfg->n = n;
+    cfg->n_levels = 0;
+    cfg->nu1 = 1;
+    cfg->nu2 = 1;
+    cfg->precision = MGMC_FP64;
+    cfg->scale_hd = 1;
+    cfg->coarse_max_n = 0;
+    return MGMC_OK;
+}
+
+mgmc_status mgmc_point_obs_rows(int dim, int n, int m, const double* xyz, int32_t* obs_site, double* obs_w)
+{
+    if ((dim != 2 && dim != 3) || n < 1 || m < 0 || (m > 0 && (!xyz || !obs_site || !obs_w)))
+        return fail(MGMC_ERR_ARG, "mgmc_point_obs_rows: bad arguments");
+    const double h = 1.0 / (double)(n + 1);
+    const int nc = 1 << dim;
+    for (int k = 0; k < m; ++k) {
+        long long cell[3];
+        double t[3];
+        for (int a = 0; a < dim; ++a) {
+            double v = xyz[(size_t)k * dim + a];
+            if (!(v > 0.0 && v < 1.0)) return fail(MGMC_ERR_ARG, "observation point outside (0,1)^dim");
+            long long c = (long long)std::floor(v / h);
+            if (c > n) c = n;
+            cell[a] = c;
+            t[a] = v / h - (double)c;
+        }
+        for (int corner = 0; corner < nc; ++corner) {
+            double w = 1.0;
+            long long idx[3] = {0, 0, 0};
+            bool inside = true;
+            for (int a = 0; a < dim; ++a) {
+                int up = (corner >> a) & 1;
+                w *= up ? t[a] : (1.0 - t[a]);
+                idx[a] = cell[a] + up - 1;
+                if (idx[a] < 0 || idx[a] >= n) inside = false;
+            }
+            size_t o = (size_t)k * nc + corner;
+            if (inside && w != 0.0) {
+                obs_site[o] = (int32_t)(idx[0] + n * (idx[1] + (dim == 3 ? (long long)n * idx[2] : 0)));
+                obs_w[o] = w;
+            } else {
+                obs_site[o] = -1;
+                obs_w[o] = 0.0;
+            }
+        }
+    }
+    return MGMC_OK;
+}
+
+mgmc_status mgmc_create(const mgmc_config* cfg_in, const mgmc_allocator* alloc, void* stream,
+                        const double* kappa2, double kappa2_const, int m, const int32_t* obs_site,
+                        const double* obs_w, int nnz_per_obs, const double* Gamma, const double* y, int n_qoi,
+                        const int32_t* qoi_site, const double* qoi_w, mgmc_handle* out)
+{
+    if (!out) return fail(MGMC_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!cfg_in) return fail(MGMC_ERR_ARG, "cfg is NULL");
+    mgmc_config cfg = *cfg_in;
+    if (cfg.dim != 2 && cfg.dim != 3) return fail(MGMC_ERR_ARG, "dim must be 2 or 3");
+    if (cfg.n < 1 || ((cfg.n + 1) & cfg.n) != 0) return fail(MGMC_ERR_ARG, "n must be 2^k - 1");
+    if (cfg.precision != MGMC_FP32 && cfg.precision != MGMC_FP64) return fail(MGMC_ERR_ARG, "bad precision");
+    if (cfg.nu1 < 0 || cfg.nu2 < 0 || cfg.nu1 > 16 || cfg.nu2 > 16) return fail(MGMC_ERR_ARG, "nu1/nu2 out of range");
+    if (m < 0 || m > MGMC_MAX_OBS) return fail(MGMC_ERR_ARG, "number of observations out of range");
+    if (m > 0 && (!obs_site || !obs_w || !Gamma || !y || nnz_per_obs < 1))
+        return fail(MGMC_ERR_ARG, "observation arrays missing");
+    if (n_qoi < 0 || (n_qoi > 0 && (!qoi_site || !qoi_w))) return fail(MGMC_ERR_ARG, "QoI arrays missing");
+    if (!kappa2 && !(std::isfinite(kappa2_const) && kappa2_const >= 0.0))
+        return fail(MGMC_ERR_ARG, "kappa2_const must be finite and non-negative");
+    long long N = 1;
+    for (int a = 0; a < cfg.dim; ++a) N *= cfg.n;
+    if (N > (1LL << 31) - 1) return fail(MGMC_ERR_ARG, "grid too large");
+    int max_levels = 1;
+    for (int nn = cfg.n; nn >= 3; nn = (nn - 1) / 2) ++max_levels;
+    if (cfg.n_levels == 0) cfg.n_levels = max_levels;
+    if (cfg.n_levels < 1 || cfg.n_levels > max_levels) return fail(MGMC_ERR_ARG, "n_levels out of range");
+    for (int t = 0; t < n_qoi; ++t)
+        if (qoi_site[t] < 0 || qoi_site[t] >= N || !std::isfinite(qoi_w[t]))
+            return fail(MGMC_ERR_ARG, "QoI site out of range or weight not finite");
+    mgmc_status dst = check_device();
+    if (dst != MGMC_OK) return dst;
+
+    HostProblem hp;
+    int code = MGMC_OK;
+    std::string err = build_hierarchy(hp, cfg.dim, cfg.n, cfg.n_levels, cfg.scale_hd, kappa2, kappa2_const, m,
+                                      obs_site, obs_w, nnz_per_obs, Gamma, y, &code);
+    if (!err.empty()) return fail((mgmc_status)code, err);
+
+    mgmc_ctx* h = new mgmc_ctx();
+    h->cfg = cfg;
+    h->L = cfg.n_levels;
+    h->m = m;
+    cudaGetDevice(&h->device);
+    h->buf.stream = (cudaStream_t)stream;
+    if (alloc && alloc->alloc && alloc->free) {
+        h->buf.alloc = *alloc;
+        h->buf.use_cuda_malloc = false;
+    }
+    int cmax = cfg.coarse_max_n > 0 ? cfg.coarse_max_n : (cfg.dim == 2 ? 63 : 15);
+    h->top = 0;
+    for (int l = 0; l < h->L; ++l)
+        if (hp.lev[l].n <= cmax) h->top = l;
+    h->n0 = hp.n0;
+    h->f_norm = hp.f_norm;
+    auto cleanup = [&](mgmc_status s) {
+        h->buf.release();
+        delete h;
+        return s;
+    };
+    mgmc_status st = MGMC_OK;
+    h->cs = (CycleState*)h->buf.get(sizeof(CycleState));
+    if (!h->cs) return cleanup(fail(MGMC_ERR_OOM, "allocator returned NULL"));
+    if (cudaMemsetAsync(h->cs, 0, sizeof(CycleState), h->buf.stream) != cudaSuccess)
+        return cleanup(fail(MGMC_ERR_CUDA, "memset failed"));
+    h->P.m = m;
+    h->P.cs = h->cs;
+    h->P.gamma_diag = hp.gamma_diag ? 1 : 0;
+    if (m > 0) {
+        h->P.Gamma_inv = upload(h, hp.Gamma_inv, st);
+        h->P.LG = upload(h, hp.LG, st);
+    }
+    h->chol = upload(h, hp.chol0, st);
+    if (st != MGMC_OK) return cleanup(fail(st, "device upload failed"));
+    st = h->fp32() ? build_device_levels<float>(h, hp) : build_device_levels<double>(h, hp);
+    if (st != MGMC_OK) return cleanup(st);
+    // QoI (finest-level padded offsets)
+    h->n_qoi = n_qoi;
+    {
+        const HostLevel& F = hp.lev[h->L - 1];
+        int pitch = (int)padded_pitch(F.n, h->fp32() ? 4 : 8);
+        long long plane = (long long)pitch * (F.n + 2);
+        long long base = 4 + pitch + (cfg.dim == 3 ? plane : 0);
+        std::vector<long long> qs;
+        std::vector<double> qw;
+        for (int t = 0; t < n_qoi; ++t) {
+            long long s = qoi_site[t];
+            int i = (int)(s % F.n), j = (int)((s / F.n) % F.n), k = cfg.dim == 3 ? (int)(s / ((long long)F.n * F.n)) : 0;
+            qs.push_back(site_offset(cfg.dim, pitch, plane, base, i, j, k));
+            qw.push_back(qoi_w[t]);
+        }
+        h->q_site = upload(h, qs, st);
+        h->q_w = upload(h, qw, st);
+    }
+    // staging and mean-solve scratch
+    size_t esz = h->fp32() ? 4 : 8;
+    h->x_stage = h->buf.get((size_t)N * esz);
+    h->u = (double*)h->buf.get(sizeof(double) * (m > 0 ? m : 1));
+    h->max_partial = (int)((N + 255) / 256);
+    h->partial = (double*)h->buf.get(sizeof(double) * h->max_partial);
+    h->rnorm = (double*)h->buf.get(sizeof(double) * 2);
+    if (!h->x_stage || !h->u || !h->partial || !h->rnorm || st != MGMC_OK)
+        return cleanup(fail(MGMC_ERR_OOM, "allocator returned NULL"));
+    if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return cleanup(fail(MGMC_ERR_CUDA, "stream creation failed"));
+    cudaError_t e = cudaStreamSynchronize(h->buf.stream);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(h->cap_stream);
+        return cleanup(fail(MGMC_ERR_CUDA, std::string("set-up upload: ") + cudaGetErrorString(e)));
+    }
+    *out = h;
+    return MGMC_OK;
+}
+
+mgmc_status mgmc_info(mgmc_handle h, int* n_levels, int* precision, int* dim)
+{
+    if (!h) return fail(MGMC_ERR_ARG, "handle is NULL");
+    if (n_levels) *n_levels = h->L;
+    if (precision) *precision = h->cfg.precision;
+    if (dim) *dim = h->cfg.dim;
+    return MGMC_OK;
+}
+
+mgmc_status mgmc_level_n(mgmc_handle h, int l, int* n)
+{
+    if (!h || !n || l < 0 || l >= h->L) return fail(MGMC_ERR_ARG, "bad level query");
+    *n = h->fp32() ? h->lf[l].n : h->ld[l].n;
+    return MGMC_OK;
+}
+
+mgmc_status mgmc_launches_per_cycle(mgmc_handle h, int* launches)
+{
+    if (!h || !launches) return fail(MGMC_ERR_ARG, "bad arguments");
+    mgmc_status st = ensure_graph(h);
+    if (st != MGMC_OK) return st;
+    *launches = h->launches;
+    return MGMC_OK;
+}
+
+static mgmc_status pack_in(mgmc_ctx* h, void* x, bool host, cudaStream_t s, long long N)
+{
+    size_t esz = h->fp32() ? 4 : 8;
+    void* src = x;
+    if (host) {
+        CUDA_TRY(cudaMemcpyAsync(h->x_stage, x, (size_t)N * esz, cudaMemcpyHostToDevice, s));
+        src = h->x_stage;
+    }
+    if (h->fp32())
+        launch_pack<float>(h->lf[h->L - 1], (float*)src, true, s);
+    else
+        launch_pack<double>(h->ld[h->L - 1], (double*)src, true, s);
+    return MGMC_OK;
+}
+
+static mgmc_status pack_out(mgmc_ctx* h, void* x, bool host, cudaStream_t s, long long N)
+{
+    size_t esz = h->fp32() ? 4 : 8;
+    void* dst = host ? h->x_stage : x;
+    if (h->fp32())
+        launch_pack<float>(h->lf[h->L - 1], (float*)dst, false, s);
+    else
+        launch_pack<double>(h->ld[h->L - 1], (double*)dst, false, s);
+    if (host) CUDA_TRY(cudaMemcpyAsync(x, h->x_stage, (size_t)N * esz, cudaMemcpyDeviceToHost, s));
+    return MGMC_OK;
+}
+
+mgmc_status mgmc_sample(mgmc_handle h, int64_t n_steps, uint64_t seed, uint64_t step_offset, uint32_t chain,
+                        void* x_inout, double* qoi_out, void* stream)
+{
+    if (!h) return fail(MGMC_ERR_ARG, "handle is NULL");
+    if (!x_inout) return fail(MGMC_ERR_ARG, "x_inout is NULL");
+    if (n_steps < 0) return fail(MGMC_ERR_ARG, "n_steps < 0");
+    if (chain > 0xFFFFu) return fail(MGMC_ERR_ARG, "chain must be < 65536");
+    if (n_steps == 0) return MGMC_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(cudaSetDevice(h->device));
+    long long N = 1;
+    for (int a = 0; a < h->cfg.dim; ++a) N *= h->cfg.n;
+    bool xhost = !is_device_ptr(x_inout);
+    bool qhost = qoi_out && !is_device_ptr(qoi_out);
+    double* qdev = qoi_out;
+    if (qhost) {
+        CUDA_TRY(cudaMallocAsync((void**)&qdev, sizeof(double) * (size_t)n_steps, s));
+    }
+    mgmc_status st = ensure_graph(h);
+    if (st != MGMC_OK) return st;
+    st = pack_in(h, x_inout, xhost, s, N);
+    if (st != MGMC_OK) return st;
+    launch_set_cycle(h->cs, seed, step_offset, chain, 1, qdev, s);
+    for (int64_t t = 0; t < n_steps; ++t) CUDA_TRY(cudaGraphLaunch(h->exec, s));
+    st = pack_out(h, x_inout, xhost, s, N);
+    if (st != MGMC_OK) return st;
+    if (qhost) {
+        CUDA_TRY(cudaMemcpyAsync(qoi_out, qdev, sizeof(double) * (size_t)n_steps, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaFreeAsync(qdev, s));
+    }
+    CUDA_TRY(cudaGetLastError());
+    if (xhost || qhost) {
+        CUDA_TRY(cudaStreamSynchronize(s));
+        CycleState csh;
+        CUDA_TRY(cudaMemcpy(&csh, h->cs, sizeof(csh), cudaMemcpyDeviceToHost));
+        if (csh.status) return fail(MGMC_ERR_NUMERIC, "non-finite QoI produced");
+    }
+    return MGMC_OK;
+}
+
+mgmc_status mgmc_mean_solve(mgmc_handle h, double rtol, int max_cycles, void* mean_out, int* cycles_done,
+                            double* rel_residual, void* stream)
+{
+    if (!h || !mean_out) return fail(MGMC_ERR_ARG, "bad arguments");
+    if (max_cycles < 0 || !(rtol >= 0.0)) return fail(MGMC_ERR_ARG, "bad rtol / max_cycles");
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(cudaSetDevice(h->device));
+    long long N = 1;
+    for (int a = 0; a < h->cfg.dim; ++a) N *= h->cfg.n;
+    bool xhost = !is_device_ptr(mean_out);
+    mgmc_status st = ensure_graph(h);
+    if (st != MGMC_OK) return st;
+    st = pack_in(h, mean_out, xhost, s, N);
+    if (st != MGMC_OK) return st;
+    launch_set_cycle(h->cs, 0, 0, 0, 0, nullptr, s);
+    auto resid = [&](double& rr) -> mgmc_status {
+        if (h->fp32())
+            launch_resid<float>(h->lf[h->L - 1], h->P, h->u, h->partial, h->max_partial, h->rnorm, s);
+        else
+            launch_resid<double>(h->ld[h->L - 1], h->P, h->u, h->partial, h->max_partial, h->rnorm, s);
+        double r2 = 0.0;
+        CUDA_TRY(cudaMemcpyAsync(&r2, h->rnorm, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        double r = std::sqrt(r2);
+        rr = h->f_norm > 0.0 ? r / h->f_norm : (r == 0.0 ? 0.0 : INFINITY);
+        return MGMC_OK;
+    };
+    double rr = 0.0;
+    st = resid(rr);
+    if (st != MGMC_OK) return st;
+    int c = 0;
+    while (rr > rtol && c < max_cycles) {
+        int chunk = c < 4 ? 1 : 2;
+        for (int t = 0; t < chunk && c < max_cycles; ++t, ++c) CUDA_TRY(cudaGraphLaunch(h->exec, s));
+        st = resid(rr);
+        if (st != MGMC_OK) return st;
+        if (!std::isfinite(rr)) return fail(MGMC_ERR_NUMERIC, "mean solve diverged");
+    }
+    st = pack_out(h, mean_out, xhost, s, N);
+    if (st != MGMC_OK) return st;
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (cycles_done) *cycles_done = c;
+    if (rel_residual) *rel_residual = rr;
+    return MGMC_OK;
+}
+
+mgmc_status mgmc_set_profiling(mgmc_handle h, int enable)
+{
+    if (!h) return fail(MGMC_ERR_ARG, "handle is NULL");
+    bool want = enable != 0;
+    if (want == h->profile) return MGMC_OK;
+    CUDA_TRY(cudaSetDevice(h->device));
+    if (want && !h->ev[0])
+        for (int i = 0; i < 4; ++i) CUDA_TRY(cudaEventCreate(&h->ev[i]));
+    h->profile = want;
+    if (h->exec) {
+        CUDA_TRY(cudaDeviceSynchronize());
+        cudaGraphExecDestroy(h->exec);
+        h->exec = nullptr;
+    }
+    return MGMC_OK;
+}
+
+mgmc_status mgmc_profile_times(mgmc_handle h, float* ms, int n, void* stream)
+{
+    if (!h || !ms || n < 2) return fail(MGMC_ERR_ARG, "bad arguments");
+    if (!h->profile || h->top >= h->L - 1)
+        return fail(MGMC_ERR_STATE, "profiling is off or the finest grid runs in the single-CTA kernel");
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    CUDA_TRY(cudaEventElapsedTime(&ms[0], h->ev[0], h->ev[1]));
+    CUDA_TRY(cudaEventElapsedTime(&ms[1], h->ev[2], h->ev[3]));
+    return MGMC_OK;
+}
+
+mgmc_status mgmc_destroy(mgmc_handle h)
+{
+    if (!h) return MGMC_OK;
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    for (int i = 0; i < 4; ++i)
+        if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    h->buf.release();
+    delete h;
+    return MGMC_OK;
+}
+
+}  // extern "C"

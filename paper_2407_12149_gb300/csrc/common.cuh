@@ -1,0 +1,160 @@
+// common.cuh -- device-side data layout and helpers of the MGMC sampler.
+//
+// Grid storage (every level, every field): a padded array with one ring of
+// zero ghost values.  Interior site (i, j[, k]) lives at element
+//   base + i + pitch * j [+ plane * k],
+//   base = 4 + pitch [+ plane],
+// so each row starts at a 16-byte boundary (4 FP32 / 2 FP64 sites), the
+// left ghost sits at column 3 and the right ghost at column n + 4.  The
+// ghosts are never written and stay zero (zero Dirichlet values, Sec. 5.1.1).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/mgmc.h"
+
+namespace mgmc {
+
+constexpr int kMaxObs = MGMC_MAX_OBS;
+
+// Per-cycle values read by the kernels of a captured cycle graph.
+struct CycleState {
+    unsigned long long seed;
+    unsigned long long cycle;   // Philox cycle index of the running V-cycle
+    unsigned int chain;
+    int noise;                  // 0: deterministic multigrid (mean solve)
+    double* qoi;                // NULL or [n_steps] QoI series
+    long long step;             // index into qoi of the running cycle
+    int status;                 // sticky error flag (non-finite value seen)
+};
+
+// One grid level on the device.  T = float or double.
+template <typename T>
+struct DevLevel {
+    int level;          // paper numbering: 0 coarsest
+    int dim;
+    int n;              // interior points per axis
+    int pitch;          // elements per padded row
+    long long plane;    // elements per padded plane
+    long long base;     // element offset of interior site 0
+    long long alloc;    // elements per padded field
+    T* x;               // state theta_l / psi_l
+    T* f;               // dense part of the right-hand side (NULL on the finest level)
+    // finest level: 5/7-point operator s (kappa^2 - Delta_h)
+    int fine;
+    T* diag;            // FP64: a_ii ; FP32: s kappa^2_i (the row-sum part)
+    T woff;             // s / h^2 (off-diagonal magnitude)
+    // coarse levels: symmetric 9/27-point Galerkin stencil, structure of arrays;
+    // slot 0 = a_ii (FP64) or the row sum sum_j a_ij (FP32), slot t >= 1 = a(i, i + o_t)
+    // for the t-th positive stencil offset o_t
+    T* coef;
+    int ncoef;
+    // B_l rows grouped by grid row (finest level; used by the residual norm)
+    const int* brow_ptr;    // [n^(dim-1) + 1]
+    const int* bent_i;      // x index of the entry
+    const int* bent_k;      // observation index
+    const double* bent_w;   // weight
+    // B_l columns (for z = B^T x)
+    const int* bcol_ptr;          // [m + 1]
+    const long long* bcol_site;   // padded element offset
+    const double* bcol_w;
+    // G_l on its support, per direction (0 forward, 1 backward)
+    int g_rows[2];
+    const long long* g_site[2];   // padded element offsets
+    const double* g_val[2];       // [rows * m]
+    // the level's right-hand side is f_l = fdense_l + B_l Gamma^-1 d_l
+    double* d;                    // [m] data vector d_l (d_L = y)
+    double* dnext;                // [m] d_{l-1} = d_l - B_l^T theta, written on the way down
+};
+
+struct DevProblem {
+    int m;                     // number of observations
+    int gamma_diag;            // Gamma (and its Cholesky factor) is diagonal
+    const double* Gamma_inv;   // [m*m]
+    const double* LG;          // [m*m] Cholesky factor L_Gamma of Gamma (lower triangular)
+    CycleState* cs;
+};
+
+__host__ __device__ inline long long site_offset(int dim, int pitch, long long plane, long long base, int i,
+                                                 int j, int k)
+{
+    return base + i + (long long)pitch * j + (dim == 3 ? plane * k : 0);
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of the
+// multiply-xor round with multipliers 0xD2511F53 / 0xCD9E8D57 and the Weyl
+// key schedule 0x9E3779B9 / 0xBB67AE85.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox10(uint4 c, unsigned k0, unsigned k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        unsigned lo0 = 0xD2511F53u * c.x;
+        unsigned hi0 = __umulhi(0xD2511F53u, c.x);
+        unsigned lo1 = 0xCD9E8D57u * c.z;
+        unsigned hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Counter words for a draw of `kind` (0 site noise, 1 low-rank noise, 2 coarsest
+// sample) on level l and sweep slot; c0 is the pair index.
+__device__ __forceinline__ uint4 noise_counter(const CycleState& cs, unsigned pair, unsigned kind, int level,
+                                               unsigned slot)
+{
+    unsigned c1 = (unsigned)cs.cycle;
+    unsigned c2 = ((unsigned)(cs.cycle >> 32) & 0xFFFFu) | (cs.chain << 16);
+    unsigned c3 = (kind << 24) | ((unsigned)level << 16) | slot;
+    return make_uint4(pair, c1, c2, c3);
+}
+
+// Box-Muller pair from one Philox block: u = (top 53 bits + 1/2) 2^-53,
+// z0 = r cos(2 pi u2), z1 = r sin(2 pi u2), r = sqrt(-2 ln u1).
+__device__ __forceinline__ void normal_pair(const uint4 w, double& z0, double& z1)
+{
+    unsigned long long k1 = (((unsigned long long)w.x << 32) | w.y) >> 11;
+    unsigned long long k2 = (((unsigned long long)w.z << 32) | w.w) >> 11;
+    double u1 = ((double)k1 + 0.5) * 0x1p-53;
+    double u2 = ((double)k2 + 0.5) * 0x1p-53;
+    double r = sqrt(-2.0 * log(u1));
+    double s, c;
+    sincospi(2.0 * u2, &s, &c);
+    z0 = r * c;
+    z1 = r * s;
+}
+
+// The same draws in FP32: u is the FP32 rounding of (k + 1/2) 2^-53, formed from
+// the two 32-bit halves so that the full 53-bit value is used.
+__device__ __forceinline__ void normal_pair(const uint4 w, float& z0, float& z1)
+{
+    float u1 = fmaf((float)w.x, 0x1p-32f, fmaf((float)(w.y & 0xFFFFF800u), 0x1p-64f, 0x1p-54f));
+    float u2 = fmaf((float)w.z, 0x1p-32f, fmaf((float)(w.w & 0xFFFFF800u), 0x1p-64f, 0x1p-54f));
+    float r = sqrtf(-2.0f * logf(u1));
+    float s, c;
+    sincospif(2.0f * u2, &s, &c);
+    z0 = r * c;
+    z1 = r * s;
+}
+
+template <typename T>
+__device__ __forceinline__ void draw_pair(const CycleState& cs, unsigned pair, unsigned kind, int level,
+                                          unsigned slot, T& z0, T& z1)
+{
+    uint4 w = philox10(noise_counter(cs, pair, kind, level, slot), (unsigned)cs.seed,
+                       (unsigned)(cs.seed >> 32));
+    normal_pair(w, z0, z1);
+}
+
+// One standard normal of the low-rank noise z'_k (kind 1).
+__device__ __forceinline__ double lowrank_normal(const CycleState& cs, int level, unsigned slot, int k)
+{
+    double z0, z1;
+    draw_pair<double>(cs, (unsigned)(k >> 1), 1u, level, slot, z0, z1);
+    return (k & 1) ? z1 : z0;
+}
+
+}  // namespace mgmc

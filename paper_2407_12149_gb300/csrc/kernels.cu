@@ -1,0 +1,635 @@
+// kernels.cu -- CUDA kernels of one MGMC V-cycle (Alg. 1) for sm_103a.
+//
+// Per level l (finest first) the host enqueues:
+//   k_sweep_colour  x nu1 sweeps x colours : forward random Gibbs sweep (Alg. 3 line 11)
+//   k_lowrank                              : theta' = theta* - G (B^T theta*) (Eq. low_rank_update)
+//   k_restrict                             : f_{l-1} = P^T (f_l - A_l theta') and
+//                                            g_{l-1} = g_l - Gamma^-1 B^T theta'
+// the grids with n <= coarse_max_n run as one k_coarse_cycle (single CTA),
+// which ends in the exact coarsest Cholesky sample (Sec. 2.5), and back up:
+//   k_prolong                              : theta += P psi_{l-1}
+//   k_sweep_colour  (reverse colours), k_lowrank (backward G)
+// and k_qoi_advance records F^T theta and advances the cycle counter.
+//
+// Low-rank bookkeeping: the right-hand side of level l is kept as
+// f_l = fdense_l + B_l Gamma^-1 d_l with a dense field fdense_l and an m-vector
+// d_l; on the finest level fdense_L = 0 and d_L = y (Eq. f_ell_definition).
+// Alg. 3 is evaluated as
+//   theta*_s = Gibbs sweep of the dense part fdense_l + D^1/2 z   (k_sweep_colour)
+//   theta'   = theta*_s - G (B^T theta*_s - d_l - L_Gamma z')     (k_lowrank)
+// which equals theta* - G B^T theta* of Eq. lowrank_gibbs_two_steps with
+// theta* = theta*_s + C (Gamma^-1 d_l + xi_LR), because C - G B^T C = G Gamma
+// (Eq. Bellstar_definition); no term of size |Gamma^-1 y| is ever formed.
+// Restriction: fdense_{l-1} = P^T (fdense_l - A_l theta'), d_{l-1} = d_l - B_l^T theta'
+// (P^T B_l = B_{l-1}, Eq. A_ell_1_B_ell_1).
+#include "kernels.cuh"
+
+namespace mgmc {
+
+// Map a work item of colour `colour` to (row j, k, x parity, x block q).
+// Fine 5/7-point levels run the two red-black groups (colour = 0 even, 1 odd);
+// Galerkin levels run the 2^d parity classes (colour = px + 2 py + 4 pz).
+template <int DIM>
+__device__ __forceinline__ bool colour_item(int n, bool redblack, int colour, long long item, int& j, int& k,
+                                            int& px, int& q)
+{
+    int nq = (n + 3) >> 2;
+    q = (int)(item % nq);
+    long long r = item / nq;
+    if (redblack) {
+        int nr = DIM == 3 ? n * n : n;
+        if (r >= nr) return false;
+        j = (int)(r % n);
+        k = DIM == 3 ? (int)(r / n) : 0;
+        px = (j + k + colour) & 1;
+    } else {
+        int py = (colour >> 1) & 1, pz = (colour >> 2) & 1;
+        int ny = (n - py + 1) >> 1;
+        int nz = DIM == 3 ? (n - pz + 1) >> 1 : 1;
+        if (r >= (long long)ny * nz) return false;
+        j = 2 * (int)(r % ny) + py;
+        k = DIM == 3 ? 2 * (int)(r / ny) + pz : 0;
+        px = colour & 1;
+    }
+    return 4 * q + px < n;
+}
+
+template <typename T, int DIM>
+__device__ __forceinline__ void sweep_item(const DevLevel<T>& L, const DevProblem& P, const CycleState& cs,
+                                           bool redblack, int colour, unsigned slot, long long item)
+{
+    int j, k, px, q;
+    if (!colour_item<DIM>(L.n, redblack, colour, item, j, k, px, q)) return;
+    int n = L.n;
+    int nq = (n + 3) >> 2;
+    int i0 = 4 * q + px;
+    bool has1 = i0 + 2 < n;
+    T z0 = T(0), z1 = T(0);
+    if (cs.noise) {
+        unsigned pair = (unsigned)((((long long)k * n + j) * nq + q) * 2 + px);
+        draw_pair<T>(cs, pair, 0u, L.level, slot, z0, z1);
+    }
+    long long e = site_offset(DIM, L.pitch, L.plane, L.base, i0, j, k);
+    if (L.fine) {
+        L.x[e] = fine_update<DIM>(L, e, z0);
+        if (has1) L.x[e + 2] = fine_update<DIM>(L, e + 2, z1);
+    } else {
+        L.x[e] = coarse_update<DIM>(L, e, z0);
+        if (has1) L.x[e + 2] = coarse_update<DIM>(L, e + 2, z1);
+    }
+}
+
+template <typename T, int DIM>
+__global__ void k_sweep_colour(DevLevel<T> L, DevProblem P, int redblack, int colour, unsigned slot)
+{
+    const CycleState cs = *P.cs;
+    long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    sweep_item<T, DIM>(L, P, cs, redblack != 0, colour, slot, item);
+}
+
+// ---------------------------------------------------------------------------
+// CTA-wide pieces (used by the single-CTA kernels)
+// ---------------------------------------------------------------------------
+template <typename T, int DIM>
+__device__ void cta_sweep(const DevLevel<T>& L, const DevProblem& P, const CycleState& cs, int dir, unsigned slot)
+{
+    // 2^d parity colours in the reading's order; the red-black groups of the
+    // 5/7-point level are unions of these classes, so the result is identical
+    const int seq2[4] = {0, 3, 2, 1};
+    const int seq3[8] = {0, 6, 5, 3, 4, 2, 1, 7};
+    const int nc = DIM == 2 ? 4 : 8;
+    int nq = (L.n + 3) >> 2;
+    for (int ci = 0; ci < nc; ++ci) {
+        int c = DIM == 2 ? seq2[dir == 0 ? ci : nc - 1 - ci] : seq3[dir == 0 ? ci : nc - 1 - ci];
+        int py = (c >> 1) & 1, pz = (c >> 2) & 1;
+        long long items = (long long)nq * ((L.n - py + 1) >> 1) * (DIM == 3 ? ((L.n - pz + 1) >> 1) : 1);
+        for (long long it = threadIdx.x; it < items; it += blockDim.x) sweep_item<T, DIM>(L, P, cs, false, c, slot, it);
+        __syncthreads();
+    }
+}
+
+// theta' = theta*_s - G (B^T theta*_s - d - L_Gamma z') (skipped for dir < 0);
+// with want_dnext also d_{l-1} = d_l - B_l^T theta'
+template <typename T>
+__device__ void cta_lowrank(const DevLevel<T>& L, const DevProblem& P, const CycleState& cs, int dir, unsigned slot,
+                            bool want_dnext)
+{
+    __shared__ double z[kMaxObs];
+    __shared__ double zp[kMaxObs];
+    const int m = P.m;
+    if (m == 0) return;
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        double acc = 0.0;
+        for (int t = L.bcol_ptr[k]; t < L.bcol_ptr[k + 1]; ++t) acc += L.bcol_w[t] * (double)L.x[L.bcol_site[t]];
+        z[k] = acc;
+        zp[k] = (dir >= 0 && cs.noise) ? lowrank_normal(cs, L.level, slot, k) : 0.0;
+    }
+    __syncthreads();
+    if (dir >= 0) {
+        // v = B^T theta*_s - d - L_Gamma z'   (kept in z)
+        double v = 0.0;
+        int k = threadIdx.x;
+        if (k < m) {
+            double lz = 0.0;
+            if (cs.noise) {
+                if (P.gamma_diag) {
+                    lz = P.LG[k * m + k] * zp[k];
+                } else {
+                    for (int t = 0; t <= k; ++t) lz += P.LG[k * m + t] * zp[t];
+                }
+            }
+            v = z[k] - L.d[k] - lz;
+        }
+        __syncthreads();
+        if (k < m) z[k] = v;
+        __syncthreads();
+        const int rows = L.g_rows[dir];
+        const double* G = L.g_val[dir];
+        for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+            double acc = 0.0;
+            for (int kk = 0; kk < m; ++kk) acc += G[(long long)r * m + kk] * z[kk];
+            long long s = L.g_site[dir][r];
+            L.x[s] = (T)((double)L.x[s] - acc);
+        }
+        __syncthreads();
+    }
+    if (!want_dnext) return;
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        double acc = 0.0;
+        for (int t = L.bcol_ptr[k]; t < L.bcol_ptr[k + 1]; ++t) acc += L.bcol_w[t] * (double)L.x[L.bcol_site[t]];
+        L.dnext[k] = L.d[k] - acc;
+    }
+    __syncthreads();
+}
+
+template <typename T, int DIM>
+__device__ __forceinline__ T restrict_site(const DevLevel<T>& F, const DevLevel<T>& C, int I, int J, int K)
+{
+    T acc = T(0);
+    const int nz = DIM == 3 ? 3 : 1;
+    for (int pz = 0; pz < nz; ++pz)
+        for (int py = 0; py < 3; ++py)
+            for (int px = 0; px < 3; ++px) {
+                int fi = 2 * I + px, fj = 2 * J + py, fk = DIM == 3 ? 2 * K + pz : 0;
+                long long e = site_offset(DIM, F.pitch, F.plane, F.base, fi, fj, fk);
+                T wgt = (T)(pw(px - 1) * pw(py - 1) * (DIM == 3 ? pw(pz - 1) : 1.0));
+                T r = (F.f ? F.f[e] : T(0)) - apply_A<DIM>(F, e);
+                acc += wgt * r;
+            }
+    return acc;
+}
+
+template <typename T, int DIM>
+__device__ __forceinline__ T prolong_site(const DevLevel<T>& C, int fi, int fj, int fk)
+{
+    // fine index f: odd -> coarse (f-1)/2 with weight 1; even -> coarse f/2-1 and f/2, weight 1/2
+    T acc = T(0);
+    int cx[2], cy[2], cz[2];
+    T wx[2], wy[2], wz[2];
+    int nx, ny, nz;
+    auto axis = [](int f, int* c, T* w, int& cnt) {
+        if (f & 1) {
+            c[0] = (f - 1) >> 1;
+            w[0] = T(1);
+            cnt = 1;
+        } else {
+            c[0] = (f >> 1) - 1;
+            c[1] = f >> 1;
+            w[0] = w[1] = T(0.5);
+            cnt = 2;
+        }
+    };
+    axis(fi, cx, wx, nx);
+    axis(fj, cy, wy, ny);
+    if (DIM == 3) {
+        axis(fk, cz, wz, nz);
+    } else {
+        cz[0] = 0;
+        wz[0] = T(1);
+        nz = 1;
+    }
+    for (int c = 0; c < nz; ++c)
+        for (int b = 0; b < ny; ++b)
+            for (int a = 0; a < nx; ++a) {
+                // ghost indices -1 and n read the zero ring
+                long long e = site_offset(DIM, C.pitch, C.plane, C.base, cx[a], cy[b], cz[c]);
+                acc += wz[c] * wy[b] * wx[a] * C.x[e];
+            }
+    return acc;
+}
+
+template <typename T, int DIM>
+__device__ void cta_restrict(const DevLevel<T>& F, const DevLevel<T>& C)
+{
+    long long N = (long long)C.n * C.n * (DIM == 3 ? C.n : 1);
+    for (long long s = threadIdx.x; s < N; s += blockDim.x) {
+        int I = (int)(s % C.n), J = (int)((s / C.n) % C.n), K = DIM == 3 ? (int)(s / ((long long)C.n * C.n)) : 0;
+        C.f[site_offset(DIM, C.pitch, C.plane, C.base, I, J, K)] = restrict_site<T, DIM>(F, C, I, J, K);
+    }
+    __syncthreads();
+}
+
+template <typename T, int DIM>
+__device__ void cta_prolong(const DevLevel<T>& C, const DevLevel<T>& F)
+{
+    long long N = (long long)F.n * F.n * (DIM == 3 ? F.n : 1);
+    for (long long s = threadIdx.x; s < N; s += blockDim.x) {
+        int i = (int)(s % F.n), j = (int)((s / F.n) % F.n), k = DIM == 3 ? (int)(s / ((long long)F.n * F.n)) : 0;
+        long long e = site_offset(DIM, F.pitch, F.plane, F.base, i, j, k);
+        F.x[e] = F.x[e] + prolong_site<T, DIM>(C, i, j, k);
+    }
+    __syncthreads();
+}
+
+template <typename T, int DIM>
+__device__ void cta_zero(const DevLevel<T>& L)
+{
+    long long N = (long long)L.n * L.n * (DIM == 3 ? L.n : 1);
+    for (long long s = threadIdx.x; s < N; s += blockDim.x) {
+        int i = (int)(s % L.n), j = (int)((s / L.n) % L.n), k = DIM == 3 ? (int)(s / ((long long)L.n * L.n)) : 0;
+        L.x[site_offset(DIM, L.pitch, L.plane, L.base, i, j, k)] = T(0);
+    }
+    __syncthreads();
+}
+
+// Exact sample theta_0 = A~_0^-1 f_0 + L_0^-T z on the coarsest grid (Sec. 2.5),
+// f_0 = fdense_0 + B_0 g_0, A~_0 = L_0 L_0^T factored in FP64 at set-up.
+template <typename T, int DIM>
+__device__ void cta_coarsest(const DevLevel<T>& L, const DevProblem& P, const CycleState& cs, const double* chol,
+                             int n0)
+{
+    __shared__ double r[MGMC_MAX_COARSEST];
+    const int n = L.n;
+    for (int s = threadIdx.x; s < n0; s += blockDim.x) {
+        int i = s % n, j = (s / n) % n, k = DIM == 3 ? s / (n * n) : 0;
+        r[s] = L.f ? (double)L.f[site_offset(DIM, L.pitch, L.plane, L.base, i, j, k)] : 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int kk = 0; kk < P.m; ++kk) {
+            double gk = 0.0;   // (Gamma^-1 d_0)_kk
+            for (int t = 0; t < P.m; ++t) gk += P.Gamma_inv[kk * P.m + t] * L.d[t];
+            for (int t = L.bcol_ptr[kk]; t < L.bcol_ptr[kk + 1]; ++t) {
+                long long e = L.bcol_site[t] - L.base;   // dense index of a coarsest site
+                int i = (int)(e % L.pitch);
+                long long rest = e / L.pitch;
+                int j, k;
+                if (DIM == 3) {
+                    // e = i + pitch j + plane k with plane = pitch (n + 2)
+                    long long pj = L.plane / L.pitch;
+                    j = (int)(rest % pj);
+                    k = (int)(rest / pj);
+                } else {
+                    j = (int)rest;
+                    k = 0;
+                }
+                r[i + n * (j + n * k)] += L.bcol_w[t] * gk;
+            }
+        }
+    }
+    __syncthreads();
+    // forward substitution L y = r, one column at a time
+    for (int i = 0; i < n0; ++i) {
+        if (threadIdx.x == 0) r[i] = r[i] / chol[(long long)i * n0 + i];
+        __syncthreads();
+        double yi = r[i];
+        for (int t = i + 1 + threadIdx.x; t < n0; t += blockDim.x) r[t] -= chol[(long long)t * n0 + i] * yi;
+        __syncthreads();
+    }
+    // y += z
+    if (cs.noise) {
+        for (int s = threadIdx.x; s < n0; s += blockDim.x) {
+            double z0, z1;
+            draw_pair<double>(cs, (unsigned)(s >> 1), 2u, 0, 0u, z0, z1);
+            r[s] += (s & 1) ? z1 : z0;
+        }
+    }
+    __syncthreads();
+    // back substitution L^T x = y (row i of L^T is column i of L)
+    for (int i = n0 - 1; i >= 0; --i) {
+        if (threadIdx.x == 0) r[i] = r[i] / chol[(long long)i * n0 + i];
+        __syncthreads();
+        double xi = r[i];
+        for (int t = threadIdx.x; t < i; t += blockDim.x) r[t] -= chol[(long long)i * n0 + t] * xi;
+        __syncthreads();
+    }
+    for (int s = threadIdx.x; s < n0; s += blockDim.x) {
+        int i = s % n, j = (s / n) % n, k = DIM == 3 ? s / (n * n) : 0;
+        L.x[site_offset(DIM, L.pitch, L.plane, L.base, i, j, k)] = (T)r[s];
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_lowrank(DevLevel<T> L, DevProblem P, int dir, unsigned slot, int want_dnext)
+{
+    const CycleState cs = *P.cs;
+    cta_lowrank<T>(L, P, cs, dir, slot, want_dnext != 0);
+}
+
+template <typename T, int DIM>
+__global__ void k_restrict(DevLevel<T> F, DevLevel<T> C)
+{
+    long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long N = (long long)C.n * C.n * (DIM == 3 ? C.n : 1);
+    if (s >= N) return;
+    int I = (int)(s % C.n), J = (int)((s / C.n) % C.n), K = DIM == 3 ? (int)(s / ((long long)C.n * C.n)) : 0;
+    C.f[site_offset(DIM, C.pitch, C.plane, C.base, I, J, K)] = restrict_site<T, DIM>(F, C, I, J, K);
+}
+
+template <typename T, int DIM>
+__global__ void k_prolong(DevLevel<T> C, DevLevel<T> F)
+{
+    long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long N = (long long)F.n * F.n * (DIM == 3 ? F.n : 1);
+    if (s >= N) return;
+    int i = (int)(s % F.n), j = (int)((s / F.n) % F.n), k = DIM == 3 ? (int)(s / ((long long)F.n * F.n)) : 0;
+    long long e = site_offset(DIM, F.pitch, F.plane, F.base, i, j, k);
+    F.x[e] = F.x[e] + prolong_site<T, DIM>(C, i, j, k);
+}
+
+// The whole V-cycle below (and including) level `top`, one CTA.
+// levels[0..top] are the device descriptors, index = paper level.
+constexpr int kCoarseThreads = 512;
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kCoarseThreads) k_coarse_cycle(const DevLevel<T>* __restrict__ levels, int top, int is_finest, DevProblem P,
+                               const double* chol, int n0, int nu1, int nu2)
+{
+    const CycleState cs = *P.cs;
+    for (int l = top; l >= 1; --l) {
+        const DevLevel<T> L = levels[l];
+        if (!(l == top && is_finest)) cta_zero<T, DIM>(L);
+        for (int s = 0; s < nu1; ++s) {
+            cta_sweep<T, DIM>(L, P, cs, 0, (unsigned)(2 * s));
+            cta_lowrank<T>(L, P, cs, 0, (unsigned)(2 * s), s == nu1 - 1);
+        }
+        if (nu1 == 0) cta_lowrank<T>(L, P, cs, -1, 0u, true);   // d_{l-1} = d_l - B^T theta
+        cta_restrict<T, DIM>(L, levels[l - 1]);
+    }
+    cta_coarsest<T, DIM>(levels[0], P, cs, chol, n0);
+    for (int l = 1; l <= top; ++l) {
+        const DevLevel<T> L = levels[l];
+        cta_prolong<T, DIM>(levels[l - 1], L);
+        for (int s = 0; s < nu2; ++s) {
+            cta_sweep<T, DIM>(L, P, cs, 1, (unsigned)(2 * s + 1));
+            cta_lowrank<T>(L, P, cs, 1, (unsigned)(2 * s + 1), false);
+        }
+    }
+}
+
+// F^T theta of the finest level into qoi[step]; then step += 1, cycle += 1.
+template <typename T>
+__global__ void k_qoi_advance(DevLevel<T> L, int n_qoi, const long long* q_site, const double* q_w, DevProblem P)
+{
+    __shared__ double part[256];
+    double acc = 0.0;
+    for (int t = threadIdx.x; t < n_qoi; t += blockDim.x) acc += q_w[t] * (double)L.x[q_site[t]];
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) part[threadIdx.x] += part[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        CycleState* cs = P.cs;
+        double q = part[0];
+        if (cs->qoi) cs->qoi[cs->step] = q;
+        if (!isfinite(q)) cs->status = 1;
+        cs->step += 1;
+        cs->cycle += 1;
+    }
+}
+
+__global__ void k_set_cycle(CycleState* cs, unsigned long long seed, unsigned long long cycle, unsigned chain,
+                            int noise, double* qoi)
+{
+    cs->seed = seed;
+    cs->cycle = cycle;
+    cs->chain = chain;
+    cs->noise = noise;
+    cs->qoi = qoi;
+    cs->step = 0;
+    cs->status = 0;
+}
+
+// dense user field <-> padded finest-level state
+template <typename T, int DIM>
+__global__ void k_pack(DevLevel<T> L, T* __restrict__ dense, int to_padded)
+{
+    long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long N = (long long)L.n * L.n * (DIM == 3 ? L.n : 1);
+    if (s >= N) return;
+    int i = (int)(s % L.n), j = (int)((s / L.n) % L.n), k = DIM == 3 ? (int)(s / ((long long)L.n * L.n)) : 0;
+    long long e = site_offset(DIM, L.pitch, L.plane, L.base, i, j, k);
+    if (to_padded)
+        L.x[e] = dense[s];
+    else
+        dense[s] = L.x[e];
+}
+
+// ---------------------------------------------------------------------------
+// residual norm pieces for the mean solve: u = Gamma^-1 (y - B^T x) (m-vector),
+// then r = B u - A x summed as ||r||^2 per block, reduced by one block.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_resid_u(DevLevel<T> L, DevProblem P, double* u)
+{
+    __shared__ double z[kMaxObs];
+    const int m = P.m;
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        double acc = 0.0;
+        for (int t = L.bcol_ptr[k]; t < L.bcol_ptr[k + 1]; ++t) acc += L.bcol_w[t] * (double)L.x[L.bcol_site[t]];
+        z[k] = acc;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < m; k += blockDim.x) z[k] = L.d[k] - z[k];   // d_L - B^T x
+    __syncthreads();
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        double acc = 0.0;
+        for (int t = 0; t < m; ++t) acc += P.Gamma_inv[k * m + t] * z[t];
+        u[k] = acc;
+    }
+}
+
+template <typename T, int DIM>
+__global__ void k_resid_norm(DevLevel<T> L, const double* u, double* partial)
+{
+    __shared__ double part[256];
+    long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long N = (long long)L.n * L.n * (DIM == 3 ? L.n : 1);
+    double v = 0.0;
+    if (s < N) {
+        int i = (int)(s % L.n), j = (int)((s / L.n) % L.n), k = DIM == 3 ? (int)(s / ((long long)L.n * L.n)) : 0;
+        long long e = site_offset(DIM, L.pitch, L.plane, L.base, i, j, k);
+        double r = -(double)apply_A<DIM>(L, e);
+        if (L.brow_ptr) {
+            int row = j + L.n * k;
+            for (int t = L.brow_ptr[row]; t < L.brow_ptr[row + 1]; ++t)
+                if (L.bent_i[t] == i) r += L.bent_w[t] * u[L.bent_k[t]];
+        }
+        v = r * r;
+    }
+    part[threadIdx.x] = v;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) part[threadIdx.x] += part[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = part[0];
+}
+
+__global__ void k_sum(const double* partial, int n, double* out)
+{
+    __shared__ double part[256];
+    double acc = 0.0;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) acc += partial[t];
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) part[threadIdx.x] += part[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = part[0];
+}
+
+// ---------------------------------------------------------------------------
+// host-side launchers
+// ---------------------------------------------------------------------------
+static inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+template <typename T>
+void launch_sweep(const DevLevel<T>& L, const DevProblem& P, int dir, unsigned slot, cudaStream_t st, int& launches)
+{
+    const int bs = 256;
+    int nq = (L.n + 3) / 4;
+    if (L.fine) {
+        long long rows = L.dim == 3 ? (long long)L.n * L.n : L.n;
+        for (int g = 0; g < 2; ++g) {
+            int colour = dir == 0 ? g : 1 - g;
+            unsigned nb = blocks_for(rows * nq, bs);
+            if (L.dim == 2)
+                k_sweep_colour<T, 2><<<nb, bs, 0, st>>>(L, P, 1, colour, slot);
+            else
+                k_sweep_colour<T, 3><<<nb, bs, 0, st>>>(L, P, 1, colour, slot);
+            ++launches;
+        }
+        return;
+    }
+    const int seq2[4] = {0, 3, 2, 1};
+    const int seq3[8] = {0, 6, 5, 3, 4, 2, 1, 7};
+    int nc = L.dim == 2 ? 4 : 8;
+    for (int ci = 0; ci < nc; ++ci) {
+        int c = L.dim == 2 ? seq2[dir == 0 ? ci : nc - 1 - ci] : seq3[dir == 0 ? ci : nc - 1 - ci];
+        int py = (c >> 1) & 1, pz = (c >> 2) & 1;
+        long long rows = (long long)((L.n - py + 1) / 2) * (L.dim == 3 ? (L.n - pz + 1) / 2 : 1);
+        unsigned nb = blocks_for(rows * nq, bs);
+        if (L.dim == 2)
+            k_sweep_colour<T, 2><<<nb, bs, 0, st>>>(L, P, 0, c, slot);
+        else
+            k_sweep_colour<T, 3><<<nb, bs, 0, st>>>(L, P, 0, c, slot);
+        ++launches;
+    }
+}
+
+template <typename T>
+void launch_lowrank(const DevLevel<T>& L, const DevProblem& P, int dir, unsigned slot, bool dnext, cudaStream_t st,
+                    int& launches)
+{
+    if (P.m == 0) return;
+    k_lowrank<T><<<1, 256, 0, st>>>(L, P, dir, slot, dnext ? 1 : 0);
+    ++launches;
+}
+
+template <typename T>
+void launch_restrict(const DevLevel<T>& F, const DevLevel<T>& C, cudaStream_t st, int& launches)
+{
+    long long N = (long long)C.n * C.n * (C.dim == 3 ? C.n : 1);
+    if (C.dim == 2)
+        k_restrict<T, 2><<<blocks_for(N, 256), 256, 0, st>>>(F, C);
+    else
+        k_restrict<T, 3><<<blocks_for(N, 256), 256, 0, st>>>(F, C);
+    ++launches;
+}
+
+template <typename T>
+void launch_prolong(const DevLevel<T>& C, const DevLevel<T>& F, cudaStream_t st, int& launches)
+{
+    long long N = (long long)F.n * F.n * (F.dim == 3 ? F.n : 1);
+    if (F.dim == 2)
+        k_prolong<T, 2><<<blocks_for(N, 256), 256, 0, st>>>(C, F);
+    else
+        k_prolong<T, 3><<<blocks_for(N, 256), 256, 0, st>>>(C, F);
+    ++launches;
+}
+
+template <typename T>
+void launch_coarse(const DevLevel<T>* levels_dev, int dim, int top, bool is_finest, const DevProblem& P,
+                   const double* chol, int n0, int nu1, int nu2, cudaStream_t st, int& launches)
+{
+    if (dim == 2)
+        k_coarse_cycle<T, 2><<<1, kCoarseThreads, 0, st>>>(levels_dev, top, is_finest ? 1 : 0, P, chol, n0, nu1, nu2);
+    else
+        k_coarse_cycle<T, 3><<<1, kCoarseThreads, 0, st>>>(levels_dev, top, is_finest ? 1 : 0, P, chol, n0, nu1, nu2);
+    ++launches;
+}
+
+template <typename T>
+void launch_qoi(const DevLevel<T>& L, int n_qoi, const long long* q_site, const double* q_w, const DevProblem& P,
+                cudaStream_t st, int& launches)
+{
+    k_qoi_advance<T><<<1, 256, 0, st>>>(L, n_qoi, q_site, q_w, P);
+    ++launches;
+}
+
+void launch_set_cycle(CycleState* cs, unsigned long long seed, unsigned long long cycle, unsigned chain, int noise,
+                      double* qoi, cudaStream_t st)
+{
+    k_set_cycle<<<1, 1, 0, st>>>(cs, seed, cycle, chain, noise, qoi);
+}
+
+template <typename T>
+void launch_pack(const DevLevel<T>& L, T* dense, bool to_padded, cudaStream_t st)
+{
+    long long N = (long long)L.n * L.n * (L.dim == 3 ? L.n : 1);
+    if (L.dim == 2)
+        k_pack<T, 2><<<blocks_for(N, 256), 256, 0, st>>>(L, dense, to_padded ? 1 : 0);
+    else
+        k_pack<T, 3><<<blocks_for(N, 256), 256, 0, st>>>(L, dense, to_padded ? 1 : 0);
+}
+
+template <typename T>
+void launch_resid(const DevLevel<T>& L, const DevProblem& P, double* u, double* partial, int max_partial,
+                  double* out, cudaStream_t st)
+{
+    if (P.m > 0) k_resid_u<T><<<1, 64, 0, st>>>(L, P, u);
+    long long N = (long long)L.n * L.n * (L.dim == 3 ? L.n : 1);
+    unsigned nb = blocks_for(N, 256);
+    (void)max_partial;
+    if (L.dim == 2)
+        k_resid_norm<T, 2><<<nb, 256, 0, st>>>(L, P.m > 0 ? u : nullptr, partial);
+    else
+        k_resid_norm<T, 3><<<nb, 256, 0, st>>>(L, P.m > 0 ? u : nullptr, partial);
+    k_sum<<<1, 256, 0, st>>>(partial, (int)nb, out);
+}
+
+#define MGMC_INSTANTIATE(T)                                                                                       \
+    template void launch_sweep<T>(const DevLevel<T>&, const DevProblem&, int, unsigned, cudaStream_t, int&);     \
+    template void launch_lowrank<T>(const DevLevel<T>&, const DevProblem&, int, unsigned, bool, cudaStream_t, int&); \
+    template void launch_restrict<T>(const DevLevel<T>&, const DevLevel<T>&, cudaStream_t, int&);                \
+    template void launch_prolong<T>(const DevLevel<T>&, const DevLevel<T>&, cudaStream_t, int&);                 \
+    template void launch_coarse<T>(const DevLevel<T>*, int, int, bool, const DevProblem&, const double*, int, int, \
+                                   int, cudaStream_t, int&);                                                     \
+    template void launch_qoi<T>(const DevLevel<T>&, int, const long long*, const double*, const DevProblem&,      \
+                                cudaStream_t, int&);                                                             \
+    template void launch_pack<T>(const DevLevel<T>&, T*, bool, cudaStream_t);                               \
+    template void launch_resid<T>(const DevLevel<T>&, const DevProblem&, double*, double*, int, double*,         \
+                                  cudaStream_t);
+
+MGMC_INSTANTIATE(float)
+MGMC_INSTANTIATE(double)
+
+}  // namespace mgmc

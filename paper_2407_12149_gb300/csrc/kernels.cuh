@@ -1,0 +1,32 @@
+// kernels.cuh -- launch wrappers of the V-cycle kernels (see kernels.cu).
+#pragma once
+#include "common.cuh"
+#include "stencil.cuh"
+
+namespace mgmc {
+
+template <typename T>
+void launch_sweep(const DevLevel<T>& L, const DevProblem& P, int dir, unsigned slot, cudaStream_t st, int& launches);
+// dir < 0: only d_{l-1} = d_l - B^T theta (no correction)
+template <typename T>
+void launch_lowrank(const DevLevel<T>& L, const DevProblem& P, int dir, unsigned slot, bool dnext, cudaStream_t st,
+                    int& launches);
+template <typename T>
+void launch_restrict(const DevLevel<T>& F, const DevLevel<T>& C, cudaStream_t st, int& launches);
+template <typename T>
+void launch_prolong(const DevLevel<T>& C, const DevLevel<T>& F, cudaStream_t st, int& launches);
+template <typename T>
+void launch_coarse(const DevLevel<T>* levels_dev, int dim, int top, bool is_finest, const DevProblem& P,
+                   const double* chol, int n0, int nu1, int nu2, cudaStream_t st, int& launches);
+template <typename T>
+void launch_qoi(const DevLevel<T>& L, int n_qoi, const long long* q_site, const double* q_w, const DevProblem& P,
+                cudaStream_t st, int& launches);
+void launch_set_cycle(CycleState* cs, unsigned long long seed, unsigned long long cycle, unsigned chain, int noise,
+                      double* qoi, cudaStream_t st);
+template <typename T>
+void launch_pack(const DevLevel<T>& L, T* dense, bool to_padded, cudaStream_t st);
+template <typename T>
+void launch_resid(const DevLevel<T>& L, const DevProblem& P, double* u, double* partial, int max_partial,
+                  double* out, cudaStream_t st);
+
+}  // namespace mgmc

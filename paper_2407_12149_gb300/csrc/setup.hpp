@@ -1,0 +1,46 @@
+// setup.hpp -- host-side (FP64) construction of the MGMC hierarchy.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace mgmc {
+
+struct HostLevel {
+    int n = 0;
+    long long N = 0;
+    std::vector<double> st;          // [N * 3^d] full stencil, offset (dx+1) + 3(dy+1) [+ 9(dz+1)]
+    // B_l by columns: entries bptr[k] .. bptr[k+1]-1 of (dense site, weight)
+    std::vector<int> bptr;
+    std::vector<long long> bsite;
+    std::vector<double> bw;
+    // G_l(dir) on its support
+    std::vector<long long> gsite[2];
+    std::vector<double> gval[2];     // [rows * m]
+};
+
+struct HostProblem {
+    int dim = 2, NS = 9, C = 4;
+    int n_levels = 1;
+    int m = 0;
+    int scale_hd = 1;
+    double woff_fine = 0.0;           // s / h^2 of the finest grid
+    std::vector<double> kappa_part;  // s * kappa^2 at the fine sites
+    std::vector<HostLevel> lev;      // 0 = coarsest
+    std::vector<double> Gamma, Gamma_inv, LG, y;
+    bool gamma_diag = true;
+    int n0 = 0;
+    std::vector<double> chol0;       // Cholesky factor of A~_0 (lower, row-major)
+    double f_norm = 0.0;             // ||f_L||_2
+};
+
+// Returns an empty string on success, otherwise an error message; *code gets
+// the mgmc_status to return.
+std::string build_hierarchy(HostProblem& hp, int dim, int n, int n_levels, int scale_hd, const double* kappa2,
+                            double kappa2_const, int m, const int32_t* obs_site, const double* obs_w,
+                            int nnz_per_obs, const double* Gamma, const double* y, int* code);
+
+// Row sums of a level's stencil (for the FP32 correction form).
+std::vector<double> row_sums(const HostProblem& hp, int l);
+
+}  // namespace mgmc

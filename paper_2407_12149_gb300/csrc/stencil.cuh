@@ -1,0 +1,168 @@
+// stencil.cuh -- per-site arithmetic of the random Gibbs smoother, the
+// residual and the grid transfers, shared by all sweep kernels.
+//
+// FP64 uses the plain form x_i <- (f_i + xi_i - sum_{j != i} a_ij x_j) / a_ii
+// (Alg. 3 as a colour-ordered Gauss-Seidel sweep).  FP32 uses the algebraically
+// identical correction form x_i <- x_i + (f_i + xi_i - (A x)_i) / a_ii with
+// (A x)_i = rowsum_i x_i + sum_{j != i} a_ij (x_j - x_i): in single precision
+// this keeps the small kappa^2 part of the operator (and so the smooth modes
+// of the field) accurate, which the plain form would round away.
+#pragma once
+#include "common.cuh"
+
+namespace mgmc {
+
+// stencil offsets in lexicographic order of (dx, dy, dz), dx fastest
+template <int DIM>
+struct Offsets {
+    static constexpr int NS = DIM == 2 ? 9 : 27;
+    static constexpr int C = (NS - 1) / 2;
+};
+
+template <int DIM>
+__device__ __forceinline__ long long off_of(int o, int pitch, long long plane)
+{
+    int dx = o % 3 - 1;
+    int dy = (o / 3) % 3 - 1;
+    int dz = DIM == 3 ? o / 9 - 1 : 0;
+    return (long long)dx + (long long)pitch * dy + plane * dz;
+}
+
+// a(i, i + o) of a coarse level, read from the symmetric half storage
+template <int DIM, typename T>
+__device__ __forceinline__ T coef_at(const DevLevel<T>& L, long long e, int o)
+{
+    constexpr int C = Offsets<DIM>::C;
+    constexpr int NS = Offsets<DIM>::NS;
+    if (o > C) return L.coef[(long long)(o - C) * L.alloc + e];
+    long long en = e + off_of<DIM>(o, L.pitch, L.plane);
+    return L.coef[(long long)(NS - 1 - o - C) * L.alloc + en];
+}
+
+// ---------------------------------------------------------------------------
+// one site update of the Gibbs sweep with right-hand side fdense_i + sqrt(a_ii) z
+// ---------------------------------------------------------------------------
+template <int DIM>
+__device__ __forceinline__ double fine_update(const DevLevel<double>& L, long long e, double z)
+{
+    const double* x = L.x;
+    double aii = L.diag[e];
+    double w = L.woff;
+    double acc = L.f ? L.f[e] : 0.0;
+    acc += sqrt(aii) * z;
+    // neighbours in the order (0,0,-1), (0,-1,0), (-1,0,0), (1,0,0), (0,1,0), (0,0,1)
+    if (DIM == 3) acc += w * x[e - L.plane];
+    acc += w * x[e - L.pitch];
+    acc += w * x[e - 1];
+    acc += w * x[e + 1];
+    acc += w * x[e + L.pitch];
+    if (DIM == 3) acc += w * x[e + L.plane];
+    return acc / aii;
+}
+
+template <int DIM>
+__device__ __forceinline__ float fine_update(const DevLevel<float>& L, long long e, float z)
+{
+    const float* x = L.x;
+    float xi = x[e];
+    float c = L.diag[e];
+    float w = L.woff;
+    float lap = (xi - x[e - L.pitch]) + (xi - x[e - 1]) + (xi - x[e + 1]) + (xi - x[e + L.pitch]);
+    if (DIM == 3) lap += (xi - x[e - L.plane]) + (xi - x[e + L.plane]);
+    float aii = fmaf(2.0f * DIM, w, c);
+    float Ax = fmaf(c, xi, w * lap);
+    float rhs = (L.f ? L.f[e] : 0.0f) + sqrtf(aii) * z;
+    return xi + (rhs - Ax) / aii;
+}
+
+template <int DIM>
+__device__ __forceinline__ double coarse_update(const DevLevel<double>& L, long long e, double z)
+{
+    constexpr int NS = Offsets<DIM>::NS;
+    constexpr int C = Offsets<DIM>::C;
+    double aii = L.coef[e];
+    double acc = L.f ? L.f[e] : 0.0;
+    acc += sqrt(aii) * z;
+#pragma unroll
+    for (int o = 0; o < NS; ++o) {
+        if (o == C) continue;
+        acc -= coef_at<DIM>(L, e, o) * L.x[e + off_of<DIM>(o, L.pitch, L.plane)];
+    }
+    return acc / aii;
+}
+
+template <int DIM>
+__device__ __forceinline__ float coarse_update(const DevLevel<float>& L, long long e, float z)
+{
+    constexpr int NS = Offsets<DIM>::NS;
+    constexpr int C = Offsets<DIM>::C;
+    float xi = L.x[e];
+    float s = L.coef[e];
+    float lap = 0.0f, offsum = 0.0f;
+#pragma unroll
+    for (int o = 0; o < NS; ++o) {
+        if (o == C) continue;
+        float a = coef_at<DIM>(L, e, o);
+        lap = fmaf(a, L.x[e + off_of<DIM>(o, L.pitch, L.plane)] - xi, lap);
+        offsum += a;
+    }
+    float aii = s - offsum;
+    float Ax = fmaf(s, xi, lap);
+    float rhs = (L.f ? L.f[e] : 0.0f) + sqrtf(aii) * z;
+    return xi + (rhs - Ax) / aii;
+}
+
+// (A x)_e of the level (dense part of the operator)
+template <int DIM>
+__device__ __forceinline__ double apply_A(const DevLevel<double>& L, long long e)
+{
+    const double* x = L.x;
+    if (L.fine) {
+        double w = -L.woff;
+        // oracle order: offsets lexicographic, centre in place
+        double acc = 0.0;
+        if (DIM == 3) acc += w * x[e - L.plane];
+        acc += w * x[e - L.pitch];
+        acc += w * x[e - 1];
+        acc += L.diag[e] * x[e];
+        acc += w * x[e + 1];
+        acc += w * x[e + L.pitch];
+        if (DIM == 3) acc += w * x[e + L.plane];
+        return acc;
+    }
+    constexpr int NS = Offsets<DIM>::NS;
+    constexpr int C = Offsets<DIM>::C;
+    double acc = 0.0;
+#pragma unroll
+    for (int o = 0; o < NS; ++o) {
+        double a = (o == C) ? L.coef[e] : coef_at<DIM>(L, e, o);
+        acc += a * x[e + off_of<DIM>(o, L.pitch, L.plane)];
+    }
+    return acc;
+}
+
+template <int DIM>
+__device__ __forceinline__ float apply_A(const DevLevel<float>& L, long long e)
+{
+    const float* x = L.x;
+    float xi = x[e];
+    if (L.fine) {
+        float lap = (xi - x[e - L.pitch]) + (xi - x[e - 1]) + (xi - x[e + 1]) + (xi - x[e + L.pitch]);
+        if (DIM == 3) lap += (xi - x[e - L.plane]) + (xi - x[e + L.plane]);
+        return fmaf(L.diag[e], xi, L.woff * lap);
+    }
+    constexpr int NS = Offsets<DIM>::NS;
+    constexpr int C = Offsets<DIM>::C;
+    float lap = 0.0f;
+#pragma unroll
+    for (int o = 0; o < NS; ++o) {
+        if (o == C) continue;
+        lap = fmaf(coef_at<DIM>(L, e, o), x[e + off_of<DIM>(o, L.pitch, L.plane)] - xi, lap);
+    }
+    return fmaf(L.coef[e], xi, lap);
+}
+
+// 1D weight of the canonical prolongation for offset p in {-1, 0, 1}
+__device__ __forceinline__ double pw(int p) { return p == 0 ? 1.0 : 0.5; }
+
+}  // namespace mgmc

@@ -1,0 +1,281 @@
+"""Thin ctypes binding of libmgmc.so (include/mgmc.h).
+
+Argument marshalling only: every step of the sampler runs in the CUDA
+kernels of the library.  PyTorch provides device memory (its caching
+allocator is handed to the library as the mgmc_allocator) and streams.
+If the library has not been built, or no CUDA device is present, the calls
+raise -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmgmc.so")
+
+MGMC_FP64 = 0
+MGMC_FP32 = 1
+MGMC_MAX_OBS = 64
+
+STATUS = {0: "MGMC_OK", 1: "MGMC_ERR_ARG", 2: "MGMC_ERR_CUDA", 3: "MGMC_ERR_OOM", 4: "MGMC_ERR_NOT_SPD",
+          5: "MGMC_ERR_TIMEOUT", 6: "MGMC_ERR_STATE", 7: "MGMC_ERR_NUMERIC"}
+
+
+class MGMCError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class mgmc_config(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("n_levels", ctypes.c_int), ("nu1", ctypes.c_int),
+                ("nu2", ctypes.c_int), ("precision", ctypes.c_int), ("scale_hd", ctypes.c_int),
+                ("coarse_max_n", ctypes.c_int)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class mgmc_allocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", ctypes.c_void_p)]
+
+
+class mgmc_stats(ctypes.Structure):
+    _fields_ = [("mean", ctypes.c_double), ("var", ctypes.c_double), ("tau_int", ctypes.c_double),
+                ("tau_err", ctypes.c_double), ("ess", ctypes.c_double), ("window", ctypes.c_int64),
+                ("n_used", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_I32P = ctypes.POINTER(ctypes.c_int32)
+_F64P = ctypes.POINTER(ctypes.c_double)
+_lib = None
+
+# every symbol include/mgmc.h declares
+EXPORTS = ("mgmc_config_default", "mgmc_create", "mgmc_point_obs_rows", "mgmc_sample", "mgmc_mean_solve",
+           "mgmc_qoi_stats", "mgmc_info", "mgmc_level_n", "mgmc_launches_per_cycle", "mgmc_set_profiling",
+           "mgmc_profile_times", "mgmc_destroy", "mgmc_last_error")
+
+
+def load():
+    """Load libmgmc.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2407_12149_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    L.mgmc_last_error.restype = ctypes.c_char_p
+    L.mgmc_config_default.argtypes = [ctypes.POINTER(mgmc_config), ctypes.c_int, ctypes.c_int]
+    L.mgmc_create.argtypes = [ctypes.POINTER(mgmc_config), ctypes.POINTER(mgmc_allocator), ctypes.c_void_p,
+                              _F64P, ctypes.c_double, ctypes.c_int, _I32P, _F64P, ctypes.c_int, _F64P, _F64P,
+                              ctypes.c_int, _I32P, _F64P, ctypes.POINTER(ctypes.c_void_p)]
+    L.mgmc_point_obs_rows.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _F64P, _I32P, _F64P]
+    L.mgmc_sample.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
+                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    L.mgmc_mean_solve.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
+                                  ctypes.POINTER(ctypes.c_int), _F64P, ctypes.c_void_p]
+    L.mgmc_qoi_stats.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
+                                 ctypes.POINTER(mgmc_stats), ctypes.c_void_p]
+    L.mgmc_info.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                            ctypes.POINTER(ctypes.c_int)]
+    L.mgmc_level_n.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    L.mgmc_launches_per_cycle.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]
+    L.mgmc_set_profiling.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    L.mgmc_profile_times.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_int, ctypes.c_void_p]
+    L.mgmc_destroy.argtypes = [ctypes.c_void_p]
+    for name in EXPORTS:
+        if name != "mgmc_last_error":
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(rc: int):
+    if rc != 0:
+        msg = load().mgmc_last_error()
+        raise MGMCError(rc, msg.decode() if msg else "")
+
+
+def _ptr(a, ctype):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+class TorchAllocator:
+    """mgmc_allocator backed by torch's CUDA caching allocator."""
+
+    def __init__(self, device: int = 0):
+        torch = _torch()
+        self.device = device
+
+        def _alloc(nbytes, stream, ctx):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(nbytes), device)
+            except Exception:
+                return None
+
+        def _free(ptr, stream, ctx):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        self._a = ALLOC_FN(_alloc)
+        self._f = FREE_FN(_free)
+        self.struct = mgmc_allocator(self._a, self._f, None)
+
+
+# --------------------------------------------------------------------------
+# functions with the C names
+# --------------------------------------------------------------------------
+
+def mgmc_point_obs_rows(dim: int, n: int, xyz: np.ndarray):
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, dim)
+    m = xyz.shape[0]
+    site = np.empty((m, 1 << dim), dtype=np.int32)
+    w = np.empty((m, 1 << dim), dtype=np.float64)
+    _check(load().mgmc_point_obs_rows(dim, n, m, _ptr(xyz, ctypes.c_double), _ptr(site, ctypes.c_int32),
+                                      _ptr(w, ctypes.c_double)))
+    return site, w
+
+
+def mgmc_create(dim, n, *, n_levels=0, nu1=1, nu2=1, precision=MGMC_FP64, scale_hd=1, coarse_max_n=0,
+                kappa2=None, kappa2_const=10.0, obs_site=None, obs_w=None, Gamma=None, y=None,
+                qoi_site=None, qoi_w=None, allocator: Optional[TorchAllocator] = None, stream=None):
+    L = load()
+    cfg = mgmc_config(dim, n, n_levels, nu1, nu2, precision, scale_hd, coarse_max_n)
+    k2 = None if kappa2 is None else np.ascontiguousarray(kappa2, dtype=np.float64).ravel()
+    if obs_site is None:
+        m, nnz, os_, ow_, G_, y_ = 0, 1, None, None, None, None
+    else:
+        os_ = np.ascontiguousarray(obs_site, dtype=np.int32)
+        ow_ = np.ascontiguousarray(obs_w, dtype=np.float64)
+        m, nnz = os_.shape
+        G_ = np.ascontiguousarray(Gamma, dtype=np.float64)
+        y_ = np.ascontiguousarray(y, dtype=np.float64)
+    if qoi_site is None:
+        nq, qs, qw = 0, None, None
+    else:
+        qs = np.ascontiguousarray(qoi_site, dtype=np.int32)
+        qw = np.ascontiguousarray(qoi_w, dtype=np.float64)
+        nq = qs.size
+    h = ctypes.c_void_p()
+    _check(L.mgmc_create(ctypes.byref(cfg), ctypes.byref(allocator.struct) if allocator else None,
+                         _stream_handle(stream), _ptr(k2, ctypes.c_double), float(kappa2_const), m,
+                         _ptr(os_, ctypes.c_int32), _ptr(ow_, ctypes.c_double), nnz, _ptr(G_, ctypes.c_double),
+                         _ptr(y_, ctypes.c_double), nq, _ptr(qs, ctypes.c_int32), _ptr(qw, ctypes.c_double),
+                         ctypes.byref(h)))
+    return h
+
+
+def mgmc_sample(h, n_steps, seed, step_offset, chain, x_ptr, qoi_ptr, stream=None):
+    _check(load().mgmc_sample(h, int(n_steps), int(seed) & (2**64 - 1), int(step_offset), int(chain),
+                              ctypes.c_void_p(x_ptr), ctypes.c_void_p(qoi_ptr) if qoi_ptr else None,
+                              _stream_handle(stream)))
+
+
+def mgmc_mean_solve(h, rtol, max_cycles, x_ptr, stream=None):
+    c = ctypes.c_int()
+    rr = ctypes.c_double()
+    _check(load().mgmc_mean_solve(h, float(rtol), int(max_cycles), ctypes.c_void_p(x_ptr), ctypes.byref(c),
+                                  ctypes.byref(rr), _stream_handle(stream)))
+    return c.value, rr.value
+
+
+def mgmc_qoi_stats(qoi_ptr, n, burn_in=0, S=1.5, stream=None):
+    out = mgmc_stats()
+    _check(load().mgmc_qoi_stats(ctypes.c_void_p(qoi_ptr), int(n), int(burn_in), float(S), ctypes.byref(out),
+                                 _stream_handle(stream)))
+    return out.as_dict()
+
+
+def mgmc_launches_per_cycle(h):
+    v = ctypes.c_int()
+    _check(load().mgmc_launches_per_cycle(h, ctypes.byref(v)))
+    return v.value
+
+
+def mgmc_set_profiling(h, enable):
+    _check(load().mgmc_set_profiling(h, 1 if enable else 0))
+
+
+def mgmc_profile_times(h, stream=None):
+    ms = (ctypes.c_float * 2)()
+    _check(load().mgmc_profile_times(h, ms, 2, _stream_handle(stream)))
+    return float(ms[0]), float(ms[1])
+
+
+def mgmc_destroy(h):
+    if h:
+        _check(load().mgmc_destroy(h))
+
+
+# --------------------------------------------------------------------------
+# convenience object over one problem
+# --------------------------------------------------------------------------
+
+class Sampler:
+    """MGMC sampler of one posterior problem (paper_2407_12149_gb300.inputs.Problem)."""
+
+    def __init__(self, problem, precision: str = "fp64", nu1: int = 1, nu2: int = 1, coarse_max_n: int = 0,
+                 device: int = 0, use_torch_allocator: bool = True):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise MGMCError(2, "no CUDA device available (the sampler has no CPU fallback)")
+        self.problem = problem
+        self.device = device
+        self.precision = MGMC_FP32 if precision == "fp32" else MGMC_FP64
+        self.dtype = torch.float32 if self.precision == MGMC_FP32 else torch.float64
+        self._alloc = TorchAllocator(device) if use_torch_allocator else None
+        p = problem
+        self.h = mgmc_create(p.dim, p.n, n_levels=p.n_levels, nu1=nu1, nu2=nu2, precision=self.precision,
+                             scale_hd=p.scale_hd, coarse_max_n=coarse_max_n, kappa2=p.kappa2,
+                             kappa2_const=p.kappa2_const, obs_site=p.obs_site, obs_w=p.obs_w, Gamma=p.Gamma,
+                             y=p.y, qoi_site=p.qoi_site, qoi_w=p.qoi_w, allocator=self._alloc)
+
+    def zeros(self):
+        torch = _torch()
+        return torch.zeros(self.problem.N, dtype=self.dtype, device=f"cuda:{self.device}")
+
+    def sample(self, x, n_steps: int, seed: int, step_offset: int = 0, chain: int = 0, qoi=None, stream=None):
+        """Advance x (torch CUDA tensor or pinned/host tensor, modified in place)."""
+        if x.dtype != self.dtype or not x.is_contiguous() or x.numel() != self.problem.N:
+            raise ValueError("x must be a contiguous tensor of N entries in the sampler's precision")
+        if qoi is not None and (qoi.dtype != _torch().float64 or qoi.numel() < n_steps):
+            raise ValueError("qoi must be a float64 tensor with at least n_steps entries")
+        mgmc_sample(self.h, n_steps, seed, step_offset, chain, x.data_ptr(),
+                    qoi.data_ptr() if qoi is not None else None, stream)
+        return x
+
+    def mean_solve(self, x, rtol=1e-10, max_cycles=200, stream=None):
+        return mgmc_mean_solve(self.h, rtol, max_cycles, x.data_ptr(), stream)
+
+    def launches_per_cycle(self):
+        return mgmc_launches_per_cycle(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            mgmc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
