@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 # profiles/fine_sweep_fp32_1023.md; None until captured for the current kernel.
 FINE_SWEEP_TRAFFIC_BYTES = None
 
-TAU_CALIBRATION = 2000     # untimed cycles used for tau_int on the device
+TAU_CALIBRATION = 2000     # default untimed cycles used for tau_int on the device
 CPU_SAMPLE_CYCLES = 12     # bounded oracle sample for the CPU baseline
 REF_MAX_STEPS = 60         # cap on timed oracle cycles in the reference arm
 
@@ -134,6 +134,9 @@ def load_tau_ref():
     return float(d["tau"]), d
 
 
+WORKLOADS = {"bayes2d-1023": 1023, "bayes2d-4095": 4095, "bayes2d-8191": 8191}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -180,7 +183,7 @@ def run_mine(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
-    p = inputs.config2()
+    p = inputs.config2(n=WORKLOADS[args.workload])
     s = M.Sampler(p, precision="fp32", device=local)
     stream = torch.cuda.current_stream()
     chain = rank
@@ -189,15 +192,16 @@ def run_mine(args):
 
     # --- untimed calibration chain: burn-in 100, then tau_int on the device ----
     x = s.zeros()
-    qcal = torch.zeros(TAU_CALIBRATION + 100, dtype=torch.float64, device=dev)
-    s.sample(x, TAU_CALIBRATION + 100, 2024, step_offset=0, chain=chain, qoi=qcal)
-    st = M.mgmc_qoi_stats(qcal.data_ptr(), TAU_CALIBRATION + 100, 100, 1.5)
+    ncal = args.tau_cycles
+    qcal = torch.zeros(ncal + 100, dtype=torch.float64, device=dev)
+    s.sample(x, ncal + 100, 2024, step_offset=0, chain=chain, qoi=qcal)
+    st = M.mgmc_qoi_stats(qcal.data_ptr(), ncal + 100, 100, 1.5)
     tau = st["tau_int"]
-    offset = TAU_CALIBRATION + 100
+    offset = ncal + 100
 
     # --- CPU baseline (rank 0, one GPU only), before the GPU timing ------------
     cpu = None
-    if rank == 0 and ws == 1:
+    if rank == 0 and ws == 1 and args.workload == "bayes2d-1023":
         try:
             tau_ref, _ = load_tau_ref()
             cpu = cpu_baseline(p, tau_ref)
@@ -271,10 +275,10 @@ def run_mine(args):
         "metric": "QoI ESS/s", "value": value, "unit": "QoI ESS/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "bayes-2d-1023: 1023^2, kappa^2 = 10 exp(g), 16 point obs, Gamma = 1e-4 I, "
-                               "10-grid V(1,1)-cycle, low-rank Gibbs smoother, FP32 sweeps / FP64 low-rank",
+        "config": {"workload": f"{p.name}: {p.n}^2, kappa^2 = 10 exp(g), 16 point obs, Gamma = 1e-4 I, "
+                               f"{p.n_levels}-grid V(1,1)-cycle, low-rank Gibbs smoother, FP32 sweeps / FP64 low-rank",
                    "v_cycles_per_s": cps, "tau_int": tau, "tau_err": st["tau_err"],
-                   "tau_from": f"device Wolff estimate on an untimed {TAU_CALIBRATION}-cycle chain",
+                   "tau_from": f"device Wolff estimate on an untimed {ncal}-cycle chain",
                    "l2": "256 MB buffer written between timed steps (inputs are smaller than L2)",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "kernel": "k_sweep_colour (finest grid, forward sweep, both colours)",
@@ -300,9 +304,15 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--workload", default="bayes2d-1023", choices=sorted(WORKLOADS),
+                    help="bayes2d-1023 is the headline workload; the larger grids are HBM-resident variants "
+                         "for the roofline")
+    ap.add_argument("--tau-cycles", type=int, default=TAU_CALIBRATION,
+                    help="length of the untimed chain that estimates tau_int (>= 200)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    args.tau_cycles = max(200, args.tau_cycles)
     if args.impl == "reference":
         run_reference(args)
     else:
