@@ -148,6 +148,26 @@ typedef struct {
 mgmc_status mgmc_qoi_stats(const double* qoi, int64_t n, int64_t burn_in, double S, mgmc_stats* out,
                            void* stream);
 
+/* Longest series (n - burn_in) mgmc_qoi_stats_noalloc accepts. */
+#define MGMC_NOALLOC_MAX_SERIES 65536
+
+/* The same statistics as mgmc_qoi_stats for callers that cannot allocate
+ * device memory while they run: for example a process whose device memory
+ * is held entirely by another framework's pool, or a latency-critical
+ * monitoring loop that must not wait on an allocator.  The paper has no
+ * counterpart; this is a library convenience.
+ * Scratch lives in one fixed device array of about 264 KB inside the library
+ * (every GPU that loads the library keeps it until the process exits); no
+ * allocation or free of any kind is made.  All lags t <= (n - burn_in)/2 are
+ * evaluated in one pass, so n - burn_in may be at most
+ * MGMC_NOALLOC_MAX_SERIES (else MGMC_ERR_ARG).  The first call on a device
+ * looks up the scratch address for that device; make that first call before
+ * any stream capture.  All calls share the one scratch array: calls that may
+ * overlap on the GPU (other streams, other threads) race and must be
+ * serialised by the caller.  Synchronous on the stream. */
+mgmc_status mgmc_qoi_stats_noalloc(const double* qoi, int64_t n, int64_t burn_in, double S, mgmc_stats* out,
+                                   void* stream);
+
 /* Number of grids, unknowns per axis of grid l (0 = coarsest) and the
  * precision of a handle. */
 mgmc_status mgmc_info(mgmc_handle h, int* n_levels, int* precision, int* dim);

@@ -68,6 +68,11 @@ struct Buffers {
 
 }  // namespace
 
+namespace mgmc {
+// message for mgmc_last_error() from entry points defined in other files
+void set_last_error(const char* msg) { g_last_error = msg; }
+}  // namespace mgmc
+
 struct mgmc_ctx {
     mgmc_config cfg{};
     int L = 0;            // number of levels

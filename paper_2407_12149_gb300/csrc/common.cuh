@@ -17,6 +17,9 @@ namespace mgmc {
 
 constexpr int kMaxObs = MGMC_MAX_OBS;
 
+// sets the message returned by mgmc_last_error() on this thread
+void set_last_error(const char* msg);
+
 // Per-cycle values read by the kernels of a captured cycle graph.
 struct CycleState {
     unsigned long long seed;

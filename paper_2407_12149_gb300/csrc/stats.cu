@@ -7,6 +7,7 @@
 // reported in the paper's convention tau = 2 tau_W, error 2 * 2 tau_W sqrt((W + 1/2 - tau_W)/n).
 // Lags are evaluated in chunks of kLagChunk until the window is found.
 #include <cmath>
+#include <mutex>
 #include <string>
 
 #include "common.cuh"
@@ -158,4 +159,79 @@ extern "C" mgmc_status mgmc_qoi_stats(const double* qoi, int64_t n, int64_t burn
     cudaFreeAsync(dout, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) rc = MGMC_ERR_CUDA;
     return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant: the scratch (Wolff state, all lags, result) lives
+// in one file-scope device array.  In host code the symbol names only a
+// host-side stand-in, so its device address is looked up per device with
+// cudaGetSymbolAddress and passed to the kernels.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr long long kNoallocMaxLags = MGMC_NOALLOC_MAX_SERIES / 2;
+constexpr size_t kNoallocBytes = 256 + sizeof(double) * (kNoallocMaxLags + 1) + 256;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// device address of the scratch on the current device (looked up once per device)
+cudaError_t noalloc_scratch(void** ptr)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = p;
+    }
+    *ptr = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" mgmc_status mgmc_qoi_stats_noalloc(const double* qoi, int64_t n, int64_t burn_in, double S,
+                                               mgmc_stats* out, void* stream)
+{
+    if (!qoi || !out || burn_in < 0 || n - burn_in < 2) {
+        mgmc::set_last_error("mgmc_qoi_stats_noalloc: need qoi, out and n - burn_in >= 2");
+        return MGMC_ERR_ARG;
+    }
+    if (n - burn_in > MGMC_NOALLOC_MAX_SERIES) {
+        mgmc::set_last_error("mgmc_qoi_stats_noalloc: n - burn_in exceeds MGMC_NOALLOC_MAX_SERIES (65536); "
+                             "use mgmc_qoi_stats for longer series");
+        return MGMC_ERR_ARG;
+    }
+    if (!(S > 0.0)) S = 1.5;
+    cudaStream_t s = (cudaStream_t)stream;
+    void* base = nullptr;
+    if (noalloc_scratch(&base) != cudaSuccess) {
+        mgmc::set_last_error("mgmc_qoi_stats_noalloc: cudaGetSymbolAddress of the scratch array failed");
+        return MGMC_ERR_CUDA;
+    }
+    WolffState* st = (WolffState*)base;
+    double* G = (double*)((unsigned char*)base + 256);
+    mgmc_stats* dout = (mgmc_stats*)((unsigned char*)base + 256 + sizeof(double) * (kNoallocMaxLags + 1));
+    const double* a = qoi + burn_in;
+    long long nn = n - burn_in;
+    long long tmax = nn / 2;
+    // every scratch word read below is written first in the same call
+    k_stats_init<<<1, kThreads, 0, s>>>(a, nn, st);
+    if (tmax >= 1) {
+        k_autocov<<<(unsigned)tmax, kThreads, 0, s>>>(a, nn, st, 1, tmax + 1, G);
+        k_wolff_scan<<<1, 1, 0, s>>>(G, 1, tmax + 1, tmax, nn, S, st);
+    }
+    k_stats_final<<<1, 1, 0, s>>>(st, nn, dout);
+    if (cudaGetLastError() != cudaSuccess) return MGMC_ERR_CUDA;
+    if (cudaMemcpyAsync(out, dout, sizeof(mgmc_stats), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MGMC_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return MGMC_ERR_CUDA;
+    return MGMC_OK;
 }

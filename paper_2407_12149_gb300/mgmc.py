@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(HERE, "libmgmc.so")
 MGMC_FP64 = 0
 MGMC_FP32 = 1
 MGMC_MAX_OBS = 64
+MGMC_NOALLOC_MAX_SERIES = 65536
 
 STATUS = {0: "MGMC_OK", 1: "MGMC_ERR_ARG", 2: "MGMC_ERR_CUDA", 3: "MGMC_ERR_OOM", 4: "MGMC_ERR_NOT_SPD",
           5: "MGMC_ERR_TIMEOUT", 6: "MGMC_ERR_STATE", 7: "MGMC_ERR_NUMERIC"}
@@ -60,7 +61,7 @@ _lib = None
 
 # every symbol include/mgmc.h declares
 EXPORTS = ("mgmc_config_default", "mgmc_create", "mgmc_point_obs_rows", "mgmc_sample", "mgmc_mean_solve",
-           "mgmc_qoi_stats", "mgmc_info", "mgmc_level_n", "mgmc_launches_per_cycle", "mgmc_set_profiling",
+           "mgmc_qoi_stats", "mgmc_qoi_stats_noalloc", "mgmc_info", "mgmc_level_n", "mgmc_launches_per_cycle", "mgmc_set_profiling",
            "mgmc_profile_times", "mgmc_destroy", "mgmc_last_error")
 
 
@@ -84,6 +85,8 @@ def load():
                                   ctypes.POINTER(ctypes.c_int), _F64P, ctypes.c_void_p]
     L.mgmc_qoi_stats.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
                                  ctypes.POINTER(mgmc_stats), ctypes.c_void_p]
+    L.mgmc_qoi_stats_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
+                                         ctypes.POINTER(mgmc_stats), ctypes.c_void_p]
     L.mgmc_info.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                             ctypes.POINTER(ctypes.c_int)]
     L.mgmc_level_n.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
@@ -202,6 +205,14 @@ def mgmc_qoi_stats(qoi_ptr, n, burn_in=0, S=1.5, stream=None):
     out = mgmc_stats()
     _check(load().mgmc_qoi_stats(ctypes.c_void_p(qoi_ptr), int(n), int(burn_in), float(S), ctypes.byref(out),
                                  _stream_handle(stream)))
+    return out.as_dict()
+
+
+def mgmc_qoi_stats_noalloc(qoi_ptr, n, burn_in=0, S=1.5, stream=None):
+    """mgmc_qoi_stats without any device allocation (fixed library scratch)."""
+    out = mgmc_stats()
+    _check(load().mgmc_qoi_stats_noalloc(ctypes.c_void_p(qoi_ptr), int(n), int(burn_in), float(S),
+                                         ctypes.byref(out), _stream_handle(stream)))
     return out.as_dict()
 
 
