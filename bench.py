@@ -27,9 +27,9 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# DRAM bytes (read + write) per launch of the timed forward sweep of the
-# finest grid, from the ncu capture summarised in
-# profiles/fine_sweep_fp32_1023.md; None until captured for the current kernel.
+# DRAM bytes (read + write) per launch of the fused forward tile kernel on the
+# finest grid (k_tile_fwd<float, 1>), from the ncu capture summarised in
+# profiles/k_tile_fwd_fp32.md; None until captured for the current kernel.
 FINE_SWEEP_TRAFFIC_BYTES = None
 
 TAU_CALIBRATION = 2000     # default untimed cycles used for tau_int on the device
@@ -268,7 +268,10 @@ def run_mine(args):
             dist.destroy_process_group()
         return
     peak, peak_kind = measured_peak()
-    sweep_bytes = 12 * N     # read x + read s*kappa^2 + write x, FP32, per forward sweep of the finest grid
+    # algorithmic bytes of one fused forward launch on the finest grid, FP32: read theta and
+    # s*kappa^2 (4 + 4 B/site), write theta*_s (4 B/site) and the restricted residual (4 B per
+    # coarse site = 1 B per fine site); the noise is generated, never stored
+    sweep_bytes = 13 * N
     fwd_avg = statistics.mean(fwd_ms)
     achieved = sweep_bytes / (fwd_avg * 1e-3) / 1e9
     line = {
@@ -281,7 +284,8 @@ def run_mine(args):
                    "tau_from": f"device Wolff estimate on an untimed {ncal}-cycle chain",
                    "l2": "256 MB buffer written between timed steps (inputs are smaller than L2)",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "kernel": "k_sweep_colour (finest grid, forward sweep, both colours)",
+        "roofline": {"bound": "hbm",
+                     "kernel": "k_tile_fwd<float,1>: finest-grid forward Gibbs sweep + residual + restriction",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": f"{peak_kind} HBM copy bandwidth",
                      "traffic": FINE_SWEEP_TRAFFIC_BYTES,

@@ -10,6 +10,7 @@
 #include "common.cuh"
 #include "kernels.cuh"
 #include "setup.hpp"
+#include "tile2d.cuh"
 
 using namespace mgmc;
 
@@ -99,6 +100,8 @@ struct mgmc_ctx {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t exec = nullptr;
     int launches = 0;
+    size_t coarse_smem = 0;   // dynamic shared memory of the coarse-grid kernel
+    bool fused = false;   // 2D, nu1 = nu2 = 1: fused tile kernels on the grids above coarse_max_n
     bool profile = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     bool fp32() const { return cfg.precision == MGMC_FP32; }
@@ -228,6 +231,99 @@ mgmc_status build_device_levels(mgmc_ctx* h, const HostProblem& hp)
         if (st != MGMC_OK) return fail(st, "device upload failed");
     }
     for (int l = 1; l < hp.n_levels; ++l) levels[l].dnext = levels[l - 1].d;
+    // G in the path precision and B^T G for every grid with a smoother
+    for (int l = 1; l < hp.n_levels && hp.m > 0; ++l) {
+        DevLevel<T>& D = levels[l];
+        HostLevel& HL = const_cast<HostLevel&>(hp.lev[l]);
+        for (int dir = 0; dir < 2; ++dir) {
+            std::vector<T> gt(HL.gval[dir].begin(), HL.gval[dir].end());
+            D.gT[dir] = upload(h, gt, st);
+        }
+        fused_extras(HL, hp, l);
+        D.BtG = upload(h, HL.BtG, st);
+        if (st != MGMC_OK) return fail(st, "device upload failed");
+    }
+    // grids inside the coarse kernel: shared-memory indices of the observation and G sites
+    for (int l = 0; l <= h->top && hp.m > 0; ++l) {
+        const HostLevel& HL = hp.lev[l];
+        DevLevel<T>& D = levels[l];
+        const int S = HL.n + 2;
+        auto sidx = [&](long long s) {
+            int i = (int)(s % HL.n), j = (int)((s / HL.n) % HL.n), k = d == 3 ? (int)(s / ((long long)HL.n * HL.n)) : 0;
+            return d == 3 ? ((k + 1) * S + (j + 1)) * S + (i + 1) : (j + 1) * S + (i + 1);
+        };
+        std::vector<int> bss, bdense;
+        for (long long s : HL.bsite) {
+            bss.push_back(sidx(s));
+            bdense.push_back((int)s);
+        }
+        D.bcol_ss = upload(h, bss, st);
+        D.bcol_dense = upload(h, bdense, st);
+        for (int dir = 0; dir < 2; ++dir) {
+            std::vector<int> gss;
+            for (long long s : HL.gsite[dir]) gss.push_back(sidx(s));
+            D.g_ss[dir] = upload(h, gss, st);
+        }
+        if (st != MGMC_OK) return fail(st, "device upload failed");
+    }
+    {
+        std::vector<int> nl;
+        for (int l = 0; l < hp.n_levels; ++l) nl.push_back(hp.lev[l].n);
+        h->coarse_smem = (size_t)coarse_smem_elems(d, nl.data(), h->top, h->top == hp.n_levels - 1) * sizeof(T);
+        cudaError_t e = coarse_prepare<T>(d, h->coarse_smem);
+        if (e != cudaSuccess)
+            return fail(MGMC_ERR_CUDA, std::string("coarse kernel set-up: ") + cudaGetErrorString(e));
+    }
+    // fused tile path: second state buffer, per-tile observation entries, G/H in T, B^T G
+    if (h->fused) {
+        for (int l = h->top + 1; l < hp.n_levels; ++l) {
+            HostLevel& HL = const_cast<HostLevel&>(hp.lev[l]);
+            DevLevel<T>& D = levels[l];
+            const DevLevel<T>& Cd = levels[l - 1];
+            size_t fbytes = (size_t)D.alloc * sizeof(T);
+            D.x2 = (T*)h->buf.get(fbytes);
+            if (!D.x2) return fail(MGMC_ERR_OOM, "allocator returned NULL");
+            CUDA_TRY(cudaMemsetAsync(D.x2, 0, fbytes, h->buf.stream));
+            const int TX = D.fine ? TileShape<T, true>::TX : TileShape<T, false>::TX;
+            const int TY = D.fine ? TileShape<T, true>::TY : TileShape<T, false>::TY;
+            D.ntx = (HL.n + TX - 1) / TX;
+            const int nty = (HL.n + TY - 1) / TY;
+            if (hp.m == 0) continue;
+            const int ntiles = D.ntx * nty;
+            std::vector<std::vector<std::pair<int, int>>> per((size_t)ntiles);
+            for (size_t t = 0; t < HL.bsite.size(); ++t) {
+                long long s = HL.bsite[t];
+                int i = (int)(s % HL.n), j = (int)(s / HL.n);
+                int tile = (j / TY) * D.ntx + (i / TX);
+                per[(size_t)tile].push_back({(i % TX) | ((j % TY) << 16), (int)t});
+            }
+            std::vector<int> tptr((size_t)ntiles + 1, 0), tloc, tent;
+            for (int t = 0; t < ntiles; ++t) {
+                for (auto& e : per[(size_t)t]) {
+                    tloc.push_back(e.first);
+                    tent.push_back(e.second);
+                }
+                tptr[(size_t)t + 1] = (int)tloc.size();
+            }
+            D.tile_ptr = upload(h, tptr, st);
+            D.tile_loc = upload(h, tloc, st);
+            D.tile_ent = upload(h, tent, st);
+            D.zparts = upload(h, std::vector<double>(HL.bsite.size(), 0.0), st);
+            const HostLevel& HC = hp.lev[l - 1];
+            std::vector<long long> hs;
+            for (long long s : HL.hsite) {
+                int i = (int)(s % HC.n), j = (int)(s / HC.n);
+                hs.push_back(site_offset(d, Cd.pitch, Cd.plane, Cd.base, i, j, 0));
+            }
+            D.h_rows = (int)hs.size();
+            D.h_site = upload(h, hs, st);
+            std::vector<T> ht(HL.hval.begin(), HL.hval.end());
+            D.hT = upload(h, ht, st);
+            if (st != MGMC_OK) return fail(st, "device upload failed");
+        }
+        cudaError_t e = tile_prepare<T>();
+        if (e != cudaSuccess) return fail(MGMC_ERR_CUDA, std::string("tile kernel set-up: ") + cudaGetErrorString(e));
+    }
     // descriptors of the levels handled by the single-CTA kernel
     size_t dbytes = sizeof(DevLevel<T>) * (size_t)(h->top + 1);
     h->levels_dev = h->buf.get(dbytes);
@@ -237,8 +333,36 @@ mgmc_status build_device_levels(mgmc_ctx* h, const HostProblem& hp)
 }
 
 template <typename T>
+void enqueue_cycle_fused(mgmc_ctx* h, cudaStream_t s, int& launches)
+{
+    auto& lv = levels_of<T>(h);
+    const int Lf = h->L - 1;
+    const DevProblem& P = h->P;
+    const bool prof = h->profile && h->top < Lf;
+    for (int l = Lf; l > h->top; --l) {
+        if (prof && l == Lf) cudaEventRecordWithFlags(h->ev[0], s, cudaEventRecordExternal);
+        launch_tile_fwd<T>(lv[l], lv[l - 1], P, l < Lf, s, launches);
+        if (prof && l == Lf) cudaEventRecordWithFlags(h->ev[1], s, cudaEventRecordExternal);
+        launch_lowrank_fused<T>(lv[l], lv[l - 1], P, true, s, launches);
+    }
+    launch_coarse<T>((const DevLevel<T>*)h->levels_dev, h->cfg.dim, h->top, h->top == Lf, P, h->chol, h->n0,
+                     h->cfg.nu1, h->cfg.nu2, h->coarse_smem, s, launches);
+    for (int l = h->top + 1; l <= Lf; ++l) {
+        if (prof && l == Lf) cudaEventRecordWithFlags(h->ev[2], s, cudaEventRecordExternal);
+        launch_tile_bwd<T>(lv[l], lv[l - 1], P, s, launches);
+        if (prof && l == Lf) cudaEventRecordWithFlags(h->ev[3], s, cudaEventRecordExternal);
+        launch_lowrank_fused<T>(lv[l], lv[l - 1], P, false, s, launches);
+    }
+    launch_qoi<T>(lv[Lf], h->n_qoi, h->q_site, h->q_w, P, s, launches);
+}
+
+template <typename T>
 void enqueue_cycle(mgmc_ctx* h, cudaStream_t s, int& launches)
 {
+    if (h->fused) {
+        enqueue_cycle_fused<T>(h, s, launches);
+        return;
+    }
     auto& lv = levels_of<T>(h);
     const int Lf = h->L - 1;
     const DevProblem& P = h->P;
@@ -256,7 +380,7 @@ void enqueue_cycle(mgmc_ctx* h, cudaStream_t s, int& launches)
         launch_restrict<T>(D, lv[l - 1], s, launches);
     }
     launch_coarse<T>((const DevLevel<T>*)h->levels_dev, h->cfg.dim, h->top, h->top == Lf, P, h->chol, h->n0,
-                     h->cfg.nu1, h->cfg.nu2, s, launches);
+                     h->cfg.nu1, h->cfg.nu2, h->coarse_smem, s, launches);
     for (int l = h->top + 1; l <= Lf; ++l) {
         const DevLevel<T>& D = lv[l];
         launch_prolong<T>(lv[l - 1], D, s, launches);
@@ -422,12 +546,23 @@ mgmc_status mgmc_create(const mgmc_config* cfg_in, const mgmc_allocator* alloc, 
         h->buf.alloc = *alloc;
         h->buf.use_cuda_malloc = false;
     }
+    // grids inside the single-CTA coarse kernel: n <= coarse_max_n, and the state and
+    // right-hand side of all of them must fit in shared memory
     int cmax = cfg.coarse_max_n > 0 ? cfg.coarse_max_n : (cfg.dim == 2 ? 63 : 15);
     h->top = 0;
-    for (int l = 0; l < h->L; ++l)
-        if (hp.lev[l].n <= cmax) h->top = l;
+    {
+        const size_t esz = cfg.precision == MGMC_FP32 ? 4 : 8;
+        const size_t budget = 200 * 1024;
+        std::vector<int> nl;
+        for (int l = 0; l < h->L; ++l) nl.push_back(hp.lev[l].n);
+        for (int l = 0; l < h->L && l < 16; ++l) {
+            size_t bytes = (size_t)coarse_smem_elems(cfg.dim, nl.data(), l, l == h->L - 1) * esz;
+            if (hp.lev[l].n <= cmax && bytes + 16384 <= budget) h->top = l;
+        }
+    }
     h->n0 = hp.n0;
     h->f_norm = hp.f_norm;
+    h->fused = cfg.dim == 2 && cfg.nu1 == 1 && cfg.nu2 == 1;
     auto cleanup = [&](mgmc_status s) {
         h->buf.release();
         delete h;

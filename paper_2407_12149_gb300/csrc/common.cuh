@@ -61,6 +61,9 @@ struct DevLevel {
     const int* bcol_ptr;          // [m + 1]
     const long long* bcol_site;   // padded element offset
     const double* bcol_w;
+    const int* bcol_ss;           // grids inside the coarse kernel: shared-memory index of the site
+    const int* bcol_dense;        // coarsest grid: dense site index
+    const int* g_ss[2];           // grids inside the coarse kernel: shared-memory index of G's sites
     // G_l on its support, per direction (0 forward, 1 backward)
     int g_rows[2];
     const long long* g_site[2];   // padded element offsets
@@ -68,6 +71,25 @@ struct DevLevel {
     // the level's right-hand side is f_l = fdense_l + B_l Gamma^-1 d_l
     double* d;                    // [m] data vector d_l (d_L = y)
     double* dnext;                // [m] d_{l-1} = d_l - B_l^T theta, written on the way down
+    // fused 2D tile path (see tile2d.cu)
+    T* x2;                        // second state buffer: theta*_s after the forward sweep
+    int ntx;                      // tiles per row
+    const int* tile_ptr;          // [ntiles + 1]: B entries inside each tile
+    const int* tile_loc;          // local site of the entry, lx | ly << 16, relative to the tile origin
+    const int* tile_ent;          // index t of the entry in the column lists bcol_*
+    double* zparts;               // [nnz] w_t * theta(site_t), written by the tile kernels
+    const T* gT[2];               // G_l(dir) in the path precision, [rows * m]
+    int h_rows;                   // H = P^T A_l G_l(forward) on the coarse grid
+    const long long* h_site;      // coarse padded offsets
+    const T* hT;                  // [rows * m]
+    const double* BtG;            // B_l^T G_l(forward), [m * m]
+};
+
+// Tile shape of the fused 2D kernels: TX x TY interior sites per CTA.
+template <typename T, bool FINE>
+struct TileShape {
+    static constexpr int TX = FINE ? 64 : 32;
+    static constexpr int TY = sizeof(T) == 4 ? 32 : 16;
 };
 
 struct DevProblem {
@@ -131,16 +153,20 @@ __device__ __forceinline__ void normal_pair(const uint4 w, double& z0, double& z
 }
 
 // The same draws in FP32: u is the FP32 rounding of (k + 1/2) 2^-53, formed from
-// the two 32-bit halves so that the full 53-bit value is used.
+// the two 32-bit halves so that the full 53-bit value is used.  The angle is
+// reduced to phi = 2 pi (u2 - 1/2) in (-pi, pi], where the hardware sine/cosine
+// is accurate to ~4e-7 absolute; cos(2 pi u2) = -cos(phi), sin(2 pi u2) = -sin(phi).
+// The logarithm keeps full single precision: near u1 = 1 the radius is small
+// and an absolute-error logarithm would be too coarse.
 __device__ __forceinline__ void normal_pair(const uint4 w, float& z0, float& z1)
 {
     float u1 = fmaf((float)w.x, 0x1p-32f, fmaf((float)(w.y & 0xFFFFF800u), 0x1p-64f, 0x1p-54f));
     float u2 = fmaf((float)w.z, 0x1p-32f, fmaf((float)(w.w & 0xFFFFF800u), 0x1p-64f, 0x1p-54f));
     float r = sqrtf(-2.0f * logf(u1));
     float s, c;
-    sincospif(2.0f * u2, &s, &c);
-    z0 = r * c;
-    z1 = r * s;
+    __sincosf(6.28318530717958648f * (u2 - 0.5f), &s, &c);
+    z0 = -r * c;
+    z1 = -r * s;
 }
 
 template <typename T>
@@ -152,12 +178,23 @@ __device__ __forceinline__ void draw_pair(const CycleState& cs, unsigned pair, u
     normal_pair(w, z0, z1);
 }
 
-// One standard normal of the low-rank noise z'_k (kind 1).
+// One standard normal of the low-rank noise z'_k (kind 1), evaluated in the
+// path precision T (the same draw in both precisions).
+template <typename T = double>
 __device__ __forceinline__ double lowrank_normal(const CycleState& cs, int level, unsigned slot, int k)
 {
-    double z0, z1;
-    draw_pair<double>(cs, (unsigned)(k >> 1), 1u, level, slot, z0, z1);
-    return (k & 1) ? z1 : z0;
+    T z0, z1;
+    draw_pair<T>(cs, (unsigned)(k >> 1), 1u, level, slot, z0, z1);
+    return (double)((k & 1) ? z1 : z0);
+}
+
+// 1/a and sqrt(a) of a positive FP32 diagonal from one reciprocal square root
+// (relative error ~2e-7, below the FP32 rounding of the state update)
+__device__ __forceinline__ void inv_and_sqrt(float a, float& inv, float& sq)
+{
+    float r = rsqrtf(a);
+    inv = r * r;
+    sq = a * r;
 }
 
 }  // namespace mgmc

@@ -5,7 +5,7 @@
 //   k_lowrank                              : theta' = theta* - G (B^T theta*) (Eq. low_rank_update)
 //   k_restrict                             : f_{l-1} = P^T (f_l - A_l theta') and
 //                                            g_{l-1} = g_l - Gamma^-1 B^T theta'
-// the grids with n <= coarse_max_n run as one k_coarse_cycle (single CTA),
+// the grids with n <= coarse_max_n run as one k_coarse_cycle (coarse.cu),
 // which ends in the exact coarsest Cholesky sample (Sec. 2.5), and back up:
 //   k_prolong                              : theta += P psi_{l-1}
 //   k_sweep_colour  (reverse colours), k_lowrank (backward G)
@@ -88,26 +88,8 @@ __global__ void k_sweep_colour(DevLevel<T> L, DevProblem P, int redblack, int co
 }
 
 // ---------------------------------------------------------------------------
-// CTA-wide pieces (used by the single-CTA kernels)
+// CTA-wide low-rank step (single-CTA kernel of the unfused path)
 // ---------------------------------------------------------------------------
-template <typename T, int DIM>
-__device__ void cta_sweep(const DevLevel<T>& L, const DevProblem& P, const CycleState& cs, int dir, unsigned slot)
-{
-    // 2^d parity colours in the reading's order; the red-black groups of the
-    // 5/7-point level are unions of these classes, so the result is identical
-    const int seq2[4] = {0, 3, 2, 1};
-    const int seq3[8] = {0, 6, 5, 3, 4, 2, 1, 7};
-    const int nc = DIM == 2 ? 4 : 8;
-    int nq = (L.n + 3) >> 2;
-    for (int ci = 0; ci < nc; ++ci) {
-        int c = DIM == 2 ? seq2[dir == 0 ? ci : nc - 1 - ci] : seq3[dir == 0 ? ci : nc - 1 - ci];
-        int py = (c >> 1) & 1, pz = (c >> 2) & 1;
-        long long items = (long long)nq * ((L.n - py + 1) >> 1) * (DIM == 3 ? ((L.n - pz + 1) >> 1) : 1);
-        for (long long it = threadIdx.x; it < items; it += blockDim.x) sweep_item<T, DIM>(L, P, cs, false, c, slot, it);
-        __syncthreads();
-    }
-}
-
 // theta' = theta*_s - G (B^T theta*_s - d - L_Gamma z') (skipped for dir < 0);
 // with want_dnext also d_{l-1} = d_l - B_l^T theta'
 template <typename T>
@@ -122,7 +104,7 @@ __device__ void cta_lowrank(const DevLevel<T>& L, const DevProblem& P, const Cyc
         double acc = 0.0;
         for (int t = L.bcol_ptr[k]; t < L.bcol_ptr[k + 1]; ++t) acc += L.bcol_w[t] * (double)L.x[L.bcol_site[t]];
         z[k] = acc;
-        zp[k] = (dir >= 0 && cs.noise) ? lowrank_normal(cs, L.level, slot, k) : 0.0;
+        zp[k] = (dir >= 0 && cs.noise) ? lowrank_normal<T>(cs, L.level, slot, k) : 0.0;
     }
     __syncthreads();
     if (dir >= 0) {
@@ -218,108 +200,6 @@ __device__ __forceinline__ T prolong_site(const DevLevel<T>& C, int fi, int fj, 
     return acc;
 }
 
-template <typename T, int DIM>
-__device__ void cta_restrict(const DevLevel<T>& F, const DevLevel<T>& C)
-{
-    long long N = (long long)C.n * C.n * (DIM == 3 ? C.n : 1);
-    for (long long s = threadIdx.x; s < N; s += blockDim.x) {
-        int I = (int)(s % C.n), J = (int)((s / C.n) % C.n), K = DIM == 3 ? (int)(s / ((long long)C.n * C.n)) : 0;
-        C.f[site_offset(DIM, C.pitch, C.plane, C.base, I, J, K)] = restrict_site<T, DIM>(F, C, I, J, K);
-    }
-    __syncthreads();
-}
-
-template <typename T, int DIM>
-__device__ void cta_prolong(const DevLevel<T>& C, const DevLevel<T>& F)
-{
-    long long N = (long long)F.n * F.n * (DIM == 3 ? F.n : 1);
-    for (long long s = threadIdx.x; s < N; s += blockDim.x) {
-        int i = (int)(s % F.n), j = (int)((s / F.n) % F.n), k = DIM == 3 ? (int)(s / ((long long)F.n * F.n)) : 0;
-        long long e = site_offset(DIM, F.pitch, F.plane, F.base, i, j, k);
-        F.x[e] = F.x[e] + prolong_site<T, DIM>(C, i, j, k);
-    }
-    __syncthreads();
-}
-
-template <typename T, int DIM>
-__device__ void cta_zero(const DevLevel<T>& L)
-{
-    long long N = (long long)L.n * L.n * (DIM == 3 ? L.n : 1);
-    for (long long s = threadIdx.x; s < N; s += blockDim.x) {
-        int i = (int)(s % L.n), j = (int)((s / L.n) % L.n), k = DIM == 3 ? (int)(s / ((long long)L.n * L.n)) : 0;
-        L.x[site_offset(DIM, L.pitch, L.plane, L.base, i, j, k)] = T(0);
-    }
-    __syncthreads();
-}
-
-// Exact sample theta_0 = A~_0^-1 f_0 + L_0^-T z on the coarsest grid (Sec. 2.5),
-// f_0 = fdense_0 + B_0 g_0, A~_0 = L_0 L_0^T factored in FP64 at set-up.
-template <typename T, int DIM>
-__device__ void cta_coarsest(const DevLevel<T>& L, const DevProblem& P, const CycleState& cs, const double* chol,
-                             int n0)
-{
-    __shared__ double r[MGMC_MAX_COARSEST];
-    const int n = L.n;
-    for (int s = threadIdx.x; s < n0; s += blockDim.x) {
-        int i = s % n, j = (s / n) % n, k = DIM == 3 ? s / (n * n) : 0;
-        r[s] = L.f ? (double)L.f[site_offset(DIM, L.pitch, L.plane, L.base, i, j, k)] : 0.0;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int kk = 0; kk < P.m; ++kk) {
-            double gk = 0.0;   // (Gamma^-1 d_0)_kk
-            for (int t = 0; t < P.m; ++t) gk += P.Gamma_inv[kk * P.m + t] * L.d[t];
-            for (int t = L.bcol_ptr[kk]; t < L.bcol_ptr[kk + 1]; ++t) {
-                long long e = L.bcol_site[t] - L.base;   // dense index of a coarsest site
-                int i = (int)(e % L.pitch);
-                long long rest = e / L.pitch;
-                int j, k;
-                if (DIM == 3) {
-                    // e = i + pitch j + plane k with plane = pitch (n + 2)
-                    long long pj = L.plane / L.pitch;
-                    j = (int)(rest % pj);
-                    k = (int)(rest / pj);
-                } else {
-                    j = (int)rest;
-                    k = 0;
-                }
-                r[i + n * (j + n * k)] += L.bcol_w[t] * gk;
-            }
-        }
-    }
-    __syncthreads();
-    // forward substitution L y = r, one column at a time
-    for (int i = 0; i < n0; ++i) {
-        if (threadIdx.x == 0) r[i] = r[i] / chol[(long long)i * n0 + i];
-        __syncthreads();
-        double yi = r[i];
-        for (int t = i + 1 + threadIdx.x; t < n0; t += blockDim.x) r[t] -= chol[(long long)t * n0 + i] * yi;
-        __syncthreads();
-    }
-    // y += z
-    if (cs.noise) {
-        for (int s = threadIdx.x; s < n0; s += blockDim.x) {
-            double z0, z1;
-            draw_pair<double>(cs, (unsigned)(s >> 1), 2u, 0, 0u, z0, z1);
-            r[s] += (s & 1) ? z1 : z0;
-        }
-    }
-    __syncthreads();
-    // back substitution L^T x = y (row i of L^T is column i of L)
-    for (int i = n0 - 1; i >= 0; --i) {
-        if (threadIdx.x == 0) r[i] = r[i] / chol[(long long)i * n0 + i];
-        __syncthreads();
-        double xi = r[i];
-        for (int t = threadIdx.x; t < i; t += blockDim.x) r[t] -= chol[(long long)i * n0 + t] * xi;
-        __syncthreads();
-    }
-    for (int s = threadIdx.x; s < n0; s += blockDim.x) {
-        int i = s % n, j = (s / n) % n, k = DIM == 3 ? s / (n * n) : 0;
-        L.x[site_offset(DIM, L.pitch, L.plane, L.base, i, j, k)] = (T)r[s];
-    }
-    __syncthreads();
-}
-
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
@@ -353,34 +233,6 @@ __global__ void k_prolong(DevLevel<T> C, DevLevel<T> F)
 
 // The whole V-cycle below (and including) level `top`, one CTA.
 // levels[0..top] are the device descriptors, index = paper level.
-constexpr int kCoarseThreads = 512;
-
-template <typename T, int DIM>
-__global__ void __launch_bounds__(kCoarseThreads) k_coarse_cycle(const DevLevel<T>* __restrict__ levels, int top, int is_finest, DevProblem P,
-                               const double* chol, int n0, int nu1, int nu2)
-{
-    const CycleState cs = *P.cs;
-    for (int l = top; l >= 1; --l) {
-        const DevLevel<T> L = levels[l];
-        if (!(l == top && is_finest)) cta_zero<T, DIM>(L);
-        for (int s = 0; s < nu1; ++s) {
-            cta_sweep<T, DIM>(L, P, cs, 0, (unsigned)(2 * s));
-            cta_lowrank<T>(L, P, cs, 0, (unsigned)(2 * s), s == nu1 - 1);
-        }
-        if (nu1 == 0) cta_lowrank<T>(L, P, cs, -1, 0u, true);   // d_{l-1} = d_l - B^T theta
-        cta_restrict<T, DIM>(L, levels[l - 1]);
-    }
-    cta_coarsest<T, DIM>(levels[0], P, cs, chol, n0);
-    for (int l = 1; l <= top; ++l) {
-        const DevLevel<T> L = levels[l];
-        cta_prolong<T, DIM>(levels[l - 1], L);
-        for (int s = 0; s < nu2; ++s) {
-            cta_sweep<T, DIM>(L, P, cs, 1, (unsigned)(2 * s + 1));
-            cta_lowrank<T>(L, P, cs, 1, (unsigned)(2 * s + 1), false);
-        }
-    }
-}
-
 // F^T theta of the finest level into qoi[step]; then step += 1, cycle += 1.
 template <typename T>
 __global__ void k_qoi_advance(DevLevel<T> L, int n_qoi, const long long* q_site, const double* q_w, DevProblem P)
@@ -567,17 +419,6 @@ void launch_prolong(const DevLevel<T>& C, const DevLevel<T>& F, cudaStream_t st,
 }
 
 template <typename T>
-void launch_coarse(const DevLevel<T>* levels_dev, int dim, int top, bool is_finest, const DevProblem& P,
-                   const double* chol, int n0, int nu1, int nu2, cudaStream_t st, int& launches)
-{
-    if (dim == 2)
-        k_coarse_cycle<T, 2><<<1, kCoarseThreads, 0, st>>>(levels_dev, top, is_finest ? 1 : 0, P, chol, n0, nu1, nu2);
-    else
-        k_coarse_cycle<T, 3><<<1, kCoarseThreads, 0, st>>>(levels_dev, top, is_finest ? 1 : 0, P, chol, n0, nu1, nu2);
-    ++launches;
-}
-
-template <typename T>
 void launch_qoi(const DevLevel<T>& L, int n_qoi, const long long* q_site, const double* q_w, const DevProblem& P,
                 cudaStream_t st, int& launches)
 {
@@ -621,8 +462,6 @@ void launch_resid(const DevLevel<T>& L, const DevProblem& P, double* u, double* 
     template void launch_lowrank<T>(const DevLevel<T>&, const DevProblem&, int, unsigned, bool, cudaStream_t, int&); \
     template void launch_restrict<T>(const DevLevel<T>&, const DevLevel<T>&, cudaStream_t, int&);                \
     template void launch_prolong<T>(const DevLevel<T>&, const DevLevel<T>&, cudaStream_t, int&);                 \
-    template void launch_coarse<T>(const DevLevel<T>*, int, int, bool, const DevProblem&, const double*, int, int, \
-                                   int, cudaStream_t, int&);                                                     \
     template void launch_qoi<T>(const DevLevel<T>&, int, const long long*, const double*, const DevProblem&,      \
                                 cudaStream_t, int&);                                                             \
     template void launch_pack<T>(const DevLevel<T>&, T*, bool, cudaStream_t);                               \

@@ -15,9 +15,13 @@ template <typename T>
 void launch_restrict(const DevLevel<T>& F, const DevLevel<T>& C, cudaStream_t st, int& launches);
 template <typename T>
 void launch_prolong(const DevLevel<T>& C, const DevLevel<T>& F, cudaStream_t st, int& launches);
+// the V-cycle of grids 0..top in one CTA with shared-memory state (coarse.cu)
+long long coarse_smem_elems(int dim, const int* n_of_level, int top, bool top_is_finest);
+template <typename T>
+cudaError_t coarse_prepare(int dim, size_t smem_bytes);
 template <typename T>
 void launch_coarse(const DevLevel<T>* levels_dev, int dim, int top, bool is_finest, const DevProblem& P,
-                   const double* chol, int n0, int nu1, int nu2, cudaStream_t st, int& launches);
+                   const double* chol, int n0, int nu1, int nu2, size_t smem_bytes, cudaStream_t st, int& launches);
 template <typename T>
 void launch_qoi(const DevLevel<T>& L, int n_qoi, const long long* q_site, const double* q_w, const DevProblem& P,
                 cudaStream_t st, int& launches);

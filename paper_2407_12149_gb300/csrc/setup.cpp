@@ -282,6 +282,63 @@ bool lowrank_setup(const HostProblem& hp, HostLevel& L, int dir)
 
 }  // namespace
 
+void fused_extras(HostLevel& L, const HostProblem& hp, int l)
+{
+    const HostLevel& Cl = hp.lev[l - 1];
+    const int d = hp.dim, m = hp.m, kz = d == 3 ? 1 : 0;
+    L.hsite.clear();
+    L.hval.clear();
+    L.BtG.assign((size_t)m * m, 0.0);
+    if (m == 0) return;
+    Grid g{d, L.n}, gc{d, Cl.n};
+    // A G on the fine grid: column-wise (A G)_j = sum_s a_{j s} G_s, a symmetric
+    std::map<long long, std::vector<double>> AG;
+    std::map<long long, size_t> grow;
+    for (size_t r = 0; r < L.gsite[0].size(); ++r) {
+        long long s = L.gsite[0][r];
+        grow[s] = r;
+        int i, j, k;
+        g.coords(s, i, j, k);
+        const double* a = &L.st[(size_t)s * hp.NS];
+        for (int oz = -kz; oz <= kz; ++oz)
+            for (int oy = -1; oy <= 1; ++oy)
+                for (int ox = -1; ox <= 1; ++ox) {
+                    double aso = a[oidx(d, ox, oy, oz)];
+                    if (aso == 0.0 || !g.inside(i + ox, j + oy, k + oz)) continue;
+                    auto& v = AG[g.idx(i + ox, j + oy, k + oz)];
+                    if (v.empty()) v.assign(m, 0.0);
+                    for (int c = 0; c < m; ++c) v[c] += aso * L.gval[0][r * m + c];
+                }
+    }
+    // H = P^T (A G)
+    std::map<long long, std::vector<double>> H;
+    for (auto& kv : AG) {
+        int i, j, k;
+        g.coords(kv.first, i, j, k);
+        for (int c2 = (d == 3 ? (k - 2) / 2 : 0); c2 <= (d == 3 ? k / 2 : 0); ++c2)
+            for (int c1 = (j - 2) / 2; c1 <= j / 2; ++c1)
+                for (int c0 = (i - 2) / 2; c0 <= i / 2; ++c0) {
+                    if (!gc.inside(c0, c1, c2)) continue;
+                    double w = hat(c0, i) * hat(c1, j) * (d == 3 ? hat(c2, k) : 1.0);
+                    if (w == 0.0) continue;
+                    auto& v = H[gc.idx(c0, c1, c2)];
+                    if (v.empty()) v.assign(m, 0.0);
+                    for (int c = 0; c < m; ++c) v[c] += w * kv.second[c];
+                }
+    }
+    for (auto& kv : H) {
+        L.hsite.push_back(kv.first);
+        L.hval.insert(L.hval.end(), kv.second.begin(), kv.second.end());
+    }
+    // B^T G
+    for (int k = 0; k < m; ++k)
+        for (int t = L.bptr[k]; t < L.bptr[k + 1]; ++t) {
+            auto it = grow.find(L.bsite[t]);
+            if (it == grow.end()) continue;
+            for (int c = 0; c < m; ++c) L.BtG[(size_t)k * m + c] += L.bw[t] * L.gval[0][it->second * m + c];
+        }
+}
+
 std::vector<double> row_sums(const HostProblem& hp, int l)
 {
     const HostLevel& L = hp.lev[l];

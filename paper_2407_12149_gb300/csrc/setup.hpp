@@ -17,6 +17,12 @@ struct HostLevel {
     // G_l(dir) on its support
     std::vector<long long> gsite[2];
     std::vector<double> gval[2];     // [rows * m]
+    // fused-path extras (forward direction): H = P^T A_l G_l on the coarse grid
+    // (fixes the restricted residual after the low-rank correction) and
+    // B_l^T G_l (m x m, row-major)
+    std::vector<long long> hsite;    // coarse dense sites
+    std::vector<double> hval;        // [rows * m]
+    std::vector<double> BtG;
 };
 
 struct HostProblem {
@@ -39,6 +45,9 @@ struct HostProblem {
 std::string build_hierarchy(HostProblem& hp, int dim, int n, int n_levels, int scale_hd, const double* kappa2,
                             double kappa2_const, int m, const int32_t* obs_site, const double* obs_w,
                             int nnz_per_obs, const double* Gamma, const double* y, int* code);
+
+// H = P^T A_l G_l(forward) and B_l^T G_l(forward) for level l >= 1.
+void fused_extras(HostLevel& L, const HostProblem& hp, int l);
 
 // Row sums of a level's stencil (for the FP32 correction form).
 std::vector<double> row_sums(const HostProblem& hp, int l);

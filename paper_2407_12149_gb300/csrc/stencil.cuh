@@ -3,7 +3,8 @@
 //
 // FP64 uses the plain form x_i <- (f_i + xi_i - sum_{j != i} a_ij x_j) / a_ii
 // (Alg. 3 as a colour-ordered Gauss-Seidel sweep).  FP32 uses the algebraically
-// identical correction form x_i <- x_i + (f_i + xi_i - (A x)_i) / a_ii with
+// identical correction form x_i <- x_i + (f_i + xi_i - (A x)_i) / a_ii (1/a_ii and
+// sqrt(a_ii) from one reciprocal square root) with
 // (A x)_i = rowsum_i x_i + sum_{j != i} a_ij (x_j - x_i): in single precision
 // this keeps the small kappa^2 part of the operator (and so the smooth modes
 // of the field) accurate, which the plain form would round away.
@@ -71,8 +72,10 @@ __device__ __forceinline__ float fine_update(const DevLevel<float>& L, long long
     if (DIM == 3) lap += (xi - x[e - L.plane]) + (xi - x[e + L.plane]);
     float aii = fmaf(2.0f * DIM, w, c);
     float Ax = fmaf(c, xi, w * lap);
-    float rhs = (L.f ? L.f[e] : 0.0f) + sqrtf(aii) * z;
-    return xi + (rhs - Ax) / aii;
+    float ia, sa;
+    inv_and_sqrt(aii, ia, sa);
+    float rhs = (L.f ? L.f[e] : 0.0f) + sa * z;
+    return xi + (rhs - Ax) * ia;
 }
 
 template <int DIM>
@@ -108,8 +111,10 @@ __device__ __forceinline__ float coarse_update(const DevLevel<float>& L, long lo
     }
     float aii = s - offsum;
     float Ax = fmaf(s, xi, lap);
-    float rhs = (L.f ? L.f[e] : 0.0f) + sqrtf(aii) * z;
-    return xi + (rhs - Ax) / aii;
+    float ia, sa;
+    inv_and_sqrt(aii, ia, sa);
+    float rhs = (L.f ? L.f[e] : 0.0f) + sa * z;
+    return xi + (rhs - Ax) * ia;
 }
 
 // (A x)_e of the level (dense part of the operator)

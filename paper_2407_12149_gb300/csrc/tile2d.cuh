@@ -1,0 +1,23 @@
+// tile2d.cuh -- launchers of the fused 2D tile kernels (tile2d.cu).
+#pragma once
+#include "common.cuh"
+
+namespace mgmc {
+
+// raise the dynamic shared-memory limit of the tile kernels (once per device)
+template <typename T>
+cudaError_t tile_prepare();
+// forward sweep of level L fused with the residual restriction into C.f;
+// x_zero: the sweep starts from psi = 0 (every grid but the finest)
+template <typename T>
+void launch_tile_fwd(const DevLevel<T>& L, const DevLevel<T>& C, const DevProblem& P, bool x_zero, cudaStream_t st,
+                     int& launches);
+// prolongation of C.x into L and the backward sweep
+template <typename T>
+void launch_tile_bwd(const DevLevel<T>& L, const DevLevel<T>& C, const DevProblem& P, cudaStream_t st, int& launches);
+// low-rank correction after a fused sweep (down: forward G, H fix-up, d_{l-1})
+template <typename T>
+void launch_lowrank_fused(const DevLevel<T>& L, const DevLevel<T>& C, const DevProblem& P, bool down, cudaStream_t st,
+                          int& launches);
+
+}  // namespace mgmc
