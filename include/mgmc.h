@@ -176,6 +176,37 @@ mgmc_status mgmc_level_n(mgmc_handle h, int l, int* n);
 /* Kernels launched per V-cycle by mgmc_sample (for launch accounting). */
 mgmc_status mgmc_launches_per_cycle(mgmc_handle h, int* launches);
 
+/* One posterior problem of a batch (the arguments of mgmc_create). */
+typedef struct {
+    const double* kappa2;
+    double kappa2_const;
+    int m;
+    const int32_t* obs_site;
+    const double* obs_w;
+    int nnz_per_obs;
+    const double* Gamma;
+    const double* y;
+    int n_qoi;
+    const int32_t* qoi_site;
+    const double* qoi_w;
+} mgmc_problem;
+
+/* A batch of independent chains (2D, nu1 = nu2 = 1, one precision; grid sizes,
+ * kappa^2, observations and QoI may differ per chain) advanced together: each
+ * phase of the V-cycle (Alg. 1) is one launch over the same grid depth of all
+ * chains, the coarse grids of each chain run in one CTA of a batched launch.
+ * Chain c uses the Philox chain id c, so it reproduces mgmc_sample with
+ * chain = c on a handle created from cfgs[c] with the same coarse_max_n
+ * (default 31 here).  All host arrays are copied. */
+mgmc_status mgmc_create_batch(int n_chains, const mgmc_config* cfgs, const mgmc_problem* problems,
+                              const mgmc_allocator* alloc, void* stream, mgmc_handle* out);
+
+/* n_steps V-cycles of every chain of a batch handle.  x_inout: host array of
+ * n_chains device pointers, chain c's dense n_c^2 state; qoi_out: NULL or
+ * device [n_chains * n_steps] (row c = chain c).  Asynchronous on stream. */
+mgmc_status mgmc_sample_batch(mgmc_handle h, int64_t n_steps, uint64_t seed, uint64_t step_offset,
+                              void* const* x_inout, double* qoi_out, void* stream);
+
 /* Benchmark timing: with enable != 0 the captured cycle records CUDA events
  * around the finest grid's forward sweep and its backward sweep (finest grid
  * above coarse_max_n only).  mgmc_profile_times synchronises the stream given

@@ -102,12 +102,26 @@ struct mgmc_ctx {
     int launches = 0;
     size_t coarse_smem = 0;   // dynamic shared memory of the coarse-grid kernel
     bool fused = false;   // 2D, nu1 = nu2 = 1: fused tile kernels on the grids above coarse_max_n
+    DevProblem* P_dev = nullptr;   // device copy of P (batched launches)
+    // batch handle: per-chain handles and the job tables of the batched launches
+    std::vector<mgmc_ctx*> sub;
+    int n_depth = 0;
+    std::vector<void*> jobs_tile, jobs_lrd, jobs_lru;
+    std::vector<int> njob_tile, nblk_tile, njob_lrd, nblk_lrd, njob_lru, nblk_lru;
+    void* jobs_coarse = nullptr;
+    void* jobs_qoi = nullptr;
+    CycleState** cs_list = nullptr;
+    size_t batch_coarse_smem = 0;
+    bool is_batch() const { return !sub.empty(); }
     bool profile = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     bool fp32() const { return cfg.precision == MGMC_FP32; }
 };
 
 namespace {
+
+template <typename T>
+mgmc_status build_batch_tables(mgmc_ctx* h);
 
 template <typename T>
 std::vector<DevLevel<T>>& levels_of(mgmc_ctx* h);
@@ -324,43 +338,47 @@ mgmc_status build_device_levels(mgmc_ctx* h, const HostProblem& hp)
         cudaError_t e = tile_prepare<T>();
         if (e != cudaSuccess) return fail(MGMC_ERR_CUDA, std::string("tile kernel set-up: ") + cudaGetErrorString(e));
     }
-    // descriptors of the levels handled by the single-CTA kernel
-    size_t dbytes = sizeof(DevLevel<T>) * (size_t)(h->top + 1);
+    // descriptors of all grids (the single-CTA kernel reads 0..top; batched launches any)
+    size_t dbytes = sizeof(DevLevel<T>) * (size_t)hp.n_levels;
     h->levels_dev = h->buf.get(dbytes);
     if (!h->levels_dev) return fail(MGMC_ERR_OOM, "allocator returned NULL");
     CUDA_TRY(cudaMemcpyAsync(h->levels_dev, levels.data(), dbytes, cudaMemcpyHostToDevice, h->buf.stream));
     return MGMC_OK;
 }
 
+// The 2D nu1 = nu2 = 1 cycle of one chain or of a batch: every phase is one
+// launch over the job table of its grid depth (depth 0 = the finest grids).
 template <typename T>
-void enqueue_cycle_fused(mgmc_ctx* h, cudaStream_t s, int& launches)
+void enqueue_cycle_batch(mgmc_ctx* h, cudaStream_t s, int& launches)
 {
-    auto& lv = levels_of<T>(h);
-    const int Lf = h->L - 1;
-    const DevProblem& P = h->P;
-    const bool prof = h->profile && h->top < Lf;
-    for (int l = Lf; l > h->top; --l) {
-        if (prof && l == Lf) cudaEventRecordWithFlags(h->ev[0], s, cudaEventRecordExternal);
-        launch_tile_fwd<T>(lv[l], lv[l - 1], P, l < Lf, s, launches);
-        if (prof && l == Lf) cudaEventRecordWithFlags(h->ev[1], s, cudaEventRecordExternal);
-        launch_lowrank_fused<T>(lv[l], lv[l - 1], P, true, s, launches);
+    const int nc = h->is_batch() ? (int)h->sub.size() : 1;
+    const bool prof = h->profile && h->n_depth > 0;
+    for (int d = 0; d < h->n_depth; ++d) {
+        if (prof && d == 0) cudaEventRecordWithFlags(h->ev[0], s, cudaEventRecordExternal);
+        launch_tile_batch<T>((const TileJob<T>*)h->jobs_tile[d], h->njob_tile[d], h->nblk_tile[d], d == 0, false,
+                             d > 0, s, launches);
+        if (prof && d == 0) cudaEventRecordWithFlags(h->ev[1], s, cudaEventRecordExternal);
+        launch_lowrank_batch<T>((const LowrankJob<T>*)h->jobs_lrd[d], h->njob_lrd[d], h->nblk_lrd[d], true, s,
+                                launches);
     }
-    launch_coarse<T>((const DevLevel<T>*)h->levels_dev, h->cfg.dim, h->top, h->top == Lf, P, h->chol, h->n0,
-                     h->cfg.nu1, h->cfg.nu2, h->coarse_smem, s, launches);
-    for (int l = h->top + 1; l <= Lf; ++l) {
-        if (prof && l == Lf) cudaEventRecordWithFlags(h->ev[2], s, cudaEventRecordExternal);
-        launch_tile_bwd<T>(lv[l], lv[l - 1], P, s, launches);
-        if (prof && l == Lf) cudaEventRecordWithFlags(h->ev[3], s, cudaEventRecordExternal);
-        launch_lowrank_fused<T>(lv[l], lv[l - 1], P, false, s, launches);
+    launch_coarse_batch<T>((const CoarseJob<T>*)h->jobs_coarse, nc, h->is_batch() ? 256 : 1024, h->batch_coarse_smem,
+                           s, launches);
+    for (int d = h->n_depth - 1; d >= 0; --d) {
+        if (prof && d == 0) cudaEventRecordWithFlags(h->ev[2], s, cudaEventRecordExternal);
+        launch_tile_batch<T>((const TileJob<T>*)h->jobs_tile[d], h->njob_tile[d], h->nblk_tile[d], d == 0, true,
+                             false, s, launches);
+        if (prof && d == 0) cudaEventRecordWithFlags(h->ev[3], s, cudaEventRecordExternal);
+        launch_lowrank_batch<T>((const LowrankJob<T>*)h->jobs_lru[d], h->njob_lru[d], h->nblk_lru[d], false, s,
+                                launches);
     }
-    launch_qoi<T>(lv[Lf], h->n_qoi, h->q_site, h->q_w, P, s, launches);
+    launch_qoi_batch<T>((const QoiJob<T>*)h->jobs_qoi, nc, s, launches);
 }
 
 template <typename T>
 void enqueue_cycle(mgmc_ctx* h, cudaStream_t s, int& launches)
 {
-    if (h->fused) {
-        enqueue_cycle_fused<T>(h, s, launches);
+    if (h->is_batch() || h->fused) {
+        enqueue_cycle_batch<T>(h, s, launches);
         return;
     }
     auto& lv = levels_of<T>(h);
@@ -584,6 +602,10 @@ mgmc_status mgmc_create(const mgmc_config* cfg_in, const mgmc_allocator* alloc, 
     if (st != MGMC_OK) return cleanup(fail(st, "device upload failed"));
     st = h->fp32() ? build_device_levels<float>(h, hp) : build_device_levels<double>(h, hp);
     if (st != MGMC_OK) return cleanup(st);
+    h->P_dev = (DevProblem*)h->buf.get(sizeof(DevProblem));
+    if (!h->P_dev) return cleanup(fail(MGMC_ERR_OOM, "allocator returned NULL"));
+    if (cudaMemcpyAsync(h->P_dev, &h->P, sizeof(DevProblem), cudaMemcpyHostToDevice, h->buf.stream) != cudaSuccess)
+        return cleanup(fail(MGMC_ERR_CUDA, "upload failed"));
     // QoI (finest-level padded offsets)
     h->n_qoi = n_qoi;
     {
@@ -611,6 +633,11 @@ mgmc_status mgmc_create(const mgmc_config* cfg_in, const mgmc_allocator* alloc, 
     h->rnorm = (double*)h->buf.get(sizeof(double) * 2);
     if (!h->x_stage || !h->u || !h->partial || !h->rnorm || st != MGMC_OK)
         return cleanup(fail(MGMC_ERR_OOM, "allocator returned NULL"));
+    // job tables of the fused 2D cycle (needs the QoI arrays above)
+    if (h->fused) {
+        st = h->fp32() ? build_batch_tables<float>(h) : build_batch_tables<double>(h);
+        if (st != MGMC_OK) return cleanup(st);
+    }
     if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
         return cleanup(fail(MGMC_ERR_CUDA, "stream creation failed"));
     cudaError_t e = cudaStreamSynchronize(h->buf.stream);
@@ -788,11 +815,167 @@ mgmc_status mgmc_profile_times(mgmc_handle h, float* ms, int n, void* stream)
     return MGMC_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+template <typename T>
+mgmc_status build_batch_tables(mgmc_ctx* h)
+{
+    std::vector<mgmc_ctx*> chains = h->is_batch() ? h->sub : std::vector<mgmc_ctx*>{h};
+    const int nc = (int)chains.size();
+    mgmc_status st = MGMC_OK;
+    int depth = 0;
+    for (mgmc_ctx* c : chains) depth = std::max(depth, c->L - 1 - c->top);
+    h->n_depth = depth;
+    for (int d = 0; d < depth; ++d) {
+        std::vector<TileJob<T>> tj;
+        std::vector<LowrankJob<T>> ld, lu;
+        int tiles = 0, bd = 0, bu = 0;
+        for (mgmc_ctx* c : chains) {
+            const int l = c->L - 1 - d;
+            if (l <= c->top) continue;
+            const auto& lv = levels_of<T>(c);
+            const DevLevel<T>* Ld = (const DevLevel<T>*)c->levels_dev + l;
+            const DevLevel<T>* Cd = (const DevLevel<T>*)c->levels_dev + (l - 1);
+            const DevLevel<T>& Lh = lv[l];
+            const int TY = Lh.fine ? TileShape<T, true>::TY : TileShape<T, false>::TY;
+            const int nty = (Lh.n + TY - 1) / TY;
+            tj.push_back({Ld, Cd, c->P_dev, tiles});
+            tiles += Lh.ntx * nty;
+            if (c->m > 0) {
+                int rd = std::max(Lh.g_rows[0], Lh.h_rows);
+                ld.push_back({Ld, Cd, c->P_dev, bd, lowrank_blocks(rd)});
+                bd += lowrank_blocks(rd);
+                lu.push_back({Ld, Cd, c->P_dev, bu, lowrank_blocks(Lh.g_rows[1])});
+                bu += lowrank_blocks(Lh.g_rows[1]);
+            }
+        }
+        h->jobs_tile.push_back(upload(h, tj, st));
+        h->njob_tile.push_back((int)tj.size());
+        h->nblk_tile.push_back(tiles);
+        h->jobs_lrd.push_back(upload(h, ld, st));
+        h->njob_lrd.push_back((int)ld.size());
+        h->nblk_lrd.push_back(bd);
+        h->jobs_lru.push_back(upload(h, lu, st));
+        h->njob_lru.push_back((int)lu.size());
+        h->nblk_lru.push_back(bu);
+    }
+    std::vector<CoarseJob<T>> cj;
+    std::vector<QoiJob<T>> qj;
+    std::vector<CycleState*> csl;
+    size_t smem = 0;
+    for (mgmc_ctx* c : chains) {
+        cj.push_back({(const DevLevel<T>*)c->levels_dev, c->top, c->top == c->L - 1 ? 1 : 0, c->P_dev, c->chol, c->n0});
+        qj.push_back({levels_of<T>(c)[c->L - 1].x, c->n_qoi, c->q_site, c->q_w, c->cs});
+        csl.push_back(c->cs);
+        smem = std::max(smem, c->coarse_smem);
+    }
+    h->jobs_coarse = upload(h, cj, st);
+    h->jobs_qoi = upload(h, qj, st);
+    h->cs_list = upload(h, csl, st);
+    h->batch_coarse_smem = smem;
+    if (st != MGMC_OK) return fail(st, "batch table upload failed");
+    cudaError_t e = coarse_prepare_batch<T>(smem);
+    if (e == cudaSuccess) e = tile_prepare_batch<T>();
+    if (e != cudaSuccess) return fail(MGMC_ERR_CUDA, std::string("batch kernel set-up: ") + cudaGetErrorString(e));
+    (void)nc;
+    return MGMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mgmc_status mgmc_create_batch(int n_chains, const mgmc_config* cfgs, const mgmc_problem* problems,
+                              const mgmc_allocator* alloc, void* stream, mgmc_handle* out)
+{
+    if (!out) return fail(MGMC_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_chains < 1 || n_chains > 65536 || !cfgs || !problems) return fail(MGMC_ERR_ARG, "bad batch arguments");
+    for (int c = 0; c < n_chains; ++c) {
+        if (cfgs[c].dim != 2 || cfgs[c].nu1 != 1 || cfgs[c].nu2 != 1)
+            return fail(MGMC_ERR_ARG, "batched chains must be 2D with nu1 = nu2 = 1");
+        if (cfgs[c].precision != cfgs[0].precision) return fail(MGMC_ERR_ARG, "batched chains share one precision");
+    }
+    mgmc_status dst = check_device();
+    if (dst != MGMC_OK) return dst;
+    mgmc_ctx* h = new mgmc_ctx();
+    h->cfg = cfgs[0];
+    cudaGetDevice(&h->device);
+    h->buf.stream = (cudaStream_t)stream;
+    if (alloc && alloc->alloc && alloc->free) {
+        h->buf.alloc = *alloc;
+        h->buf.use_cuda_malloc = false;
+    }
+    auto cleanup = [&](mgmc_status s) {
+        for (mgmc_ctx* c : h->sub) mgmc_destroy(c);
+        h->sub.clear();
+        h->buf.release();
+        delete h;
+        return s;
+    };
+    for (int c = 0; c < n_chains; ++c) {
+        mgmc_config cfg = cfgs[c];
+        if (cfg.coarse_max_n == 0) cfg.coarse_max_n = 31;
+        const mgmc_problem& p = problems[c];
+        mgmc_handle sh = nullptr;
+        mgmc_status s = mgmc_create(&cfg, alloc, stream, p.kappa2, p.kappa2_const, p.m, p.obs_site, p.obs_w,
+                                    p.nnz_per_obs, p.Gamma, p.y, p.n_qoi, p.qoi_site, p.qoi_w, &sh);
+        if (s != MGMC_OK) {
+            std::string msg = "chain " + std::to_string(c) + ": " + g_last_error;
+            return cleanup(fail(s, msg));
+        }
+        h->sub.push_back(sh);
+    }
+    mgmc_status st = h->fp32() ? build_batch_tables<float>(h) : build_batch_tables<double>(h);
+    if (st != MGMC_OK) return cleanup(st);
+    if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return cleanup(fail(MGMC_ERR_CUDA, "stream creation failed"));
+    if (cudaStreamSynchronize(h->buf.stream) != cudaSuccess) return cleanup(fail(MGMC_ERR_CUDA, "set-up failed"));
+    *out = h;
+    return MGMC_OK;
+}
+
+mgmc_status mgmc_sample_batch(mgmc_handle h, int64_t n_steps, uint64_t seed, uint64_t step_offset,
+                              void* const* x_inout, double* qoi_out, void* stream)
+{
+    if (!h || !h->is_batch()) return fail(MGMC_ERR_ARG, "not a batch handle");
+    if (!x_inout || n_steps < 0) return fail(MGMC_ERR_ARG, "bad arguments");
+    if (n_steps == 0) return MGMC_OK;
+    const int nc = (int)h->sub.size();
+    for (int c = 0; c < nc; ++c)
+        if (!x_inout[c] || !is_device_ptr(x_inout[c])) return fail(MGMC_ERR_ARG, "batch states must be device memory");
+    if (qoi_out && !is_device_ptr(qoi_out)) return fail(MGMC_ERR_ARG, "batch QoI buffer must be device memory");
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(cudaSetDevice(h->device));
+    mgmc_status st = ensure_graph(h);
+    if (st != MGMC_OK) return st;
+    for (int c = 0; c < nc; ++c) {
+        mgmc_ctx* sc = h->sub[c];
+        long long N = (long long)sc->cfg.n * sc->cfg.n;
+        st = pack_in(sc, x_inout[c], false, s, N);
+        if (st != MGMC_OK) return st;
+    }
+    launch_set_cycle_batch(h->cs_list, nc, seed, step_offset, 1, qoi_out, n_steps, s);
+    for (int64_t t = 0; t < n_steps; ++t) CUDA_TRY(cudaGraphLaunch(h->exec, s));
+    for (int c = 0; c < nc; ++c) {
+        mgmc_ctx* sc = h->sub[c];
+        long long N = (long long)sc->cfg.n * sc->cfg.n;
+        st = pack_out(sc, x_inout[c], false, s, N);
+        if (st != MGMC_OK) return st;
+    }
+    CUDA_TRY(cudaGetLastError());
+    return MGMC_OK;
+}
+
 mgmc_status mgmc_destroy(mgmc_handle h)
 {
     if (!h) return MGMC_OK;
     cudaSetDevice(h->device);
     cudaDeviceSynchronize();
+    for (mgmc_ctx* c : h->sub) mgmc_destroy(c);
+    h->sub.clear();
     for (int i = 0; i < 4; ++i)
         if (h->ev[i]) cudaEventDestroy(h->ev[i]);
     if (h->exec) cudaGraphExecDestroy(h->exec);

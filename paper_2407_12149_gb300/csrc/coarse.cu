@@ -400,11 +400,10 @@ long long coarse_smem_elems(int dim, const int* n_of_level, int top, bool top_is
 }
 
 template <typename T, int DIM>
-__global__ void __launch_bounds__(coarse_threads<DIM>())
-    k_coarse_cycle(const DevLevel<T>* __restrict__ levels, int top, int is_finest, DevProblem P, const double* chol,
-                   int n0, int nu1, int nu2)
+__device__ __forceinline__ void coarse_body(const DevLevel<T>* __restrict__ levels, int top, int is_finest,
+                                            const DevProblem& P, const double* chol, int n0, int nu1, int nu2,
+                                            unsigned char* smem_raw)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     T* base = reinterpret_cast<T*>(smem_raw);
     // block layout per grid: X, F, coefficient slots (in that order)
     auto blk = [&](int l, int which) -> T* {
@@ -487,6 +486,101 @@ __global__ void __launch_bounds__(coarse_threads<DIM>())
         }
     }
 }
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(coarse_threads<DIM>())
+    k_coarse_cycle(const DevLevel<T>* __restrict__ levels, int top, int is_finest, DevProblem P, const double* chol,
+                   int n0, int nu1, int nu2)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    coarse_body<T, DIM>(levels, top, is_finest, P, chol, n0, nu1, nu2, smem_raw);
+}
+
+// Batched: one CTA per chain (2D).  The same instantiation serves a single chain
+// (1024 threads, latency) and many chains (256 threads, several chains per SM);
+// the thread count never changes the arithmetic.
+constexpr int kCoarseBatchMaxThreads = 1024;
+
+template <typename T>
+__global__ void __launch_bounds__(kCoarseBatchMaxThreads) k_coarse_cycle_batch(const CoarseJob<T>* __restrict__ jobs)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const CoarseJob<T>& J = jobs[blockIdx.x];
+    coarse_body<T, 2>(J.levels, J.top, J.is_finest, *J.P, J.chol, J.n0, 1, 1, smem_raw);
+}
+
+// F^T theta of every chain's finest grid, then step += 1, cycle += 1 (one CTA per chain)
+template <typename T>
+__global__ void k_qoi_batch(const QoiJob<T>* __restrict__ jobs)
+{
+    __shared__ double part[256];
+    const QoiJob<T>& J = jobs[blockIdx.x];
+    double acc = 0.0;
+    for (int t = threadIdx.x; t < J.n_qoi; t += blockDim.x) acc += J.q_w[t] * (double)J.x[J.q_site[t]];
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) part[threadIdx.x] += part[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        CycleState* cs = J.cs;
+        double q = part[0];
+        if (cs->qoi) cs->qoi[cs->step] = q;
+        if (!isfinite(q)) cs->status = 1;
+        cs->step += 1;
+        cs->cycle += 1;
+    }
+}
+
+__global__ void k_set_cycle_batch(CycleState* const* cs, int n, unsigned long long seed, unsigned long long cycle,
+                                  int noise, double* qoi, long long n_steps)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    CycleState* s = cs[c];
+    s->seed = seed;
+    s->cycle = cycle;
+    s->chain = (unsigned)c;
+    s->noise = noise;
+    s->qoi = qoi ? qoi + (long long)c * n_steps : nullptr;
+    s->step = 0;
+    s->status = 0;
+}
+
+template <typename T>
+cudaError_t coarse_prepare_batch(size_t smem_bytes)
+{
+    return cudaFuncSetAttribute(k_coarse_cycle_batch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+}
+
+template <typename T>
+void launch_coarse_batch(const CoarseJob<T>* jobs, int n, int threads, size_t smem_bytes, cudaStream_t st,
+                         int& launches)
+{
+    k_coarse_cycle_batch<T><<<n, threads, smem_bytes, st>>>(jobs);
+    ++launches;
+}
+
+template <typename T>
+void launch_qoi_batch(const QoiJob<T>* jobs, int n, cudaStream_t st, int& launches)
+{
+    k_qoi_batch<T><<<n, 256, 0, st>>>(jobs);
+    ++launches;
+}
+
+void launch_set_cycle_batch(CycleState* const* cs, int n, unsigned long long seed, unsigned long long cycle, int noise,
+                            double* qoi, long long n_steps, cudaStream_t st)
+{
+    k_set_cycle_batch<<<(n + 127) / 128, 128, 0, st>>>(cs, n, seed, cycle, noise, qoi, n_steps);
+}
+
+template cudaError_t coarse_prepare_batch<float>(size_t);
+template cudaError_t coarse_prepare_batch<double>(size_t);
+template void launch_coarse_batch<float>(const CoarseJob<float>*, int, int, size_t, cudaStream_t, int&);
+template void launch_coarse_batch<double>(const CoarseJob<double>*, int, int, size_t, cudaStream_t, int&);
+template void launch_qoi_batch<float>(const QoiJob<float>*, int, cudaStream_t, int&);
+template void launch_qoi_batch<double>(const QoiJob<double>*, int, cudaStream_t, int&);
 
 template <typename T>
 cudaError_t coarse_prepare(int dim, size_t smem_bytes)

@@ -15,6 +15,35 @@ template <typename T>
 void launch_restrict(const DevLevel<T>& F, const DevLevel<T>& C, cudaStream_t st, int& launches);
 template <typename T>
 void launch_prolong(const DevLevel<T>& C, const DevLevel<T>& F, cudaStream_t st, int& launches);
+// one chain of a batched coarse-grid launch
+template <typename T>
+struct CoarseJob {
+    const DevLevel<T>* levels;   // device descriptors of grids 0 .. L-1
+    int top;
+    int is_finest;
+    const DevProblem* P;
+    const double* chol;
+    int n0;
+};
+// one chain of a batched QoI launch
+template <typename T>
+struct QoiJob {
+    const T* x;                  // finest-grid state
+    int n_qoi;
+    const long long* q_site;
+    const double* q_w;
+    CycleState* cs;
+};
+template <typename T>
+cudaError_t coarse_prepare_batch(size_t smem_bytes);
+template <typename T>
+void launch_coarse_batch(const CoarseJob<T>* jobs, int n, int threads, size_t smem_bytes, cudaStream_t st,
+                         int& launches);
+template <typename T>
+void launch_qoi_batch(const QoiJob<T>* jobs, int n, cudaStream_t st, int& launches);
+void launch_set_cycle_batch(CycleState* const* cs, int n, unsigned long long seed, unsigned long long cycle, int noise,
+                            double* qoi, long long n_steps, cudaStream_t st);
+
 // the V-cycle of grids 0..top in one CTA with shared-memory state (coarse.cu)
 long long coarse_smem_elems(int dim, const int* n_of_level, int top, bool top_is_finest);
 template <typename T>

@@ -314,16 +314,16 @@ __device__ __forceinline__ void tile_store(const DevLevel<T>& L, T* dst, const T
 }  // namespace
 
 template <typename T, bool FINE>
-__global__ void __launch_bounds__(kTileThreads) k_tile_fwd(DevLevel<T> L, DevLevel<T> C, DevProblem P, int x_zero)
+__device__ __forceinline__ void tile_fwd_body(const DevLevel<T>& L, const DevLevel<T>& C, const DevProblem& P,
+                                              int x_zero, int bx, int by, unsigned char* smem_raw)
 {
     using G = TileGeom<T, FINE, false>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     T* X = reinterpret_cast<T*>(smem_raw);
     T* Cf = X + G::SX * G::SY;
     T* F = Cf + G::NCOEF * G::SX * G::SY;
     T* Rr = F + (FINE ? 0 : G::SX * G::SY);
     const CycleState cs = *P.cs;
-    const int x0 = blockIdx.x * G::TX, y0 = blockIdx.y * G::TY;
+    const int x0 = bx * G::TX, y0 = by * G::TY;
     const int gx0 = x0 - G::RX, gy0 = y0 - G::R;
     stage<T, G::SX, G::SY>(X, x_zero ? nullptr : L.x, L, gx0, gy0);
     if (FINE) {
@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(kTileThreads) k_tile_fwd(DevLevel<T> L, DevLev
     }
     __syncthreads();
     tile_sweep<T, FINE, false, G>(L, cs, X, Cf, F, x0, y0, 0u);
-    const int tile = blockIdx.y * L.ntx + blockIdx.x;
+    const int tile = by * L.ntx + bx;
     tile_zparts<T, G>(L, X, tile);
     // residual r = fdense - A theta*_s on [x0, x0+TX] x [y0, y0+TY] (inside the grid)
     constexpr int RW = G::TX + 1;
@@ -370,16 +370,16 @@ __global__ void __launch_bounds__(kTileThreads) k_tile_fwd(DevLevel<T> L, DevLev
 }
 
 template <typename T, bool FINE>
-__global__ void __launch_bounds__(kTileThreads) k_tile_bwd(DevLevel<T> L, DevLevel<T> C, DevProblem P)
+__device__ __forceinline__ void tile_bwd_body(const DevLevel<T>& L, const DevLevel<T>& C, const DevProblem& P, int bx,
+                                              int by, unsigned char* smem_raw)
 {
     using G = TileGeom<T, FINE, true>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     T* X = reinterpret_cast<T*>(smem_raw);
     T* Cf = X + G::SX * G::SY;
     T* F = Cf + G::NCOEF * G::SX * G::SY;
     T* Ps = F + (FINE ? 0 : G::SX * G::SY);
     const CycleState cs = *P.cs;
-    const int x0 = blockIdx.x * G::TX, y0 = blockIdx.y * G::TY;
+    const int x0 = bx * G::TX, y0 = by * G::TY;
     const int gx0 = x0 - G::RX, gy0 = y0 - G::R;
     stage<T, G::SX, G::SY>(X, L.x2, L, gx0, gy0);
     if (FINE) {
@@ -417,8 +417,57 @@ __global__ void __launch_bounds__(kTileThreads) k_tile_bwd(DevLevel<T> L, DevLev
     }
     __syncthreads();
     tile_sweep<T, FINE, true, G>(L, cs, X, Cf, F, x0, y0, 1u);
-    tile_zparts<T, G>(L, X, blockIdx.y * L.ntx + blockIdx.x);
+    tile_zparts<T, G>(L, X, by * L.ntx + bx);
     tile_store<T, G>(L, L.x, X, x0, y0);
+}
+
+template <typename T, bool FINE>
+__global__ void __launch_bounds__(kTileThreads) k_tile_fwd(DevLevel<T> L, DevLevel<T> C, DevProblem P, int x_zero)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    tile_fwd_body<T, FINE>(L, C, P, x_zero, blockIdx.x, blockIdx.y, smem_raw);
+}
+
+template <typename T, bool FINE>
+__global__ void __launch_bounds__(kTileThreads) k_tile_bwd(DevLevel<T> L, DevLevel<T> C, DevProblem P)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    tile_bwd_body<T, FINE>(L, C, P, blockIdx.x, blockIdx.y, smem_raw);
+}
+
+// Batched forms: one launch covers the same grid depth of many chains.  Block b
+// belongs to the job whose tile range [tile0, tile0 + ntiles) contains b.
+template <typename T>
+__device__ __forceinline__ int find_job(const TileJob<T>* jobs, int njobs, int b)
+{
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].tile0 <= b)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename T, bool FINE>
+__global__ void __launch_bounds__(kTileThreads) k_tile_fwd_batch(const TileJob<T>* __restrict__ jobs, int njobs,
+                                                                 int x_zero)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const TileJob<T>& J = jobs[find_job(jobs, njobs, blockIdx.x)];
+    const int t = blockIdx.x - J.tile0;
+    tile_fwd_body<T, FINE>(*J.L, *J.C, *J.P, x_zero, t % J.L->ntx, t / J.L->ntx, smem_raw);
+}
+
+template <typename T, bool FINE>
+__global__ void __launch_bounds__(kTileThreads) k_tile_bwd_batch(const TileJob<T>* __restrict__ jobs, int njobs)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const TileJob<T>& J = jobs[find_job(jobs, njobs, blockIdx.x)];
+    const int t = blockIdx.x - J.tile0;
+    tile_bwd_body<T, FINE>(*J.L, *J.C, *J.P, t % J.L->ntx, t / J.L->ntx, smem_raw);
 }
 
 // Low-rank step after a fused sweep (Alg. 3 last line, see kernels.cu):
@@ -427,7 +476,8 @@ __global__ void __launch_bounds__(kTileThreads) k_tile_bwd(DevLevel<T> L, DevLev
 // on the way down also f_{l-1} += H v (H = P^T A G) and
 // d_{l-1} = d_l - B^T theta' = d_l - z + (B^T G) v.
 template <typename T>
-__global__ void k_lowrank_fused(DevLevel<T> L, DevLevel<T> C, DevProblem P, int down)
+__device__ __forceinline__ void lowrank_fused_body(const DevLevel<T>& L, const DevLevel<T>& C, const DevProblem& P,
+                                                   int down, int blk, int nblk)
 {
     __shared__ double z[kMaxObs];
     __shared__ double zp[kMaxObs];
@@ -455,22 +505,22 @@ __global__ void k_lowrank_fused(DevLevel<T> L, DevLevel<T> C, DevProblem P, int 
     }
     __syncthreads();
     T* x = down ? L.x2 : L.x;
-    const int stride = gridDim.x * blockDim.x;
+    const int stride = nblk * blockDim.x;
     const T* Gm = L.gT[dir];
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < L.g_rows[dir]; r += stride) {
+    for (int r = blk * blockDim.x + threadIdx.x; r < L.g_rows[dir]; r += stride) {
         T acc = T(0);
         for (int k = 0; k < m; ++k) acc += Gm[(long long)r * m + k] * (T)v[k];
         long long s = L.g_site[dir][r];
         x[s] = x[s] - acc;
     }
     if (!down) return;
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < L.h_rows; r += stride) {
+    for (int r = blk * blockDim.x + threadIdx.x; r < L.h_rows; r += stride) {
         T acc = T(0);
         for (int k = 0; k < m; ++k) acc += L.hT[(long long)r * m + k] * (T)v[k];
         long long s = L.h_site[r];
         C.f[s] = C.f[s] + acc;
     }
-    if (blockIdx.x == 0)
+    if (blk == 0)
         for (int k = threadIdx.x; k < m; k += blockDim.x) {
             double acc = 0.0;
             for (int t = 0; t < m; ++t) acc += L.BtG[k * m + t] * v[t];
@@ -478,9 +528,38 @@ __global__ void k_lowrank_fused(DevLevel<T> L, DevLevel<T> C, DevProblem P, int 
         }
 }
 
+template <typename T>
+__global__ void k_lowrank_fused(DevLevel<T> L, DevLevel<T> C, DevProblem P, int down)
+{
+    lowrank_fused_body<T>(L, C, P, down, blockIdx.x, gridDim.x);
+}
+
+// batched: job j owns blocks [block0, block0 + nblocks)
+template <typename T>
+__global__ void k_lowrank_fused_batch(const LowrankJob<T>* __restrict__ jobs, int njobs, int down)
+{
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].block0 <= (int)blockIdx.x)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const LowrankJob<T>& J = jobs[lo];
+    lowrank_fused_body<T>(*J.L, *J.C, *J.P, down, blockIdx.x - J.block0, J.nblocks);
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+int lowrank_blocks(int rows)
+{
+    int blocks = (rows + 255) / 256;
+    if (blocks < 1) blocks = 1;
+    if (blocks > 64) blocks = 64;
+    return blocks;
+}
 template <typename T, bool FINE>
 static void tile_dims(const DevLevel<T>& L, dim3& grid)
 {
@@ -541,10 +620,55 @@ void launch_lowrank_fused(const DevLevel<T>& L, const DevLevel<T>& C, const DevP
     if (P.m == 0) return;
     int rows = L.g_rows[down ? 0 : 1];
     if (down && L.h_rows > rows) rows = L.h_rows;
-    int blocks = (rows + 255) / 256;
-    if (blocks < 1) blocks = 1;
-    if (blocks > 64) blocks = 64;
-    k_lowrank_fused<T><<<blocks, 256, 0, st>>>(L, C, P, down ? 1 : 0);
+    k_lowrank_fused<T><<<lowrank_blocks(rows), 256, 0, st>>>(L, C, P, down ? 1 : 0);
+    ++launches;
+}
+
+template <typename T>
+cudaError_t tile_prepare_batch()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_tile_fwd_batch<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)TileGeom<T, true, false>::smem_bytes());
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_tile_fwd_batch<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TileGeom<T, false, false>::smem_bytes());
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_tile_bwd_batch<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TileGeom<T, true, true>::smem_bytes());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_tile_bwd_batch<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)TileGeom<T, false, true>::smem_bytes());
+}
+
+template <typename T>
+void launch_tile_batch(const TileJob<T>* jobs, int njobs, int nblocks, bool fine, bool bwd, bool x_zero,
+                       cudaStream_t st, int& launches)
+{
+    if (nblocks <= 0) return;
+    if (!bwd) {
+        if (fine)
+            k_tile_fwd_batch<T, true><<<nblocks, kTileThreads, TileGeom<T, true, false>::smem_bytes(), st>>>(
+                jobs, njobs, x_zero ? 1 : 0);
+        else
+            k_tile_fwd_batch<T, false><<<nblocks, kTileThreads, TileGeom<T, false, false>::smem_bytes(), st>>>(
+                jobs, njobs, x_zero ? 1 : 0);
+    } else {
+        if (fine)
+            k_tile_bwd_batch<T, true><<<nblocks, kTileThreads, TileGeom<T, true, true>::smem_bytes(), st>>>(jobs,
+                                                                                                             njobs);
+        else
+            k_tile_bwd_batch<T, false><<<nblocks, kTileThreads, TileGeom<T, false, true>::smem_bytes(), st>>>(jobs,
+                                                                                                               njobs);
+    }
+    ++launches;
+}
+
+template <typename T>
+void launch_lowrank_batch(const LowrankJob<T>* jobs, int njobs, int nblocks, bool down, cudaStream_t st,
+                          int& launches)
+{
+    if (nblocks <= 0) return;
+    k_lowrank_fused_batch<T><<<nblocks, 256, 0, st>>>(jobs, njobs, down ? 1 : 0);
     ++launches;
 }
 
@@ -554,7 +678,10 @@ void launch_lowrank_fused(const DevLevel<T>& L, const DevLevel<T>& C, const DevP
                                      int&);                                                                       \
     template void launch_tile_bwd<T>(const DevLevel<T>&, const DevLevel<T>&, const DevProblem&, cudaStream_t, int&); \
     template void launch_lowrank_fused<T>(const DevLevel<T>&, const DevLevel<T>&, const DevProblem&, bool,         \
-                                          cudaStream_t, int&);
+                                          cudaStream_t, int&);                                                     \
+    template cudaError_t tile_prepare_batch<T>();                                                                 \
+    template void launch_tile_batch<T>(const TileJob<T>*, int, int, bool, bool, bool, cudaStream_t, int&);         \
+    template void launch_lowrank_batch<T>(const LowrankJob<T>*, int, int, bool, cudaStream_t, int&);
 
 MGMC_TILE_INST(float)
 MGMC_TILE_INST(double)

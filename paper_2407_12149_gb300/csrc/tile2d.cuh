@@ -4,6 +4,24 @@
 
 namespace mgmc {
 
+// one chain's grid in a batched tile launch: blocks [tile0, tile0 + ntiles)
+template <typename T>
+struct TileJob {
+    const DevLevel<T>* L;
+    const DevLevel<T>* C;
+    const DevProblem* P;
+    int tile0;
+};
+// one chain's grid in a batched low-rank launch: blocks [block0, block0 + nblocks)
+template <typename T>
+struct LowrankJob {
+    const DevLevel<T>* L;
+    const DevLevel<T>* C;
+    const DevProblem* P;
+    int block0;
+    int nblocks;
+};
+
 // raise the dynamic shared-memory limit of the tile kernels (once per device)
 template <typename T>
 cudaError_t tile_prepare();
@@ -19,5 +37,15 @@ void launch_tile_bwd(const DevLevel<T>& L, const DevLevel<T>& C, const DevProble
 template <typename T>
 void launch_lowrank_fused(const DevLevel<T>& L, const DevLevel<T>& C, const DevProblem& P, bool down, cudaStream_t st,
                           int& launches);
+
+template <typename T>
+cudaError_t tile_prepare_batch();
+template <typename T>
+void launch_tile_batch(const TileJob<T>* jobs, int njobs, int nblocks, bool fine, bool bwd, bool x_zero,
+                       cudaStream_t st, int& launches);
+template <typename T>
+void launch_lowrank_batch(const LowrankJob<T>* jobs, int njobs, int nblocks, bool down, cudaStream_t st,
+                          int& launches);
+int lowrank_blocks(int rows);
 
 }  // namespace mgmc

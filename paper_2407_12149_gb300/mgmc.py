@@ -46,6 +46,14 @@ class mgmc_allocator(ctypes.Structure):
     _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", ctypes.c_void_p)]
 
 
+class mgmc_problem(ctypes.Structure):
+    _fields_ = [("kappa2", ctypes.POINTER(ctypes.c_double)), ("kappa2_const", ctypes.c_double), ("m", ctypes.c_int),
+                ("obs_site", ctypes.POINTER(ctypes.c_int32)), ("obs_w", ctypes.POINTER(ctypes.c_double)),
+                ("nnz_per_obs", ctypes.c_int), ("Gamma", ctypes.POINTER(ctypes.c_double)),
+                ("y", ctypes.POINTER(ctypes.c_double)), ("n_qoi", ctypes.c_int),
+                ("qoi_site", ctypes.POINTER(ctypes.c_int32)), ("qoi_w", ctypes.POINTER(ctypes.c_double))]
+
+
 class mgmc_stats(ctypes.Structure):
     _fields_ = [("mean", ctypes.c_double), ("var", ctypes.c_double), ("tau_int", ctypes.c_double),
                 ("tau_err", ctypes.c_double), ("ess", ctypes.c_double), ("window", ctypes.c_int64),
@@ -62,7 +70,7 @@ _lib = None
 # every symbol include/mgmc.h declares
 EXPORTS = ("mgmc_config_default", "mgmc_create", "mgmc_point_obs_rows", "mgmc_sample", "mgmc_mean_solve",
            "mgmc_qoi_stats", "mgmc_qoi_stats_noalloc", "mgmc_info", "mgmc_level_n", "mgmc_launches_per_cycle", "mgmc_set_profiling",
-           "mgmc_profile_times", "mgmc_destroy", "mgmc_last_error")
+           "mgmc_profile_times", "mgmc_create_batch", "mgmc_sample_batch", "mgmc_destroy", "mgmc_last_error")
 
 
 def load():
@@ -93,6 +101,10 @@ def load():
     L.mgmc_launches_per_cycle.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]
     L.mgmc_set_profiling.argtypes = [ctypes.c_void_p, ctypes.c_int]
     L.mgmc_profile_times.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_int, ctypes.c_void_p]
+    L.mgmc_create_batch.argtypes = [ctypes.c_int, ctypes.POINTER(mgmc_config), ctypes.POINTER(mgmc_problem),
+                                    ctypes.POINTER(mgmc_allocator), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+    L.mgmc_sample_batch.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64,
+                                    ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_void_p]
     L.mgmc_destroy.argtypes = [ctypes.c_void_p]
     for name in EXPORTS:
         if name != "mgmc_last_error":
@@ -276,6 +288,80 @@ class Sampler:
 
     def mean_solve(self, x, rtol=1e-10, max_cycles=200, stream=None):
         return mgmc_mean_solve(self.h, rtol, max_cycles, x.data_ptr(), stream)
+
+    def launches_per_cycle(self):
+        return mgmc_launches_per_cycle(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            mgmc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchSampler:
+    """Many independent chains (inputs.Problem list, 2D) advanced by batched launches.
+
+    Chain c uses the Philox chain id c: it reproduces Sampler(problems[c],
+    coarse_max_n=coarse_max_n).sample(..., chain=c)."""
+
+    def __init__(self, problems, precision: str = "fp32", coarse_max_n: int = 31, device: int = 0,
+                 use_torch_allocator: bool = True):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise MGMCError(2, "no CUDA device available (the sampler has no CPU fallback)")
+        self.problems = list(problems)
+        self.device = device
+        self.precision = MGMC_FP32 if precision == "fp32" else MGMC_FP64
+        self.dtype = torch.float32 if self.precision == MGMC_FP32 else torch.float64
+        self._alloc = TorchAllocator(device) if use_torch_allocator else None
+        n = len(self.problems)
+        cfgs = (mgmc_config * n)()
+        probs = (mgmc_problem * n)()
+        self._keep = []
+        for c, p in enumerate(self.problems):
+            cfgs[c] = mgmc_config(p.dim, p.n, p.n_levels, 1, 1, self.precision, p.scale_hd, coarse_max_n)
+            arrs = {}
+            arrs["k2"] = None if p.kappa2 is None else np.ascontiguousarray(p.kappa2, dtype=np.float64)
+            if p.obs_site is not None:
+                arrs["os"] = np.ascontiguousarray(p.obs_site, dtype=np.int32)
+                arrs["ow"] = np.ascontiguousarray(p.obs_w, dtype=np.float64)
+                arrs["G"] = np.ascontiguousarray(p.Gamma, dtype=np.float64)
+                arrs["y"] = np.ascontiguousarray(p.y, dtype=np.float64)
+            if p.qoi_site is not None:
+                arrs["qs"] = np.ascontiguousarray(p.qoi_site, dtype=np.int32)
+                arrs["qw"] = np.ascontiguousarray(p.qoi_w, dtype=np.float64)
+            self._keep.append(arrs)
+            probs[c] = mgmc_problem(
+                _ptr(arrs["k2"], ctypes.c_double), float(p.kappa2_const), p.m,
+                _ptr(arrs.get("os"), ctypes.c_int32), _ptr(arrs.get("ow"), ctypes.c_double),
+                int(arrs["os"].shape[1]) if "os" in arrs else 1,
+                _ptr(arrs.get("G"), ctypes.c_double), _ptr(arrs.get("y"), ctypes.c_double),
+                int(arrs["qs"].size) if "qs" in arrs else 0,
+                _ptr(arrs.get("qs"), ctypes.c_int32), _ptr(arrs.get("qw"), ctypes.c_double))
+        h = ctypes.c_void_p()
+        _check(load().mgmc_create_batch(n, cfgs, probs, ctypes.byref(self._alloc.struct) if self._alloc else None,
+                                        _stream_handle(None), ctypes.byref(h)))
+        self.h = h
+
+    def zeros(self):
+        torch = _torch()
+        return [torch.zeros(p.N, dtype=self.dtype, device=f"cuda:{self.device}") for p in self.problems]
+
+    def sample(self, xs, n_steps, seed, step_offset=0, qoi=None, stream=None):
+        n = len(self.problems)
+        ptrs = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+        if qoi is not None and (qoi.dtype != _torch().float64 or qoi.numel() < n * n_steps):
+            raise ValueError("qoi must be a float64 device tensor with n_chains * n_steps entries")
+        _check(load().mgmc_sample_batch(self.h, int(n_steps), int(seed) & (2**64 - 1), int(step_offset), ptrs,
+                                        ctypes.c_void_p(qoi.data_ptr()) if qoi is not None else None,
+                                        _stream_handle(stream)))
+        return xs
 
     def launches_per_cycle(self):
         return mgmc_launches_per_cycle(self.h)
