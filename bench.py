@@ -1,11 +1,14 @@
-"""Benchmark of the GB300 MGMC sampler on the 1023^2 Bayesian workload.
+"""Benchmark of the GB300 MGMC sampler on the 1023^2 Bayesian posterior.
 
-Workload: 2D unit square, 1023 x 1023 interior grid (h = 1/1024), non-stationary
+Posterior: 2D unit square, 1023 x 1023 interior grid (h = 1/1024), non-stationary
 kappa^2 = 10 exp(g), 16 point observations, Gamma = 1e-4 I, 10-grid V-cycle with
 the paper's low-rank Gibbs smoother (nu1 = nu2 = 1), FP32 sweeps with FP64
-low-rank / coarsest / QoI arithmetic.  One step = one MGMC V-cycle (the whole
-hot path) of one chain.  The metric is QoI ESS/s = (V-cycles/s) / tau_int, with
-tau_int measured on the device (Wolff window) from an untimed 2000-cycle chain.
+low-rank / coarsest / QoI arithmetic.  The default workload advances 32
+independent chains of this posterior with batched launches (the batched + FP32
+form); one step = one V-cycle (the whole hot path) of every chain.  The metric
+is QoI ESS/s = (chain V-cycles/s) / tau_int, tau_int measured on the device
+(Wolff window) from untimed 2000-cycle chains.  The plain FP64 single-chain GPU
+sampler is timed in the same run for comparison (config.plain_fp64_single_chain).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
 
@@ -134,7 +137,13 @@ def load_tau_ref():
     return float(d["tau"]), d
 
 
-WORKLOADS = {"bayes2d-1023": 1023, "bayes2d-4095": 4095, "bayes2d-8191": 8191}
+WORKLOADS = {
+    "batch32-bayes2d-1023": {"n": 1023, "chains": 32},   # headline: batched FP32 chains of the 1023^2 posterior
+    "bayes2d-1023": {"n": 1023, "chains": 1},
+    "bayes2d-4095": {"n": 4095, "chains": 1},            # HBM-resident single-grid variants (roofline)
+    "bayes2d-8191": {"n": 8191, "chains": 1},
+    "batch512-mixed": {"n": 511, "chains": 512, "mixed": True},   # 128 chains each of 63^2 .. 511^2
+}
 
 
 def run_reference(args):
@@ -171,6 +180,21 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def make_sampler(M, inputs, wl, precision, local):
+    """Sampler (one chain) or BatchSampler (many chains) of a workload."""
+    if wl["chains"] == 1:
+        p = inputs.config2(n=wl["n"])
+        return M.Sampler(p, precision=precision, device=local), [p]
+    if wl.get("mixed"):
+        ps = [inputs.make_problem(f"mixed-{c}", 2, n, kappa2_seed=c, m=8 + (c % 25), obs_seed=1000 + c,
+                                  qoi_cells=max(2, (46 * (n + 1)) // 1024))
+              for c, n in enumerate([63, 127, 255, 511] * (wl["chains"] // 4))]
+    else:
+        p = inputs.config2(n=wl["n"])
+        ps = [p] * wl["chains"]
+    return M.BatchSampler(ps, precision=precision, device=local), ps
+
+
 def run_mine(args):
     import torch
     ws, rank, local = dist_env()
@@ -183,38 +207,51 @@ def run_mine(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
-    p = inputs.config2(n=WORKLOADS[args.workload])
-    s = M.Sampler(p, precision="fp32", device=local)
+    wl = WORKLOADS[args.workload]
+    s, ps = make_sampler(M, inputs, wl, "fp32", local)
+    nch = len(ps)
+    batch = nch > 1
     stream = torch.cuda.current_stream()
-    chain = rank
-    N = p.N
+    sites = sum(p.N for p in ps)
     launches = s.launches_per_cycle()
+    # chains of this rank: Philox chain ids rank * nch + c (independent replicas across ranks)
+    xs = s.zeros() if batch else [s.zeros()]
 
-    # --- untimed calibration chain: burn-in 100, then tau_int on the device ----
-    x = s.zeros()
+    def cycle(n_steps, offset, qoi=None):
+        if batch:
+            s.sample(xs, n_steps, 2024 + 7919 * rank, step_offset=offset, qoi=qoi)
+        else:
+            s.sample(xs[0], n_steps, 2024, step_offset=offset, chain=rank, qoi=qoi)
+
+    # --- untimed calibration chains: burn-in 100, then tau_int on the device ---
     ncal = args.tau_cycles
-    qcal = torch.zeros(ncal + 100, dtype=torch.float64, device=dev)
-    s.sample(x, ncal + 100, 2024, step_offset=0, chain=chain, qoi=qcal)
-    st = M.mgmc_qoi_stats(qcal.data_ptr(), ncal + 100, 100, 1.5)
-    tau = st["tau_int"]
+    qcal = torch.zeros(nch * (ncal + 100), dtype=torch.float64, device=dev)
+    cycle(ncal + 100, 0, qcal)
+    taus, errs = [], []
+    for c in range(nch):
+        st = M.mgmc_qoi_stats(qcal.data_ptr() + 8 * c * (ncal + 100), ncal + 100, 100, 1.5)
+        taus.append(st["tau_int"])
+        errs.append(st["tau_err"])
+    tau = statistics.mean(taus)
+    tau_err = (statistics.stdev(taus) / len(taus) ** 0.5) if len(taus) > 1 else errs[0]
     offset = ncal + 100
 
     # --- CPU baseline (rank 0, one GPU only), before the GPU timing ------------
     cpu = None
-    if rank == 0 and ws == 1 and args.workload == "bayes2d-1023":
+    if rank == 0 and ws == 1 and wl["n"] == 1023 and not wl.get("mixed"):
         try:
             tau_ref, _ = load_tau_ref()
-            cpu = cpu_baseline(p, tau_ref)
+            cpu = cpu_baseline(inputs.config2(), tau_ref)
         except Exception as e:  # report, do not fail the GPU measurement
             cpu = {"value": None, "unit": "QoI ESS/s", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
 
     # --- device-timed steps ----------------------------------------------------
     M.mgmc_set_profiling(s.h, True)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)    # 256 MB > L2
-    qstep = torch.zeros(1, dtype=torch.float64, device=dev)
+    qstep = torch.zeros(nch, dtype=torch.float64, device=dev)
     for w in range(args.warmup):
         flush.fill_(float(w))
-        s.sample(x, 1, 2024, step_offset=offset, chain=chain, qoi=qstep)
+        cycle(1, offset, qstep)
         offset += 1
     torch.cuda.synchronize()
     if dist:
@@ -227,7 +264,7 @@ def run_mine(args):
     for k in range(args.steps):
         flush.fill_(float(k))
         ev[k][0].record(stream)
-        s.sample(x, 1, 2024, step_offset=offset, chain=chain, qoi=qstep)
+        cycle(1, offset, qstep)
         ev[k][1].record(stream)
         offset += 1
         f_ms, b_ms = M.mgmc_profile_times(s.h)   # synchronises the stream
@@ -242,59 +279,96 @@ def run_mine(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
         dist.barrier()
-    cps = ws * args.steps / (total_ms / 1e3)
+    cps = ws * nch * args.steps / (total_ms / 1e3)       # chain V-cycles per second, whole job
     value = cps / tau
 
     # --- end-to-end through the public API with pinned host buffers -----------
     M.mgmc_set_profiling(s.h, False)
-    xh = x.cpu().pin_memory()
-    qh = torch.zeros(1, dtype=torch.float64).pin_memory()
-    n_e2e = args.steps
+    xh = [x.cpu().pin_memory() for x in xs]
+    qh = torch.zeros(nch, dtype=torch.float64).pin_memory()
+    n_e2e = max(3, min(args.steps, 20))
     if dist:
         dist.barrier()
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(n_e2e):
-        s.sample(xh, 1, 2024, step_offset=offset, chain=chain, qoi=qh)   # H2D x, cycle, D2H x + QoI
+        if batch:
+            for x, h in zip(xs, xh):
+                x.copy_(h, non_blocking=True)                     # H2D of every chain's state
+            s.sample(xs, 1, 2024 + 7919 * rank, step_offset=offset, qoi=qstep)
+            for x, h in zip(xs, xh):
+                h.copy_(x, non_blocking=True)                     # D2H of the new states
+            qh.copy_(qstep, non_blocking=True)
+            torch.cuda.synchronize()
+        else:
+            s.sample(xh[0], 1, 2024, step_offset=offset, chain=rank, qoi=qh[:1])   # host buffers: H2D, cycle, D2H
         offset += 1
     e2e_s = time.perf_counter() - t0
     if dist:
         t = torch.tensor([e2e_s], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    e2e_value = ws * n_e2e / e2e_s / tau
+    e2e_value = ws * nch * n_e2e / e2e_s / tau
+
+    # --- plain FP64 single-chain GPU MGMC on the same posterior (comparison) ---
+    plain = None
+    if rank == 0 and not wl.get("mixed") and wl["n"] <= 1023:
+        s64 = M.Sampler(inputs.config2(n=wl["n"]), precision="fp64", device=local)
+        x64 = s64.zeros()
+        s64.sample(x64, 20, 99)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s64.sample(x64, 200, 99, step_offset=20)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        cps64 = 200 / (e0.elapsed_time(e1) / 1e3)
+        plain = {"v_cycles_per_s": cps64, "ess_per_s": cps64 / tau,
+                 "note": "plain FP64 GPU MGMC, one chain, same posterior, 200 back-to-back cycles (L2-warm); "
+                         "same law as the measured chains, so the same tau_int"}
+        s64.close()
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
     peak, peak_kind = measured_peak()
-    # algorithmic bytes of one fused forward launch on the finest grid, FP32: read theta and
-    # s*kappa^2 (4 + 4 B/site), write theta*_s (4 B/site) and the restricted residual (4 B per
+    fine_sites = sum(p.N for p in ps if p.n > 31)
+    # algorithmic bytes of the depth-0 forward launch (every chain's finest grid), FP32: read theta
+    # and s*kappa^2 (4 + 4 B/site), write theta*_s (4 B/site) and the restricted residual (4 B per
     # coarse site = 1 B per fine site); the noise is generated, never stored
-    sweep_bytes = 13 * N
+    sweep_bytes = 13 * fine_sites
     fwd_avg = statistics.mean(fwd_ms)
     achieved = sweep_bytes / (fwd_avg * 1e-3) / 1e9
+    desc = ("32 independent chains of " if batch and not wl.get("mixed") else "") + \
+        (f"{nch} chains, grids 63^2..511^2 (128 x 4 sizes), own kappa^2 and 8-32 obs" if wl.get("mixed") else
+         f"{ps[0].n}^2 Bayesian posterior: kappa^2 = 10 exp(g), 16 point obs, Gamma = 1e-4 I, "
+         f"{ps[0].n_levels}-grid V(1,1)-cycle, low-rank Gibbs smoother")
     line = {
         "metric": "QoI ESS/s", "value": value, "unit": "QoI ESS/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{p.name}: {p.n}^2, kappa^2 = 10 exp(g), 16 point obs, Gamma = 1e-4 I, "
-                               f"{p.n_levels}-grid V(1,1)-cycle, low-rank Gibbs smoother, FP32 sweeps / FP64 low-rank",
-                   "v_cycles_per_s": cps, "tau_int": tau, "tau_err": st["tau_err"],
-                   "tau_from": f"device Wolff estimate on an untimed {ncal}-cycle chain",
-                   "l2": "256 MB buffer written between timed steps (inputs are smaller than L2)",
-                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "config": {"workload": f"{args.workload}: {desc}; FP32 sweeps, FP64 low-rank/coarsest/QoI",
+                   "chains_per_gpu": nch, "sites_per_gpu": sites,
+                   "v_cycles_per_s": cps, "site_updates_per_s": cps * sites / nch * 2,
+                   "tau_int": tau, "tau_err": tau_err,
+                   "tau_from": f"device Wolff estimates of {nch} untimed {ncal}-cycle chains (mean)",
+                   "l2": "256 MB buffer written between timed steps (inputs are smaller than L2 per chain)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "launches_per_cycle": launches,
+                   "plain_fp64_single_chain": plain},
         "roofline": {"bound": "hbm",
-                     "kernel": "k_tile_fwd<float,1>: finest-grid forward Gibbs sweep + residual + restriction",
+                     "kernel": "k_tile_fwd_batch<float,1>: finest-grid forward Gibbs sweep + residual + "
+                               "restriction, all chains",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": f"{peak_kind} HBM copy bandwidth",
                      "traffic": FINE_SWEEP_TRAFFIC_BYTES,
                      "algorithmic_bytes": sweep_bytes, "avg_ms": fwd_avg,
                      "bwd_sweep_avg_ms": statistics.mean(bwd_ms)},
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": "QoI ESS/s", "h2d_bytes_per_step": 4 * N,
-                "d2h_bytes_per_step": 4 * N + 8},
-        "gpu_launches": args.steps * (launches + 3),
+        "e2e": {"value": e2e_value, "unit": "QoI ESS/s", "h2d_bytes_per_step": 4 * sites,
+                "d2h_bytes_per_step": 4 * sites + 8 * nch},
+        "gpu_launches": args.steps * (launches + 2 * nch + 1),
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)
@@ -308,9 +382,9 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
-    ap.add_argument("--workload", default="bayes2d-1023", choices=sorted(WORKLOADS),
-                    help="bayes2d-1023 is the headline workload; the larger grids are HBM-resident variants "
-                         "for the roofline")
+    ap.add_argument("--workload", default="batch32-bayes2d-1023", choices=sorted(WORKLOADS),
+                    help="batch32-bayes2d-1023 (headline): 32 FP32 chains of the 1023^2 posterior; bayes2d-1023: "
+                         "one chain; bayes2d-4095/8191: HBM-resident single grids; batch512-mixed: 512 chains")
     ap.add_argument("--tau-cycles", type=int, default=TAU_CALIBRATION,
                     help="length of the untimed chain that estimates tau_int (>= 200)")
     args = ap.parse_args()

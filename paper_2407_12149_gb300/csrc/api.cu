@@ -807,7 +807,8 @@ mgmc_status mgmc_set_profiling(mgmc_handle h, int enable)
 mgmc_status mgmc_profile_times(mgmc_handle h, float* ms, int n, void* stream)
 {
     if (!h || !ms || n < 2) return fail(MGMC_ERR_ARG, "bad arguments");
-    if (!h->profile || h->top >= h->L - 1)
+    const bool tiled = (h->is_batch() || h->fused) ? h->n_depth > 0 : h->top < h->L - 1;
+    if (!h->profile || !tiled)
         return fail(MGMC_ERR_STATE, "profiling is off or the finest grid runs in the single-CTA kernel");
     CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
     CUDA_TRY(cudaEventElapsedTime(&ms[0], h->ev[0], h->ev[1]));
