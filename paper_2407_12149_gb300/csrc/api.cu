@@ -361,8 +361,12 @@ void enqueue_cycle_batch(mgmc_ctx* h, cudaStream_t s, int& launches)
         launch_lowrank_batch<T>((const LowrankJob<T>*)h->jobs_lrd[d], h->njob_lrd[d], h->nblk_lrd[d], true, s,
                                 launches);
     }
-    launch_coarse_batch<T>((const CoarseJob<T>*)h->jobs_coarse, nc, h->is_batch() ? 256 : 1024, h->batch_coarse_smem,
-                           s, launches);
+    // one CTA per chain: 1024 threads while the chains leave SMs free (latency-bound
+    // grids), 256 once several chains share an SM
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    const int coarse_threads = (!h->is_batch() || nc <= 2 * sms) ? 1024 : 256;
+    launch_coarse_batch<T>((const CoarseJob<T>*)h->jobs_coarse, nc, coarse_threads, h->batch_coarse_smem, s, launches);
     for (int d = h->n_depth - 1; d >= 0; --d) {
         if (prof && d == 0) cudaEventRecordWithFlags(h->ev[2], s, cudaEventRecordExternal);
         launch_tile_batch<T>((const TileJob<T>*)h->jobs_tile[d], h->njob_tile[d], h->nblk_tile[d], d == 0, true,

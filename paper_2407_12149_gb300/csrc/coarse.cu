@@ -496,7 +496,7 @@ __global__ void __launch_bounds__(coarse_threads<DIM>())
     coarse_body<T, DIM>(levels, top, is_finest, P, chol, n0, nu1, nu2, smem_raw);
 }
 
-// Batched: one CTA per chain (2D).  The same instantiation serves a single chain
+// Batched: one CTA per chain (2D).  The same instantiation serves few chains
 // (1024 threads, latency) and many chains (256 threads, several chains per SM);
 // the thread count never changes the arithmetic.
 constexpr int kCoarseBatchMaxThreads = 1024;

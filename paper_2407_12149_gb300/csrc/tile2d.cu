@@ -61,7 +61,8 @@ struct TileGeom {
     static constexpr int SY = TY + 2 * R;
     static constexpr int NCOEF = FINE ? 1 : 5;
     static constexpr int NFLD = 1 + NCOEF + (FINE ? 0 : 1);  // x, coefficients, fdense
-    static constexpr int RES = (TX + 1) * (TY + 1);         // residual on tile + high ring
+    static constexpr int RW4 = TX + 4;                      // FP32 residual row: whole 4-site groups
+    static constexpr int RES = sizeof(T) == 4 ? RW4 * (TY + 1) : (TX + 1) * (TY + 1);  // residual on tile + high ring
     static constexpr int PX = SX / 2 + 2;                   // coarse psi tile (backward)
     static constexpr int PY = SY / 2 + 2;
     static constexpr size_t smem_bytes()
@@ -72,24 +73,44 @@ struct TileGeom {
 
 namespace {
 
-// dst[ly * SX + lx] = src at interior (gx0 + lx, gy0 + ly); zero outside the padded array
-template <typename T, int SX, int SY>
-__device__ __forceinline__ void stage(T* dst, const T* src, const DevLevel<T>& L, int gx0, int gy0)
+// Asynchronous 16-byte global -> shared copies (cp.async, Sec. "asynchronous
+// copy" of the PTX ISA): every copy of the staged tile is in flight at once and
+// a source size of 0 zero-fills the destination.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid)
 {
-    using V = typename Vec<T>::type;
+    unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid)
+{
+    unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, bool valid)
+{
+    unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 8 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// dst[ly * SX + lx] <- src at interior (gx0 + lx, gy0 + ly); zero outside the padded
+// array or when src is NULL.  Issues the copies only: cp_async_wait_all() and a CTA
+// barrier make them visible.  `any` is a valid global address used as the (unread)
+// source of zero-filled copies.
+template <typename T, int SX, int SY>
+__device__ __forceinline__ void stage(T* dst, const T* src, const DevLevel<T>& L, int gx0, int gy0, const T* any)
+{
     constexpr int VN = Vec<T>::N;
     constexpr int NV = SX / VN;
-    for (int idx = threadIdx.x; idx < NV * SY; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < NV * SY; idx += kTileThreads) {
         int vx = idx % NV, ly = idx / NV;
         int i = gx0 + vx * VN, j = gy0 + ly;
-        V v;
-        if (src && j >= -1 && j <= L.n && i + 4 >= 0 && i + 4 + VN <= L.pitch) {
-            long long e = (long long)L.pitch * (j + 1) + (i + 4);
-            v = *reinterpret_cast<const V*>(src + e);
-        } else {
-            v = V{};
-        }
-        *reinterpret_cast<V*>(dst + ly * SX + vx * VN) = v;
+        bool ok = src && j >= -1 && j <= L.n && i + 4 >= 0 && i + 4 + VN <= L.pitch;
+        const T* g = ok ? src + ((long long)L.pitch * (j + 1) + (i + 4)) : any;
+        cp_async16(dst + ly * SX + vx * VN, g, ok);
     }
 }
 
@@ -218,6 +239,221 @@ __device__ __forceinline__ float Ax_9(const float* X, const float* Cf, int l)
     return fmaf(Cf[l], xi, lap);
 }
 
+// --- FP32 group updates: the two same-colour sites (components q = px, px + 2) of
+// the 4-site group whose first site is at the 16-byte aligned index lb.  Whole
+// float4 rows are read; the one column outside the group (lb - 1 for px = 0,
+// lb + 4 for px = 1) is read as a scalar.  The group's float4 is written back
+// whole: its other two sites have the other colour and are not written by any
+// thread in this phase.  Same operations, in the same order, as upd_fine / upd_9.
+__device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void sts4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+// component k of the row (k = -1 and k = 4 are the scalar e outside the group)
+__device__ __forceinline__ float cmp(const float4& v, float e, int k)
+{
+    return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : k == 3 ? v.w : e;
+}
+__device__ __forceinline__ float fine_site(float xi, float up, float lf, float rt, float dn, float c, float w, float z)
+{
+    float lap = (xi - up) + (xi - lf) + (xi - rt) + (xi - dn);
+    float aii = fmaf(4.0f, w, c);
+    float Ax = fmaf(c, xi, w * lap);
+    float ia, sa;
+    inv_and_sqrt(aii, ia, sa);
+    float rhs = 0.0f + sa * z;
+    return xi + (rhs - Ax) * ia;
+}
+
+template <int SX>
+__device__ __forceinline__ void pair_fine(float* X, const float* C0, int lb, int px, float w, float z0, float z1,
+                                          bool v0, bool v1)
+{
+    const float4 r0 = lds4(X + lb), ru = lds4(X + lb - SX), rd = lds4(X + lb + SX), c = lds4(C0 + lb);
+    const float e = X[px ? lb + 4 : lb - 1];
+    const bool o = px != 0;
+    // site a: component px; site b: component px + 2
+    const float xa = o ? r0.y : r0.x, xb = o ? r0.w : r0.z;
+    const float na = fine_site(xa, o ? ru.y : ru.x, o ? r0.x : e, o ? r0.z : r0.y, o ? rd.y : rd.x,
+                               o ? c.y : c.x, w, z0);
+    const float nb = fine_site(xb, o ? ru.w : ru.z, o ? r0.z : r0.y, o ? e : r0.w, o ? rd.w : rd.z,
+                               o ? c.w : c.z, w, z1);
+    float4 r = r0;
+    if (o) {
+        if (v0) r.y = na;
+        if (v1) r.w = nb;
+    } else {
+        if (v0) r.x = na;
+        if (v1) r.z = nb;
+    }
+    sts4(X + lb, r);
+}
+
+// rows of one 9-point group item: X rows -1, 0, +1; coefficient slot 0 and slots
+// 1..4 on row 0; slots 2..4 on row -1; the dense right-hand side
+struct Rows9 {
+    float4 xm, x0, xp, s0, c1, c2, c3, c4, c2m, c3m, c4m, f;
+    float exm, ex0, exp, c1e, c4me, c2me;  // the column outside the group (left or right, see cmp)
+};
+
+template <int Q>
+__device__ __forceinline__ float site9(const Rows9& r, float z)
+{
+    const float xi = cmp(r.x0, 0.f, Q);
+    float lap = 0.0f, offsum = 0.0f, a;
+    // o = 0: (-1,-1)
+    a = cmp(r.c4m, r.c4me, Q - 1);
+    lap = fmaf(a, cmp(r.xm, r.exm, Q - 1) - xi, lap);
+    offsum += a;
+    // o = 1: (0,-1)
+    a = cmp(r.c3m, 0.f, Q);
+    lap = fmaf(a, cmp(r.xm, r.exm, Q) - xi, lap);
+    offsum += a;
+    // o = 2: (+1,-1)
+    a = cmp(r.c2m, r.c2me, Q + 1);
+    lap = fmaf(a, cmp(r.xm, r.exm, Q + 1) - xi, lap);
+    offsum += a;
+    // o = 3: (-1,0)
+    a = cmp(r.c1, r.c1e, Q - 1);
+    lap = fmaf(a, cmp(r.x0, r.ex0, Q - 1) - xi, lap);
+    offsum += a;
+    // o = 5: (+1,0)
+    a = cmp(r.c1, 0.f, Q);
+    lap = fmaf(a, cmp(r.x0, r.ex0, Q + 1) - xi, lap);
+    offsum += a;
+    // o = 6: (-1,+1)
+    a = cmp(r.c2, 0.f, Q);
+    lap = fmaf(a, cmp(r.xp, r.exp, Q - 1) - xi, lap);
+    offsum += a;
+    // o = 7: (0,+1)
+    a = cmp(r.c3, 0.f, Q);
+    lap = fmaf(a, cmp(r.xp, r.exp, Q) - xi, lap);
+    offsum += a;
+    // o = 8: (+1,+1)
+    a = cmp(r.c4, 0.f, Q);
+    lap = fmaf(a, cmp(r.xp, r.exp, Q + 1) - xi, lap);
+    offsum += a;
+    const float s = cmp(r.s0, 0.f, Q);
+    const float aii = s - offsum;
+    const float Ax = fmaf(s, xi, lap);
+    float ia, sa;
+    inv_and_sqrt(aii, ia, sa);
+    const float rhs = cmp(r.f, 0.f, Q) + sa * z;
+    return xi + (rhs - Ax) * ia;
+}
+
+template <int PX, int SX, int SXY>
+__device__ __forceinline__ void pair_9(float* X, const float* Cf, const float* F, int lb, float z0, float z1, bool v0,
+                                       bool v1)
+{
+    Rows9 r;
+    r.xm = lds4(X + lb - SX);
+    r.x0 = lds4(X + lb);
+    r.xp = lds4(X + lb + SX);
+    r.s0 = lds4(Cf + lb);
+    r.c1 = lds4(Cf + SXY + lb);
+    r.c2 = lds4(Cf + 2 * SXY + lb);
+    r.c3 = lds4(Cf + 3 * SXY + lb);
+    r.c4 = lds4(Cf + 4 * SXY + lb);
+    r.c2m = lds4(Cf + 2 * SXY + lb - SX);
+    r.c3m = lds4(Cf + 3 * SXY + lb - SX);
+    r.c4m = lds4(Cf + 4 * SXY + lb - SX);
+    r.f = lds4(F + lb);
+    if (PX == 0) {
+        r.exm = X[lb - SX - 1];
+        r.ex0 = X[lb - 1];
+        r.exp = X[lb + SX - 1];
+        r.c1e = Cf[SXY + lb - 1];
+        r.c4me = Cf[4 * SXY + lb - SX - 1];
+        r.c2me = 0.f;
+    } else {
+        r.exm = X[lb - SX + 4];
+        r.ex0 = X[lb + 4];
+        r.exp = X[lb + SX + 4];
+        r.c1e = 0.f;
+        r.c4me = 0.f;
+        r.c2me = Cf[2 * SXY + lb - SX + 4];
+    }
+    const float na = site9<PX>(r, z0);
+    const float nb = site9<PX + 2>(r, z1);
+    float4 o = r.x0;
+    if (PX == 0) {
+        if (v0) o.x = na;
+        if (v1) o.z = nb;
+    } else {
+        if (v0) o.y = na;
+        if (v1) o.w = nb;
+    }
+    sts4(X + lb, o);
+}
+
+// --- FP32 residual of 4 consecutive sites (components 0..3 of the group at lb):
+// A theta in the same order of operations as Ax_fine / Ax_9.
+template <int SX>
+__device__ __forceinline__ float4 ax4_fine(const float* X, const float* C0, int lb, float w)
+{
+    const float4 r0 = lds4(X + lb), ru = lds4(X + lb - SX), rd = lds4(X + lb + SX), c = lds4(C0 + lb);
+    const float el = X[lb - 1], er = X[lb + 4];
+    auto one = [&](float xi, float up, float lf, float rt, float dn, float cc) {
+        float lap = (xi - up) + (xi - lf) + (xi - rt) + (xi - dn);
+        return fmaf(cc, xi, w * lap);
+    };
+    return make_float4(one(r0.x, ru.x, el, r0.y, rd.x, c.x), one(r0.y, ru.y, r0.x, r0.z, rd.y, c.y),
+                       one(r0.z, ru.z, r0.y, r0.w, rd.z, c.z), one(r0.w, ru.w, r0.z, er, rd.w, c.w));
+}
+
+// rows for the 4-site residual: extras on both sides
+struct Rows9R {
+    Rows9 r;      // extras of r on the left (exm, ex0, exp, c1e, c4me)
+    float xmr, x0r, xpr, c2mr;  // right extras
+};
+
+template <int Q>
+__device__ __forceinline__ float ax9q(const Rows9R& R)
+{
+    const Rows9& r = R.r;
+    auto X = [&](const float4& v, float el, float er, int k) { return k < 0 ? el : k > 3 ? er : cmp(v, 0.f, k); };
+    const float xi = cmp(r.x0, 0.f, Q);
+    float lap = 0.0f;
+    lap = fmaf(cmp(r.c4m, r.c4me, Q - 1), X(r.xm, r.exm, R.xmr, Q - 1) - xi, lap);
+    lap = fmaf(cmp(r.c3m, 0.f, Q), X(r.xm, r.exm, R.xmr, Q) - xi, lap);
+    lap = fmaf(Q + 1 > 3 ? R.c2mr : cmp(r.c2m, 0.f, Q + 1), X(r.xm, r.exm, R.xmr, Q + 1) - xi, lap);
+    lap = fmaf(cmp(r.c1, r.c1e, Q - 1), X(r.x0, r.ex0, R.x0r, Q - 1) - xi, lap);
+    lap = fmaf(cmp(r.c1, 0.f, Q), X(r.x0, r.ex0, R.x0r, Q + 1) - xi, lap);
+    lap = fmaf(cmp(r.c2, 0.f, Q), X(r.xp, r.exp, R.xpr, Q - 1) - xi, lap);
+    lap = fmaf(cmp(r.c3, 0.f, Q), X(r.xp, r.exp, R.xpr, Q) - xi, lap);
+    lap = fmaf(cmp(r.c4, 0.f, Q), X(r.xp, r.exp, R.xpr, Q + 1) - xi, lap);
+    return fmaf(cmp(r.s0, 0.f, Q), xi, lap);
+}
+
+template <int SX, int SXY>
+__device__ __forceinline__ float4 res4_9(const float* X, const float* Cf, const float* F, int lb)
+{
+    Rows9R R;
+    Rows9& r = R.r;
+    r.xm = lds4(X + lb - SX);
+    r.x0 = lds4(X + lb);
+    r.xp = lds4(X + lb + SX);
+    r.s0 = lds4(Cf + lb);
+    r.c1 = lds4(Cf + SXY + lb);
+    r.c2 = lds4(Cf + 2 * SXY + lb);
+    r.c3 = lds4(Cf + 3 * SXY + lb);
+    r.c4 = lds4(Cf + 4 * SXY + lb);
+    r.c2m = lds4(Cf + 2 * SXY + lb - SX);
+    r.c3m = lds4(Cf + 3 * SXY + lb - SX);
+    r.c4m = lds4(Cf + 4 * SXY + lb - SX);
+    r.f = lds4(F + lb);
+    r.exm = X[lb - SX - 1];
+    r.ex0 = X[lb - 1];
+    r.exp = X[lb + SX - 1];
+    r.c1e = Cf[SXY + lb - 1];
+    r.c4me = Cf[4 * SXY + lb - SX - 1];
+    r.c2me = 0.f;
+    R.xmr = X[lb - SX + 4];
+    R.x0r = X[lb + 4];
+    R.xpr = X[lb + SX + 4];
+    R.c2mr = Cf[2 * SXY + lb - SX + 4];
+    return make_float4(r.f.x - ax9q<0>(R), r.f.y - ax9q<1>(R), r.f.z - ax9q<2>(R), r.f.w - ax9q<3>(R));
+}
+
 __host__ __device__ constexpr int colour_seq4(int p) { return p == 0 ? 0 : p == 1 ? 3 : p == 2 ? 2 : 1; }
 
 // One colour of a sweep on the staged tile.  Work items are (4-site group, row)
@@ -259,13 +495,23 @@ __device__ __forceinline__ void tile_phase(const DevLevel<T>& L, const CycleStat
             unsigned pair = (unsigned)(((long long)j * nq + (q0 + gq)) * 2 + px);
             draw_pair<T>(cs, pair, 0u, L.level, slot, z0, z1);
         }
-        const int l0 = (dy + G::R) * SX + (dx0 + G::RX);
-        if (FINE) {
-            if (v0) X[l0] = upd_fine<SX>(X, Cf, l0, L.woff, z0);
-            if (v1) X[l0 + 2] = upd_fine<SX>(X, Cf, l0 + 2, L.woff, z1);
+        if constexpr (sizeof(T) == 4) {
+            // FP32: whole 4-site groups as float4 rows of the staged tile
+            const int lb = (dy + G::R) * SX + (4 * gq + G::RX);
+            if constexpr (FINE)
+                pair_fine<SX>((float*)X, (const float*)Cf, lb, px, (float)L.woff, (float)z0, (float)z1, v0, v1);
+            else
+                pair_9<colour & 1, SX, SXY>((float*)X, (const float*)Cf, (const float*)F, lb, (float)z0, (float)z1,
+                                            v0, v1);
         } else {
-            if (v0) X[l0] = upd_9<SX, SXY>(X, Cf, F, l0, z0);
-            if (v1) X[l0 + 2] = upd_9<SX, SXY>(X, Cf, F, l0 + 2, z1);
+            const int l0 = (dy + G::R) * SX + (dx0 + G::RX);
+            if (FINE) {
+                if (v0) X[l0] = upd_fine<SX>(X, Cf, l0, L.woff, z0);
+                if (v1) X[l0 + 2] = upd_fine<SX>(X, Cf, l0 + 2, L.woff, z1);
+            } else {
+                if (v0) X[l0] = upd_9<SX, SXY>(X, Cf, F, l0, z0);
+                if (v1) X[l0 + 2] = upd_9<SX, SXY>(X, Cf, F, l0 + 2, z1);
+            }
         }
     }
 }
@@ -325,46 +571,101 @@ __device__ __forceinline__ void tile_fwd_body(const DevLevel<T>& L, const DevLev
     const CycleState cs = *P.cs;
     const int x0 = bx * G::TX, y0 = by * G::TY;
     const int gx0 = x0 - G::RX, gy0 = y0 - G::R;
-    stage<T, G::SX, G::SY>(X, x_zero ? nullptr : L.x, L, gx0, gy0);
+    stage<T, G::SX, G::SY>(X, x_zero ? nullptr : L.x, L, gx0, gy0, L.x);
     if (FINE) {
-        stage<T, G::SX, G::SY>(Cf, L.diag, L, gx0, gy0);
+        stage<T, G::SX, G::SY>(Cf, L.diag, L, gx0, gy0, L.x);
     } else {
         for (int t = 0; t < G::NCOEF; ++t)
-            stage<T, G::SX, G::SY>(Cf + t * G::SX * G::SY, L.coef + (long long)t * L.alloc, L, gx0, gy0);
-        stage<T, G::SX, G::SY>(F, L.f, L, gx0, gy0);
+            stage<T, G::SX, G::SY>(Cf + t * G::SX * G::SY, L.coef + (long long)t * L.alloc, L, gx0, gy0, L.x);
+        stage<T, G::SX, G::SY>(F, L.f, L, gx0, gy0, L.x);
     }
+    cp_async_wait_all();
     __syncthreads();
     tile_sweep<T, FINE, false, G>(L, cs, X, Cf, F, x0, y0, 0u);
     const int tile = by * L.ntx + bx;
     tile_zparts<T, G>(L, X, tile);
     // residual r = fdense - A theta*_s on [x0, x0+TX] x [y0, y0+TY] (inside the grid)
-    constexpr int RW = G::TX + 1;
-    for (int idx = threadIdx.x; idx < G::RES; idx += blockDim.x) {
-        int rx = idx % RW, ry = idx / RW;
-        int i = x0 + rx, j = y0 + ry;
-        T r = T(0);
-        if (i < L.n && j < L.n) {
-            int l = (j - gy0) * G::SX + (i - gx0);
-            if (FINE)
-                r = T(0) - Ax_fine<G::SX>(X, Cf, l, L.woff);
-            else
-                r = F[l] - Ax_9<G::SX, G::SX * G::SY>(X, Cf, l);
-        }
-        Rr[idx] = r;
-    }
-    __syncthreads();
-    // restriction onto the coarse sites of the tile: f_c = sum_p w(p) r(2I + p)
     const int I0 = x0 >> 1, J0 = y0 >> 1;
-    for (int idx = threadIdx.x; idx < (G::TX / 2) * (G::TY / 2); idx += blockDim.x) {
-        int I = I0 + idx % (G::TX / 2), J = J0 + idx / (G::TX / 2);
-        if (I >= C.n || J >= C.n) continue;
-        T acc = T(0);
-        for (int b = 0; b < 3; ++b)
-            for (int a = 0; a < 3; ++a) {
-                T wgt = (T)(pw(a - 1) * pw(b - 1));
-                acc += wgt * Rr[(2 * J + b - y0) * RW + (2 * I + a - x0)];
+    if constexpr (sizeof(T) == 4) {
+        // FP32: 4-site groups over [x0, x0 + TX + 3]; the columns past x0 + TX are not used
+        constexpr int RW = G::RW4;
+        constexpr int NGX = RW / 4;
+        float* R4 = (float*)Rr;
+        for (int idx = threadIdx.x; idx < NGX * (G::TY + 1); idx += kTileThreads) {
+            const int gx = idx % NGX, ry = idx / NGX;
+            const int i = x0 + 4 * gx, j = y0 + ry;
+            const int lb = (ry + G::R) * G::SX + (4 * gx + G::RX);
+            float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (j < L.n && i < L.n) {
+                if (FINE) {
+                    const float4 a = ax4_fine<G::SX>((const float*)X, (const float*)Cf, lb, (float)L.woff);
+                    r = make_float4(0.0f - a.x, 0.0f - a.y, 0.0f - a.z, 0.0f - a.w);
+                } else {
+                    r = res4_9<G::SX, G::SX * G::SY>((const float*)X, (const float*)Cf, (const float*)F, lb);
+                }
+                if (i + 1 >= L.n) r.y = 0.f;
+                if (i + 2 >= L.n) r.z = 0.f;
+                if (i + 3 >= L.n) r.w = 0.f;
             }
-        C.f[site_offset(2, C.pitch, C.plane, C.base, I, J, 0)] = acc;
+            sts4(R4 + ry * RW + 4 * gx, r);
+        }
+        __syncthreads();
+        // restriction of two coarse sites per item: f_c = sum_p w(p) r(2I + p),
+        // fine columns 2I .. 2I + 4 of three rows
+        for (int idx = threadIdx.x; idx < (G::TX / 4) * (G::TY / 2); idx += kTileThreads) {
+            const int I = I0 + 2 * (idx % (G::TX / 4)), J = J0 + idx / (G::TX / 4);
+            if (I >= C.n || J >= C.n) continue;
+            const int cb = (2 * J - y0) * RW + (2 * I - x0);
+            float4 v[3];
+            float e[3];
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                v[b] = lds4(R4 + cb + b * RW);
+                e[b] = R4[cb + b * RW + 4];
+            }
+            float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const float wb = b == 1 ? 1.0f : 0.5f;
+                acc0 += (0.5f * wb) * v[b].x;
+                acc0 += (1.0f * wb) * v[b].y;
+                acc0 += (0.5f * wb) * v[b].z;
+                acc1 += (0.5f * wb) * v[b].z;
+                acc1 += (1.0f * wb) * v[b].w;
+                acc1 += (0.5f * wb) * e[b];
+            }
+            long long o = site_offset(2, C.pitch, C.plane, C.base, I, J, 0);
+            C.f[o] = (T)acc0;
+            if (I + 1 < C.n) C.f[o + 1] = (T)acc1;
+        }
+    } else {
+        constexpr int RW = G::TX + 1;
+        for (int idx = threadIdx.x; idx < G::RES; idx += blockDim.x) {
+            int rx = idx % RW, ry = idx / RW;
+            int i = x0 + rx, j = y0 + ry;
+            T r = T(0);
+            if (i < L.n && j < L.n) {
+                int l = (j - gy0) * G::SX + (i - gx0);
+                if (FINE)
+                    r = T(0) - Ax_fine<G::SX>(X, Cf, l, L.woff);
+                else
+                    r = F[l] - Ax_9<G::SX, G::SX * G::SY>(X, Cf, l);
+            }
+            Rr[idx] = r;
+        }
+        __syncthreads();
+        // restriction onto the coarse sites of the tile: f_c = sum_p w(p) r(2I + p)
+        for (int idx = threadIdx.x; idx < (G::TX / 2) * (G::TY / 2); idx += blockDim.x) {
+            int I = I0 + idx % (G::TX / 2), J = J0 + idx / (G::TX / 2);
+            if (I >= C.n || J >= C.n) continue;
+            T acc = T(0);
+            for (int b = 0; b < 3; ++b)
+                for (int a = 0; a < 3; ++a) {
+                    T wgt = (T)(pw(a - 1) * pw(b - 1));
+                    acc += wgt * Rr[(2 * J + b - y0) * RW + (2 * I + a - x0)];
+                }
+            C.f[site_offset(2, C.pitch, C.plane, C.base, I, J, 0)] = acc;
+        }
     }
     tile_store<T, G>(L, L.x2, X, x0, y0);
 }
@@ -381,39 +682,88 @@ __device__ __forceinline__ void tile_bwd_body(const DevLevel<T>& L, const DevLev
     const CycleState cs = *P.cs;
     const int x0 = bx * G::TX, y0 = by * G::TY;
     const int gx0 = x0 - G::RX, gy0 = y0 - G::R;
-    stage<T, G::SX, G::SY>(X, L.x2, L, gx0, gy0);
+    stage<T, G::SX, G::SY>(X, L.x2, L, gx0, gy0, L.x);
     if (FINE) {
-        stage<T, G::SX, G::SY>(Cf, L.diag, L, gx0, gy0);
+        stage<T, G::SX, G::SY>(Cf, L.diag, L, gx0, gy0, L.x);
     } else {
         for (int t = 0; t < G::NCOEF; ++t)
-            stage<T, G::SX, G::SY>(Cf + t * G::SX * G::SY, L.coef + (long long)t * L.alloc, L, gx0, gy0);
-        stage<T, G::SX, G::SY>(F, L.f, L, gx0, gy0);
+            stage<T, G::SX, G::SY>(Cf + t * G::SX * G::SY, L.coef + (long long)t * L.alloc, L, gx0, gy0, L.x);
+        stage<T, G::SX, G::SY>(F, L.f, L, gx0, gy0, L.x);
     }
     // coarse psi around the tile (ghost indices -1 and n_c read the zero ring)
     const int Ilo = (gx0 >> 1) - 1, Jlo = (gy0 >> 1) - 1;
-    for (int idx = threadIdx.x; idx < G::PX * G::PY; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < G::PX * G::PY; idx += kTileThreads) {
         int I = Ilo + idx % G::PX, J = Jlo + idx / G::PX;
-        T v = T(0);
-        if (J >= -1 && J <= C.n && I + 4 >= 0 && I + 4 < C.pitch) v = C.x[(long long)C.pitch * (J + 1) + (I + 4)];
-        Ps[idx] = v;
+        bool ok = J >= -1 && J <= C.n && I + 4 >= 0 && I + 4 < C.pitch;
+        const T* g = ok ? C.x + ((long long)C.pitch * (J + 1) + (I + 4)) : C.x;
+        if (sizeof(T) == 4)
+            cp_async4(Ps + idx, g, ok);
+        else
+            cp_async8(Ps + idx, g, ok);
     }
+    cp_async_wait_all();
     __syncthreads();
     // theta' + P psi on the staged region (interior sites only)
-    for (int idx = threadIdx.x; idx < G::SX * G::SY; idx += blockDim.x) {
-        int lx = idx % G::SX, ly = idx / G::SX;
-        int i = gx0 + lx, j = gy0 + ly;
-        if (i < 0 || i >= L.n || j < 0 || j >= L.n) continue;
-        int cx[2], cy[2], nx, ny;
-        T wx[2], wy[2];
-        if (i & 1) { cx[0] = (i - 1) >> 1; wx[0] = T(1); nx = 1; }
-        else { cx[0] = (i >> 1) - 1; cx[1] = i >> 1; wx[0] = wx[1] = T(0.5); nx = 2; }
-        if (j & 1) { cy[0] = (j - 1) >> 1; wy[0] = T(1); ny = 1; }
-        else { cy[0] = (j >> 1) - 1; cy[1] = j >> 1; wy[0] = wy[1] = T(0.5); ny = 2; }
-        T acc = T(0);
-        for (int b = 0; b < ny; ++b)
-            for (int a = 0; a < nx; ++a)
-                acc += T(1) * wy[b] * wx[a] * Ps[(cy[b] - Jlo) * G::PX + (cx[a] - Ilo)];
-        X[idx] = X[idx] + acc;
+    if constexpr (sizeof(T) == 4) {
+        // FP32: one 4-site group (i = gx0 + 4v even) per item; fine site i + c takes
+        // the coarse columns a - 1, a (c = 0), a (c = 1), a, a + 1 (c = 2), a + 1 (c = 3),
+        // a = i / 2, i.e. Ps columns 2v, 2v + 1, 2v + 2; the same sums as below
+        constexpr int NV = G::SX / 4;
+        float* Xf = (float*)X;
+        const float* Pf = (const float*)Ps;
+        for (int idx = threadIdx.x; idx < NV * G::SY; idx += kTileThreads) {
+            const int v = idx % NV, ly = idx / NV;
+            const int i = gx0 + 4 * v, j = gy0 + ly;
+            if (j < 0 || j >= L.n || i + 3 < 0 || i >= L.n) continue;
+            // coarse rows: j odd -> (j - 1) / 2 (weight 1); j even -> j / 2 - 1, j / 2 (1/2 each)
+            const int odd = j & 1;
+            const int pr0 = odd ? ((ly - 1) >> 1) + 1 : (ly >> 1);
+            const float wy = odd ? 1.0f : 0.5f;
+            float p0[3], p1[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                p0[c] = Pf[pr0 * G::PX + 2 * v + c];
+                p1[c] = odd ? 0.f : Pf[(pr0 + 1) * G::PX + 2 * v + c];
+            }
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+            a0 += 1.0f * wy * 0.5f * p0[0];
+            a0 += 1.0f * wy * 0.5f * p0[1];
+            a1 += 1.0f * wy * 1.0f * p0[1];
+            a2 += 1.0f * wy * 0.5f * p0[1];
+            a2 += 1.0f * wy * 0.5f * p0[2];
+            a3 += 1.0f * wy * 1.0f * p0[2];
+            if (!odd) {
+                a0 += 1.0f * wy * 0.5f * p1[0];
+                a0 += 1.0f * wy * 0.5f * p1[1];
+                a1 += 1.0f * wy * 1.0f * p1[1];
+                a2 += 1.0f * wy * 0.5f * p1[1];
+                a2 += 1.0f * wy * 0.5f * p1[2];
+                a3 += 1.0f * wy * 1.0f * p1[2];
+            }
+            float4 x = lds4(Xf + ly * G::SX + 4 * v);
+            if (i >= 0) x.x = x.x + a0;
+            if (i + 1 >= 0 && i + 1 < L.n) x.y = x.y + a1;
+            if (i + 2 >= 0 && i + 2 < L.n) x.z = x.z + a2;
+            if (i + 3 < L.n) x.w = x.w + a3;
+            sts4(Xf + ly * G::SX + 4 * v, x);
+        }
+    } else {
+        for (int idx = threadIdx.x; idx < G::SX * G::SY; idx += blockDim.x) {
+            int lx = idx % G::SX, ly = idx / G::SX;
+            int i = gx0 + lx, j = gy0 + ly;
+            if (i < 0 || i >= L.n || j < 0 || j >= L.n) continue;
+            int cx[2], cy[2], nx, ny;
+            T wx[2], wy[2];
+            if (i & 1) { cx[0] = (i - 1) >> 1; wx[0] = T(1); nx = 1; }
+            else { cx[0] = (i >> 1) - 1; cx[1] = i >> 1; wx[0] = wx[1] = T(0.5); nx = 2; }
+            if (j & 1) { cy[0] = (j - 1) >> 1; wy[0] = T(1); ny = 1; }
+            else { cy[0] = (j >> 1) - 1; cy[1] = j >> 1; wy[0] = wy[1] = T(0.5); ny = 2; }
+            T acc = T(0);
+            for (int b = 0; b < ny; ++b)
+                for (int a = 0; a < nx; ++a)
+                    acc += T(1) * wy[b] * wx[a] * Ps[(cy[b] - Jlo) * G::PX + (cx[a] - Ilo)];
+            X[idx] = X[idx] + acc;
+        }
     }
     __syncthreads();
     tile_sweep<T, FINE, true, G>(L, cs, X, Cf, F, x0, y0, 1u);
