@@ -217,11 +217,12 @@ def run_mine(args):
     # chains of this rank: Philox chain ids rank * nch + c (independent replicas across ranks)
     xs = s.zeros() if batch else [s.zeros()]
 
-    def cycle(n_steps, offset, qoi=None):
+    def cycle(n_steps, offset, qoi=None, resume=False):
+        # resume: continue from the states the handle holds (no copy of the chains in or out)
         if batch:
-            s.sample(xs, n_steps, 2024 + 7919 * rank, step_offset=offset, qoi=qoi)
+            s.sample(None if resume else xs, n_steps, 2024 + 7919 * rank, step_offset=offset, qoi=qoi)
         else:
-            s.sample(xs[0], n_steps, 2024, step_offset=offset, chain=rank, qoi=qoi)
+            s.sample(None if resume else xs[0], n_steps, 2024, step_offset=offset, chain=rank, qoi=qoi)
 
     # --- untimed calibration chains: burn-in 100, then tau_int on the device ---
     ncal = args.tau_cycles
@@ -251,7 +252,7 @@ def run_mine(args):
     qstep = torch.zeros(nch, dtype=torch.float64, device=dev)
     for w in range(args.warmup):
         flush.fill_(float(w))
-        cycle(1, offset, qstep)
+        cycle(1, offset, qstep, resume=True)
         offset += 1
     torch.cuda.synchronize()
     if dist:
@@ -264,7 +265,7 @@ def run_mine(args):
     for k in range(args.steps):
         flush.fill_(float(k))
         ev[k][0].record(stream)
-        cycle(1, offset, qstep)
+        cycle(1, offset, qstep, resume=True)
         ev[k][1].record(stream)
         offset += 1
         f_ms, b_ms = M.mgmc_profile_times(s.h)   # synchronises the stream
@@ -284,6 +285,11 @@ def run_mine(args):
 
     # --- end-to-end through the public API with pinned host buffers -----------
     M.mgmc_set_profiling(s.h, False)
+    for c, x in enumerate(xs):                      # the chains' current states
+        if batch:
+            s.get_state(c, x)
+        else:
+            s.get_state(x)
     xh = [x.cpu().pin_memory() for x in xs]
     qh = torch.zeros(nch, dtype=torch.float64).pin_memory()
     n_e2e = max(3, min(args.steps, 20))
@@ -353,7 +359,9 @@ def run_mine(args):
                    "v_cycles_per_s": cps, "site_updates_per_s": cps * sites / nch * 2,
                    "tau_int": tau, "tau_err": tau_err,
                    "tau_from": f"device Wolff estimates of {nch} untimed {ncal}-cycle chains (mean)",
-                   "l2": "256 MB buffer written between timed steps (inputs are smaller than L2 per chain)",
+                   "l2": "256 MB buffer written between timed steps",
+                   "step": "one V-cycle of every chain, states resident on the device (mgmc_sample[_batch] "
+                           "with x = NULL); e2e copies them in and out through host memory every step",
                    "parallelism": "replicas" if ws > 1 else "single GPU",
                    "launches_per_cycle": launches,
                    "plain_fp64_single_chain": plain},
@@ -368,7 +376,7 @@ def run_mine(args):
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "QoI ESS/s", "h2d_bytes_per_step": 4 * sites,
                 "d2h_bytes_per_step": 4 * sites + 8 * nch},
-        "gpu_launches": args.steps * (launches + 2 * nch + 1),
+        "gpu_launches": args.steps * (launches + 1),
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)

@@ -118,7 +118,10 @@ mgmc_status mgmc_point_obs_rows(int dim, int n, int m, const double* xyz, int32_
  * run bit for bit.  chain (< 65536) selects an independent random stream.
  * qoi_out: NULL or [n_steps] doubles (device or host) receiving F_L^T x
  * after every cycle.  Host buffers are staged through device memory on the
- * stream and the call synchronises it before returning. */
+ * stream and the call synchronises it before returning.
+ * x_inout = NULL continues from the state the handle holds (the state after
+ * the previous call, zero after mgmc_create) and leaves the new state there:
+ * nothing is copied in or out; mgmc_get_state reads it. */
 mgmc_status mgmc_sample(mgmc_handle h, int64_t n_steps, uint64_t seed, uint64_t step_offset,
                         uint32_t chain, void* x_inout, double* qoi_out, void* stream);
 
@@ -202,10 +205,17 @@ mgmc_status mgmc_create_batch(int n_chains, const mgmc_config* cfgs, const mgmc_
                               const mgmc_allocator* alloc, void* stream, mgmc_handle* out);
 
 /* n_steps V-cycles of every chain of a batch handle.  x_inout: host array of
- * n_chains device pointers, chain c's dense n_c^2 state; qoi_out: NULL or
+ * n_chains device pointers, chain c's dense n_c^2 state, or NULL to continue
+ * from the states the handle holds (as in mgmc_sample); qoi_out: NULL or
  * device [n_chains * n_steps] (row c = chain c).  Asynchronous on stream. */
 mgmc_status mgmc_sample_batch(mgmc_handle h, int64_t n_steps, uint64_t seed, uint64_t step_offset,
                               void* const* x_inout, double* qoi_out, void* stream);
+
+/* Copy the state a handle holds for chain `chain` (0 for a single-chain handle,
+ * 0 .. n_chains-1 for a batch) into x_out: dense n^dim field in the handle's
+ * precision, device or host memory (host: the call synchronises the stream).
+ * MGMC_ERR_ARG for a bad chain index or NULL x_out. */
+mgmc_status mgmc_get_state(mgmc_handle h, int chain, void* x_out, void* stream);
 
 /* Benchmark timing: with enable != 0 the captured cycle records CUDA events
  * around the finest grid's forward sweep and its backward sweep (finest grid

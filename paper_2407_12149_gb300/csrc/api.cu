@@ -108,8 +108,11 @@ struct mgmc_ctx {
     int n_depth = 0;
     std::vector<void*> jobs_tile, jobs_lrd, jobs_lru;
     std::vector<int> njob_tile, nblk_tile, njob_lrd, nblk_lrd, njob_lru, nblk_lru;
+    std::vector<int> per_tile, per_lrd, per_lru;
     void* jobs_coarse = nullptr;
     void* jobs_qoi = nullptr;
+    void* jobs_pack = nullptr;    // PackJob<T> per chain (2D fused path)
+    int pack_max_n = 0;
     CycleState** cs_list = nullptr;
     size_t batch_coarse_smem = 0;
     bool is_batch() const { return !sub.empty(); }
@@ -355,11 +358,11 @@ void enqueue_cycle_batch(mgmc_ctx* h, cudaStream_t s, int& launches)
     const bool prof = h->profile && h->n_depth > 0;
     for (int d = 0; d < h->n_depth; ++d) {
         if (prof && d == 0) cudaEventRecordWithFlags(h->ev[0], s, cudaEventRecordExternal);
-        launch_tile_batch<T>((const TileJob<T>*)h->jobs_tile[d], h->njob_tile[d], h->nblk_tile[d], d == 0, false,
-                             d > 0, s, launches);
+        launch_tile_batch<T>((const TileJob<T>*)h->jobs_tile[d], h->njob_tile[d], h->per_tile[d], h->nblk_tile[d],
+                             d == 0, false, d > 0, s, launches);
         if (prof && d == 0) cudaEventRecordWithFlags(h->ev[1], s, cudaEventRecordExternal);
-        launch_lowrank_batch<T>((const LowrankJob<T>*)h->jobs_lrd[d], h->njob_lrd[d], h->nblk_lrd[d], true, s,
-                                launches);
+        launch_lowrank_batch<T>((const LowrankJob<T>*)h->jobs_lrd[d], h->njob_lrd[d], h->per_lrd[d], h->nblk_lrd[d],
+                                true, s, launches);
     }
     // one CTA per chain: 1024 threads while the chains leave SMs free (latency-bound
     // grids), 256 once several chains share an SM
@@ -369,11 +372,11 @@ void enqueue_cycle_batch(mgmc_ctx* h, cudaStream_t s, int& launches)
     launch_coarse_batch<T>((const CoarseJob<T>*)h->jobs_coarse, nc, coarse_threads, h->batch_coarse_smem, s, launches);
     for (int d = h->n_depth - 1; d >= 0; --d) {
         if (prof && d == 0) cudaEventRecordWithFlags(h->ev[2], s, cudaEventRecordExternal);
-        launch_tile_batch<T>((const TileJob<T>*)h->jobs_tile[d], h->njob_tile[d], h->nblk_tile[d], d == 0, true,
-                             false, s, launches);
+        launch_tile_batch<T>((const TileJob<T>*)h->jobs_tile[d], h->njob_tile[d], h->per_tile[d], h->nblk_tile[d],
+                             d == 0, true, false, s, launches);
         if (prof && d == 0) cudaEventRecordWithFlags(h->ev[3], s, cudaEventRecordExternal);
-        launch_lowrank_batch<T>((const LowrankJob<T>*)h->jobs_lru[d], h->njob_lru[d], h->nblk_lru[d], false, s,
-                                launches);
+        launch_lowrank_batch<T>((const LowrankJob<T>*)h->jobs_lru[d], h->njob_lru[d], h->per_lru[d], h->nblk_lru[d],
+                                false, s, launches);
     }
     launch_qoi_batch<T>((const QoiJob<T>*)h->jobs_qoi, nc, s, launches);
 }
@@ -686,10 +689,17 @@ static mgmc_status pack_in(mgmc_ctx* h, void* x, bool host, cudaStream_t s, long
         CUDA_TRY(cudaMemcpyAsync(h->x_stage, x, (size_t)N * esz, cudaMemcpyHostToDevice, s));
         src = h->x_stage;
     }
-    if (h->fp32())
+    if (h->jobs_pack) {
+        void* d[1] = {src};
+        if (h->fp32())
+            launch_pack_batch<float>((const PackJob<float>*)h->jobs_pack, d, 1, h->pack_max_n, true, s);
+        else
+            launch_pack_batch<double>((const PackJob<double>*)h->jobs_pack, d, 1, h->pack_max_n, true, s);
+    } else if (h->fp32()) {
         launch_pack<float>(h->lf[h->L - 1], (float*)src, true, s);
-    else
+    } else {
         launch_pack<double>(h->ld[h->L - 1], (double*)src, true, s);
+    }
     return MGMC_OK;
 }
 
@@ -697,10 +707,17 @@ static mgmc_status pack_out(mgmc_ctx* h, void* x, bool host, cudaStream_t s, lon
 {
     size_t esz = h->fp32() ? 4 : 8;
     void* dst = host ? h->x_stage : x;
-    if (h->fp32())
+    if (h->jobs_pack) {
+        void* d[1] = {dst};
+        if (h->fp32())
+            launch_pack_batch<float>((const PackJob<float>*)h->jobs_pack, d, 1, h->pack_max_n, false, s);
+        else
+            launch_pack_batch<double>((const PackJob<double>*)h->jobs_pack, d, 1, h->pack_max_n, false, s);
+    } else if (h->fp32()) {
         launch_pack<float>(h->lf[h->L - 1], (float*)dst, false, s);
-    else
+    } else {
         launch_pack<double>(h->ld[h->L - 1], (double*)dst, false, s);
+    }
     if (host) CUDA_TRY(cudaMemcpyAsync(x, h->x_stage, (size_t)N * esz, cudaMemcpyDeviceToHost, s));
     return MGMC_OK;
 }
@@ -709,7 +726,6 @@ mgmc_status mgmc_sample(mgmc_handle h, int64_t n_steps, uint64_t seed, uint64_t 
                         void* x_inout, double* qoi_out, void* stream)
 {
     if (!h) return fail(MGMC_ERR_ARG, "handle is NULL");
-    if (!x_inout) return fail(MGMC_ERR_ARG, "x_inout is NULL");
     if (n_steps < 0) return fail(MGMC_ERR_ARG, "n_steps < 0");
     if (chain > 0xFFFFu) return fail(MGMC_ERR_ARG, "chain must be < 65536");
     if (n_steps == 0) return MGMC_OK;
@@ -717,7 +733,8 @@ mgmc_status mgmc_sample(mgmc_handle h, int64_t n_steps, uint64_t seed, uint64_t 
     CUDA_TRY(cudaSetDevice(h->device));
     long long N = 1;
     for (int a = 0; a < h->cfg.dim; ++a) N *= h->cfg.n;
-    bool xhost = !is_device_ptr(x_inout);
+    const bool resume = x_inout == nullptr;
+    bool xhost = !resume && !is_device_ptr(x_inout);
     bool qhost = qoi_out && !is_device_ptr(qoi_out);
     double* qdev = qoi_out;
     if (qhost) {
@@ -725,12 +742,16 @@ mgmc_status mgmc_sample(mgmc_handle h, int64_t n_steps, uint64_t seed, uint64_t 
     }
     mgmc_status st = ensure_graph(h);
     if (st != MGMC_OK) return st;
-    st = pack_in(h, x_inout, xhost, s, N);
-    if (st != MGMC_OK) return st;
+    if (!resume) {
+        st = pack_in(h, x_inout, xhost, s, N);
+        if (st != MGMC_OK) return st;
+    }
     launch_set_cycle(h->cs, seed, step_offset, chain, 1, qdev, s);
     for (int64_t t = 0; t < n_steps; ++t) CUDA_TRY(cudaGraphLaunch(h->exec, s));
-    st = pack_out(h, x_inout, xhost, s, N);
-    if (st != MGMC_OK) return st;
+    if (!resume) {
+        st = pack_out(h, x_inout, xhost, s, N);
+        if (st != MGMC_OK) return st;
+    }
     if (qhost) {
         CUDA_TRY(cudaMemcpyAsync(qoi_out, qdev, sizeof(double) * (size_t)n_steps, cudaMemcpyDeviceToHost, s));
         CUDA_TRY(cudaFreeAsync(qdev, s));
@@ -841,21 +862,30 @@ mgmc_status build_batch_tables(mgmc_ctx* h)
             const int l = c->L - 1 - d;
             if (l <= c->top) continue;
             const auto& lv = levels_of<T>(c);
-            const DevLevel<T>* Ld = (const DevLevel<T>*)c->levels_dev + l;
-            const DevLevel<T>* Cd = (const DevLevel<T>*)c->levels_dev + (l - 1);
             const DevLevel<T>& Lh = lv[l];
+            const DevLevel<T>& Ch = lv[l - 1];
             const int TY = Lh.fine ? TileShape<T, true>::TY : TileShape<T, false>::TY;
             const int nty = (Lh.n + TY - 1) / TY;
-            tj.push_back({Ld, Cd, c->P_dev, tiles});
+            tj.push_back({Lh, Ch, c->P, tiles, Lh.ntx * nty});
             tiles += Lh.ntx * nty;
             if (c->m > 0) {
                 int rd = std::max(Lh.g_rows[0], Lh.h_rows);
-                ld.push_back({Ld, Cd, c->P_dev, bd, lowrank_blocks(rd)});
+                ld.push_back({Lh, Ch, c->P, bd, lowrank_blocks(rd)});
                 bd += lowrank_blocks(rd);
-                lu.push_back({Ld, Cd, c->P_dev, bu, lowrank_blocks(Lh.g_rows[1])});
+                lu.push_back({Lh, Ch, c->P, bu, lowrank_blocks(Lh.g_rows[1])});
                 bu += lowrank_blocks(Lh.g_rows[1]);
             }
         }
+        // common block count of the jobs of one launch (0: they differ)
+        auto common = [](const auto& v, auto count) {
+            int per = v.empty() ? 0 : count(v[0]);
+            for (const auto& j : v)
+                if (count(j) != per) return 0;
+            return per;
+        };
+        h->per_tile.push_back(common(tj, [](const TileJob<T>& j) { return j.ntiles; }));
+        h->per_lrd.push_back(common(ld, [](const LowrankJob<T>& j) { return j.nblocks; }));
+        h->per_lru.push_back(common(lu, [](const LowrankJob<T>& j) { return j.nblocks; }));
         h->jobs_tile.push_back(upload(h, tj, st));
         h->njob_tile.push_back((int)tj.size());
         h->nblk_tile.push_back(tiles);
@@ -868,16 +898,21 @@ mgmc_status build_batch_tables(mgmc_ctx* h)
     }
     std::vector<CoarseJob<T>> cj;
     std::vector<QoiJob<T>> qj;
+    std::vector<PackJob<T>> pj;
     std::vector<CycleState*> csl;
     size_t smem = 0;
     for (mgmc_ctx* c : chains) {
         cj.push_back({(const DevLevel<T>*)c->levels_dev, c->top, c->top == c->L - 1 ? 1 : 0, c->P_dev, c->chol, c->n0});
-        qj.push_back({levels_of<T>(c)[c->L - 1].x, c->n_qoi, c->q_site, c->q_w, c->cs});
+        const DevLevel<T>& Fh = levels_of<T>(c)[c->L - 1];
+        qj.push_back({Fh.x, c->n_qoi, c->q_site, c->q_w, c->cs});
+        pj.push_back({Fh.x, Fh.n, Fh.pitch, Fh.base});
+        h->pack_max_n = std::max(h->pack_max_n, Fh.n);
         csl.push_back(c->cs);
         smem = std::max(smem, c->coarse_smem);
     }
     h->jobs_coarse = upload(h, cj, st);
     h->jobs_qoi = upload(h, qj, st);
+    h->jobs_pack = upload(h, pj, st);
     h->cs_list = upload(h, csl, st);
     h->batch_coarse_smem = smem;
     if (st != MGMC_OK) return fail(st, "batch table upload failed");
@@ -946,31 +981,48 @@ mgmc_status mgmc_sample_batch(mgmc_handle h, int64_t n_steps, uint64_t seed, uin
                               void* const* x_inout, double* qoi_out, void* stream)
 {
     if (!h || !h->is_batch()) return fail(MGMC_ERR_ARG, "not a batch handle");
-    if (!x_inout || n_steps < 0) return fail(MGMC_ERR_ARG, "bad arguments");
+    if (n_steps < 0) return fail(MGMC_ERR_ARG, "bad arguments");
     if (n_steps == 0) return MGMC_OK;
     const int nc = (int)h->sub.size();
-    for (int c = 0; c < nc; ++c)
-        if (!x_inout[c] || !is_device_ptr(x_inout[c])) return fail(MGMC_ERR_ARG, "batch states must be device memory");
+    const bool resume = x_inout == nullptr;
+    if (!resume)
+        for (int c = 0; c < nc; ++c)
+            if (!x_inout[c] || !is_device_ptr(x_inout[c]))
+                return fail(MGMC_ERR_ARG, "batch states must be device memory");
     if (qoi_out && !is_device_ptr(qoi_out)) return fail(MGMC_ERR_ARG, "batch QoI buffer must be device memory");
     cudaStream_t s = (cudaStream_t)stream;
     CUDA_TRY(cudaSetDevice(h->device));
     mgmc_status st = ensure_graph(h);
     if (st != MGMC_OK) return st;
-    for (int c = 0; c < nc; ++c) {
-        mgmc_ctx* sc = h->sub[c];
-        long long N = (long long)sc->cfg.n * sc->cfg.n;
-        st = pack_in(sc, x_inout[c], false, s, N);
-        if (st != MGMC_OK) return st;
-    }
+    auto pack = [&](bool in) {
+        if (h->fp32())
+            launch_pack_batch<float>((const PackJob<float>*)h->jobs_pack, x_inout, nc, h->pack_max_n, in, s);
+        else
+            launch_pack_batch<double>((const PackJob<double>*)h->jobs_pack, x_inout, nc, h->pack_max_n, in, s);
+    };
+    if (!resume) pack(true);
     launch_set_cycle_batch(h->cs_list, nc, seed, step_offset, 1, qoi_out, n_steps, s);
     for (int64_t t = 0; t < n_steps; ++t) CUDA_TRY(cudaGraphLaunch(h->exec, s));
-    for (int c = 0; c < nc; ++c) {
-        mgmc_ctx* sc = h->sub[c];
-        long long N = (long long)sc->cfg.n * sc->cfg.n;
-        st = pack_out(sc, x_inout[c], false, s, N);
-        if (st != MGMC_OK) return st;
-    }
+    if (!resume) pack(false);
     CUDA_TRY(cudaGetLastError());
+    return MGMC_OK;
+}
+
+mgmc_status mgmc_get_state(mgmc_handle h, int chain, void* x_out, void* stream)
+{
+    if (!h || !x_out) return fail(MGMC_ERR_ARG, "handle or x_out is NULL");
+    const int nc = h->is_batch() ? (int)h->sub.size() : 1;
+    if (chain < 0 || chain >= nc) return fail(MGMC_ERR_ARG, "chain index out of range");
+    mgmc_ctx* c = h->is_batch() ? h->sub[chain] : h;
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(cudaSetDevice(h->device));
+    long long N = 1;
+    for (int a = 0; a < c->cfg.dim; ++a) N *= c->cfg.n;
+    const bool host = !is_device_ptr(x_out);
+    mgmc_status st = pack_out(c, x_out, host, s, N);
+    if (st != MGMC_OK) return st;
+    CUDA_TRY(cudaGetLastError());
+    if (host) CUDA_TRY(cudaStreamSynchronize(s));
     return MGMC_OK;
 }
 

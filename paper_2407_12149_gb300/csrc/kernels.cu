@@ -283,6 +283,24 @@ __global__ void k_pack(DevLevel<T> L, T* __restrict__ dense, int to_padded)
         dense[s] = L.x[e];
 }
 
+// Batched 2D form: block (j, c) moves row j of chain c (no divisions).
+struct DensePtrs {
+    void* p[kPackChunk];
+};
+template <typename T>
+__global__ void k_pack_batch(const PackJob<T>* __restrict__ jobs, DensePtrs dense, int to_padded)
+{
+    const PackJob<T> J = jobs[blockIdx.y];
+    const int j = blockIdx.x;
+    if (j >= J.n) return;
+    T* d = (T*)dense.p[blockIdx.y] + (long long)j * J.n;
+    T* x = J.x + J.base + (long long)J.pitch * j;
+    if (to_padded)
+        for (int i = threadIdx.x; i < J.n; i += blockDim.x) x[i] = d[i];
+    else
+        for (int i = threadIdx.x; i < J.n; i += blockDim.x) d[i] = x[i];
+}
+
 // ---------------------------------------------------------------------------
 // residual norm pieces for the mean solve: u = Gamma^-1 (y - B^T x) (m-vector),
 // then r = B u - A x summed as ||r||^2 per block, reduced by one block.
@@ -443,6 +461,18 @@ void launch_pack(const DevLevel<T>& L, T* dense, bool to_padded, cudaStream_t st
 }
 
 template <typename T>
+void launch_pack_batch(const PackJob<T>* jobs, void* const* dense, int count, int max_n, bool to_padded,
+                       cudaStream_t st)
+{
+    for (int c0 = 0; c0 < count; c0 += kPackChunk) {
+        const int k = count - c0 < kPackChunk ? count - c0 : kPackChunk;
+        DensePtrs d{};
+        for (int c = 0; c < k; ++c) d.p[c] = dense[c0 + c];
+        k_pack_batch<T><<<dim3((unsigned)max_n, (unsigned)k), 256, 0, st>>>(jobs + c0, d, to_padded ? 1 : 0);
+    }
+}
+
+template <typename T>
 void launch_resid(const DevLevel<T>& L, const DevProblem& P, double* u, double* partial, int max_partial,
                   double* out, cudaStream_t st)
 {
@@ -465,6 +495,7 @@ void launch_resid(const DevLevel<T>& L, const DevProblem& P, double* u, double* 
     template void launch_qoi<T>(const DevLevel<T>&, int, const long long*, const double*, const DevProblem&,      \
                                 cudaStream_t, int&);                                                             \
     template void launch_pack<T>(const DevLevel<T>&, T*, bool, cudaStream_t);                               \
+    template void launch_pack_batch<T>(const PackJob<T>*, void* const*, int, int, bool, cudaStream_t);         \
     template void launch_resid<T>(const DevLevel<T>&, const DevProblem&, double*, double*, int, double*,         \
                                   cudaStream_t);
 

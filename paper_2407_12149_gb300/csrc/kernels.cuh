@@ -58,6 +58,19 @@ void launch_set_cycle(CycleState* cs, unsigned long long seed, unsigned long lon
                       double* qoi, cudaStream_t st);
 template <typename T>
 void launch_pack(const DevLevel<T>& L, T* dense, bool to_padded, cudaStream_t st);
+// 2D dense user fields <-> padded finest-level states of many chains, one launch per
+// kPackChunk chains; jobs[c] is the static part, dense[c] the caller's array
+template <typename T>
+struct PackJob {
+    T* x;            // padded finest-level state
+    int n;
+    int pitch;
+    long long base;
+};
+constexpr int kPackChunk = 256;
+template <typename T>
+void launch_pack_batch(const PackJob<T>* jobs, void* const* dense, int count, int max_n, bool to_padded,
+                       cudaStream_t st);
 template <typename T>
 void launch_resid(const DevLevel<T>& L, const DevProblem& P, double* u, double* partial, int max_partial,
                   double* out, cudaStream_t st);

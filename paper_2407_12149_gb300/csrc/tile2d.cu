@@ -57,13 +57,18 @@ struct TileGeom {
     // residual on ring 1 -- the coarse patches reach one site past the tile -- reads it)
     static constexpr int R = BWD ? NC : NC + 2;
     static constexpr int RX = (R + VEC - 1) / VEC * VEC;  // the same along x, in whole vectors
-    static constexpr int SX = TX + 2 * RX;
+    static constexpr int SW = TX + 2 * RX;                  // staged columns
+    // row pitch in shared memory: the FP32 9-point tiles get 4 or 12 extra columns so
+    // that the float4 rows of neighbouring work items (two grid rows apart) fall on
+    // different bank groups
+    static constexpr int PAD = (sizeof(T) == 4 && !FINE) ? (BWD ? 12 : 4) : 0;
+    static constexpr int SX = SW + PAD;
     static constexpr int SY = TY + 2 * R;
     static constexpr int NCOEF = FINE ? 1 : 5;
     static constexpr int NFLD = 1 + NCOEF + (FINE ? 0 : 1);  // x, coefficients, fdense
     static constexpr int RW4 = TX + 4;                      // FP32 residual row: whole 4-site groups
     static constexpr int RES = sizeof(T) == 4 ? RW4 * (TY + 1) : (TX + 1) * (TY + 1);  // residual on tile + high ring
-    static constexpr int PX = SX / 2 + 2;                   // coarse psi tile (backward)
+    static constexpr int PX = SW / 2 + 2;                   // coarse psi tile (backward)
     static constexpr int PY = SY / 2 + 2;
     static constexpr size_t smem_bytes()
     {
@@ -100,11 +105,11 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // array or when src is NULL.  Issues the copies only: cp_async_wait_all() and a CTA
 // barrier make them visible.  `any` is a valid global address used as the (unread)
 // source of zero-filled copies.
-template <typename T, int SX, int SY>
+template <typename T, int SW, int SX, int SY>
 __device__ __forceinline__ void stage(T* dst, const T* src, const DevLevel<T>& L, int gx0, int gy0, const T* any)
 {
     constexpr int VN = Vec<T>::N;
-    constexpr int NV = SX / VN;
+    constexpr int NV = SW / VN;
     for (int idx = threadIdx.x; idx < NV * SY; idx += kTileThreads) {
         int vx = idx % NV, ly = idx / NV;
         int i = gx0 + vx * VN, j = gy0 + ly;
@@ -568,17 +573,17 @@ __device__ __forceinline__ void tile_fwd_body(const DevLevel<T>& L, const DevLev
     T* Cf = X + G::SX * G::SY;
     T* F = Cf + G::NCOEF * G::SX * G::SY;
     T* Rr = F + (FINE ? 0 : G::SX * G::SY);
-    const CycleState cs = *P.cs;
     const int x0 = bx * G::TX, y0 = by * G::TY;
     const int gx0 = x0 - G::RX, gy0 = y0 - G::R;
-    stage<T, G::SX, G::SY>(X, x_zero ? nullptr : L.x, L, gx0, gy0, L.x);
+    stage<T, G::SW, G::SX, G::SY>(X, x_zero ? nullptr : L.x, L, gx0, gy0, L.x);
     if (FINE) {
-        stage<T, G::SX, G::SY>(Cf, L.diag, L, gx0, gy0, L.x);
+        stage<T, G::SW, G::SX, G::SY>(Cf, L.diag, L, gx0, gy0, L.x);
     } else {
         for (int t = 0; t < G::NCOEF; ++t)
-            stage<T, G::SX, G::SY>(Cf + t * G::SX * G::SY, L.coef + (long long)t * L.alloc, L, gx0, gy0, L.x);
-        stage<T, G::SX, G::SY>(F, L.f, L, gx0, gy0, L.x);
+            stage<T, G::SW, G::SX, G::SY>(Cf + t * G::SX * G::SY, L.coef + (long long)t * L.alloc, L, gx0, gy0, L.x);
+        stage<T, G::SW, G::SX, G::SY>(F, L.f, L, gx0, gy0, L.x);
     }
+    const CycleState cs = *P.cs;  // read while the copies are in flight
     cp_async_wait_all();
     __syncthreads();
     tile_sweep<T, FINE, false, G>(L, cs, X, Cf, F, x0, y0, 0u);
@@ -679,16 +684,15 @@ __device__ __forceinline__ void tile_bwd_body(const DevLevel<T>& L, const DevLev
     T* Cf = X + G::SX * G::SY;
     T* F = Cf + G::NCOEF * G::SX * G::SY;
     T* Ps = F + (FINE ? 0 : G::SX * G::SY);
-    const CycleState cs = *P.cs;
     const int x0 = bx * G::TX, y0 = by * G::TY;
     const int gx0 = x0 - G::RX, gy0 = y0 - G::R;
-    stage<T, G::SX, G::SY>(X, L.x2, L, gx0, gy0, L.x);
+    stage<T, G::SW, G::SX, G::SY>(X, L.x2, L, gx0, gy0, L.x);
     if (FINE) {
-        stage<T, G::SX, G::SY>(Cf, L.diag, L, gx0, gy0, L.x);
+        stage<T, G::SW, G::SX, G::SY>(Cf, L.diag, L, gx0, gy0, L.x);
     } else {
         for (int t = 0; t < G::NCOEF; ++t)
-            stage<T, G::SX, G::SY>(Cf + t * G::SX * G::SY, L.coef + (long long)t * L.alloc, L, gx0, gy0, L.x);
-        stage<T, G::SX, G::SY>(F, L.f, L, gx0, gy0, L.x);
+            stage<T, G::SW, G::SX, G::SY>(Cf + t * G::SX * G::SY, L.coef + (long long)t * L.alloc, L, gx0, gy0, L.x);
+        stage<T, G::SW, G::SX, G::SY>(F, L.f, L, gx0, gy0, L.x);
     }
     // coarse psi around the tile (ghost indices -1 and n_c read the zero ring)
     const int Ilo = (gx0 >> 1) - 1, Jlo = (gy0 >> 1) - 1;
@@ -701,6 +705,7 @@ __device__ __forceinline__ void tile_bwd_body(const DevLevel<T>& L, const DevLev
         else
             cp_async8(Ps + idx, g, ok);
     }
+    const CycleState cs = *P.cs;  // read while the copies are in flight
     cp_async_wait_all();
     __syncthreads();
     // theta' + P psi on the staged region (interior sites only)
@@ -708,7 +713,7 @@ __device__ __forceinline__ void tile_bwd_body(const DevLevel<T>& L, const DevLev
         // FP32: one 4-site group (i = gx0 + 4v even) per item; fine site i + c takes
         // the coarse columns a - 1, a (c = 0), a (c = 1), a, a + 1 (c = 2), a + 1 (c = 3),
         // a = i / 2, i.e. Ps columns 2v, 2v + 1, 2v + 2; the same sums as below
-        constexpr int NV = G::SX / 4;
+        constexpr int NV = G::SW / 4;
         float* Xf = (float*)X;
         const float* Pf = (const float*)Ps;
         for (int idx = threadIdx.x; idx < NV * G::SY; idx += kTileThreads) {
@@ -748,8 +753,8 @@ __device__ __forceinline__ void tile_bwd_body(const DevLevel<T>& L, const DevLev
             sts4(Xf + ly * G::SX + 4 * v, x);
         }
     } else {
-        for (int idx = threadIdx.x; idx < G::SX * G::SY; idx += blockDim.x) {
-            int lx = idx % G::SX, ly = idx / G::SX;
+        for (int idx = threadIdx.x; idx < G::SW * G::SY; idx += blockDim.x) {
+            int lx = idx % G::SW, ly = idx / G::SW;
             int i = gx0 + lx, j = gy0 + ly;
             if (i < 0 || i >= L.n || j < 0 || j >= L.n) continue;
             int cx[2], cy[2], nx, ny;
@@ -762,7 +767,7 @@ __device__ __forceinline__ void tile_bwd_body(const DevLevel<T>& L, const DevLev
             for (int b = 0; b < ny; ++b)
                 for (int a = 0; a < nx; ++a)
                     acc += T(1) * wy[b] * wx[a] * Ps[(cy[b] - Jlo) * G::PX + (cx[a] - Ilo)];
-            X[idx] = X[idx] + acc;
+            X[ly * G::SX + lx] = X[ly * G::SX + lx] + acc;
         }
     }
     __syncthreads();
@@ -785,15 +790,22 @@ __global__ void __launch_bounds__(kTileThreads) k_tile_bwd(DevLevel<T> L, DevLev
     tile_bwd_body<T, FINE>(L, C, P, blockIdx.x, blockIdx.y, smem_raw);
 }
 
-// Batched forms: one launch covers the same grid depth of many chains.  Block b
-// belongs to the job whose tile range [tile0, tile0 + ntiles) contains b.
 template <typename T>
-__device__ __forceinline__ int find_job(const TileJob<T>* jobs, int njobs, int b)
+__device__ __forceinline__ int job_first(const TileJob<T>& j) { return j.tile0; }
+template <typename T>
+__device__ __forceinline__ int job_first(const LowrankJob<T>& j) { return j.block0; }
+
+// Batched forms: one launch covers the same grid depth of many chains.  Block b
+// belongs to the job whose block range [first, first + count) contains b: found by
+// division when every job has `per` blocks, else by binary search.
+template <typename Job>
+__device__ __forceinline__ int find_job(const Job* jobs, int njobs, int per, int b)
 {
+    if (per > 0) return b / per;
     int lo = 0, hi = njobs - 1;
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
-        if (jobs[mid].tile0 <= b)
+        if (job_first(jobs[mid]) <= b)
             lo = mid;
         else
             hi = mid - 1;
@@ -801,23 +813,37 @@ __device__ __forceinline__ int find_job(const TileJob<T>* jobs, int njobs, int b
     return lo;
 }
 
-template <typename T, bool FINE>
-__global__ void __launch_bounds__(kTileThreads) k_tile_fwd_batch(const TileJob<T>* __restrict__ jobs, int njobs,
-                                                                 int x_zero)
+// the job descriptor into shared memory, 8-byte words in parallel (one round trip)
+template <typename Job>
+__device__ __forceinline__ void load_job(Job& dst, const Job* src)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const TileJob<T>& J = jobs[find_job(jobs, njobs, blockIdx.x)];
-    const int t = blockIdx.x - J.tile0;
-    tile_fwd_body<T, FINE>(*J.L, *J.C, *J.P, x_zero, t % J.L->ntx, t / J.L->ntx, smem_raw);
+    static_assert(sizeof(Job) % 8 == 0, "job descriptors are copied as 8-byte words");
+    const unsigned long long* s = reinterpret_cast<const unsigned long long*>(src);
+    unsigned long long* d = reinterpret_cast<unsigned long long*>(&dst);
+    for (int w = threadIdx.x; w < (int)(sizeof(Job) / 8); w += blockDim.x) d[w] = s[w];
+    __syncthreads();
 }
 
 template <typename T, bool FINE>
-__global__ void __launch_bounds__(kTileThreads) k_tile_bwd_batch(const TileJob<T>* __restrict__ jobs, int njobs)
+__global__ void __launch_bounds__(kTileThreads) k_tile_fwd_batch(const TileJob<T>* __restrict__ jobs, int njobs,
+                                                                 int per, int x_zero)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const TileJob<T>& J = jobs[find_job(jobs, njobs, blockIdx.x)];
+    __shared__ __align__(16) TileJob<T> J;
+    load_job(J, jobs + find_job(jobs, njobs, per, blockIdx.x));
     const int t = blockIdx.x - J.tile0;
-    tile_bwd_body<T, FINE>(*J.L, *J.C, *J.P, t % J.L->ntx, t / J.L->ntx, smem_raw);
+    tile_fwd_body<T, FINE>(J.L, J.C, J.P, x_zero, t % J.L.ntx, t / J.L.ntx, smem_raw);
+}
+
+template <typename T, bool FINE>
+__global__ void __launch_bounds__(kTileThreads) k_tile_bwd_batch(const TileJob<T>* __restrict__ jobs, int njobs,
+                                                                 int per)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(16) TileJob<T> J;
+    load_job(J, jobs + find_job(jobs, njobs, per, blockIdx.x));
+    const int t = blockIdx.x - J.tile0;
+    tile_bwd_body<T, FINE>(J.L, J.C, J.P, t % J.L.ntx, t / J.L.ntx, smem_raw);
 }
 
 // Low-rank step after a fused sweep (Alg. 3 last line, see kernels.cu):
@@ -886,18 +912,11 @@ __global__ void k_lowrank_fused(DevLevel<T> L, DevLevel<T> C, DevProblem P, int 
 
 // batched: job j owns blocks [block0, block0 + nblocks)
 template <typename T>
-__global__ void k_lowrank_fused_batch(const LowrankJob<T>* __restrict__ jobs, int njobs, int down)
+__global__ void k_lowrank_fused_batch(const LowrankJob<T>* __restrict__ jobs, int njobs, int per, int down)
 {
-    int lo = 0, hi = njobs - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (jobs[mid].block0 <= (int)blockIdx.x)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    const LowrankJob<T>& J = jobs[lo];
-    lowrank_fused_body<T>(*J.L, *J.C, *J.P, down, blockIdx.x - J.block0, J.nblocks);
+    __shared__ __align__(16) LowrankJob<T> J;
+    load_job(J, jobs + find_job(jobs, njobs, per, blockIdx.x));
+    lowrank_fused_body<T>(J.L, J.C, J.P, down, blockIdx.x - J.block0, J.nblocks);
 }
 
 // ---------------------------------------------------------------------------
@@ -991,34 +1010,34 @@ cudaError_t tile_prepare_batch()
 }
 
 template <typename T>
-void launch_tile_batch(const TileJob<T>* jobs, int njobs, int nblocks, bool fine, bool bwd, bool x_zero,
+void launch_tile_batch(const TileJob<T>* jobs, int njobs, int per, int nblocks, bool fine, bool bwd, bool x_zero,
                        cudaStream_t st, int& launches)
 {
     if (nblocks <= 0) return;
     if (!bwd) {
         if (fine)
             k_tile_fwd_batch<T, true><<<nblocks, kTileThreads, TileGeom<T, true, false>::smem_bytes(), st>>>(
-                jobs, njobs, x_zero ? 1 : 0);
+                jobs, njobs, per, x_zero ? 1 : 0);
         else
             k_tile_fwd_batch<T, false><<<nblocks, kTileThreads, TileGeom<T, false, false>::smem_bytes(), st>>>(
-                jobs, njobs, x_zero ? 1 : 0);
+                jobs, njobs, per, x_zero ? 1 : 0);
     } else {
         if (fine)
-            k_tile_bwd_batch<T, true><<<nblocks, kTileThreads, TileGeom<T, true, true>::smem_bytes(), st>>>(jobs,
-                                                                                                             njobs);
+            k_tile_bwd_batch<T, true><<<nblocks, kTileThreads, TileGeom<T, true, true>::smem_bytes(), st>>>(
+                jobs, njobs, per);
         else
-            k_tile_bwd_batch<T, false><<<nblocks, kTileThreads, TileGeom<T, false, true>::smem_bytes(), st>>>(jobs,
-                                                                                                               njobs);
+            k_tile_bwd_batch<T, false><<<nblocks, kTileThreads, TileGeom<T, false, true>::smem_bytes(), st>>>(
+                jobs, njobs, per);
     }
     ++launches;
 }
 
 template <typename T>
-void launch_lowrank_batch(const LowrankJob<T>* jobs, int njobs, int nblocks, bool down, cudaStream_t st,
+void launch_lowrank_batch(const LowrankJob<T>* jobs, int njobs, int per, int nblocks, bool down, cudaStream_t st,
                           int& launches)
 {
     if (nblocks <= 0) return;
-    k_lowrank_fused_batch<T><<<nblocks, 256, 0, st>>>(jobs, njobs, down ? 1 : 0);
+    k_lowrank_fused_batch<T><<<nblocks, 256, 0, st>>>(jobs, njobs, per, down ? 1 : 0);
     ++launches;
 }
 
@@ -1030,8 +1049,8 @@ void launch_lowrank_batch(const LowrankJob<T>* jobs, int njobs, int nblocks, boo
     template void launch_lowrank_fused<T>(const DevLevel<T>&, const DevLevel<T>&, const DevProblem&, bool,         \
                                           cudaStream_t, int&);                                                     \
     template cudaError_t tile_prepare_batch<T>();                                                                 \
-    template void launch_tile_batch<T>(const TileJob<T>*, int, int, bool, bool, bool, cudaStream_t, int&);         \
-    template void launch_lowrank_batch<T>(const LowrankJob<T>*, int, int, bool, cudaStream_t, int&);
+    template void launch_tile_batch<T>(const TileJob<T>*, int, int, int, bool, bool, bool, cudaStream_t, int&);    \
+    template void launch_lowrank_batch<T>(const LowrankJob<T>*, int, int, int, bool, cudaStream_t, int&);
 
 MGMC_TILE_INST(float)
 MGMC_TILE_INST(double)

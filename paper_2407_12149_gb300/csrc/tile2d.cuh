@@ -4,20 +4,23 @@
 
 namespace mgmc {
 
-// one chain's grid in a batched tile launch: blocks [tile0, tile0 + ntiles)
+// One chain's grid in a batched tile launch: blocks [tile0, tile0 + ntiles).
+// The descriptors are held by value so that a CTA fetches everything it needs
+// with one parallel copy into shared memory.
 template <typename T>
 struct TileJob {
-    const DevLevel<T>* L;
-    const DevLevel<T>* C;
-    const DevProblem* P;
+    DevLevel<T> L;
+    DevLevel<T> C;
+    DevProblem P;
     int tile0;
+    int ntiles;
 };
 // one chain's grid in a batched low-rank launch: blocks [block0, block0 + nblocks)
 template <typename T>
 struct LowrankJob {
-    const DevLevel<T>* L;
-    const DevLevel<T>* C;
-    const DevProblem* P;
+    DevLevel<T> L;
+    DevLevel<T> C;
+    DevProblem P;
     int block0;
     int nblocks;
 };
@@ -40,11 +43,12 @@ void launch_lowrank_fused(const DevLevel<T>& L, const DevLevel<T>& C, const DevP
 
 template <typename T>
 cudaError_t tile_prepare_batch();
+// per: the common block count of every job (0 if they differ)
 template <typename T>
-void launch_tile_batch(const TileJob<T>* jobs, int njobs, int nblocks, bool fine, bool bwd, bool x_zero,
+void launch_tile_batch(const TileJob<T>* jobs, int njobs, int per, int nblocks, bool fine, bool bwd, bool x_zero,
                        cudaStream_t st, int& launches);
 template <typename T>
-void launch_lowrank_batch(const LowrankJob<T>* jobs, int njobs, int nblocks, bool down, cudaStream_t st,
+void launch_lowrank_batch(const LowrankJob<T>* jobs, int njobs, int per, int nblocks, bool down, cudaStream_t st,
                           int& launches);
 int lowrank_blocks(int rows);
 

@@ -70,7 +70,8 @@ _lib = None
 # every symbol include/mgmc.h declares
 EXPORTS = ("mgmc_config_default", "mgmc_create", "mgmc_point_obs_rows", "mgmc_sample", "mgmc_mean_solve",
            "mgmc_qoi_stats", "mgmc_qoi_stats_noalloc", "mgmc_info", "mgmc_level_n", "mgmc_launches_per_cycle", "mgmc_set_profiling",
-           "mgmc_profile_times", "mgmc_create_batch", "mgmc_sample_batch", "mgmc_destroy", "mgmc_last_error")
+           "mgmc_profile_times", "mgmc_create_batch", "mgmc_sample_batch", "mgmc_get_state", "mgmc_destroy",
+           "mgmc_last_error")
 
 
 def load():
@@ -105,6 +106,7 @@ def load():
                                     ctypes.POINTER(mgmc_allocator), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
     L.mgmc_sample_batch.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64,
                                     ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_void_p]
+    L.mgmc_get_state.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
     L.mgmc_destroy.argtypes = [ctypes.c_void_p]
     for name in EXPORTS:
         if name != "mgmc_last_error":
@@ -199,6 +201,10 @@ def mgmc_create(dim, n, *, n_levels=0, nu1=1, nu2=1, precision=MGMC_FP64, scale_
     return h
 
 
+def mgmc_get_state(h, chain, x_ptr, stream=None):
+    _check(load().mgmc_get_state(h, int(chain), ctypes.c_void_p(x_ptr), _stream_handle(stream)))
+
+
 def mgmc_sample(h, n_steps, seed, step_offset, chain, x_ptr, qoi_ptr, stream=None):
     _check(load().mgmc_sample(h, int(n_steps), int(seed) & (2**64 - 1), int(step_offset), int(chain),
                               ctypes.c_void_p(x_ptr), ctypes.c_void_p(qoi_ptr) if qoi_ptr else None,
@@ -277,13 +283,21 @@ class Sampler:
         return torch.zeros(self.problem.N, dtype=self.dtype, device=f"cuda:{self.device}")
 
     def sample(self, x, n_steps: int, seed: int, step_offset: int = 0, chain: int = 0, qoi=None, stream=None):
-        """Advance x (torch CUDA tensor or pinned/host tensor, modified in place)."""
-        if x.dtype != self.dtype or not x.is_contiguous() or x.numel() != self.problem.N:
+        """Advance x (torch CUDA tensor or pinned/host tensor, modified in place);
+        x = None continues from the state the handle holds (see get_state)."""
+        if x is not None and (x.dtype != self.dtype or not x.is_contiguous() or x.numel() != self.problem.N):
             raise ValueError("x must be a contiguous tensor of N entries in the sampler's precision")
         if qoi is not None and (qoi.dtype != _torch().float64 or qoi.numel() < n_steps):
             raise ValueError("qoi must be a float64 tensor with at least n_steps entries")
-        mgmc_sample(self.h, n_steps, seed, step_offset, chain, x.data_ptr(),
+        mgmc_sample(self.h, n_steps, seed, step_offset, chain, x.data_ptr() if x is not None else None,
                     qoi.data_ptr() if qoi is not None else None, stream)
+        return x
+
+    def get_state(self, x, stream=None):
+        """Copy the state the handle holds into x (device or host tensor)."""
+        if x.dtype != self.dtype or not x.is_contiguous() or x.numel() != self.problem.N:
+            raise ValueError("x must be a contiguous tensor of N entries in the sampler's precision")
+        mgmc_get_state(self.h, 0, x.data_ptr(), stream)
         return x
 
     def mean_solve(self, x, rtol=1e-10, max_cycles=200, stream=None):
@@ -354,14 +368,23 @@ class BatchSampler:
         return [torch.zeros(p.N, dtype=self.dtype, device=f"cuda:{self.device}") for p in self.problems]
 
     def sample(self, xs, n_steps, seed, step_offset=0, qoi=None, stream=None):
+        """xs: one device tensor per chain (modified in place), or None to continue
+        from the states the handle holds (see get_state)."""
         n = len(self.problems)
-        ptrs = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+        ptrs = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs]) if xs is not None else None
         if qoi is not None and (qoi.dtype != _torch().float64 or qoi.numel() < n * n_steps):
             raise ValueError("qoi must be a float64 device tensor with n_chains * n_steps entries")
         _check(load().mgmc_sample_batch(self.h, int(n_steps), int(seed) & (2**64 - 1), int(step_offset), ptrs,
                                         ctypes.c_void_p(qoi.data_ptr()) if qoi is not None else None,
                                         _stream_handle(stream)))
         return xs
+
+    def get_state(self, c, x, stream=None):
+        """Copy chain c's state into x (device or host tensor of N_c entries)."""
+        if x.dtype != self.dtype or not x.is_contiguous() or x.numel() != self.problems[c].N:
+            raise ValueError("x must be a contiguous tensor of N entries in the sampler's precision")
+        mgmc_get_state(self.h, c, x.data_ptr(), stream)
+        return x
 
     def launches_per_cycle(self):
         return mgmc_launches_per_cycle(self.h)

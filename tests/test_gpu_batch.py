@@ -62,3 +62,37 @@ def test_batch_chain_matches_oracle(torch_mod):
         xg = xs[c].cpu().numpy()
         rms = np.sqrt(np.mean(xo ** 2))
         assert np.all(np.abs(xg - xo) <= 1e-11 * np.maximum(np.abs(xo), rms))
+
+
+def test_resume_and_get_state_reproduce_one_run(torch_mod):
+    """x = None continues from the held state: split runs equal one run bit for bit."""
+    torch = torch_mod
+    from paper_2407_12149_gb300.mgmc import BatchSampler, Sampler
+    ps = _problems()[:4]
+    b1, b2 = BatchSampler(ps, precision="fp32"), BatchSampler(ps, precision="fp32")
+    xa, xb = b1.zeros(), b2.zeros()
+    qa = torch.zeros(len(ps) * 5, dtype=torch.float64, device="cuda")
+    b1.sample(xa, 5, 9, step_offset=3, qoi=qa)
+    b2.sample(xb, 2, 9, step_offset=3)
+    qb = torch.zeros(len(ps) * 3, dtype=torch.float64, device="cuda")
+    b2.sample(None, 3, 9, step_offset=5, qoi=qb)
+    for c, p in enumerate(ps):
+        got = torch.empty(p.N, dtype=torch.float32, device="cuda")
+        b2.get_state(c, got)
+        torch.cuda.synchronize()
+        assert torch.equal(got, xa[c]), f"chain {c}"
+        assert torch.equal(qb[c * 3:(c + 1) * 3], qa[c * 5 + 2:(c + 1) * 5]), f"chain {c} qoi"
+        host = torch.empty(p.N, dtype=torch.float32)
+        b2.get_state(c, host)
+        assert torch.equal(host, xa[c].cpu())
+    # single-chain handle
+    p = ps[1]
+    s1, s2 = Sampler(p, precision="fp64"), Sampler(p, precision="fp64")
+    x1, x2 = s1.zeros(), s2.zeros()
+    s1.sample(x1, 4, 5, chain=2)
+    s2.sample(x2, 1, 5, chain=2)
+    s2.sample(None, 3, 5, step_offset=1, chain=2)
+    y = torch.empty_like(x1)
+    s2.get_state(y)
+    torch.cuda.synchronize()
+    assert torch.equal(y, x1)
