@@ -107,6 +107,7 @@ struct mgmc_ctx {
     std::vector<mgmc_ctx*> sub;
     int n_depth = 0;
     std::vector<void*> jobs_tile, jobs_lrd, jobs_lru;
+    std::vector<void*> maps_fwd, maps_bwd;   // TileMaps per tile job, per depth
     std::vector<int> njob_tile, nblk_tile, njob_lrd, nblk_lrd, njob_lru, nblk_lru;
     std::vector<int> per_tile, per_lrd, per_lru;
     void* jobs_coarse = nullptr;
@@ -338,8 +339,7 @@ mgmc_status build_device_levels(mgmc_ctx* h, const HostProblem& hp)
             D.hT = upload(h, ht, st);
             if (st != MGMC_OK) return fail(st, "device upload failed");
         }
-        cudaError_t e = tile_prepare<T>();
-        if (e != cudaSuccess) return fail(MGMC_ERR_CUDA, std::string("tile kernel set-up: ") + cudaGetErrorString(e));
+
     }
     // descriptors of all grids (the single-CTA kernel reads 0..top; batched launches any)
     size_t dbytes = sizeof(DevLevel<T>) * (size_t)hp.n_levels;
@@ -358,8 +358,8 @@ void enqueue_cycle_batch(mgmc_ctx* h, cudaStream_t s, int& launches)
     const bool prof = h->profile && h->n_depth > 0;
     for (int d = 0; d < h->n_depth; ++d) {
         if (prof && d == 0) cudaEventRecordWithFlags(h->ev[0], s, cudaEventRecordExternal);
-        launch_tile_batch<T>((const TileJob<T>*)h->jobs_tile[d], h->njob_tile[d], h->per_tile[d], h->nblk_tile[d],
-                             d == 0, false, d > 0, s, launches);
+        launch_tile_batch<T>((const TileJob<T>*)h->jobs_tile[d], (const TileMaps*)h->maps_fwd[d], h->njob_tile[d],
+                             h->per_tile[d], h->nblk_tile[d], d == 0, false, d > 0, s, launches);
         if (prof && d == 0) cudaEventRecordWithFlags(h->ev[1], s, cudaEventRecordExternal);
         launch_lowrank_batch<T>((const LowrankJob<T>*)h->jobs_lrd[d], h->njob_lrd[d], h->per_lrd[d], h->nblk_lrd[d],
                                 true, s, launches);
@@ -372,8 +372,8 @@ void enqueue_cycle_batch(mgmc_ctx* h, cudaStream_t s, int& launches)
     launch_coarse_batch<T>((const CoarseJob<T>*)h->jobs_coarse, nc, coarse_threads, h->batch_coarse_smem, s, launches);
     for (int d = h->n_depth - 1; d >= 0; --d) {
         if (prof && d == 0) cudaEventRecordWithFlags(h->ev[2], s, cudaEventRecordExternal);
-        launch_tile_batch<T>((const TileJob<T>*)h->jobs_tile[d], h->njob_tile[d], h->per_tile[d], h->nblk_tile[d],
-                             d == 0, true, false, s, launches);
+        launch_tile_batch<T>((const TileJob<T>*)h->jobs_tile[d], (const TileMaps*)h->maps_bwd[d], h->njob_tile[d],
+                             h->per_tile[d], h->nblk_tile[d], d == 0, true, false, s, launches);
         if (prof && d == 0) cudaEventRecordWithFlags(h->ev[3], s, cudaEventRecordExternal);
         launch_lowrank_batch<T>((const LowrankJob<T>*)h->jobs_lru[d], h->njob_lru[d], h->per_lru[d], h->nblk_lru[d],
                                 false, s, launches);
@@ -761,6 +761,7 @@ mgmc_status mgmc_sample(mgmc_handle h, int64_t n_steps, uint64_t seed, uint64_t 
         CUDA_TRY(cudaStreamSynchronize(s));
         CycleState csh;
         CUDA_TRY(cudaMemcpy(&csh, h->cs, sizeof(csh), cudaMemcpyDeviceToHost));
+        if (csh.status == 2) return fail(MGMC_ERR_TIMEOUT, "a tile kernel's staging wait gave up");
         if (csh.status) return fail(MGMC_ERR_NUMERIC, "non-finite QoI produced");
     }
     return MGMC_OK;
@@ -856,6 +857,7 @@ mgmc_status build_batch_tables(mgmc_ctx* h)
     h->n_depth = depth;
     for (int d = 0; d < depth; ++d) {
         std::vector<TileJob<T>> tj;
+        std::vector<TileMaps> mf, mb;
         std::vector<LowrankJob<T>> ld, lu;
         int tiles = 0, bd = 0, bu = 0;
         for (mgmc_ctx* c : chains) {
@@ -868,6 +870,10 @@ mgmc_status build_batch_tables(mgmc_ctx* h)
             const int nty = (Lh.n + TY - 1) / TY;
             tj.push_back({Lh, Ch, c->P, tiles, Lh.ntx * nty});
             tiles += Lh.ntx * nty;
+            mf.emplace_back();
+            mb.emplace_back();
+            if (!make_tile_maps<T>(Lh, Ch, false, &mf.back()) || !make_tile_maps<T>(Lh, Ch, true, &mb.back()))
+                return fail(MGMC_ERR_CUDA, "TMA descriptor encoding failed");
             if (c->m > 0) {
                 int rd = std::max(Lh.g_rows[0], Lh.h_rows);
                 ld.push_back({Lh, Ch, c->P, bd, lowrank_blocks(rd)});
@@ -887,6 +893,8 @@ mgmc_status build_batch_tables(mgmc_ctx* h)
         h->per_lrd.push_back(common(ld, [](const LowrankJob<T>& j) { return j.nblocks; }));
         h->per_lru.push_back(common(lu, [](const LowrankJob<T>& j) { return j.nblocks; }));
         h->jobs_tile.push_back(upload(h, tj, st));
+        h->maps_fwd.push_back(upload(h, mf, st));
+        h->maps_bwd.push_back(upload(h, mb, st));
         h->njob_tile.push_back((int)tj.size());
         h->nblk_tile.push_back(tiles);
         h->jobs_lrd.push_back(upload(h, ld, st));

@@ -505,6 +505,8 @@ template <typename T>
 __global__ void __launch_bounds__(kCoarseBatchMaxThreads) k_coarse_cycle_batch(const CoarseJob<T>* __restrict__ jobs)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_launch_dependents();
+    pdl_wait();
     const CoarseJob<T>& J = jobs[blockIdx.x];
     coarse_body<T, 2>(J.levels, J.top, J.is_finest, *J.P, J.chol, J.n0, 1, 1, smem_raw);
 }
@@ -514,6 +516,8 @@ template <typename T>
 __global__ void k_qoi_batch(const QoiJob<T>* __restrict__ jobs)
 {
     __shared__ double part[256];
+    pdl_launch_dependents();
+    pdl_wait();
     const QoiJob<T>& J = jobs[blockIdx.x];
     double acc = 0.0;
     for (int t = threadIdx.x; t < J.n_qoi; t += blockDim.x) acc += J.q_w[t] * (double)J.x[J.q_site[t]];
@@ -558,14 +562,14 @@ template <typename T>
 void launch_coarse_batch(const CoarseJob<T>* jobs, int n, int threads, size_t smem_bytes, cudaStream_t st,
                          int& launches)
 {
-    k_coarse_cycle_batch<T><<<n, threads, smem_bytes, st>>>(jobs);
+    launch_pdl(k_coarse_cycle_batch<T>, dim3((unsigned)n), dim3((unsigned)threads), smem_bytes, st, jobs);
     ++launches;
 }
 
 template <typename T>
 void launch_qoi_batch(const QoiJob<T>* jobs, int n, cudaStream_t st, int& launches)
 {
-    k_qoi_batch<T><<<n, 256, 0, st>>>(jobs);
+    launch_pdl(k_qoi_batch<T>, dim3((unsigned)n), dim3(256), 0, st, jobs);
     ++launches;
 }
 

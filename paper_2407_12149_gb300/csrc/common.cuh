@@ -188,6 +188,19 @@ __device__ __forceinline__ double lowrank_normal(const CycleState& cs, int level
     return (double)((k & 1) ? z1 : z0);
 }
 
+// Programmatic dependent launch (PTX griddepcontrol): kernels of the captured
+// cycle are launched with programmatic stream serialisation, so a kernel's CTAs
+// may start while its predecessor drains.  Every such kernel lets its dependents
+// launch as soon as its own CTAs are running and calls pdl_wait() in every CTA
+// before it touches anything an earlier kernel wrote (the wait returns once the
+// predecessor has completed and its memory is visible; since every kernel waits,
+// completion is transitive along the chain).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents()
+{
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
 // 1/a and sqrt(a) of a positive FP32 diagonal from one reciprocal square root
 // (relative error ~2e-7, below the FP32 rounding of the state update)
 __device__ __forceinline__ void inv_and_sqrt(float a, float& inv, float& sq)
@@ -195,6 +208,24 @@ __device__ __forceinline__ void inv_and_sqrt(float a, float& inv, float& sq)
     float r = rsqrtf(a);
     inv = r * r;
     sq = a * r;
+}
+
+// host: launch with programmatic stream serialisation (see pdl_wait)
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
 }  // namespace mgmc

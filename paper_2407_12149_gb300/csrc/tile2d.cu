@@ -22,6 +22,9 @@
 // parity colours in the order (0,0), (1,1), (0,1), (1,0).  The per-site
 // arithmetic is the same as in stencil.cuh (FP64 plain form, FP32 correction
 // form) in the same order of operations.
+#include <cstring>
+#include <mutex>
+
 #include "kernels.cuh"
 #include "tile2d.cuh"
 
@@ -42,8 +45,6 @@ struct Vec<double> {
     static constexpr int N = 2;
 };
 
-constexpr int kTileThreads = 256;
-
 }  // namespace
 
 template <typename T, bool FINE, bool BWD>
@@ -52,72 +53,50 @@ struct TileGeom {
     static constexpr int TY = TileShape<T, FINE>::TY;
     static constexpr int VEC = Vec<T>::N;
     static constexpr int NC = FINE ? 2 : 4;
+    // threads per CTA (256 measured faster than 384 on the 5-point grid, whose two
+    // colour phases have ~650 work items per tile; ~250 per phase on 9-point grids)
+    static constexpr int NT = 256;
     // rings of state staged around the tile: backward NC (the last colour ends on
     // the tile); forward NC + 2 (the last colour must also cover ring 2 because the
     // residual on ring 1 -- the coarse patches reach one site past the tile -- reads it)
     static constexpr int R = BWD ? NC : NC + 2;
-    static constexpr int RX = (R + VEC - 1) / VEC * VEC;  // the same along x, in whole vectors
+    static constexpr int RX = (R + VEC - 1) / VEC * VEC;  // the same along x, in whole 16-byte vectors
     static constexpr int SW = TX + 2 * RX;                  // staged columns
-    // row pitch in shared memory: the FP32 9-point tiles get 4 or 12 extra columns so
-    // that the float4 rows of neighbouring work items (two grid rows apart) fall on
-    // different bank groups
+    // row pitch in shared memory (= the TMA box width): the FP32 9-point tiles get 4
+    // or 12 extra columns so that the float4 rows of neighbouring work items (two
+    // grid rows apart) fall on different bank groups
     static constexpr int PAD = (sizeof(T) == 4 && !FINE) ? (BWD ? 12 : 4) : 0;
     static constexpr int SX = SW + PAD;
     static constexpr int SY = TY + 2 * R;
     static constexpr int NCOEF = FINE ? 1 : 5;
     static constexpr int NFLD = 1 + NCOEF + (FINE ? 0 : 1);  // x, coefficients, fdense
+    // field stride in elements: every field (a TMA destination) starts on 128 bytes
+    static constexpr int FS = (SX * SY * (int)sizeof(T) + 127) / 128 * 128 / (int)sizeof(T);
     static constexpr int RW4 = TX + 4;                      // FP32 residual row: whole 4-site groups
     static constexpr int RES = sizeof(T) == 4 ? RW4 * (TY + 1) : (TX + 1) * (TY + 1);  // residual on tile + high ring
-    static constexpr int PX = SW / 2 + 2;                   // coarse psi tile (backward)
+    // backward: coarse psi around the tile, columns cx0 .. cx0 + PX - 1 with
+    // cx0 = (gx0 >> 1) - 1; the box starts POFF columns earlier, on a 16-byte boundary
+    // (cx0 + 4 = x0 / 2 + 3 - RX / 2 and x0 / 2 is a multiple of the vector width)
+    static constexpr int PX = SW / 2 + 2;
     static constexpr int PY = SY / 2 + 2;
-    static constexpr size_t smem_bytes()
-    {
-        return sizeof(T) * ((size_t)NFLD * SX * SY + (BWD ? (size_t)PX * PY : (size_t)RES));
-    }
+    static constexpr int POFF = ((3 - RX / 2) % VEC + VEC) % VEC;
+    static constexpr int PXA = (PX + POFF + VEC - 1) / VEC * VEC;
+    static constexpr int PSZ = (PXA * PY * (int)sizeof(T) + 127) / 128 * 128 / (int)sizeof(T);
+    // tensor maps: x source, coefficient fields, fdense (9-point), psi (backward)
+    static constexpr int NMAP = NFLD + (BWD ? 1 : 0);
+    // stage buffers: two on the 5-point grid (tile k + 1 is copied while tile k is
+    // computed), one on the 9-point grids (7 fields; three CTAs per SM overlap instead)
+    static constexpr int NSTAGE = FINE ? 2 : 1;
+    static constexpr int STAGE = NFLD * FS + (BWD ? PSZ : 0);  // elements per stage buffer
+    static constexpr unsigned BOX_BYTES = (unsigned)(SX * SY * sizeof(T));
+    static constexpr unsigned PSI_BYTES = (unsigned)(PXA * PY * sizeof(T));
+    // TMA: box corners x0 - RX + 4 and (psi) x0 / 2 - RX / 2 + 3 - POFF must be multiples of
+    // 16 bytes, box rows (SX, PXA) whole 16-byte vectors, boxes at most 256 per side
+    static_assert(RX % VEC == 0 && TX % (2 * VEC) == 0 && SX % VEC == 0 && PXA % VEC == 0, "TMA alignment");
+    static_assert(SX <= 256 && SY <= 256 && PXA <= 256 && PY <= 256, "TMA box size");
 };
 
 namespace {
-
-// Asynchronous 16-byte global -> shared copies (cp.async, Sec. "asynchronous
-// copy" of the PTX ISA): every copy of the staged tile is in flight at once and
-// a source size of 0 zero-fills the destination.
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid)
-{
-    unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 16 : 0)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid)
-{
-    unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 4 : 0)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* dst, const void* src, bool valid)
-{
-    unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 8 : 0)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-
-// dst[ly * SX + lx] <- src at interior (gx0 + lx, gy0 + ly); zero outside the padded
-// array or when src is NULL.  Issues the copies only: cp_async_wait_all() and a CTA
-// barrier make them visible.  `any` is a valid global address used as the (unread)
-// source of zero-filled copies.
-template <typename T, int SW, int SX, int SY>
-__device__ __forceinline__ void stage(T* dst, const T* src, const DevLevel<T>& L, int gx0, int gy0, const T* any)
-{
-    constexpr int VN = Vec<T>::N;
-    constexpr int NV = SW / VN;
-    for (int idx = threadIdx.x; idx < NV * SY; idx += kTileThreads) {
-        int vx = idx % NV, ly = idx / NV;
-        int i = gx0 + vx * VN, j = gy0 + ly;
-        bool ok = src && j >= -1 && j <= L.n && i + 4 >= 0 && i + 4 + VN <= L.pitch;
-        const T* g = ok ? src + ((long long)L.pitch * (j + 1) + (i + 4)) : any;
-        cp_async16(dst + ly * SX + vx * VN, g, ok);
-    }
-}
 
 // --- per-site arithmetic on the staged tile (same operations as stencil.cuh) ---
 template <int SX>
@@ -470,7 +449,7 @@ __device__ __forceinline__ void tile_phase(const DevLevel<T>& L, const CycleStat
                                            const T* F, int x0, int y0, unsigned slot)
 {
     constexpr int SX = G::SX;
-    constexpr int SXY = G::SX * G::SY;
+    constexpr int SXY = G::FS;  // stride between the staged fields
     constexpr int colour = FINE ? (BWD ? 1 - P : P) : (BWD ? colour_seq4(G::NC - 1 - P) : colour_seq4(P));
     constexpr int rp = BWD ? G::NC - 1 - P : G::NC + 1 - P;
     // groups gq = GQ0 .. (TX + rp - 1) / 4 relative to x0 / 4, GQ0 = floor(-rp / 4)
@@ -484,7 +463,7 @@ __device__ __forceinline__ void tile_phase(const DevLevel<T>& L, const CycleStat
     const int n = L.n;
     const int nq = (n + 3) >> 2;
     const int q0 = x0 >> 2;
-    for (int it = threadIdx.x; it < NQ * NR; it += kTileThreads) {
+    for (int it = threadIdx.x; it < NQ * NR; it += G::NT) {
         const int gq = it % NQ + GQ0;
         const int dy = DY0 + STEP * (it / NQ);
         const int j = y0 + dy;
@@ -564,28 +543,20 @@ __device__ __forceinline__ void tile_store(const DevLevel<T>& L, T* dst, const T
 
 }  // namespace
 
+// Forward tile (Alg. 1 pre-smoothing + restriction) on a staged stage buffer:
+// X (state, zero-filled here when the sweep starts from psi = 0), Cf (operator
+// fields), F (dense right-hand side, 9-point grids), Rr (residual scratch).
 template <typename T, bool FINE>
-__device__ __forceinline__ void tile_fwd_body(const DevLevel<T>& L, const DevLevel<T>& C, const DevProblem& P,
-                                              int x_zero, int bx, int by, unsigned char* smem_raw)
+__device__ __forceinline__ void tile_fwd_compute(const DevLevel<T>& L, const DevLevel<T>& C, const CycleState& cs,
+                                                 int x_zero, int bx, int by, T* X, const T* Cf, const T* F, T* Rr)
 {
     using G = TileGeom<T, FINE, false>;
-    T* X = reinterpret_cast<T*>(smem_raw);
-    T* Cf = X + G::SX * G::SY;
-    T* F = Cf + G::NCOEF * G::SX * G::SY;
-    T* Rr = F + (FINE ? 0 : G::SX * G::SY);
     const int x0 = bx * G::TX, y0 = by * G::TY;
     const int gx0 = x0 - G::RX, gy0 = y0 - G::R;
-    stage<T, G::SW, G::SX, G::SY>(X, x_zero ? nullptr : L.x, L, gx0, gy0, L.x);
-    if (FINE) {
-        stage<T, G::SW, G::SX, G::SY>(Cf, L.diag, L, gx0, gy0, L.x);
-    } else {
-        for (int t = 0; t < G::NCOEF; ++t)
-            stage<T, G::SW, G::SX, G::SY>(Cf + t * G::SX * G::SY, L.coef + (long long)t * L.alloc, L, gx0, gy0, L.x);
-        stage<T, G::SW, G::SX, G::SY>(F, L.f, L, gx0, gy0, L.x);
+    if (x_zero) {
+        for (int idx = threadIdx.x; idx < G::SX * G::SY; idx += G::NT) X[idx] = T(0);
+        __syncthreads();
     }
-    const CycleState cs = *P.cs;  // read while the copies are in flight
-    cp_async_wait_all();
-    __syncthreads();
     tile_sweep<T, FINE, false, G>(L, cs, X, Cf, F, x0, y0, 0u);
     const int tile = by * L.ntx + bx;
     tile_zparts<T, G>(L, X, tile);
@@ -596,7 +567,7 @@ __device__ __forceinline__ void tile_fwd_body(const DevLevel<T>& L, const DevLev
         constexpr int RW = G::RW4;
         constexpr int NGX = RW / 4;
         float* R4 = (float*)Rr;
-        for (int idx = threadIdx.x; idx < NGX * (G::TY + 1); idx += kTileThreads) {
+        for (int idx = threadIdx.x; idx < NGX * (G::TY + 1); idx += G::NT) {
             const int gx = idx % NGX, ry = idx / NGX;
             const int i = x0 + 4 * gx, j = y0 + ry;
             const int lb = (ry + G::R) * G::SX + (4 * gx + G::RX);
@@ -606,7 +577,7 @@ __device__ __forceinline__ void tile_fwd_body(const DevLevel<T>& L, const DevLev
                     const float4 a = ax4_fine<G::SX>((const float*)X, (const float*)Cf, lb, (float)L.woff);
                     r = make_float4(0.0f - a.x, 0.0f - a.y, 0.0f - a.z, 0.0f - a.w);
                 } else {
-                    r = res4_9<G::SX, G::SX * G::SY>((const float*)X, (const float*)Cf, (const float*)F, lb);
+                    r = res4_9<G::SX, G::FS>((const float*)X, (const float*)Cf, (const float*)F, lb);
                 }
                 if (i + 1 >= L.n) r.y = 0.f;
                 if (i + 2 >= L.n) r.z = 0.f;
@@ -617,7 +588,7 @@ __device__ __forceinline__ void tile_fwd_body(const DevLevel<T>& L, const DevLev
         __syncthreads();
         // restriction of two coarse sites per item: f_c = sum_p w(p) r(2I + p),
         // fine columns 2I .. 2I + 4 of three rows
-        for (int idx = threadIdx.x; idx < (G::TX / 4) * (G::TY / 2); idx += kTileThreads) {
+        for (int idx = threadIdx.x; idx < (G::TX / 4) * (G::TY / 2); idx += G::NT) {
             const int I = I0 + 2 * (idx % (G::TX / 4)), J = J0 + idx / (G::TX / 4);
             if (I >= C.n || J >= C.n) continue;
             const int cb = (2 * J - y0) * RW + (2 * I - x0);
@@ -645,7 +616,7 @@ __device__ __forceinline__ void tile_fwd_body(const DevLevel<T>& L, const DevLev
         }
     } else {
         constexpr int RW = G::TX + 1;
-        for (int idx = threadIdx.x; idx < G::RES; idx += blockDim.x) {
+        for (int idx = threadIdx.x; idx < G::RES; idx += G::NT) {
             int rx = idx % RW, ry = idx / RW;
             int i = x0 + rx, j = y0 + ry;
             T r = T(0);
@@ -654,13 +625,13 @@ __device__ __forceinline__ void tile_fwd_body(const DevLevel<T>& L, const DevLev
                 if (FINE)
                     r = T(0) - Ax_fine<G::SX>(X, Cf, l, L.woff);
                 else
-                    r = F[l] - Ax_9<G::SX, G::SX * G::SY>(X, Cf, l);
+                    r = F[l] - Ax_9<G::SX, G::FS>(X, Cf, l);
             }
             Rr[idx] = r;
         }
         __syncthreads();
         // restriction onto the coarse sites of the tile: f_c = sum_p w(p) r(2I + p)
-        for (int idx = threadIdx.x; idx < (G::TX / 2) * (G::TY / 2); idx += blockDim.x) {
+        for (int idx = threadIdx.x; idx < (G::TX / 2) * (G::TY / 2); idx += G::NT) {
             int I = I0 + idx % (G::TX / 2), J = J0 + idx / (G::TX / 2);
             if (I >= C.n || J >= C.n) continue;
             T acc = T(0);
@@ -675,39 +646,17 @@ __device__ __forceinline__ void tile_fwd_body(const DevLevel<T>& L, const DevLev
     tile_store<T, G>(L, L.x2, X, x0, y0);
 }
 
+// Backward tile (prolongation + Alg. 1 post-smoothing) on a staged stage buffer:
+// X (theta*' of the forward pass), Cf, F, Ps (coarse psi box, origin POFF columns
+// before cx0 = (gx0 >> 1) - 1, row cy0 = (gy0 >> 1) - 1).
 template <typename T, bool FINE>
-__device__ __forceinline__ void tile_bwd_body(const DevLevel<T>& L, const DevLevel<T>& C, const DevProblem& P, int bx,
-                                              int by, unsigned char* smem_raw)
+__device__ __forceinline__ void tile_bwd_compute(const DevLevel<T>& L, const CycleState& cs, int bx, int by, T* X,
+                                                 const T* Cf, const T* F, const T* Ps)
 {
     using G = TileGeom<T, FINE, true>;
-    T* X = reinterpret_cast<T*>(smem_raw);
-    T* Cf = X + G::SX * G::SY;
-    T* F = Cf + G::NCOEF * G::SX * G::SY;
-    T* Ps = F + (FINE ? 0 : G::SX * G::SY);
     const int x0 = bx * G::TX, y0 = by * G::TY;
     const int gx0 = x0 - G::RX, gy0 = y0 - G::R;
-    stage<T, G::SW, G::SX, G::SY>(X, L.x2, L, gx0, gy0, L.x);
-    if (FINE) {
-        stage<T, G::SW, G::SX, G::SY>(Cf, L.diag, L, gx0, gy0, L.x);
-    } else {
-        for (int t = 0; t < G::NCOEF; ++t)
-            stage<T, G::SW, G::SX, G::SY>(Cf + t * G::SX * G::SY, L.coef + (long long)t * L.alloc, L, gx0, gy0, L.x);
-        stage<T, G::SW, G::SX, G::SY>(F, L.f, L, gx0, gy0, L.x);
-    }
-    // coarse psi around the tile (ghost indices -1 and n_c read the zero ring)
-    const int Ilo = (gx0 >> 1) - 1, Jlo = (gy0 >> 1) - 1;
-    for (int idx = threadIdx.x; idx < G::PX * G::PY; idx += kTileThreads) {
-        int I = Ilo + idx % G::PX, J = Jlo + idx / G::PX;
-        bool ok = J >= -1 && J <= C.n && I + 4 >= 0 && I + 4 < C.pitch;
-        const T* g = ok ? C.x + ((long long)C.pitch * (J + 1) + (I + 4)) : C.x;
-        if (sizeof(T) == 4)
-            cp_async4(Ps + idx, g, ok);
-        else
-            cp_async8(Ps + idx, g, ok);
-    }
-    const CycleState cs = *P.cs;  // read while the copies are in flight
-    cp_async_wait_all();
-    __syncthreads();
+    const int Ilo = (gx0 >> 1) - 1 - G::POFF, Jlo = (gy0 >> 1) - 1;
     // theta' + P psi on the staged region (interior sites only)
     if constexpr (sizeof(T) == 4) {
         // FP32: one 4-site group (i = gx0 + 4v even) per item; fine site i + c takes
@@ -716,7 +665,7 @@ __device__ __forceinline__ void tile_bwd_body(const DevLevel<T>& L, const DevLev
         constexpr int NV = G::SW / 4;
         float* Xf = (float*)X;
         const float* Pf = (const float*)Ps;
-        for (int idx = threadIdx.x; idx < NV * G::SY; idx += kTileThreads) {
+        for (int idx = threadIdx.x; idx < NV * G::SY; idx += G::NT) {
             const int v = idx % NV, ly = idx / NV;
             const int i = gx0 + 4 * v, j = gy0 + ly;
             if (j < 0 || j >= L.n || i + 3 < 0 || i >= L.n) continue;
@@ -727,8 +676,8 @@ __device__ __forceinline__ void tile_bwd_body(const DevLevel<T>& L, const DevLev
             float p0[3], p1[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                p0[c] = Pf[pr0 * G::PX + 2 * v + c];
-                p1[c] = odd ? 0.f : Pf[(pr0 + 1) * G::PX + 2 * v + c];
+                p0[c] = Pf[pr0 * G::PXA + G::POFF + 2 * v + c];
+                p1[c] = odd ? 0.f : Pf[(pr0 + 1) * G::PXA + G::POFF + 2 * v + c];
             }
             float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
             a0 += 1.0f * wy * 0.5f * p0[0];
@@ -753,7 +702,7 @@ __device__ __forceinline__ void tile_bwd_body(const DevLevel<T>& L, const DevLev
             sts4(Xf + ly * G::SX + 4 * v, x);
         }
     } else {
-        for (int idx = threadIdx.x; idx < G::SW * G::SY; idx += blockDim.x) {
+        for (int idx = threadIdx.x; idx < G::SW * G::SY; idx += G::NT) {
             int lx = idx % G::SW, ly = idx / G::SW;
             int i = gx0 + lx, j = gy0 + ly;
             if (i < 0 || i >= L.n || j < 0 || j >= L.n) continue;
@@ -766,7 +715,7 @@ __device__ __forceinline__ void tile_bwd_body(const DevLevel<T>& L, const DevLev
             T acc = T(0);
             for (int b = 0; b < ny; ++b)
                 for (int a = 0; a < nx; ++a)
-                    acc += T(1) * wy[b] * wx[a] * Ps[(cy[b] - Jlo) * G::PX + (cx[a] - Ilo)];
+                    acc += T(1) * wy[b] * wx[a] * Ps[(cy[b] - Jlo) * G::PXA + (cx[a] - Ilo)];
             X[ly * G::SX + lx] = X[ly * G::SX + lx] + acc;
         }
     }
@@ -776,28 +725,73 @@ __device__ __forceinline__ void tile_bwd_body(const DevLevel<T>& L, const DevLev
     tile_store<T, G>(L, L.x, X, x0, y0);
 }
 
-template <typename T, bool FINE>
-__global__ void __launch_bounds__(kTileThreads) k_tile_fwd(DevLevel<T> L, DevLevel<T> C, DevProblem P, int x_zero)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    tile_fwd_body<T, FINE>(L, C, P, x_zero, blockIdx.x, blockIdx.y, smem_raw);
-}
 
-template <typename T, bool FINE>
-__global__ void __launch_bounds__(kTileThreads) k_tile_bwd(DevLevel<T> L, DevLevel<T> C, DevProblem P)
+// ---------------------------------------------------------------------------
+// TMA staging (PTX cp.async.bulk.tensor, mbarrier).  Each field of a stage is
+// one 2D tiled bulk tensor copy of the padded array, the box anchored at the
+// staged region's corner in padded coordinates; the parts of a box outside the
+// array are filled with zeros -- the ghost ring's value.  The copies of a stage
+// complete on one mbarrier (arrive + expected transaction bytes).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    tile_bwd_body<T, FINE>(L, C, P, blockIdx.x, blockIdx.y, smem_raw);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(bar)) : "memory");
 }
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// wait for the completion of the barrier phase of the given parity; false after 1 s
+constexpr unsigned long long kWaitNs = 1000000000ull;
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity)
+{
+    if (mbar_test(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (unsigned it = 1; it < (1u << 30); ++it) {
+        if (mbar_test(bar, parity)) return true;
+        if ((it & 63) == 0 && global_ns() - t0 > kWaitNs) return false;
+    }
+    return false;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, unsigned long long* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];\n" ::"r"(smem_addr(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
+// orders this thread's generic-proxy accesses of shared memory before later
+// async-proxy (TMA) writes to it
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
 
 template <typename T>
 __device__ __forceinline__ int job_first(const TileJob<T>& j) { return j.tile0; }
 template <typename T>
 __device__ __forceinline__ int job_first(const LowrankJob<T>& j) { return j.block0; }
 
-// Batched forms: one launch covers the same grid depth of many chains.  Block b
-// belongs to the job whose block range [first, first + count) contains b: found by
-// division when every job has `per` blocks, else by binary search.
+// Batched launches cover the same grid depth of many chains.  Item b (a tile or a
+// block) belongs to the job whose range [first, first + count) contains it: found
+// by division when every job has `per` items, else by binary search.
 template <typename Job>
 __device__ __forceinline__ int find_job(const Job* jobs, int njobs, int per, int b)
 {
@@ -824,26 +818,144 @@ __device__ __forceinline__ void load_job(Job& dst, const Job* src)
     __syncthreads();
 }
 
-template <typename T, bool FINE>
-__global__ void __launch_bounds__(kTileThreads) k_tile_fwd_batch(const TileJob<T>* __restrict__ jobs, int njobs,
-                                                                 int per, int x_zero)
+constexpr int kHdrBytes = (int)((sizeof(TileJob<double>) + 127) / 128 * 128);
+static_assert(sizeof(TileJob<float>) <= (size_t)kHdrBytes, "tile job header slot");
+
+template <typename T, bool FINE, bool BWD>
+constexpr size_t tile_smem_bytes()
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ __align__(16) TileJob<T> J;
-    load_job(J, jobs + find_job(jobs, njobs, per, blockIdx.x));
-    const int t = blockIdx.x - J.tile0;
-    tile_fwd_body<T, FINE>(J.L, J.C, J.P, x_zero, t % J.L.ntx, t / J.L.ntx, smem_raw);
+    using G = TileGeom<T, FINE, BWD>;
+    return 2 * (size_t)kHdrBytes + 128 + sizeof(T) * ((size_t)G::NSTAGE * G::STAGE + (BWD ? 0 : (size_t)G::RES));
 }
 
-template <typename T, bool FINE>
-__global__ void __launch_bounds__(kTileThreads) k_tile_bwd_batch(const TileJob<T>* __restrict__ jobs, int njobs,
-                                                                 int per)
+// Persistent tile kernel of one grid depth of every chain.  Tile order: with
+// cpj > 0 every chain owns cpj consecutive CTAs, which stride through its tiles
+// in row order (the CTAs of a chain work on neighbouring tiles at the same time,
+// so halo rows are read from L2, and each CTA loads one job descriptor); with
+// cpj = 0 (more chains than CTAs) all CTAs stride through all tiles.  With two
+// stage buffers the copies of tile k + 1 are issued before tile k is computed.
+// A stage that does not arrive within 1 s sets the chain's status to 2
+// (MGMC_ERR_TIMEOUT), waits (bounded) for the copies in flight and ends the CTA.
+template <typename T, bool FINE, bool BWD>
+__global__ void __launch_bounds__(TileGeom<T, FINE, BWD>::NT, 3)
+    k_tile_batch(const TileJob<T>* __restrict__ jobs, const TileMaps* __restrict__ maps, int njobs, int per,
+                 int ntiles, int cpj, int x_zero)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ __align__(16) TileJob<T> J;
-    load_job(J, jobs + find_job(jobs, njobs, per, blockIdx.x));
-    const int t = blockIdx.x - J.tile0;
-    tile_bwd_body<T, FINE>(J.L, J.C, J.P, t % J.L.ntx, t / J.L.ntx, smem_raw);
+    using G = TileGeom<T, FINE, BWD>;
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    // TMA destinations start on 128-byte boundaries (the launch adds 128 bytes of slack)
+    unsigned char* smem_raw =
+        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
+    TileJob<T>* hdr[2] = {reinterpret_cast<TileJob<T>*>(smem_raw),
+                          reinterpret_cast<TileJob<T>*>(smem_raw + kHdrBytes)};
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + 2 * kHdrBytes);
+    T* buf = reinterpret_cast<T*>(smem_raw + 2 * kHdrBytes + 128);
+    T* Rr = buf + G::NSTAGE * G::STAGE;
+    __shared__ CycleState cs_s[2];
+    __shared__ int jid[2];
+
+    pdl_launch_dependents();
+    // tiles tb, tb + step, ... < te
+    int tb, te, step;
+    if (cpj > 0) {
+        const int j = blockIdx.x / cpj;
+        const int first = per > 0 ? j * per : jobs[j].tile0;
+        tb = first + (int)(blockIdx.x % cpj);
+        te = first + (per > 0 ? per : jobs[j].ntiles);
+        step = cpj;
+    } else {
+        tb = blockIdx.x;
+        te = ntiles;
+        step = gridDim.x;
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0]);
+        mbar_init(&bar[1]);
+        fence_mbar_init();
+        jid[0] = jid[1] = -1;
+    }
+    __syncthreads();
+    pdl_wait();
+    if (tb >= te) return;
+
+    // header and cycle state of tile t's chain into slot hs
+    auto fetch = [&](int t, int hs) {
+        const int j = find_job(jobs, njobs, per, t);
+        if (jid[hs] == j) return;
+        const bool other = jid[hs ^ 1] == j;
+        __syncthreads();  // every thread has read jid[]
+        if (other) {
+            const unsigned long long* s = reinterpret_cast<const unsigned long long*>(hdr[hs ^ 1]);
+            unsigned long long* d = reinterpret_cast<unsigned long long*>(hdr[hs]);
+            for (int w = threadIdx.x; w < (int)(sizeof(TileJob<T>) / 8); w += G::NT) d[w] = s[w];
+            if (threadIdx.x == 0) cs_s[hs] = cs_s[hs ^ 1];
+            __syncthreads();
+        } else {
+            load_job(*hdr[hs], jobs + j);
+            if (threadIdx.x == 0) cs_s[hs] = *hdr[hs]->P.cs;
+        }
+        if (threadIdx.x == 0) jid[hs] = j;
+        __syncthreads();
+    };
+    // the TMA copies of tile t (header in slot hs) into stage buffer ds (thread 0)
+    auto issue = [&](int t, int hs, int ds) {
+        const TileJob<T>& J = *hdr[hs];
+        const int lt = t - J.tile0;
+        const int x0 = (lt % J.L.ntx) * G::TX, y0 = (lt / J.L.ntx) * G::TY;
+        const int cx = x0 - G::RX + 4, cy = y0 - G::R + 1;  // padded coordinates of the box corner
+        const CUtensorMap* M = maps[jid[hs]].m;
+        T* b = buf + ds * G::STAGE;
+        const bool loadx = BWD || !x_zero;
+        unsigned bytes = (unsigned)(G::NFLD - (loadx ? 0 : 1)) * G::BOX_BYTES + (BWD ? G::PSI_BYTES : 0u);
+        mbar_expect_tx(&bar[ds], bytes);
+        if (loadx) tma_load_2d(b, &M[0], cx, cy, &bar[ds]);
+        for (int f = 1; f < G::NFLD; ++f) tma_load_2d(b + f * G::FS, &M[f], cx, cy, &bar[ds]);
+        if (BWD) {
+            const int gx0 = x0 - G::RX, gy0 = y0 - G::R;
+            tma_load_2d(b + G::NFLD * G::FS, &M[G::NFLD], ((gx0 >> 1) - 1 - G::POFF) + 4, ((gy0 >> 1) - 1) + 1,
+                        &bar[ds]);
+        }
+    };
+
+    fetch(tb, 0);
+    if (threadIdx.x == 0) issue(tb, 0, 0);
+    for (int t = tb, k = 0; t < te; t += step, ++k) {
+        const int hs = k & 1;
+        const int ds = G::NSTAGE == 2 ? (k & 1) : 0;
+        const unsigned parity = (unsigned)((G::NSTAGE == 2 ? (k >> 1) : k) & 1);
+        const bool more = t + step < te;
+        if (G::NSTAGE == 2 && more) {
+            fetch(t + step, hs ^ 1);
+            if (threadIdx.x == 0) issue(t + step, hs ^ 1, ds ^ 1);
+        }
+        const bool ok = mbar_wait(&bar[ds], parity);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                hdr[hs]->P.cs->status = 2;
+                __threadfence();
+                mbar_wait(&bar[ds], parity);
+                if (G::NSTAGE == 2 && more) mbar_wait(&bar[ds ^ 1], (unsigned)(((k + 1) >> 1) & 1));
+            }
+            __syncthreads();
+            return;
+        }
+        const TileJob<T>& J = *hdr[hs];
+        const int lt = t - J.tile0;
+        const int bx = lt % J.L.ntx, by = lt / J.L.ntx;
+        T* b = buf + ds * G::STAGE;
+        if constexpr (BWD)
+            tile_bwd_compute<T, FINE>(J.L, cs_s[hs], bx, by, b, b + G::FS, b + (1 + G::NCOEF) * G::FS,
+                                      b + G::NFLD * G::FS);
+        else
+            tile_fwd_compute<T, FINE>(J.L, J.C, cs_s[hs], x_zero, bx, by, b, b + G::FS, b + (1 + G::NCOEF) * G::FS,
+                                      Rr);
+        fence_proxy_async();
+        __syncthreads();
+        if (G::NSTAGE == 1 && more) {
+            fetch(t + step, hs ^ 1);
+            if (threadIdx.x == 0) issue(t + step, hs ^ 1, 0);
+        }
+    }
 }
 
 // Low-rank step after a fused sweep (Alg. 3 last line, see kernels.cu):
@@ -851,6 +963,89 @@ __global__ void __launch_bounds__(kTileThreads) k_tile_bwd_batch(const TileJob<T
 //   theta' = theta*_s - G v on the support of G;
 // on the way down also f_{l-1} += H v (H = P^T A G) and
 // d_{l-1} = d_l - B^T theta' = d_l - z + (B^T G) v.
+// The same step when m <= kLrReg and every thread holds at most one row of G
+// (and of H): all loads that do not depend on v -- the thread's G/H row, its
+// site and the value there, B^T G, d, the Cholesky diagonal -- are issued before
+// z and v are formed, so the step costs about three round trips to memory.  The
+// sums run in the same order as the general path.
+constexpr int kLrReg = 16;
+
+template <typename T>
+__device__ __forceinline__ void lowrank_fused_short(const DevLevel<T>& L, const DevLevel<T>& C, const DevProblem& P,
+                                                    int down, int blk, double* z, double* zp, double* v)
+{
+    const int m = P.m;
+    const int dir = down ? 0 : 1;
+    const unsigned slot = down ? 0u : 1u;
+    T* x = down ? L.x2 : L.x;
+    const int r0 = blk * blockDim.x + threadIdx.x;
+    const int k0 = threadIdx.x;
+    const bool hg = r0 < L.g_rows[dir];
+    const bool hh = down && r0 < L.h_rows;
+    const bool hk = k0 < m;
+    const bool hb = down && blk == 0 && hk;
+    T gr[kLrReg], hr[kLrReg];
+    double bg[kLrReg];
+#pragma unroll
+    for (int k = 0; k < kLrReg; ++k) {
+        gr[k] = (hg && k < m) ? L.gT[dir][(long long)r0 * m + k] : T(0);
+        hr[k] = (hh && k < m) ? L.hT[(long long)r0 * m + k] : T(0);
+        bg[k] = (hb && k < m) ? L.BtG[k0 * m + k] : 0.0;
+    }
+    const long long gs = hg ? L.g_site[dir][r0] : 0;
+    const long long hs = hh ? L.h_site[r0] : 0;
+    const CycleState cs = *P.cs;
+    int t0 = 0, t1 = 0;
+    double dk = 0.0, lgk = 0.0;
+    if (hk) {
+        t0 = L.bcol_ptr[k0];
+        t1 = L.bcol_ptr[k0 + 1];
+        dk = L.d[k0];
+        if (P.gamma_diag) lgk = P.LG[k0 * m + k0];
+    }
+    const T xv = hg ? x[gs] : T(0);
+    const T fv = hh ? C.f[hs] : T(0);
+    if (hk) {
+        double acc = 0.0;
+        for (int t = t0; t < t1; ++t) acc += L.zparts[t];
+        z[k0] = acc;
+        zp[k0] = cs.noise ? lowrank_normal<T>(cs, L.level, slot, k0) : 0.0;
+    }
+    __syncthreads();
+    if (hk) {
+        double lz = 0.0;
+        if (cs.noise) {
+            if (P.gamma_diag)
+                lz = lgk * zp[k0];
+            else
+                for (int t = 0; t <= k0; ++t) lz += P.LG[k0 * m + t] * zp[t];
+        }
+        v[k0] = z[k0] - dk - lz;
+    }
+    __syncthreads();
+    if (hg) {
+        T acc = T(0);
+#pragma unroll
+        for (int k = 0; k < kLrReg; ++k)
+            if (k < m) acc += gr[k] * (T)v[k];
+        x[gs] = xv - acc;
+    }
+    if (hh) {
+        T acc = T(0);
+#pragma unroll
+        for (int k = 0; k < kLrReg; ++k)
+            if (k < m) acc += hr[k] * (T)v[k];
+        C.f[hs] = fv + acc;
+    }
+    if (hb) {
+        double acc = 0.0;
+#pragma unroll
+        for (int k = 0; k < kLrReg; ++k)
+            if (k < m) acc += bg[k] * v[k];
+        L.dnext[k0] = dk - z[k0] + acc;
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void lowrank_fused_body(const DevLevel<T>& L, const DevLevel<T>& C, const DevProblem& P,
                                                    int down, int blk, int nblk)
@@ -858,10 +1053,15 @@ __device__ __forceinline__ void lowrank_fused_body(const DevLevel<T>& L, const D
     __shared__ double z[kMaxObs];
     __shared__ double zp[kMaxObs];
     __shared__ double v[kMaxObs];
-    const CycleState cs = *P.cs;
     const int m = P.m;
     const int dir = down ? 0 : 1;
     const unsigned slot = down ? 0u : 1u;
+    const int stride = nblk * blockDim.x;
+    if (m <= kLrReg && L.g_rows[dir] <= stride && (!down || L.h_rows <= stride)) {
+        lowrank_fused_short<T>(L, C, P, down, blk, z, zp, v);
+        return;
+    }
+    const CycleState cs = *P.cs;
     for (int k = threadIdx.x; k < m; k += blockDim.x) {
         double acc = 0.0;
         for (int t = L.bcol_ptr[k]; t < L.bcol_ptr[k + 1]; ++t) acc += L.zparts[t];
@@ -881,7 +1081,6 @@ __device__ __forceinline__ void lowrank_fused_body(const DevLevel<T>& L, const D
     }
     __syncthreads();
     T* x = down ? L.x2 : L.x;
-    const int stride = nblk * blockDim.x;
     const T* Gm = L.gT[dir];
     for (int r = blk * blockDim.x + threadIdx.x; r < L.g_rows[dir]; r += stride) {
         T acc = T(0);
@@ -904,18 +1103,14 @@ __device__ __forceinline__ void lowrank_fused_body(const DevLevel<T>& L, const D
         }
 }
 
-template <typename T>
-__global__ void k_lowrank_fused(DevLevel<T> L, DevLevel<T> C, DevProblem P, int down)
-{
-    lowrank_fused_body<T>(L, C, P, down, blockIdx.x, gridDim.x);
-}
-
 // batched: job j owns blocks [block0, block0 + nblocks)
 template <typename T>
 __global__ void k_lowrank_fused_batch(const LowrankJob<T>* __restrict__ jobs, int njobs, int per, int down)
 {
     __shared__ __align__(16) LowrankJob<T> J;
-    load_job(J, jobs + find_job(jobs, njobs, per, blockIdx.x));
+    pdl_launch_dependents();
+    load_job(J, jobs + find_job(jobs, njobs, per, blockIdx.x));   // static table
+    pdl_wait();
     lowrank_fused_body<T>(J.L, J.C, J.P, down, blockIdx.x - J.block0, J.nblocks);
 }
 
@@ -929,106 +1124,133 @@ int lowrank_blocks(int rows)
     if (blocks > 64) blocks = 64;
     return blocks;
 }
-template <typename T, bool FINE>
-static void tile_dims(const DevLevel<T>& L, dim3& grid)
+namespace {
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_tiled()
 {
-    grid = dim3((unsigned)((L.n + TileShape<T, FINE>::TX - 1) / TileShape<T, FINE>::TX),
-                (unsigned)((L.n + TileShape<T, FINE>::TY - 1) / TileShape<T, FINE>::TY));
+    static std::once_flag once;
+    static EncodeTiled fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    });
+    return fn;
 }
 
+// 2D tiled map of a padded field: pitch x rows elements, box bw x bh, zero fill outside
 template <typename T>
-cudaError_t tile_prepare()
+bool encode_field(CUtensorMap* m, const T* base, int pitch, int rows, int bw, int bh)
 {
-    cudaError_t e = cudaSuccess;
-    e = cudaFuncSetAttribute(k_tile_fwd<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)TileGeom<T, true, false>::smem_bytes());
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_tile_fwd<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)TileGeom<T, false, false>::smem_bytes());
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_tile_bwd<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)TileGeom<T, true, true>::smem_bytes());
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_tile_bwd<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)TileGeom<T, false, true>::smem_bytes());
+    EncodeTiled fn = encode_tiled();
+    if (!fn || !base) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)pitch, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)pitch * sizeof(T)};
+    cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh};
+    cuuint32_t es[2] = {1, 1};
+    return fn(m, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, (void*)base,
+              dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <typename T>
-void launch_tile_fwd(const DevLevel<T>& L, const DevLevel<T>& C, const DevProblem& P, bool x_zero, cudaStream_t st,
-                     int& launches)
+template <typename T, bool FINE, bool BWD>
+bool make_maps(const DevLevel<T>& L, const DevLevel<T>& C, TileMaps* out)
 {
-    dim3 grid;
-    if (L.fine) {
-        tile_dims<T, true>(L, grid);
-        k_tile_fwd<T, true><<<grid, kTileThreads, TileGeom<T, true, false>::smem_bytes(), st>>>(L, C, P, x_zero);
+    using G = TileGeom<T, FINE, BWD>;
+    static_assert(G::NMAP <= kTileMaxMaps, "tensor maps per tile job");
+    const int rows = L.n + 2;
+    bool ok = encode_field<T>(&out->m[0], BWD ? L.x2 : L.x, L.pitch, rows, G::SX, G::SY);
+    if (FINE) {
+        ok = ok && encode_field<T>(&out->m[1], L.diag, L.pitch, rows, G::SX, G::SY);
     } else {
-        tile_dims<T, false>(L, grid);
-        k_tile_fwd<T, false><<<grid, kTileThreads, TileGeom<T, false, false>::smem_bytes(), st>>>(L, C, P, x_zero);
+        for (int t = 0; t < G::NCOEF; ++t)
+            ok = ok && encode_field<T>(&out->m[1 + t], L.coef + (long long)t * L.alloc, L.pitch, rows, G::SX, G::SY);
+        ok = ok && encode_field<T>(&out->m[1 + G::NCOEF], L.f, L.pitch, rows, G::SX, G::SY);
     }
-    ++launches;
+    if (BWD) ok = ok && encode_field<T>(&out->m[G::NFLD], C.x, C.pitch, C.n + 2, G::PXA, G::PY);
+    return ok;
 }
 
-template <typename T>
-void launch_tile_bwd(const DevLevel<T>& L, const DevLevel<T>& C, const DevProblem& P, cudaStream_t st, int& launches)
+// resident CTAs per SM of each tile kernel (filled by tile_prepare_batch) and the SM count
+int g_tile_ctas[2][2][2];  // [fp64][fine][bwd]
+int g_sms = 0;
+
+template <typename T, bool FINE, bool BWD>
+cudaError_t prepare_one()
 {
-    dim3 grid;
-    if (L.fine) {
-        tile_dims<T, true>(L, grid);
-        k_tile_bwd<T, true><<<grid, kTileThreads, TileGeom<T, true, true>::smem_bytes(), st>>>(L, C, P);
-    } else {
-        tile_dims<T, false>(L, grid);
-        k_tile_bwd<T, false><<<grid, kTileThreads, TileGeom<T, false, true>::smem_bytes(), st>>>(L, C, P);
-    }
-    ++launches;
+    const size_t smem = tile_smem_bytes<T, FINE, BWD>() + 128;
+    cudaError_t e = cudaFuncSetAttribute(k_tile_batch<T, FINE, BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tile_batch<T, FINE, BWD>, TileGeom<T, FINE, BWD>::NT,
+                                                      smem);
+    if (e != cudaSuccess) return e;
+    g_tile_ctas[sizeof(T) == 8][FINE][BWD] = nb > 0 ? nb : 1;
+    return cudaSuccess;
 }
 
-template <typename T>
-void launch_lowrank_fused(const DevLevel<T>& L, const DevLevel<T>& C, const DevProblem& P, bool down, cudaStream_t st,
-                          int& launches)
+template <typename T, bool FINE, bool BWD>
+void launch_one(const TileJob<T>* jobs, const TileMaps* maps, int njobs, int per, int ntiles, bool x_zero,
+                cudaStream_t st)
 {
-    if (P.m == 0) return;
-    int rows = L.g_rows[down ? 0 : 1];
-    if (down && L.h_rows > rows) rows = L.h_rows;
-    k_lowrank_fused<T><<<lowrank_blocks(rows), 256, 0, st>>>(L, C, P, down ? 1 : 0);
-    ++launches;
+    long long grid = (long long)g_tile_ctas[sizeof(T) == 8][FINE][BWD] * (g_sms > 0 ? g_sms : 1);
+    // chains with a common tile count and no more chains than resident CTAs: cpj CTAs per chain
+    int cpj = 0;
+    if (per > 0 && njobs <= grid) {
+        cpj = (int)(grid / njobs);
+        if (cpj > per) cpj = per;
+        grid = (long long)cpj * njobs;
+    } else if (grid > ntiles) {
+        grid = ntiles;
+    }
+    launch_pdl(k_tile_batch<T, FINE, BWD>, dim3((unsigned)grid), dim3(TileGeom<T, FINE, BWD>::NT),
+               tile_smem_bytes<T, FINE, BWD>() + 128, st, jobs, maps, njobs, per, ntiles, cpj, x_zero ? 1 : 0);
+}
+
+}  // namespace
+
+template <typename T>
+bool make_tile_maps(const DevLevel<T>& L, const DevLevel<T>& C, bool bwd, TileMaps* out)
+{
+    std::memset(out, 0, sizeof(*out));
+    if (L.fine)
+        return bwd ? make_maps<T, true, true>(L, C, out) : make_maps<T, true, false>(L, C, out);
+    return bwd ? make_maps<T, false, true>(L, C, out) : make_maps<T, false, false>(L, C, out);
 }
 
 template <typename T>
 cudaError_t tile_prepare_batch()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_tile_fwd_batch<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)TileGeom<T, true, false>::smem_bytes());
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_tile_fwd_batch<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)TileGeom<T, false, false>::smem_bytes());
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_tile_bwd_batch<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)TileGeom<T, true, true>::smem_bytes());
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_tile_bwd_batch<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)TileGeom<T, false, true>::smem_bytes());
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = prepare_one<T, true, false>();
+    if (e == cudaSuccess) e = prepare_one<T, true, true>();
+    if (e == cudaSuccess) e = prepare_one<T, false, false>();
+    if (e == cudaSuccess) e = prepare_one<T, false, true>();
+    if (e == cudaSuccess && !encode_tiled()) e = cudaErrorNotSupported;
+    return e;
 }
 
 template <typename T>
-void launch_tile_batch(const TileJob<T>* jobs, int njobs, int per, int nblocks, bool fine, bool bwd, bool x_zero,
-                       cudaStream_t st, int& launches)
+void launch_tile_batch(const TileJob<T>* jobs, const TileMaps* maps, int njobs, int per, int ntiles, bool fine,
+                       bool bwd, bool x_zero, cudaStream_t st, int& launches)
 {
-    if (nblocks <= 0) return;
-    if (!bwd) {
-        if (fine)
-            k_tile_fwd_batch<T, true><<<nblocks, kTileThreads, TileGeom<T, true, false>::smem_bytes(), st>>>(
-                jobs, njobs, per, x_zero ? 1 : 0);
-        else
-            k_tile_fwd_batch<T, false><<<nblocks, kTileThreads, TileGeom<T, false, false>::smem_bytes(), st>>>(
-                jobs, njobs, per, x_zero ? 1 : 0);
-    } else {
-        if (fine)
-            k_tile_bwd_batch<T, true><<<nblocks, kTileThreads, TileGeom<T, true, true>::smem_bytes(), st>>>(
-                jobs, njobs, per);
-        else
-            k_tile_bwd_batch<T, false><<<nblocks, kTileThreads, TileGeom<T, false, true>::smem_bytes(), st>>>(
-                jobs, njobs, per);
-    }
+    if (ntiles <= 0) return;
+    if (fine)
+        bwd ? launch_one<T, true, true>(jobs, maps, njobs, per, ntiles, x_zero, st)
+            : launch_one<T, true, false>(jobs, maps, njobs, per, ntiles, x_zero, st);
+    else
+        bwd ? launch_one<T, false, true>(jobs, maps, njobs, per, ntiles, x_zero, st)
+            : launch_one<T, false, false>(jobs, maps, njobs, per, ntiles, x_zero, st);
     ++launches;
 }
 
@@ -1037,19 +1259,15 @@ void launch_lowrank_batch(const LowrankJob<T>* jobs, int njobs, int per, int nbl
                           int& launches)
 {
     if (nblocks <= 0) return;
-    k_lowrank_fused_batch<T><<<nblocks, 256, 0, st>>>(jobs, njobs, per, down ? 1 : 0);
+    launch_pdl(k_lowrank_fused_batch<T>, dim3((unsigned)nblocks), dim3(256), 0, st, jobs, njobs, per, down ? 1 : 0);
     ++launches;
 }
 
 #define MGMC_TILE_INST(T)                                                                                        \
-    template cudaError_t tile_prepare<T>();                                                                       \
-    template void launch_tile_fwd<T>(const DevLevel<T>&, const DevLevel<T>&, const DevProblem&, bool, cudaStream_t, \
-                                     int&);                                                                       \
-    template void launch_tile_bwd<T>(const DevLevel<T>&, const DevLevel<T>&, const DevProblem&, cudaStream_t, int&); \
-    template void launch_lowrank_fused<T>(const DevLevel<T>&, const DevLevel<T>&, const DevProblem&, bool,         \
-                                          cudaStream_t, int&);                                                     \
+    template bool make_tile_maps<T>(const DevLevel<T>&, const DevLevel<T>&, bool, TileMaps*);                    \
     template cudaError_t tile_prepare_batch<T>();                                                                 \
-    template void launch_tile_batch<T>(const TileJob<T>*, int, int, int, bool, bool, bool, cudaStream_t, int&);    \
+    template void launch_tile_batch<T>(const TileJob<T>*, const TileMaps*, int, int, int, bool, bool, bool,       \
+                                       cudaStream_t, int&);                                                       \
     template void launch_lowrank_batch<T>(const LowrankJob<T>*, int, int, int, bool, cudaStream_t, int&);
 
 MGMC_TILE_INST(float)

@@ -64,6 +64,48 @@ def test_batch_chain_matches_oracle(torch_mod):
         assert np.all(np.abs(xg - xo) <= 1e-11 * np.maximum(np.abs(xo), rms))
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_persistent_tiles_span_chains(torch_mod, precision):
+    """A batch with many more tiles than resident CTAs (each CTA walks a range of
+    tiles across chain boundaries, with staged copies of the next tile in flight)
+    equals the solo runs bit for bit."""
+    torch = torch_mod
+    from paper_2407_12149_gb300.mgmc import BatchSampler, Sampler
+    ps = [inputs.make_problem(f"w{c}", 2, 511, kappa2_seed=300 + c, m=8 + c, obs_seed=400 + c, qoi_cells=64)
+          for c in range(10)]
+    b = BatchSampler(ps, precision=precision)
+    xs = b.zeros()
+    b.sample(xs, 3, 17, step_offset=2)
+    torch.cuda.synchronize()
+    for c in (0, 4, 9):
+        s = Sampler(ps[c], precision=precision, coarse_max_n=31)
+        x = s.zeros()
+        s.sample(x, 3, 17, step_offset=2, chain=c)
+        torch.cuda.synchronize()
+        assert torch.equal(x, xs[c]), f"chain {c}"
+        s.close()
+
+
+def test_fp32_batch_with_galerkin_tiles_matches_oracle(torch_mod):
+    """FP32 batched chains whose 9-point grids 127^2 and 63^2 run in tile kernels,
+    per site against the FP64 oracle after 60 cycles (tolerance 2e-4 of the RMS)."""
+    torch = torch_mod
+    from paper_2407_12149_gb300.mgmc import BatchSampler
+    ps = [inputs.make_problem(f"g{c}", 2, 255, kappa2_seed=500 + c, m=12, obs_seed=600 + c, qoi_cells=64)
+          for c in range(2)]
+    b = BatchSampler(ps, precision="fp32")
+    xs = b.zeros()
+    b.sample(xs, 60, 23)
+    torch.cuda.synchronize()
+    for c, p in enumerate(ps):
+        o = oracle.Oracle(p.dim, p.n, p.n_levels, kappa2=p.kappa2, obs_site=p.obs_site, obs_w=p.obs_w,
+                          Gamma=p.Gamma, y=p.y)
+        xo = o.sample(60, 23, chain=c, qoi=False)
+        xg = xs[c].cpu().numpy().astype(np.float64)
+        rms = np.sqrt(np.mean(xo ** 2))
+        assert np.abs(xg - xo).max() <= 2e-4 * rms, f"chain {c}"
+
+
 def test_resume_and_get_state_reproduce_one_run(torch_mod):
     """x = None continues from the held state: split runs equal one run bit for bit."""
     torch = torch_mod
