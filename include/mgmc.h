@@ -228,6 +228,21 @@ mgmc_status mgmc_profile_times(mgmc_handle h, float* ms, int n, void* stream);
 
 mgmc_status mgmc_destroy(mgmc_handle h);
 
+/* ------------------------------------------------------------------------
+ * Tensor-core GEMM (BF16 in, FP32 accumulate) on which the learned warm
+ * start's convolutions run; exported for testing and reuse:
+ *   C[M][N] = A[M][K] * B[N][K]^T  (+ bias[n]) (ReLU)
+ * A: device BF16 row-major [M][lda], B: device BF16 row-major [N][ldb]
+ * (lda, ldb >= K and multiples of 8; base addresses 16-byte aligned).
+ * epilogue: bit 0 add bias (device float [N]), bit 1 ReLU, bit 2 store BF16
+ * (else float).  splits > 1 (FP32 output only): the K range is cut into
+ * `splits` parts summed in a fixed order (deterministic).  C: device [M][N].
+ * Asynchronous on stream; MGMC_ERR_TIMEOUT is reported by the next call that
+ * synchronises (a bounded wait inside the kernel gave up).
+ * ------------------------------------------------------------------------ */
+mgmc_status mgmc_tc_gemm(const void* A, int lda, const void* B, int ldb, void* C, int M, int N, int K, int splits,
+                         int epilogue, const float* bias, void* stream);
+
 /* Message of the last failing call on this thread; valid until the next call. */
 const char* mgmc_last_error(void);
 

@@ -27,6 +27,7 @@
 
 #include "kernels.cuh"
 #include "tile2d.cuh"
+#include "tma.cuh"
 
 namespace mgmc {
 
@@ -726,63 +727,10 @@ __device__ __forceinline__ void tile_bwd_compute(const DevLevel<T>& L, const Cyc
 }
 
 
-// ---------------------------------------------------------------------------
-// TMA staging (PTX cp.async.bulk.tensor, mbarrier).  Each field of a stage is
-// one 2D tiled bulk tensor copy of the padded array, the box anchored at the
-// staged region's corner in padded coordinates; the parts of a box outside the
-// array are filled with zeros -- the ghost ring's value.  The copies of a stage
-// complete on one mbarrier (arrive + expected transaction bytes).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init(unsigned long long* bar)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(bar)) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity)
-{
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-// wait for the completion of the barrier phase of the given parity; false after 1 s
-constexpr unsigned long long kWaitNs = 1000000000ull;
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity)
-{
-    if (mbar_test(bar, parity)) return true;
-    const unsigned long long t0 = global_ns();
-    for (unsigned it = 1; it < (1u << 30); ++it) {
-        if (mbar_test(bar, parity)) return true;
-        if ((it & 63) == 0 && global_ns() - t0 > kWaitNs) return false;
-    }
-    return false;
-}
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, unsigned long long* bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-        "[%4];\n" ::"r"(smem_addr(dst)),
-        "l"(map), "r"(x), "r"(y), "r"(smem_addr(bar))
-        : "memory");
-}
-// orders this thread's generic-proxy accesses of shared memory before later
-// async-proxy (TMA) writes to it
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+// TMA staging: each field of a stage is one 2D tiled bulk tensor copy of the
+// padded array (tma.cuh), the box anchored at the staged region's corner in
+// padded coordinates; the parts of a box outside the array are filled with
+// zeros -- the ghost ring's value.  The copies of a stage complete on one mbarrier.
 
 template <typename T>
 __device__ __forceinline__ int job_first(const TileJob<T>& j) { return j.tile0; }
@@ -1126,30 +1074,11 @@ int lowrank_blocks(int rows)
 }
 namespace {
 
-using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiled encode_tiled()
-{
-    static std::once_flag once;
-    static EncodeTiled fn = nullptr;
-    std::call_once(once, [] {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiled>(p);
-    });
-    return fn;
-}
-
 // 2D tiled map of a padded field: pitch x rows elements, box bw x bh, zero fill outside
 template <typename T>
 bool encode_field(CUtensorMap* m, const T* base, int pitch, int rows, int bw, int bh)
 {
-    EncodeTiled fn = encode_tiled();
+    EncodeTiled fn = tensor_map_encoder();
     if (!fn || !base) return false;
     cuuint64_t dims[2] = {(cuuint64_t)pitch, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)pitch * sizeof(T)};
@@ -1236,7 +1165,7 @@ cudaError_t tile_prepare_batch()
     if (e == cudaSuccess) e = prepare_one<T, true, true>();
     if (e == cudaSuccess) e = prepare_one<T, false, false>();
     if (e == cudaSuccess) e = prepare_one<T, false, true>();
-    if (e == cudaSuccess && !encode_tiled()) e = cudaErrorNotSupported;
+    if (e == cudaSuccess && !tensor_map_encoder()) e = cudaErrorNotSupported;
     return e;
 }
 

@@ -71,7 +71,7 @@ _lib = None
 EXPORTS = ("mgmc_config_default", "mgmc_create", "mgmc_point_obs_rows", "mgmc_sample", "mgmc_mean_solve",
            "mgmc_qoi_stats", "mgmc_qoi_stats_noalloc", "mgmc_info", "mgmc_level_n", "mgmc_launches_per_cycle", "mgmc_set_profiling",
            "mgmc_profile_times", "mgmc_create_batch", "mgmc_sample_batch", "mgmc_get_state", "mgmc_destroy",
-           "mgmc_last_error")
+           "mgmc_tc_gemm", "mgmc_last_error")
 
 
 def load():
@@ -107,6 +107,9 @@ def load():
     L.mgmc_sample_batch.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64,
                                     ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_void_p]
     L.mgmc_get_state.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    L.mgmc_tc_gemm.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                               ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                               ctypes.c_void_p]
     L.mgmc_destroy.argtypes = [ctypes.c_void_p]
     for name in EXPORTS:
         if name != "mgmc_last_error":
@@ -199,6 +202,24 @@ def mgmc_create(dim, n, *, n_levels=0, nu1=1, nu2=1, precision=MGMC_FP64, scale_
                          _ptr(y_, ctypes.c_double), nq, _ptr(qs, ctypes.c_int32), _ptr(qw, ctypes.c_double),
                          ctypes.byref(h)))
     return h
+
+
+EPI_BIAS, EPI_RELU, EPI_BF16 = 1, 2, 4
+
+
+def tc_gemm(A, B, out=None, splits=1, epilogue=0, bias=None, stream=None):
+    """C = A B^T on the tensor cores: A [M][K], B [N][K] bfloat16 CUDA tensors
+    (row strides multiples of 8); returns C [M][N] float32 (bfloat16 with EPI_BF16)."""
+    torch = _torch()
+    M, K = A.shape
+    N = B.shape[0]
+    if out is None:
+        out = torch.empty(M, N, dtype=torch.bfloat16 if epilogue & EPI_BF16 else torch.float32, device=A.device)
+    _check(load().mgmc_tc_gemm(ctypes.c_void_p(A.data_ptr()), A.stride(0), ctypes.c_void_p(B.data_ptr()),
+                               B.stride(0), ctypes.c_void_p(out.data_ptr()), M, N, K, splits, epilogue,
+                               ctypes.c_void_p(bias.data_ptr()) if bias is not None else None,
+                               _stream_handle(stream)))
+    return out
 
 
 def mgmc_get_state(h, chain, x_ptr, stream=None):
