@@ -143,6 +143,7 @@ WORKLOADS = {
     "bayes2d-4095": {"n": 4095, "chains": 1},            # HBM-resident single-grid variants (roofline)
     "bayes2d-8191": {"n": 8191, "chains": 1},
     "batch512-mixed": {"n": 511, "chains": 512, "mixed": True},   # 128 chains each of 63^2 .. 511^2
+    "warmstart-255": {"n": 255, "chains": 64, "warm": True},       # learned warm start (U-Net), 255^2
 }
 
 
@@ -384,6 +385,142 @@ def run_mine(args):
         dist.destroy_process_group()
 
 
+def warm_problems(n, count, first):
+    """Seeded 255^2-type problems of the learned warm start: kappa^2 = 10 exp(g) (own
+    seed each), m ~ U{8..32} uniform point observations, Gamma = 1e-4 I, central QoI."""
+    import numpy as np
+    from paper_2407_12149_gb300 import inputs
+    out = []
+    for s in range(first, first + count):
+        m = int(np.random.default_rng(30000 + s).integers(8, 33))
+        out.append(inputs.make_problem(f"warm-{s}", 2, n, kappa2_seed=10000 + s, m=m, obs_seed=20000 + s,
+                                       qoi_cells=max(2, (46 * (n + 1)) // 1024)))
+    return out
+
+
+def burn_in(q, qmu, sig):
+    """Cycles until the chains' mean normalised QoI error is within one Monte Carlo
+    standard error: first t with |mean_k (q[k,t] - qmu[k]) / sig[k]| <= 1 / sqrt(chains)."""
+    import numpy as np
+    d = ((q - qmu[:, None]) / sig[:, None]).mean(axis=0)
+    ok = np.abs(d) <= 1.0 / np.sqrt(q.shape[0])
+    return int(np.argmax(ok)) if ok.any() else q.shape[1], d
+
+
+def run_warmstart(args):
+    """Learned warm start (255^2): U-Net trained on FP64 mean-solve targets, then
+    burn-in of held-out FP32 chains started from the U-Net estimate vs from 0."""
+    import numpy as np
+    import torch
+    from paper_2407_12149_gb300 import build
+    from paper_2407_12149_gb300 import mgmc as M
+    build.build()
+    dev = torch.device("cuda", 0)
+    n, n_test, n_train = 255, 64, args.warm_train
+    t0 = time.perf_counter()
+    train = warm_problems(n, n_train, 0)
+    test = warm_problems(n, n_test, 1_000_000)
+
+    def targets(ps):
+        T = torch.zeros(len(ps), n * n, dtype=torch.float64, device=dev)
+        for k, p in enumerate(ps):
+            s = M.Sampler(p, precision="fp64", coarse_max_n=31)
+            s.mean_solve(T[k], rtol=1e-10, max_cycles=100)
+            s.close()
+        return T
+
+    Xtr = torch.from_numpy(np.stack([M.unet_inputs(p) for p in train]).view(np.int16)).to(dev)
+    Xte = torch.from_numpy(np.stack([M.unet_inputs(p) for p in test]).view(np.int16)).to(dev)
+    Ttr = targets(train).float()
+    Tte = targets(test)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+
+    net = M.Unet(n, c0=32, max_batch=8, seed=1)
+    t1 = time.perf_counter()
+    losses = net.train(Xtr, Ttr, epochs=args.warm_epochs, batch=8, lr=1e-3, shuffle_seed=2)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t1
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    mu_hat = net.predict(Xte, precision="fp32")
+    e1.record()
+    torch.cuda.synchronize()
+    pred_ms = e0.elapsed_time(e1)
+    err = (mu_hat.double() - Tte).norm(dim=1) / Tte.norm(dim=1)
+
+    # chains of the held-out problems from 0 and from the estimate, FP32 batched
+    K = args.warm_cycles
+    runs = {}
+    for name, init in (("zero", None), ("unet", mu_hat)):
+        b = M.BatchSampler(test, precision="fp32")
+        xs = b.zeros()
+        if init is not None:
+            for k, x in enumerate(xs):
+                x.copy_(init[k])
+        q = torch.zeros(n_test * K, dtype=torch.float64, device=dev)
+        b.sample(xs, K, 77, qoi=q)
+        torch.cuda.synchronize()
+        runs[name] = q.view(n_test, K).cpu().numpy()
+        b.close()
+    qmu = np.array([float(np.dot(p.qoi_w, Tte[k].cpu().numpy()[p.qoi_site])) for k, p in enumerate(test)])
+    tail = np.concatenate([runs["zero"][:, K // 2:], runs["unet"][:, K // 2:]], axis=1)
+    sig = tail.std(axis=1, ddof=1)
+    b_zero, d_zero = burn_in(runs["zero"], qmu, sig)
+    b_unet, d_unet = burn_in(runs["unet"], qmu, sig)
+
+    # tensor-core roofline of the GEMM on the largest convolution shapes of a batch of 8
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except Exception:
+        pass
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+
+    def gemm_tflops(Mr, N, Kd, reps=10):
+        g = torch.Generator(device=dev).manual_seed(1)
+        A = torch.randn(Mr, Kd, generator=g, device=dev).bfloat16()
+        B = torch.randn(N, Kd, generator=g, device=dev).bfloat16()
+        C = torch.empty(Mr, N, dtype=torch.float32, device=dev)
+        for _ in range(3):
+            M.tc_gemm(A, B, out=C)
+        a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            M.tc_gemm(A, B, out=C)
+        b2.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b2) / reps
+        return 2.0 * Mr * N * Kd / (ms * 1e-3) / 1e12, ms
+
+    bott, bott_ms = gemm_tflops(64 * 32 * 32, 256, 2304)     # bottom-level convolution of 64 samples
+    big, big_ms = gemm_tflops(8192, 8192, 8192, reps=5)
+    line = {
+        "metric": "burn-in V-cycles (learned warm start)", "value": b_unet, "unit": "V-cycles",
+        "n_gpus": 1, "steps": K, "warmup": 0, "ms_per_step": None, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": f"warmstart-255: U-Net (c0 = 32, {net.n_params} parameters) trained on {n_train} "
+                               f"FP64 mean-solve targets of seeded 255^2 posteriors (kappa^2 = 10 exp(g), m ~ U{{8..32}}, "
+                               f"Gamma = 1e-4 I), {n_test} held-out problems, FP32 batched chains",
+                   "burn_in_from_zero": b_zero, "burn_in_from_unet": b_unet,
+                   "burn_in_rule": "first cycle with |mean_k (q_kt - F mu_k) / sd_k| <= 1 / sqrt(64)",
+                   "mean_error_trace_zero": [round(float(v), 3) for v in d_zero[:12]],
+                   "mean_error_trace_unet": [round(float(v), 3) for v in d_unet[:12]],
+                   "mu_rel_l2_error_mean": float(err.mean()), "mu_rel_l2_error_max": float(err.max()),
+                   "train_epochs": args.warm_epochs, "train_loss_first_last": [float(losses[0]), float(losses[-1])],
+                   "train_s": train_s, "data_generation_s": gen_s,
+                   "predict_ms_per_problem": pred_ms / n_test},
+        "roofline": {"bound": "tensor", "kernel": "k_tc_gemm<256>: bottom-level convolution GEMM of 64 samples "
+                                                  "(M = 64 x 32^2 pixels, N = 256, K = 9 x 256)",
+                     "achieved": bott, "peak": peak, "unit": "TFLOP/s", "frac": bott / peak,
+                     "peak_kind": "measured cuBLAS bf16 burst" if peaks else "fallback",
+                     "avg_ms": bott_ms, "square_8192_tflops": big, "traffic": None},
+        "cpu_baseline": None, "e2e": None, "gpu_launches": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -395,12 +532,17 @@ def main():
                          "one chain; bayes2d-4095/8191: HBM-resident single grids; batch512-mixed: 512 chains")
     ap.add_argument("--tau-cycles", type=int, default=TAU_CALIBRATION,
                     help="length of the untimed chain that estimates tau_int (>= 200)")
+    ap.add_argument("--warm-train", type=int, default=512, help="warmstart-255: training problems")
+    ap.add_argument("--warm-epochs", type=int, default=20, help="warmstart-255: training epochs")
+    ap.add_argument("--warm-cycles", type=int, default=40, help="warmstart-255: chain length of the burn-in test")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     args.tau_cycles = max(200, args.tau_cycles)
     if args.impl == "reference":
         run_reference(args)
+    elif WORKLOADS[args.workload].get("warm"):
+        run_warmstart(args)
     else:
         run_mine(args)
 

@@ -229,6 +229,53 @@ mgmc_status mgmc_profile_times(mgmc_handle h, float* ms, int n, void* stream);
 mgmc_status mgmc_destroy(mgmc_handle h);
 
 /* ------------------------------------------------------------------------
+ * Learned warm start (not in the paper): a U-Net maps three input channels
+ * on the (n+1) x (n+1) grid -- log(kappa^2 / 10), the summed observation row
+ * weights sum_k B_{k,i} and the weighted data sum_k B_{k,i} y_k, with the last
+ * row and column zero -- to an estimate of the posterior mean mu = A~^-1 f
+ * (Sec. 3.2), to be used ONLY as a chain's initial state: the chain's law is
+ * that of the sampler whatever x_0 is; a good x_0 shortens burn-in.
+ * Channels-last BF16 activations and weights, FP32 accumulation on the tcgen05
+ * tensor cores.  c0 channels at full resolution, doubling at each of three
+ * 2x2 average poolings; two 3x3 conv + ReLU per level; nearest upsampling and
+ * concatenation with the encoder output on the way up; a 1x1 output.  Loss:
+ * mean squared error on the n x n interior; optimiser: Adam (beta 0.9, 0.999,
+ * eps 1e-8).  Parameters as one flat FP32 vector: per 3x3 convolution W
+ * [cout][3][3][cin] then b [cout] in the order e0a e0b e1a e1b e2a e2b ba bb
+ * d2a d2b d1a d1b d0a d0b, then the output layer w [c0], b [1].
+ * Data layouts: inputs [samples][n+1][n+1][3] BF16 (bits as uint16), device;
+ * targets and predictions [samples][n*n] dense like mgmc_sample's x (site
+ * i + n j), device.  Calls are synchronous on the handle's stream.
+ * ------------------------------------------------------------------------ */
+typedef struct mgmc_unet* mgmc_unet_handle;
+
+/* n = 2^k - 1 >= 31, c0 in {8, 16, 32} (c0 = 32: 1 946 881 parameters),
+ * max_batch <= 64 samples per step; He-normal initial weights from seed. */
+mgmc_status mgmc_unet_create(int n, int c0, int max_batch, uint64_t seed, const mgmc_allocator* alloc, void* stream,
+                             mgmc_unet_handle* out);
+mgmc_status mgmc_unet_n_params(mgmc_unet_handle u, int64_t* count);
+mgmc_status mgmc_unet_get_params(mgmc_unet_handle u, float* host_out);
+/* also resets the Adam moments and step count */
+mgmc_status mgmc_unet_set_params(mgmc_unet_handle u, const float* host_in);
+/* host helper: the input channels of one problem (same arguments as mgmc_create's
+ * kappa^2 and observation rows) into out [n+1][n+1][3] BF16 (host) */
+mgmc_status mgmc_unet_inputs(int n, const double* kappa2, double kappa2_const, int m, const int32_t* obs_site,
+                             const double* obs_w, int nnz_per_obs, const double* y, uint16_t* out);
+/* loss (mean squared error) of `batch` samples and its gradient (host, flat
+ * like the parameters); either output may be NULL */
+mgmc_status mgmc_unet_gradient(mgmc_unet_handle u, int batch, const void* inputs_bf16, const float* targets,
+                               float* loss_out, float* grad_out);
+/* `epochs` passes of Adam over n_samples (seeded shuffles, n_samples / batch
+ * steps each); epoch_loss: NULL or host [epochs] mean training loss */
+mgmc_status mgmc_unet_train(mgmc_unet_handle u, int64_t n_samples, const void* inputs_bf16, const float* targets,
+                            int epochs, int batch, float lr, uint64_t shuffle_seed, float* epoch_loss);
+/* the estimate of mu for n_samples problems into x_out [n_samples][n*n], FP32
+ * or FP64 (precision = MGMC_FP32 / MGMC_FP64) */
+mgmc_status mgmc_unet_predict(mgmc_unet_handle u, int64_t n_samples, const void* inputs_bf16, void* x_out,
+                              int precision);
+mgmc_status mgmc_unet_destroy(mgmc_unet_handle u);
+
+/* ------------------------------------------------------------------------
  * Tensor-core GEMM (BF16 in, FP32 accumulate) on which the learned warm
  * start's convolutions run; exported for testing and reuse:
  *   C[M][N] = A[M][K] * B[N][K]^T  (+ bias[n]) (ReLU)

@@ -210,3 +210,68 @@ def make_inputs(n, kappa2, obs_site, obs_w, y):
                 x[j, i, 1] += obs_w[k, t]
                 x[j, i, 2] += obs_w[k, t] * y[k]
     return x
+
+
+class SplitMix64:
+    """splitmix64 (Steele, Lea & Flood, OOPSLA 2014): state += 0x9E3779B97F4A7C15, then
+    two xor-shift-multiply rounds and a final xor-shift.  uniform() = (top 53 bits + 1/2)
+    2^-53; normal() = Box-Muller cosine branch, one pair of uniforms per draw."""
+    MASK = (1 << 64) - 1
+
+    def __init__(self, seed):
+        self.s = seed & self.MASK
+
+    def next(self):
+        self.s = (self.s + 0x9E3779B97F4A7C15) & self.MASK
+        z = self.s
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & self.MASK
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & self.MASK
+        return z ^ (z >> 31)
+
+    def uniform(self):
+        return ((self.next() >> 11) + 0.5) * 2.0 ** -53
+
+    def normal(self):
+        r = np.sqrt(-2.0 * np.log(self.uniform()))
+        return r * np.cos(2.0 * np.pi * self.uniform())
+
+
+def init_params(c0, seed):
+    """He-normal initial weights (std sqrt(2 / (9 cin)), drawn in the flat order, stored
+    as FP32), zero biases, output weights of std sqrt(1 / c0) and zero output bias."""
+    r = SplitMix64(seed)
+    parts = []
+    for _, _, ci, co in layer_table(c0):
+        sd = np.sqrt(2.0 / (9 * ci))
+        parts += [np.array([sd * r.normal() for _ in range(co * 9 * ci)], dtype=np.float32), np.zeros(co)]
+    parts += [np.array([np.sqrt(1.0 / c0) * r.normal() for _ in range(c0)], dtype=np.float32), np.zeros(1)]
+    return np.concatenate(parts).astype(np.float64)
+
+
+def epoch_permutation(n_samples, r):
+    """Fisher-Yates from the last position: swap i with next() mod (i + 1), i = n-1 .. 1."""
+    perm = list(range(n_samples))
+    for i in range(n_samples - 1, 0, -1):
+        j = r.next() % (i + 1)
+        perm[i], perm[j] = perm[j], perm[i]
+    return perm
+
+
+def train(theta, x, t, c0, epochs, batch, lr, shuffle_seed, bf16=False):
+    """Adam over shuffled mini-batches (n_samples // batch steps per epoch); returns the
+    final parameters and the mean training loss of each epoch."""
+    m = np.zeros_like(theta)
+    v = np.zeros_like(theta)
+    r = SplitMix64(shuffle_seed)
+    step, losses = 0, []
+    for _ in range(epochs):
+        perm = epoch_permutation(x.shape[0], r)
+        acc, nb = 0.0, x.shape[0] // batch
+        for b in range(nb):
+            idx = perm[b * batch:(b + 1) * batch]
+            loss, g = loss_and_grad(theta, x[idx], t[idx], c0, bf16)
+            step += 1
+            theta, m, v = adam_step(theta, m, v, g, step, lr)
+            acc += loss
+        losses.append(acc / nb)
+    return theta, np.array(losses)

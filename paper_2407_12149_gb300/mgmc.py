@@ -71,7 +71,9 @@ _lib = None
 EXPORTS = ("mgmc_config_default", "mgmc_create", "mgmc_point_obs_rows", "mgmc_sample", "mgmc_mean_solve",
            "mgmc_qoi_stats", "mgmc_qoi_stats_noalloc", "mgmc_info", "mgmc_level_n", "mgmc_launches_per_cycle", "mgmc_set_profiling",
            "mgmc_profile_times", "mgmc_create_batch", "mgmc_sample_batch", "mgmc_get_state", "mgmc_destroy",
-           "mgmc_tc_gemm", "mgmc_last_error")
+           "mgmc_tc_gemm", "mgmc_unet_create", "mgmc_unet_n_params", "mgmc_unet_get_params",
+           "mgmc_unet_set_params", "mgmc_unet_inputs", "mgmc_unet_gradient", "mgmc_unet_train",
+           "mgmc_unet_predict", "mgmc_unet_destroy", "mgmc_last_error")
 
 
 def load():
@@ -110,6 +112,19 @@ def load():
     L.mgmc_tc_gemm.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                ctypes.c_void_p]
+    L.mgmc_unet_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                   ctypes.POINTER(mgmc_allocator), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+    L.mgmc_unet_n_params.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]
+    L.mgmc_unet_get_params.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    L.mgmc_unet_set_params.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    L.mgmc_unet_inputs.argtypes = [ctypes.c_int, _F64P, ctypes.c_double, ctypes.c_int, _I32P, _F64P, ctypes.c_int,
+                                   _F64P, ctypes.c_void_p]
+    L.mgmc_unet_gradient.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_void_p]
+    L.mgmc_unet_train.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                  ctypes.c_int, ctypes.c_float, ctypes.c_uint64, ctypes.c_void_p]
+    L.mgmc_unet_predict.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+    L.mgmc_unet_destroy.argtypes = [ctypes.c_void_p]
     L.mgmc_destroy.argtypes = [ctypes.c_void_p]
     for name in EXPORTS:
         if name != "mgmc_last_error":
@@ -413,6 +428,90 @@ class BatchSampler:
     def close(self):
         if getattr(self, "h", None):
             mgmc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def unet_inputs(p):
+    """Input channels [n+1][n+1][3] (BF16 bits as uint16, host numpy) of an inputs.Problem."""
+    n = p.n
+    out = np.zeros((n + 1) * (n + 1) * 3, dtype=np.uint16)
+    k2 = None if p.kappa2 is None else np.ascontiguousarray(p.kappa2, dtype=np.float64)
+    if p.obs_site is not None:
+        os_ = np.ascontiguousarray(p.obs_site, dtype=np.int32)
+        ow = np.ascontiguousarray(p.obs_w, dtype=np.float64)
+        y = np.ascontiguousarray(p.y, dtype=np.float64)
+        nnz = int(os_.shape[1])
+    else:
+        os_ = ow = y = None
+        nnz = 1
+    _check(load().mgmc_unet_inputs(n, _ptr(k2, ctypes.c_double), float(p.kappa2_const), p.m,
+                                   _ptr(os_, ctypes.c_int32), _ptr(ow, ctypes.c_double), nnz,
+                                   _ptr(y, ctypes.c_double), out.ctypes.data_as(ctypes.c_void_p)))
+    return out.reshape(n + 1, n + 1, 3)
+
+
+class Unet:
+    """The learned warm start (mgmc_unet_*).  Inputs: CUDA tensors holding BF16 bits
+    (int16 or bfloat16) [samples][n+1][n+1][3]; targets: float32 CUDA [samples][n*n]."""
+
+    def __init__(self, n, c0=32, max_batch=8, seed=0, device=0, use_torch_allocator=True):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise MGMCError(2, "no CUDA device available (the U-Net has no CPU fallback)")
+        self.n, self.c0, self.max_batch, self.device = n, c0, max_batch, device
+        self._alloc = TorchAllocator(device) if use_torch_allocator else None
+        h = ctypes.c_void_p()
+        _check(load().mgmc_unet_create(n, c0, max_batch, int(seed) & (2**64 - 1),
+                                       ctypes.byref(self._alloc.struct) if self._alloc else None,
+                                       _stream_handle(None), ctypes.byref(h)))
+        self.h = h
+        cnt = ctypes.c_int64()
+        _check(load().mgmc_unet_n_params(self.h, ctypes.byref(cnt)))
+        self.n_params = int(cnt.value)
+
+    def get_params(self):
+        out = np.zeros(self.n_params, dtype=np.float32)
+        _check(load().mgmc_unet_get_params(self.h, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def set_params(self, theta):
+        theta = np.ascontiguousarray(theta, dtype=np.float32)
+        _check(load().mgmc_unet_set_params(self.h, theta.ctypes.data_as(ctypes.c_void_p)))
+
+    def gradient(self, inputs, targets, batch):
+        loss = ctypes.c_float()
+        g = np.zeros(self.n_params, dtype=np.float32)
+        _check(load().mgmc_unet_gradient(self.h, batch, ctypes.c_void_p(inputs.data_ptr()),
+                                         ctypes.c_void_p(targets.data_ptr()), ctypes.byref(loss),
+                                         g.ctypes.data_as(ctypes.c_void_p)))
+        return float(loss.value), g
+
+    def train(self, inputs, targets, epochs, batch, lr, shuffle_seed=0):
+        losses = np.zeros(max(epochs, 1), dtype=np.float32)
+        _check(load().mgmc_unet_train(self.h, targets.shape[0], ctypes.c_void_p(inputs.data_ptr()),
+                                      ctypes.c_void_p(targets.data_ptr()), epochs, batch, float(lr),
+                                      int(shuffle_seed) & (2**64 - 1), losses.ctypes.data_as(ctypes.c_void_p)))
+        return losses[:epochs]
+
+    def predict(self, inputs, precision="fp32"):
+        torch = _torch()
+        ns = inputs.shape[0]
+        dt = torch.float32 if precision == "fp32" else torch.float64
+        out = torch.empty(ns, self.n * self.n, dtype=dt, device=inputs.device)
+        _check(load().mgmc_unet_predict(self.h, ns, ctypes.c_void_p(inputs.data_ptr()),
+                                        ctypes.c_void_p(out.data_ptr()),
+                                        MGMC_FP32 if precision == "fp32" else MGMC_FP64))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().mgmc_unet_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -80,3 +80,15 @@ def test_input_channels_of_interior_observations():
     assert np.isclose(x[..., 1].sum(), 1.0) and np.isclose(x[..., 2].sum(), 2.0)
     assert x[2, 2, 1] == 0.4 and x[1, 1, 2] == 0.2 and x[1, 2, 1] == 0.2  # x[j, i]
     assert np.all(x[n, :, :] == 0) and np.all(x[:, n, :] == 0)
+
+
+def test_splitmix64_reference_values():
+    # splitmix64 from seed 0: the first outputs of the published generator
+    r = U.SplitMix64(0)
+    assert [r.next() for _ in range(3)] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_epoch_permutation_is_a_permutation():
+    r = U.SplitMix64(9)
+    for n in (1, 2, 17):
+        assert sorted(U.epoch_permutation(n, r)) == list(range(n))
