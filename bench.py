@@ -30,10 +30,11 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# DRAM bytes (read + write) per launch of the fused forward tile kernel on the
-# finest grid (k_tile_fwd<float, 1>), from the ncu capture summarised in
-# profiles/k_tile_fwd_fp32.md; None until captured for the current kernel.
-FINE_SWEEP_TRAFFIC_BYTES = None
+# DRAM bytes (read + write) per launch of the finest-grid forward tile kernel
+# (k_tile_batch<float, 1, 0>) on the 32 x 1023^2 batch, from the ncu capture
+# summarised in profiles/k_tile_batch_fine_fwd_batch32_bayes2d_1023.md; None
+# for other workloads and whenever that kernel changes before it is re-captured.
+FINE_SWEEP_TRAFFIC_BYTES = 415.0e6
 
 TAU_CALIBRATION = 2000     # default untimed cycles used for tau_int on the device
 CPU_SAMPLE_CYCLES = 12     # bounded oracle sample for the CPU baseline
@@ -371,7 +372,7 @@ def run_mine(args):
                                "restriction, all chains",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": f"{peak_kind} HBM copy bandwidth",
-                     "traffic": FINE_SWEEP_TRAFFIC_BYTES,
+                     "traffic": FINE_SWEEP_TRAFFIC_BYTES if args.workload == "batch32-bayes2d-1023" else None,
                      "algorithmic_bytes": sweep_bytes, "avg_ms": fwd_avg,
                      "bwd_sweep_avg_ms": statistics.mean(bwd_ms)},
         "cpu_baseline": cpu,
