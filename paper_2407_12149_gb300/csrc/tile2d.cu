@@ -89,6 +89,9 @@ struct TileGeom {
     // computed), one on the 9-point grids (7 fields; three CTAs per SM overlap instead)
     static constexpr int NSTAGE = FINE ? 2 : 1;
     static constexpr int STAGE = NFLD * FS + (BWD ? PSZ : 0);  // elements per stage buffer
+    // single-stage backward kernels keep a second state buffer: the next tile's state
+    // is copied into it while the current tile still stores its own
+    static constexpr int XALT = (NSTAGE == 1 && BWD) ? FS : 0;
     static constexpr unsigned BOX_BYTES = (unsigned)(SX * SY * sizeof(T));
     static constexpr unsigned PSI_BYTES = (unsigned)(PXA * PY * sizeof(T));
     // TMA: box corners x0 - RX + 4 and (psi) x0 / 2 - RX / 2 + 3 - POFF must be multiples of
@@ -547,9 +550,12 @@ __device__ __forceinline__ void tile_store(const DevLevel<T>& L, T* dst, const T
 // Forward tile (Alg. 1 pre-smoothing + restriction) on a staged stage buffer:
 // X (state, zero-filled here when the sweep starts from psi = 0), Cf (operator
 // fields), F (dense right-hand side, 9-point grids), Rr (residual scratch).
-template <typename T, bool FINE>
+// fields_free() is called by every thread once Cf and F are no longer read (after the
+// residual), so the next tile's copies can start while the restriction runs.
+template <typename T, bool FINE, typename Hook>
 __device__ __forceinline__ void tile_fwd_compute(const DevLevel<T>& L, const DevLevel<T>& C, const CycleState& cs,
-                                                 int x_zero, int bx, int by, T* X, const T* Cf, const T* F, T* Rr)
+                                                 int x_zero, int bx, int by, T* X, const T* Cf, const T* F, T* Rr,
+                                                 Hook&& fields_free)
 {
     using G = TileGeom<T, FINE, false>;
     const int x0 = bx * G::TX, y0 = by * G::TY;
@@ -587,6 +593,7 @@ __device__ __forceinline__ void tile_fwd_compute(const DevLevel<T>& L, const Dev
             sts4(R4 + ry * RW + 4 * gx, r);
         }
         __syncthreads();
+        fields_free();
         // restriction of two coarse sites per item: f_c = sum_p w(p) r(2I + p),
         // fine columns 2I .. 2I + 4 of three rows
         for (int idx = threadIdx.x; idx < (G::TX / 4) * (G::TY / 2); idx += G::NT) {
@@ -631,6 +638,7 @@ __device__ __forceinline__ void tile_fwd_compute(const DevLevel<T>& L, const Dev
             Rr[idx] = r;
         }
         __syncthreads();
+        fields_free();
         // restriction onto the coarse sites of the tile: f_c = sum_p w(p) r(2I + p)
         for (int idx = threadIdx.x; idx < (G::TX / 2) * (G::TY / 2); idx += G::NT) {
             int I = I0 + idx % (G::TX / 2), J = J0 + idx / (G::TX / 2);
@@ -650,9 +658,11 @@ __device__ __forceinline__ void tile_fwd_compute(const DevLevel<T>& L, const Dev
 // Backward tile (prolongation + Alg. 1 post-smoothing) on a staged stage buffer:
 // X (theta*' of the forward pass), Cf, F, Ps (coarse psi box, origin POFF columns
 // before cx0 = (gx0 >> 1) - 1, row cy0 = (gy0 >> 1) - 1).
-template <typename T, bool FINE>
+// fields_free() is called by every thread once Cf, F and Ps are no longer read
+// (after the sweep).
+template <typename T, bool FINE, typename Hook>
 __device__ __forceinline__ void tile_bwd_compute(const DevLevel<T>& L, const CycleState& cs, int bx, int by, T* X,
-                                                 const T* Cf, const T* F, const T* Ps)
+                                                 const T* Cf, const T* F, const T* Ps, Hook&& fields_free)
 {
     using G = TileGeom<T, FINE, true>;
     const int x0 = bx * G::TX, y0 = by * G::TY;
@@ -722,6 +732,7 @@ __device__ __forceinline__ void tile_bwd_compute(const DevLevel<T>& L, const Cyc
     }
     __syncthreads();
     tile_sweep<T, FINE, true, G>(L, cs, X, Cf, F, x0, y0, 1u);
+    fields_free();
     tile_zparts<T, G>(L, X, by * L.ntx + bx);
     tile_store<T, G>(L, L.x, X, x0, y0);
 }
@@ -773,7 +784,8 @@ template <typename T, bool FINE, bool BWD>
 constexpr size_t tile_smem_bytes()
 {
     using G = TileGeom<T, FINE, BWD>;
-    return 2 * (size_t)kHdrBytes + 128 + sizeof(T) * ((size_t)G::NSTAGE * G::STAGE + (BWD ? 0 : (size_t)G::RES));
+    return 2 * (size_t)kHdrBytes + 128 +
+           sizeof(T) * ((size_t)G::NSTAGE * G::STAGE + G::XALT + (BWD ? 0 : (size_t)G::RES));
 }
 
 // Persistent tile kernel of one grid depth of every chain.  Tile order: with
@@ -798,7 +810,7 @@ __global__ void __launch_bounds__(TileGeom<T, FINE, BWD>::NT, 3)
                           reinterpret_cast<TileJob<T>*>(smem_raw + kHdrBytes)};
     unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + 2 * kHdrBytes);
     T* buf = reinterpret_cast<T*>(smem_raw + 2 * kHdrBytes + 128);
-    T* Rr = buf + G::NSTAGE * G::STAGE;
+    T* Rr = buf + G::NSTAGE * G::STAGE + G::XALT;
     __shared__ CycleState cs_s[2];
     __shared__ int jid[2];
 
@@ -845,8 +857,11 @@ __global__ void __launch_bounds__(TileGeom<T, FINE, BWD>::NT, 3)
         if (threadIdx.x == 0) jid[hs] = j;
         __syncthreads();
     };
-    // the TMA copies of tile t (header in slot hs) into stage buffer ds (thread 0)
-    auto issue = [&](int t, int hs, int ds) {
+    // state buffer of the k-th tile: field 0 of its stage, or the second state buffer
+    // for odd k of a single-stage backward kernel
+    auto xbuf = [&](int k, int ds) { return (G::XALT && (k & 1)) ? buf + G::STAGE : buf + ds * G::STAGE; };
+    // the TMA copies of tile t (header in slot hs) into stage buffer ds, its state into xd (thread 0)
+    auto issue = [&](int t, int hs, int ds, T* xd) {
         const TileJob<T>& J = *hdr[hs];
         const int lt = t - J.tile0;
         const int x0 = (lt % J.L.ntx) * G::TX, y0 = (lt / J.L.ntx) * G::TY;
@@ -856,7 +871,7 @@ __global__ void __launch_bounds__(TileGeom<T, FINE, BWD>::NT, 3)
         const bool loadx = BWD || !x_zero;
         unsigned bytes = (unsigned)(G::NFLD - (loadx ? 0 : 1)) * G::BOX_BYTES + (BWD ? G::PSI_BYTES : 0u);
         mbar_expect_tx(&bar[ds], bytes);
-        if (loadx) tma_load_2d(b, &M[0], cx, cy, &bar[ds]);
+        if (loadx) tma_load_2d(xd, &M[0], cx, cy, &bar[ds]);
         for (int f = 1; f < G::NFLD; ++f) tma_load_2d(b + f * G::FS, &M[f], cx, cy, &bar[ds]);
         if (BWD) {
             const int gx0 = x0 - G::RX, gy0 = y0 - G::R;
@@ -865,8 +880,12 @@ __global__ void __launch_bounds__(TileGeom<T, FINE, BWD>::NT, 3)
         }
     };
 
+    // single-stage kernels issue the next tile's copies as soon as the current tile no
+    // longer reads its operator fields (the state is not copied forward from psi = 0,
+    // and has its own second buffer backward)
+    const bool early = G::NSTAGE == 1 && (BWD || x_zero);
     fetch(tb, 0);
-    if (threadIdx.x == 0) issue(tb, 0, 0);
+    if (threadIdx.x == 0) issue(tb, 0, 0, xbuf(0, 0));
     for (int t = tb, k = 0; t < te; t += step, ++k) {
         const int hs = k & 1;
         const int ds = G::NSTAGE == 2 ? (k & 1) : 0;
@@ -874,7 +893,7 @@ __global__ void __launch_bounds__(TileGeom<T, FINE, BWD>::NT, 3)
         const bool more = t + step < te;
         if (G::NSTAGE == 2 && more) {
             fetch(t + step, hs ^ 1);
-            if (threadIdx.x == 0) issue(t + step, hs ^ 1, ds ^ 1);
+            if (threadIdx.x == 0) issue(t + step, hs ^ 1, ds ^ 1, xbuf(k + 1, ds ^ 1));
         }
         const bool ok = mbar_wait(&bar[ds], parity);
         if (__syncthreads_or(!ok)) {
@@ -891,17 +910,24 @@ __global__ void __launch_bounds__(TileGeom<T, FINE, BWD>::NT, 3)
         const int lt = t - J.tile0;
         const int bx = lt % J.L.ntx, by = lt / J.L.ntx;
         T* b = buf + ds * G::STAGE;
+        auto fields_free = [&]() {
+            if (!(early && more)) return;
+            fence_proxy_async();
+            fetch(t + step, hs ^ 1);
+            __syncthreads();
+            if (threadIdx.x == 0) issue(t + step, hs ^ 1, 0, xbuf(k + 1, 0));
+        };
         if constexpr (BWD)
-            tile_bwd_compute<T, FINE>(J.L, cs_s[hs], bx, by, b, b + G::FS, b + (1 + G::NCOEF) * G::FS,
-                                      b + G::NFLD * G::FS);
+            tile_bwd_compute<T, FINE>(J.L, cs_s[hs], bx, by, xbuf(k, ds), b + G::FS, b + (1 + G::NCOEF) * G::FS,
+                                      b + G::NFLD * G::FS, fields_free);
         else
-            tile_fwd_compute<T, FINE>(J.L, J.C, cs_s[hs], x_zero, bx, by, b, b + G::FS, b + (1 + G::NCOEF) * G::FS,
-                                      Rr);
+            tile_fwd_compute<T, FINE>(J.L, J.C, cs_s[hs], x_zero, bx, by, xbuf(k, ds), b + G::FS,
+                                      b + (1 + G::NCOEF) * G::FS, Rr, fields_free);
         fence_proxy_async();
         __syncthreads();
-        if (G::NSTAGE == 1 && more) {
+        if (G::NSTAGE == 1 && !early && more) {
             fetch(t + step, hs ^ 1);
-            if (threadIdx.x == 0) issue(t + step, hs ^ 1, 0);
+            if (threadIdx.x == 0) issue(t + step, hs ^ 1, 0, xbuf(k + 1, 0));
         }
     }
 }
