@@ -168,11 +168,13 @@ __device__ void s_sweep(const DevLevel<T>& L, const CycleState& cs, T* X, const 
     const int nq = (n + 3) >> 2;
     const int npairs = 2 * nq * n * (DIM == 3 ? n : 1);
     if (cs.noise) {
+        const uint4 ctr = noise_counter(cs, 0u, 0u, L.level, slot);
+        const unsigned k0 = (unsigned)cs.seed, k1 = (unsigned)(cs.seed >> 32);
         for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
             const int px = p & 1, q = (p >> 1) % nq;
             if (4 * q + px >= n) continue;
             T z0, z1;
-            draw_pair<T>(cs, (unsigned)p, 0u, L.level, slot, z0, z1);
+            draw_pair_ctr<T>(ctr, (unsigned)p, k0, k1, z0, z1);
             Z[2 * p] = z0;
             Z[2 * p + 1] = z1;
         }

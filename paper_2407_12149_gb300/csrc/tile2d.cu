@@ -467,6 +467,10 @@ __device__ __forceinline__ void tile_phase(const DevLevel<T>& L, const CycleStat
     const int n = L.n;
     const int nq = (n + 3) >> 2;
     const int q0 = x0 >> 2;
+    // counter words and key of this sweep's site noise, out of the item loop
+    const uint4 ctr = noise_counter(cs, 0u, 0u, L.level, slot);
+    const unsigned k0 = (unsigned)cs.seed, k1 = (unsigned)(cs.seed >> 32);
+    const bool noise = cs.noise != 0;
     for (int it = threadIdx.x; it < NQ * NR; it += G::NT) {
         const int gq = it % NQ + GQ0;
         const int dy = DY0 + STEP * (it / NQ);
@@ -479,9 +483,9 @@ __device__ __forceinline__ void tile_phase(const DevLevel<T>& L, const CycleStat
         const bool v1 = rowok && dx1 >= -rp && dx1 < G::TX + rp && i1 >= 0 && i1 < n;
         if (!v0 && !v1) continue;
         T z0 = T(0), z1 = T(0);
-        if (cs.noise) {
-            unsigned pair = (unsigned)(((long long)j * nq + (q0 + gq)) * 2 + px);
-            draw_pair<T>(cs, pair, 0u, L.level, slot, z0, z1);
+        if (noise) {
+            const unsigned pair = (unsigned)(((long long)j * nq + (q0 + gq)) * 2 + px);
+            draw_pair_ctr<T>(ctr, pair, k0, k1, z0, z1);
         }
         if constexpr (sizeof(T) == 4) {
             // FP32: whole 4-site groups as float4 rows of the staged tile
