@@ -138,3 +138,29 @@ def test_resume_and_get_state_reproduce_one_run(torch_mod):
     s2.get_state(y)
     torch.cuda.synchronize()
     assert torch.equal(y, x1)
+
+
+@pytest.mark.parametrize("precision,m", [("fp64", 40), ("fp64", 16), ("fp32", 40)])
+def test_uniform_batch_low_rank_tails_match_oracle(torch_mod, precision, m):
+    """Chains of one size get CTA groups of their own in the tile launches; the
+    low-rank step after each sweep (Alg. 3) takes its register form at m = 16 and
+    its general form at m = 40."""
+    torch = torch_mod
+    from paper_2407_12149_gb300.mgmc import BatchSampler
+    ps = [inputs.make_problem(f"u{c}", 2, 127, kappa2_seed=700 + c, m=m, obs_seed=800 + c, qoi_cells=32)
+          for c in range(3)]
+    b = BatchSampler(ps, precision=precision)
+    xs = b.zeros()
+    n_steps = 6 if precision == "fp64" else 40
+    b.sample(xs, n_steps, 41)
+    torch.cuda.synchronize()
+    for c, p in enumerate(ps):
+        o = oracle.Oracle(p.dim, p.n, p.n_levels, kappa2=p.kappa2, obs_site=p.obs_site, obs_w=p.obs_w,
+                          Gamma=p.Gamma, y=p.y)
+        xo = o.sample(n_steps, 41, chain=c, qoi=False)
+        xg = xs[c].cpu().numpy().astype(np.float64)
+        rms = np.sqrt(np.mean(xo ** 2))
+        if precision == "fp64":
+            assert np.all(np.abs(xg - xo) <= 1e-11 * np.maximum(np.abs(xo), rms)), f"chain {c}"
+        else:
+            assert np.abs(xg - xo).max() <= 2e-4 * rms, f"chain {c}"
