@@ -144,6 +144,7 @@ WORKLOADS = {
     "bayes2d-4095": {"n": 4095, "chains": 1},            # HBM-resident single-grid variants (roofline)
     "bayes2d-8191": {"n": 8191, "chains": 1},
     "batch512-mixed": {"n": 511, "chains": 512, "mixed": True},   # 128 chains each of 63^2 .. 511^2
+    "bayes3d-127": {"n": 127, "chains": 1, "dim": 3},     # 127^3, kappa^2 = 25, 32 obs, coarsest 3^3
     "warmstart-255": {"n": 255, "chains": 64, "warm": True},       # learned warm start (U-Net), 255^2
 }
 
@@ -182,10 +183,15 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def single_problem(inputs, wl):
+    """The posterior of a single-chain (or one-posterior batch) workload."""
+    return inputs.config3(n=wl["n"]) if wl.get("dim") == 3 else inputs.config2(n=wl["n"])
+
+
 def make_sampler(M, inputs, wl, precision, local):
     """Sampler (one chain) or BatchSampler (many chains) of a workload."""
     if wl["chains"] == 1:
-        p = inputs.config2(n=wl["n"])
+        p = single_problem(inputs, wl)
         return M.Sampler(p, precision=precision, device=local), [p]
     if wl.get("mixed"):
         ps = [inputs.make_problem(f"mixed-{c}", 2, n, kappa2_seed=c, m=8 + (c % 25), obs_seed=1000 + c,
@@ -241,7 +247,7 @@ def run_mine(args):
 
     # --- CPU baseline (rank 0, one GPU only), before the GPU timing ------------
     cpu = None
-    if rank == 0 and ws == 1 and wl["n"] == 1023 and not wl.get("mixed"):
+    if rank == 0 and ws == 1 and wl["n"] == 1023 and not wl.get("mixed") and wl.get("dim", 2) == 2:
         try:
             tau_ref, _ = load_tau_ref()
             cpu = cpu_baseline(inputs.config2(), tau_ref)
@@ -321,7 +327,7 @@ def run_mine(args):
     # --- plain FP64 single-chain GPU MGMC on the same posterior (comparison) ---
     plain = None
     if rank == 0 and not wl.get("mixed") and wl["n"] <= 1023:
-        s64 = M.Sampler(inputs.config2(n=wl["n"]), precision="fp64", device=local)
+        s64 = M.Sampler(single_problem(inputs, wl), precision="fp64", device=local)
         x64 = s64.zeros()
         s64.sample(x64, 20, 99)
         torch.cuda.synchronize()
@@ -342,16 +348,28 @@ def run_mine(args):
         return
     peak, peak_kind = measured_peak()
     fine_sites = sum(p.N for p in ps if p.n > 31)
-    # algorithmic bytes of the depth-0 forward launch (every chain's finest grid), FP32: read theta
-    # and s*kappa^2 (4 + 4 B/site), write theta*_s (4 B/site) and the restricted residual (4 B per
-    # coarse site = 1 B per fine site); the noise is generated, never stored
-    sweep_bytes = 13 * fine_sites
     fwd_avg = statistics.mean(fwd_ms)
+    if wl.get("dim") == 3:
+        # the timed region is the finest grid's forward sweep (two red-black colour launches); with constant
+        # kappa^2 the sweep must read and write theta (4 + 4 B/site) -- the kernel also reads the
+        # s*kappa^2 field (4 B/site), which the algorithmic figure does not count
+        sweep_bytes = 8 * fine_sites
+        kernel = "k_sweep_colour<float,3>: finest-grid forward Gibbs sweep (two red-black colour launches)"
+    else:
+        # algorithmic bytes of the depth-0 forward launch (every chain's finest grid), FP32: read theta
+        # and s*kappa^2 (4 + 4 B/site), write theta*_s (4 B/site) and the restricted residual (4 B per
+        # coarse site = 1 B per fine site); the noise is generated, never stored
+        sweep_bytes = 13 * fine_sites
+        kernel = "k_tile_fwd_batch<float,1>: finest-grid forward Gibbs sweep + residual + restriction, all chains"
     achieved = sweep_bytes / (fwd_avg * 1e-3) / 1e9
-    desc = ("32 independent chains of " if batch and not wl.get("mixed") else "") + \
-        (f"{nch} chains, grids 63^2..511^2 (128 x 4 sizes), own kappa^2 and 8-32 obs" if wl.get("mixed") else
-         f"{ps[0].n}^2 Bayesian posterior: kappa^2 = 10 exp(g), 16 point obs, Gamma = 1e-4 I, "
-         f"{ps[0].n_levels}-grid V(1,1)-cycle, low-rank Gibbs smoother")
+    if wl.get("dim") == 3:
+        desc = (f"{ps[0].n}^3 Bayesian posterior: kappa^2 = 25, 32 point obs, Gamma = 1e-4 I, "
+                f"{ps[0].n_levels}-grid V(1,1)-cycle, coarsest 3^3, low-rank Gibbs smoother")
+    else:
+        desc = ("32 independent chains of " if batch and not wl.get("mixed") else "") + \
+            (f"{nch} chains, grids 63^2..511^2 (128 x 4 sizes), own kappa^2 and 8-32 obs" if wl.get("mixed") else
+             f"{ps[0].n}^2 Bayesian posterior: kappa^2 = 10 exp(g), 16 point obs, Gamma = 1e-4 I, "
+             f"{ps[0].n_levels}-grid V(1,1)-cycle, low-rank Gibbs smoother")
     line = {
         "metric": "QoI ESS/s", "value": value, "unit": "QoI ESS/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -368,8 +386,7 @@ def run_mine(args):
                    "launches_per_cycle": launches,
                    "plain_fp64_single_chain": plain},
         "roofline": {"bound": "hbm",
-                     "kernel": "k_tile_fwd_batch<float,1>: finest-grid forward Gibbs sweep + residual + "
-                               "restriction, all chains",
+                     "kernel": kernel,
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": f"{peak_kind} HBM copy bandwidth",
                      "traffic": FINE_SWEEP_TRAFFIC_BYTES if args.workload == "batch32-bayes2d-1023" else None,

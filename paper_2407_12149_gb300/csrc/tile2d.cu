@@ -810,8 +810,8 @@ __global__ void __launch_bounds__(TileGeom<T, FINE, BWD>::NT, 3)
     // TMA destinations start on 128-byte boundaries (the launch adds 128 bytes of slack)
     unsigned char* smem_raw =
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
-    TileJob<T>* hdr[2] = {reinterpret_cast<TileJob<T>*>(smem_raw),
-                          reinterpret_cast<TileJob<T>*>(smem_raw + kHdrBytes)};
+    // header slot s (computed, not an indexed array: that would live in local memory)
+    auto hdr = [smem_raw](int s) { return reinterpret_cast<TileJob<T>*>(smem_raw + s * kHdrBytes); };
     unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + 2 * kHdrBytes);
     T* buf = reinterpret_cast<T*>(smem_raw + 2 * kHdrBytes + 128);
     T* Rr = buf + G::NSTAGE * G::STAGE + G::XALT;
@@ -849,14 +849,14 @@ __global__ void __launch_bounds__(TileGeom<T, FINE, BWD>::NT, 3)
         const bool other = jid[hs ^ 1] == j;
         __syncthreads();  // every thread has read jid[]
         if (other) {
-            const unsigned long long* s = reinterpret_cast<const unsigned long long*>(hdr[hs ^ 1]);
-            unsigned long long* d = reinterpret_cast<unsigned long long*>(hdr[hs]);
+            const unsigned long long* s = reinterpret_cast<const unsigned long long*>(hdr(hs ^ 1));
+            unsigned long long* d = reinterpret_cast<unsigned long long*>(hdr(hs));
             for (int w = threadIdx.x; w < (int)(sizeof(TileJob<T>) / 8); w += G::NT) d[w] = s[w];
             if (threadIdx.x == 0) cs_s[hs] = cs_s[hs ^ 1];
             __syncthreads();
         } else {
-            load_job(*hdr[hs], jobs + j);
-            if (threadIdx.x == 0) cs_s[hs] = *hdr[hs]->P.cs;
+            load_job(*hdr(hs), jobs + j);
+            if (threadIdx.x == 0) cs_s[hs] = *hdr(hs)->P.cs;
         }
         if (threadIdx.x == 0) jid[hs] = j;
         __syncthreads();
@@ -866,7 +866,7 @@ __global__ void __launch_bounds__(TileGeom<T, FINE, BWD>::NT, 3)
     auto xbuf = [&](int k, int ds) { return (G::XALT && (k & 1)) ? buf + G::STAGE : buf + ds * G::STAGE; };
     // the TMA copies of tile t (header in slot hs) into stage buffer ds, its state into xd (thread 0)
     auto issue = [&](int t, int hs, int ds, T* xd) {
-        const TileJob<T>& J = *hdr[hs];
+        const TileJob<T>& J = *hdr(hs);
         const int lt = t - J.tile0;
         const int x0 = (lt % J.L.ntx) * G::TX, y0 = (lt / J.L.ntx) * G::TY;
         const int cx = x0 - G::RX + 4, cy = y0 - G::R + 1;  // padded coordinates of the box corner
@@ -902,7 +902,7 @@ __global__ void __launch_bounds__(TileGeom<T, FINE, BWD>::NT, 3)
         const bool ok = mbar_wait(&bar[ds], parity);
         if (__syncthreads_or(!ok)) {
             if (threadIdx.x == 0) {
-                hdr[hs]->P.cs->status = 2;
+                hdr(hs)->P.cs->status = 2;
                 __threadfence();
                 mbar_wait(&bar[ds], parity);
                 if (G::NSTAGE == 2 && more) mbar_wait(&bar[ds ^ 1], (unsigned)(((k + 1) >> 1) & 1));
@@ -910,7 +910,7 @@ __global__ void __launch_bounds__(TileGeom<T, FINE, BWD>::NT, 3)
             __syncthreads();
             return;
         }
-        const TileJob<T>& J = *hdr[hs];
+        const TileJob<T>& J = *hdr(hs);
         const int lt = t - J.tile0;
         const int bx = lt % J.L.ntx, by = lt / J.L.ntx;
         T* b = buf + ds * G::STAGE;
