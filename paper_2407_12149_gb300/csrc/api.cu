@@ -292,6 +292,16 @@ mgmc_status build_device_levels(mgmc_ctx* h, const HostProblem& hp)
         if (e != cudaSuccess)
             return fail(MGMC_ERR_CUDA, std::string("coarse kernel set-up: ") + cudaGetErrorString(e));
     }
+    // general path: residual field of every smoothed grid, low-rank scratch
+    if (!h->fused) {
+        for (int l = h->top + 1; l < hp.n_levels; ++l) {
+            DevLevel<T>& D = levels[l];
+            D.res = (T*)h->buf.get((size_t)D.alloc * sizeof(T));
+            if (!D.res) return fail(MGMC_ERR_OOM, "allocator returned NULL");
+            if (hp.m > 0) D.lrv = upload(h, std::vector<double>((size_t)2 * hp.m, 0.0), st);
+        }
+        if (st != MGMC_OK) return fail(st, "device upload failed");
+    }
     // fused tile path: second state buffer, per-tile observation entries, G/H in T, B^T G
     if (h->fused) {
         for (int l = h->top + 1; l < hp.n_levels; ++l) {

@@ -83,6 +83,9 @@ struct DevLevel {
     const long long* h_site;      // coarse padded offsets
     const T* hT;                  // [rows * m]
     const double* BtG;            // B_l^T G_l(forward), [m * m]
+    // general (unfused) path
+    double* lrv;                  // [2m] v, then z = B^T theta*_s, of the level's last low-rank step
+    T* res;                       // residual f_l - A_l theta on the padded layout (restriction input)
 };
 
 // Tile shape of the fused 2D kernels: TX x TY interior sites per CTA.

@@ -1,14 +1,15 @@
 // kernels.cu -- CUDA kernels of one MGMC V-cycle (Alg. 1) for sm_103a.
 //
 // Per level l (finest first) the host enqueues:
-//   k_sweep_colour  x nu1 sweeps x colours : forward random Gibbs sweep (Alg. 3 line 11)
-//   k_lowrank                              : theta' = theta* - G (B^T theta*) (Eq. low_rank_update)
-//   k_restrict                             : f_{l-1} = P^T (f_l - A_l theta') and
-//                                            g_{l-1} = g_l - Gamma^-1 B^T theta'
+//   k_sweep_colour  x nu1 sweeps x colours : forward random Gibbs sweep (Alg. 3)
+//   k_lowrank_v, k_lowrank_apply           : theta' = theta* - G (B^T theta*) (Eq. low_rank_update):
+//                                            one CTA forms the m-vector, many CTAs apply G's rows
+//   k_residual, k_restrict                 : r = f_l - A_l theta' on the fine grid, then
+//                                            f_{l-1} = P^T r and d_{l-1} = d_l - B_l^T theta'
 // the grids with n <= coarse_max_n run as one k_coarse_cycle (coarse.cu),
 // which ends in the exact coarsest Cholesky sample (Sec. 2.5), and back up:
 //   k_prolong                              : theta += P psi_{l-1}
-//   k_sweep_colour  (reverse colours), k_lowrank (backward G)
+//   k_sweep_colour  (reverse colours), k_lowrank_v + k_lowrank_apply (backward G)
 // and k_qoi_advance records F^T theta and advances the cycle counter.
 //
 // Low-rank bookkeeping: the right-hand side of level l is kept as
@@ -16,12 +17,13 @@
 // d_l; on the finest level fdense_L = 0 and d_L = y (Eq. f_ell_definition).
 // Alg. 3 is evaluated as
 //   theta*_s = Gibbs sweep of the dense part fdense_l + D^1/2 z   (k_sweep_colour)
-//   theta'   = theta*_s - G (B^T theta*_s - d_l - L_Gamma z')     (k_lowrank)
+//   theta'   = theta*_s - G (B^T theta*_s - d_l - L_Gamma z')     (k_lowrank_v, k_lowrank_apply)
 // which equals theta* - G B^T theta* of Eq. lowrank_gibbs_two_steps with
 // theta* = theta*_s + C (Gamma^-1 d_l + xi_LR), because C - G B^T C = G Gamma
 // (Eq. Bellstar_definition); no term of size |Gamma^-1 y| is ever formed.
 // Restriction: fdense_{l-1} = P^T (fdense_l - A_l theta'), d_{l-1} = d_l - B_l^T theta'
-// (P^T B_l = B_{l-1}, Eq. A_ell_1_B_ell_1).
+// (P^T B_l = B_{l-1}, Eq. A_ell_1_B_ell_1); B_l^T theta' = z - (B_l^T G) v needs no
+// second read of theta'.
 #include "kernels.cuh"
 
 namespace mgmc {
@@ -87,80 +89,6 @@ __global__ void k_sweep_colour(DevLevel<T> L, DevProblem P, int redblack, int co
     sweep_item<T, DIM>(L, P, cs, redblack != 0, colour, slot, item);
 }
 
-// ---------------------------------------------------------------------------
-// CTA-wide low-rank step (single-CTA kernel of the unfused path)
-// ---------------------------------------------------------------------------
-// theta' = theta*_s - G (B^T theta*_s - d - L_Gamma z') (skipped for dir < 0);
-// with want_dnext also d_{l-1} = d_l - B_l^T theta'
-template <typename T>
-__device__ void cta_lowrank(const DevLevel<T>& L, const DevProblem& P, const CycleState& cs, int dir, unsigned slot,
-                            bool want_dnext)
-{
-    __shared__ double z[kMaxObs];
-    __shared__ double zp[kMaxObs];
-    const int m = P.m;
-    if (m == 0) return;
-    for (int k = threadIdx.x; k < m; k += blockDim.x) {
-        double acc = 0.0;
-        for (int t = L.bcol_ptr[k]; t < L.bcol_ptr[k + 1]; ++t) acc += L.bcol_w[t] * (double)L.x[L.bcol_site[t]];
-        z[k] = acc;
-        zp[k] = (dir >= 0 && cs.noise) ? lowrank_normal<T>(cs, L.level, slot, k) : 0.0;
-    }
-    __syncthreads();
-    if (dir >= 0) {
-        // v = B^T theta*_s - d - L_Gamma z'   (kept in z)
-        double v = 0.0;
-        int k = threadIdx.x;
-        if (k < m) {
-            double lz = 0.0;
-            if (cs.noise) {
-                if (P.gamma_diag) {
-                    lz = P.LG[k * m + k] * zp[k];
-                } else {
-                    for (int t = 0; t <= k; ++t) lz += P.LG[k * m + t] * zp[t];
-                }
-            }
-            v = z[k] - L.d[k] - lz;
-        }
-        __syncthreads();
-        if (k < m) z[k] = v;
-        __syncthreads();
-        const int rows = L.g_rows[dir];
-        const double* G = L.g_val[dir];
-        for (int r = threadIdx.x; r < rows; r += blockDim.x) {
-            double acc = 0.0;
-            for (int kk = 0; kk < m; ++kk) acc += G[(long long)r * m + kk] * z[kk];
-            long long s = L.g_site[dir][r];
-            L.x[s] = (T)((double)L.x[s] - acc);
-        }
-        __syncthreads();
-    }
-    if (!want_dnext) return;
-    for (int k = threadIdx.x; k < m; k += blockDim.x) {
-        double acc = 0.0;
-        for (int t = L.bcol_ptr[k]; t < L.bcol_ptr[k + 1]; ++t) acc += L.bcol_w[t] * (double)L.x[L.bcol_site[t]];
-        L.dnext[k] = L.d[k] - acc;
-    }
-    __syncthreads();
-}
-
-template <typename T, int DIM>
-__device__ __forceinline__ T restrict_site(const DevLevel<T>& F, const DevLevel<T>& C, int I, int J, int K)
-{
-    T acc = T(0);
-    const int nz = DIM == 3 ? 3 : 1;
-    for (int pz = 0; pz < nz; ++pz)
-        for (int py = 0; py < 3; ++py)
-            for (int px = 0; px < 3; ++px) {
-                int fi = 2 * I + px, fj = 2 * J + py, fk = DIM == 3 ? 2 * K + pz : 0;
-                long long e = site_offset(DIM, F.pitch, F.plane, F.base, fi, fj, fk);
-                T wgt = (T)(pw(px - 1) * pw(py - 1) * (DIM == 3 ? pw(pz - 1) : 1.0));
-                T r = (F.f ? F.f[e] : T(0)) - apply_A<DIM>(F, e);
-                acc += wgt * r;
-            }
-    return acc;
-}
-
 template <typename T, int DIM>
 __device__ __forceinline__ T prolong_site(const DevLevel<T>& C, int fi, int fj, int fk)
 {
@@ -203,13 +131,80 @@ __device__ __forceinline__ T prolong_site(const DevLevel<T>& C, int fi, int fj, 
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// Low-rank step of the unfused path (Alg. 3), two launches.  k_lowrank_v (one CTA):
+// z = B^T theta*_s, v = z - d - L_Gamma z' into lrv (dir >= 0); for dir < 0 (no
+// smoothing) only d_{l-1} = d_l - z.
+// ---------------------------------------------------------------------------
 template <typename T>
-__global__ void k_lowrank(DevLevel<T> L, DevProblem P, int dir, unsigned slot, int want_dnext)
+__global__ void k_lowrank_v(DevLevel<T> L, DevProblem P, int dir, unsigned slot, int want_dnext)
 {
+    __shared__ double z[kMaxObs];
+    __shared__ double zp[kMaxObs];
     const CycleState cs = *P.cs;
-    cta_lowrank<T>(L, P, cs, dir, slot, want_dnext != 0);
+    const int m = P.m;
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        double acc = 0.0;
+        for (int t = L.bcol_ptr[k]; t < L.bcol_ptr[k + 1]; ++t) acc += L.bcol_w[t] * (double)L.x[L.bcol_site[t]];
+        z[k] = acc;
+        zp[k] = (dir >= 0 && cs.noise) ? lowrank_normal<T>(cs, L.level, slot, k) : 0.0;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        if (dir >= 0) {
+            double lz = 0.0;
+            if (cs.noise) {
+                if (P.gamma_diag)
+                    lz = P.LG[k * m + k] * zp[k];
+                else
+                    for (int t = 0; t <= k; ++t) lz += P.LG[k * m + t] * zp[t];
+            }
+            L.lrv[k] = z[k] - L.d[k] - lz;
+            L.lrv[m + k] = z[k];
+        } else if (want_dnext) {
+            L.dnext[k] = L.d[k] - z[k];
+        }
+    }
 }
 
+// theta' = theta*_s - G v on G's rows, spread over the grid; with want_dnext block 0
+// also forms d_{l-1} = d_l - B^T theta' = d_l - z + (B^T G) v
+template <typename T>
+__global__ void k_lowrank_apply(DevLevel<T> L, DevProblem P, int dir, int want_dnext)
+{
+    __shared__ double v[kMaxObs];
+    const int m = P.m;
+    for (int k = threadIdx.x; k < m; k += blockDim.x) v[k] = L.lrv[k];
+    __syncthreads();
+    const int rows = L.g_rows[dir];
+    const double* G = L.g_val[dir];
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int kk = 0; kk < m; ++kk) acc += G[(long long)r * m + kk] * v[kk];
+        const long long s = L.g_site[dir][r];
+        L.x[s] = (T)((double)L.x[s] - acc);
+    }
+    if (want_dnext && blockIdx.x == 0)
+        for (int k = threadIdx.x; k < m; k += blockDim.x) {
+            double acc = 0.0;
+            for (int t = 0; t < m; ++t) acc += L.BtG[k * m + t] * v[t];
+            L.dnext[k] = L.d[k] - L.lrv[m + k] + acc;
+        }
+}
+
+// r = f_l - A_l theta at every interior site of the fine grid (the restriction's input)
+template <typename T, int DIM>
+__global__ void k_residual(DevLevel<T> F)
+{
+    long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long N = (long long)F.n * F.n * (DIM == 3 ? F.n : 1);
+    if (s >= N) return;
+    int i = (int)(s % F.n), j = (int)((s / F.n) % F.n), k = DIM == 3 ? (int)(s / ((long long)F.n * F.n)) : 0;
+    long long e = site_offset(DIM, F.pitch, F.plane, F.base, i, j, k);
+    F.res[e] = (F.f ? F.f[e] : T(0)) - apply_A<DIM>(F, e);
+}
+
+// f_c(I) = sum_p w(p) r(2I + p) over the 3^d fine sites 2I + p, p in {0, 1, 2}^d, from the residual field
 template <typename T, int DIM>
 __global__ void k_restrict(DevLevel<T> F, DevLevel<T> C)
 {
@@ -217,7 +212,17 @@ __global__ void k_restrict(DevLevel<T> F, DevLevel<T> C)
     long long N = (long long)C.n * C.n * (DIM == 3 ? C.n : 1);
     if (s >= N) return;
     int I = (int)(s % C.n), J = (int)((s / C.n) % C.n), K = DIM == 3 ? (int)(s / ((long long)C.n * C.n)) : 0;
-    C.f[site_offset(DIM, C.pitch, C.plane, C.base, I, J, K)] = restrict_site<T, DIM>(F, C, I, J, K);
+    T acc = T(0);
+    const int nz = DIM == 3 ? 3 : 1;
+    for (int pz = 0; pz < nz; ++pz)
+        for (int py = 0; py < 3; ++py)
+            for (int px = 0; px < 3; ++px) {
+                long long e = site_offset(DIM, F.pitch, F.plane, F.base, 2 * I + px, 2 * J + py,
+                                          DIM == 3 ? 2 * K + pz : 0);
+                T wgt = (T)(pw(px - 1) * pw(py - 1) * (DIM == 3 ? pw(pz - 1) : 1.0));
+                acc += wgt * F.res[e];
+            }
+    C.f[site_offset(DIM, C.pitch, C.plane, C.base, I, J, K)] = acc;
 }
 
 template <typename T, int DIM>
@@ -410,19 +415,29 @@ void launch_lowrank(const DevLevel<T>& L, const DevProblem& P, int dir, unsigned
                     int& launches)
 {
     if (P.m == 0) return;
-    k_lowrank<T><<<1, 256, 0, st>>>(L, P, dir, slot, dnext ? 1 : 0);
+    k_lowrank_v<T><<<1, 256, 0, st>>>(L, P, dir, slot, dnext ? 1 : 0);
+    ++launches;
+    if (dir < 0) return;
+    const int rows = L.g_rows[dir];
+    int nb = (rows + 255) / 256;
+    nb = nb < 1 ? 1 : (nb > 1024 ? 1024 : nb);
+    k_lowrank_apply<T><<<nb, 256, 0, st>>>(L, P, dir, dnext ? 1 : 0);
     ++launches;
 }
 
 template <typename T>
 void launch_restrict(const DevLevel<T>& F, const DevLevel<T>& C, cudaStream_t st, int& launches)
 {
+    long long NF = (long long)F.n * F.n * (F.dim == 3 ? F.n : 1);
     long long N = (long long)C.n * C.n * (C.dim == 3 ? C.n : 1);
-    if (C.dim == 2)
+    if (C.dim == 2) {
+        k_residual<T, 2><<<blocks_for(NF, 256), 256, 0, st>>>(F);
         k_restrict<T, 2><<<blocks_for(N, 256), 256, 0, st>>>(F, C);
-    else
+    } else {
+        k_residual<T, 3><<<blocks_for(NF, 256), 256, 0, st>>>(F);
         k_restrict<T, 3><<<blocks_for(N, 256), 256, 0, st>>>(F, C);
-    ++launches;
+    }
+    launches += 2;
 }
 
 template <typename T>
