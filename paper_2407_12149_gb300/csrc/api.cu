@@ -590,7 +590,7 @@ mgmc_status mgmc_create(const mgmc_config* cfg_in, const mgmc_allocator* alloc, 
         const size_t budget = 200 * 1024;
         std::vector<int> nl;
         for (int l = 0; l < h->L; ++l) nl.push_back(hp.lev[l].n);
-        for (int l = 0; l < h->L && l < 16; ++l) {
+        for (int l = 0; l < h->L && l < kCoarseMaxLevels; ++l) {
             size_t bytes = (size_t)coarse_smem_elems(cfg.dim, nl.data(), l, l == h->L - 1) * esz;
             if (hp.lev[l].n <= cmax && bytes + 16384 <= budget) h->top = l;
         }

@@ -160,8 +160,8 @@ template <typename T, int DIM>
 __device__ void s_sweep(const DevLevel<T>& L, const CycleState& cs, T* X, const T* F, const T* CS, T* Z, int dir,
                         unsigned slot)
 {
-    const int seq2[4] = {0, 3, 2, 1};
-    const int seq3[8] = {0, 6, 5, 3, 4, 2, 1, 7};
+    // colour orders (0, 3, 2, 1) and (0, 6, 5, 3, 4, 2, 1, 7) as packed nibbles (no local-memory table)
+    auto seq = [](int i) { return (int)(((DIM == 2 ? 0x1230u : 0x71243560u) >> (4 * i)) & 0xFu); };
     constexpr int NCOL = DIM == 2 ? 4 : 8;
     const int n = L.n, S = n + 2;
     const int SZ = DIM == 3 ? S * S * S : S * S;
@@ -181,7 +181,7 @@ __device__ void s_sweep(const DevLevel<T>& L, const CycleState& cs, T* X, const 
         __syncthreads();
     }
     for (int ci = 0; ci < NCOL; ++ci) {
-        const int c = DIM == 2 ? seq2[dir == 0 ? ci : NCOL - 1 - ci] : seq3[dir == 0 ? ci : NCOL - 1 - ci];
+        const int c = seq(dir == 0 ? ci : NCOL - 1 - ci);
         const int px = c & 1, py = (c >> 1) & 1, pz = (c >> 2) & 1;
         const int ny = (n - py + 1) >> 1;
         const int nz = DIM == 3 ? (n - pz + 1) >> 1 : 1;
@@ -401,34 +401,55 @@ long long coarse_smem_elems(int dim, const int* n_of_level, int top, bool top_is
     return tot;
 }
 
+// 8-byte words of a trivially copyable descriptor, all threads of the CTA
+template <typename D>
+__device__ __forceinline__ void copy_words(D* dst, const D* src)
+{
+    static_assert(sizeof(D) % 8 == 0, "descriptors are copied as 8-byte words");
+    const unsigned long long* s = reinterpret_cast<const unsigned long long*>(src);
+    unsigned long long* d = reinterpret_cast<unsigned long long*>(dst);
+    for (int w = threadIdx.x; w < (int)(sizeof(D) / 8); w += blockDim.x) d[w] = s[w];
+}
+
 template <typename T, int DIM>
 __device__ __forceinline__ void coarse_body(const DevLevel<T>* __restrict__ levels, int top, int is_finest,
-                                            const DevProblem& P, const double* chol, int n0, int nu1, int nu2,
+                                            const DevProblem& Pg, const double* chol, int n0, int nu1, int nu2,
                                             unsigned char* smem_raw)
 {
+    // the grids' descriptors and the problem in shared memory, and the offset of every
+    // grid's block: the phases below read them at shared-memory latency
+    __shared__ __align__(16) DevLevel<T> lv[kCoarseMaxLevels];
+    __shared__ __align__(16) DevProblem P;
+    __shared__ int blk_off[kCoarseMaxLevels];
+    for (int l = 0; l <= top; ++l) copy_words(&lv[l], &levels[l]);
+    copy_words(&P, &Pg);
+    __syncthreads();
+    auto grid_sz = [&](int l) {
+        const int S = lv[l].n + 2;
+        return DIM == 3 ? S * S * S : S * S;
+    };
+    auto nblocks = [&](int l) { return 2 + (lv[l].fine ? 1 : (DIM == 2 ? 5 : 14)); };
+    if (threadIdx.x == 0) {
+        int o = 0;
+        for (int l = 0; l <= top; ++l) {
+            blk_off[l] = o;
+            o += nblocks(l) * grid_sz(l);
+        }
+    }
+    __syncthreads();
     T* base = reinterpret_cast<T*>(smem_raw);
     // block layout per grid: X, F, coefficient slots (in that order)
-    auto blk = [&](int l, int which) -> T* {
-        T* p = base;
-        for (int q = 0; q < l; ++q) {
-            const int S = levels[q].n + 2;
-            const int sz = DIM == 3 ? S * S * S : S * S;
-            p += (2 + (levels[q].fine ? 1 : (DIM == 2 ? 5 : 14))) * sz;
-        }
-        const int S = levels[l].n + 2;
-        const int sz = DIM == 3 ? S * S * S : S * S;
-        return p + which * sz;
-    };
+    auto blk = [&](int l, int which) -> T* { return base + blk_off[l] + which * grid_sz(l); };
     // zero everything, then stage the coefficients of every grid and the top grid's
     // right-hand side (and the chain state when the top grid is the finest)
-    T* Z = blk(top, 2 + (levels[top].fine ? 1 : (DIM == 2 ? 5 : 14)));   // normals of one sweep
+    T* Z = blk(top, nblocks(top));   // normals of one sweep
     {
         const long long tot = (long long)(Z - base);
         for (long long i = threadIdx.x; i < tot; i += blockDim.x) base[i] = T(0);
     }
     __syncthreads();
     for (int l = 0; l <= top; ++l) {
-        const DevLevel<T> L = levels[l];
+        const DevLevel<T>& L = lv[l];
         const int n = L.n, S = n + 2;
         const int sz = DIM == 3 ? S * S * S : S * S;
         const int nco = L.fine ? 1 : (DIM == 2 ? 5 : 14);
@@ -453,7 +474,7 @@ __device__ __forceinline__ void coarse_body(const DevLevel<T>* __restrict__ leve
     __syncthreads();
     const CycleState cs = *P.cs;
     for (int l = top; l >= 1; --l) {
-        const DevLevel<T> L = levels[l];
+        const DevLevel<T>& L = lv[l];
         T* X = blk(l, 0);
         T* F = blk(l, 1);
         const T* CS = blk(l, 2);
@@ -462,15 +483,15 @@ __device__ __forceinline__ void coarse_body(const DevLevel<T>* __restrict__ leve
             s_lowrank<T>(L, P, cs, X, 0, (unsigned)(2 * s), s == nu1 - 1);
         }
         if (nu1 == 0) s_lowrank<T>(L, P, cs, X, -1, 0u, true);
-        s_restrict<T, DIM>(L, X, F, CS, levels[l - 1], blk(l - 1, 1));
+        s_restrict<T, DIM>(L, X, F, CS, lv[l - 1], blk(l - 1, 1));
     }
-    s_coarsest<T, DIM>(levels[0], P, cs, blk(0, 0), blk(0, 1), chol, n0);
+    s_coarsest<T, DIM>(lv[0], P, cs, blk(0, 0), blk(0, 1), chol, n0);
     for (int l = 1; l <= top; ++l) {
-        const DevLevel<T> L = levels[l];
+        const DevLevel<T>& L = lv[l];
         T* X = blk(l, 0);
         const T* F = blk(l, 1);
         const T* CS = blk(l, 2);
-        s_prolong<T, DIM>(levels[l - 1], blk(l - 1, 0), L, X);
+        s_prolong<T, DIM>(lv[l - 1], blk(l - 1, 0), L, X);
         for (int s = 0; s < nu2; ++s) {
             s_sweep<T, DIM>(L, cs, X, F, CS, Z, 1, (unsigned)(2 * s + 1));
             s_lowrank<T>(L, P, cs, X, 1, (unsigned)(2 * s + 1), false);
@@ -478,7 +499,7 @@ __device__ __forceinline__ void coarse_body(const DevLevel<T>* __restrict__ leve
     }
     // the top grid's final state goes back to global memory
     {
-        const DevLevel<T> L = levels[top];
+        const DevLevel<T>& L = lv[top];
         const T* X = blk(top, 0);
         const int n = L.n, S = n + 2;
         const int N = n * n * (DIM == 3 ? n : 1);

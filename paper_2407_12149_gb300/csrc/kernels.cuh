@@ -45,6 +45,8 @@ void launch_set_cycle_batch(CycleState* const* cs, int n, unsigned long long see
                             double* qoi, long long n_steps, cudaStream_t st);
 
 // the V-cycle of grids 0..top in one CTA with shared-memory state (coarse.cu)
+// grids a coarse kernel holds at most (their descriptors are staged in shared memory)
+constexpr int kCoarseMaxLevels = 8;
 long long coarse_smem_elems(int dim, const int* n_of_level, int top, bool top_is_finest);
 template <typename T>
 cudaError_t coarse_prepare(int dim, size_t smem_bytes);
