@@ -146,6 +146,7 @@ WORKLOADS = {
     "batch512-mixed": {"n": 511, "chains": 512, "mixed": True},   # 128 chains each of 63^2 .. 511^2
     "bayes3d-127": {"n": 127, "chains": 1, "dim": 3},     # 127^3, kappa^2 = 25, 32 obs, coarsest 3^3
     "warmstart-255": {"n": 255, "chains": 64, "warm": True},       # learned warm start (U-Net), 255^2
+    "gibbs-vs-mgmc-2d": {"n": 511, "chains": 1, "table": True},   # Table 1 comparison, 31^2 .. 511^2
 }
 
 
@@ -539,6 +540,87 @@ def run_warmstart(args):
     print(json.dumps(line), flush=True)
 
 
+def run_gibbs_table(args):
+    """The comparison of the paper's Table 1 (Sec. 5.2) on the 2D posterior of the headline
+    workload (kappa^2 = 10 exp(g), 16 point observations), FP32, one chain per sampler and
+    grid: IACT of the QoI (device Wolff estimate after a burn-in), time per step (CUDA
+    events over back-to-back steps, state resident) and time per independent sample for
+    the plain Gibbs sampler (one symmetric low-rank Gibbs sweep per step) and MGMC
+    (V(1,1)-cycle); the exact Cholesky sampler (single-grid hierarchy, FP64) on 31^2."""
+    import torch
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    from paper_2407_12149_gb300 import build, inputs
+    from paper_2407_12149_gb300 import mgmc as M
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(gpu_id_for_smi(torch, local))
+
+    def measure(s, n_chain, burn, n_time):
+        x = s.zeros()
+        q = torch.zeros(n_chain + burn, dtype=torch.float64, device=dev)
+        s.sample(x, n_chain + burn, 2024, qoi=q)
+        torch.cuda.synchronize()
+        st = M.mgmc_qoi_stats(q.data_ptr(), n_chain + burn, burn, 1.5)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.sample(None, 5, 2024, step_offset=n_chain + burn)
+        e0.record(stream)
+        s.sample(None, n_time, 2024, step_offset=n_chain + burn + 5)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / n_time
+        return st["tau_int"], st["tau_err"], ms
+
+    rows = []
+    for n in (31, 63, 127, 255, 511):
+        p = inputs.config2(n=n)
+        row = {"n": n}
+        # Gibbs: tau grows like h^-2 (about 100 at 31^2 for kappa^2 = 10); chains of up to 400 000 steps
+        n_g = min(400000, 20000 * ((n + 1) // 32) ** 2)
+        s = M.Sampler(p, precision="fp32", gibbs=True, device=local)
+        tg, eg, msg = measure(s, n_g, 2000, 200)
+        s.close()
+        s = M.Sampler(p, precision="fp32", device=local)
+        tm, em, msm = measure(s, 5000, 100, 200)
+        s.close()
+        row.update({"gibbs_steps": n_g, "tau_gibbs": tg, "tau_gibbs_err": eg, "ms_per_step_gibbs": msg,
+                    "ms_per_indep_gibbs": msg * tg, "tau_mgmc": tm, "tau_mgmc_err": em, "ms_per_step_mgmc": msm,
+                    "ms_per_indep_mgmc": msm * tm})
+        if n == 31:
+            pc = inputs.config2(n=31, n_levels=1)
+            s = M.Sampler(pc, precision="fp64", device=local)
+            x = s.zeros()
+            s.sample(x, 5, 1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.sample(None, 50, 1, step_offset=5)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            row["ms_per_sample_cholesky"] = e0.elapsed_time(e1) / 50
+            s.close()
+        rows.append(row)
+    clk = clocks.stop()
+    big = rows[-1]
+    line = {
+        "metric": "time per independent QoI sample (MGMC, 511^2)", "value": big["ms_per_indep_mgmc"], "unit": "ms",
+        "n_gpus": 1, "steps": 200, "warmup": 5, "ms_per_step": big["ms_per_step_mgmc"], "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "gibbs-vs-mgmc-2d: the Sec. 5.2 / Table 1 comparison on the 2D posterior "
+                               "(kappa^2 = 10 exp(g), 16 point obs, Gamma = 1e-4 I), 31^2 .. 511^2, one FP32 "
+                               "chain per sampler and grid; Cholesky = single-grid exact sampler (FP64, one CTA)",
+                   "table": rows,
+                   "tau_from": "device Wolff estimate (S = 1.5) of each chain after its burn-in (Gibbs 2000, MGMC 100)",
+                   "timing": "CUDA events over 200 back-to-back steps, state resident (grids up to 511^2 are "
+                             "L2-resident)"},
+        "roofline": None, "cpu_baseline": None, "e2e": None,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -561,6 +643,8 @@ def main():
         run_reference(args)
     elif WORKLOADS[args.workload].get("warm"):
         run_warmstart(args)
+    elif WORKLOADS[args.workload].get("table"):
+        run_gibbs_table(args)
     else:
         run_mine(args)
 

@@ -83,6 +83,13 @@ typedef struct {
     int scale_hd;     /* 1: A = h^d (kappa^2 - Delta_h) (default); 0: kappa^2 - Delta_h */
     int coarse_max_n; /* grids with n <= coarse_max_n run inside one single-CTA kernel;
                          0 selects the default (63 in 2D, 15 in 3D) */
+    int gibbs;        /* 0: the MGMC V-cycle (Alg. 1).  1: the plain Gibbs sampler the
+                         paper compares against (Sec. 5.2): one step is nu1 forward and
+                         nu2 backward sweeps of the low-rank Gibbs smoother (Alg. 3) on
+                         the finest grid alone, with the MGMC cycle's noise slots and no
+                         coarse-grid correction.  Needs n_levels >= 2 (the finest grid's
+                         low-rank data are those of MGMC); single-chain handles only
+                         (mgmc_create_batch returns MGMC_ERR_ARG). */
 } mgmc_config;
 
 /* Fill cfg with the paper's defaults for a dim-dimensional n^dim grid. */

@@ -63,6 +63,7 @@ def lib():
                                                  _c_dbl_p, _c_dbl_p, _c_dbl_p, _c_dbl_p, _c_dbl_p]
         L.oracle_sample.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64,
                                     ctypes.c_uint32, ctypes.c_int, _c_dbl_p, _c_dbl_p]
+        L.oracle_sample_gibbs.argtypes = L.oracle_sample.argtypes
         L.oracle_mean_solve.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, _c_dbl_p,
                                         ctypes.POINTER(ctypes.c_int), _c_dbl_p]
         L.oracle_fine_rhs.argtypes = [ctypes.c_void_p, _c_dbl_p]
@@ -193,11 +194,13 @@ class Oracle:
             raise OracleError(rc)
         return x
 
-    def sample(self, n_steps, seed, x=None, step_offset=0, chain=0, noise=True, qoi=True):
+    def sample(self, n_steps, seed, x=None, step_offset=0, chain=0, noise=True, qoi=True, gibbs=False):
+        """n_steps MGMC V-cycles, or with gibbs=True steps of the plain Gibbs sampler (Sec. 5.2)."""
         x = np.zeros(self.N) if x is None else np.array(x, dtype=np.float64, copy=True).ravel()
         q = np.zeros(max(n_steps, 1)) if qoi else None
-        rc = lib().oracle_sample(self._h, int(n_steps), int(seed) & (2**64 - 1), int(step_offset),
-                                 int(chain), 1 if noise else 0, _dp(x), _dp(q))
+        fn = lib().oracle_sample_gibbs if gibbs else lib().oracle_sample
+        rc = fn(self._h, int(n_steps), int(seed) & (2**64 - 1), int(step_offset),
+                int(chain), 1 if noise else 0, _dp(x), _dp(q))
         if rc:
             raise OracleError(rc)
         return (x, q[:n_steps]) if qoi else x

@@ -1047,6 +1047,30 @@ int oracle_sample(oracle_problem* p, int64_t n_steps, uint64_t seed, uint64_t st
     return 0;
 }
 
+/* Sec. 5.2, "Gibbs sampler": the symmetric low-rank Gibbs sweeps of the finest
+ * level alone (Alg. 3 forward nu1 times, then backward nu2 times). */
+int oracle_sample_gibbs(oracle_problem* p, int64_t n_steps, uint64_t seed, uint64_t step_offset,
+                        uint32_t chain, int noise, double* x, double* qoi_out)
+{
+    if (!p || !x || n_steps < 0 || p->n_levels < 2) return ERR_ARG;
+    p->seed = seed;
+    p->chain = chain;
+    p->noise = noise ? 1 : 0;
+    const int l = p->n_levels - 1;
+    olevel* Lf = &p->lev[l];
+    for (int64_t s = 0; s < n_steps; ++s) {
+        p->cycle = step_offset + (uint64_t)s;
+        memset(Lf->f, 0, sizeof(double) * Lf->N);      /* fd_L = 0 */
+        if (p->m > 0) memcpy(Lf->dv, p->y, sizeof(double) * p->m);   /* d_L = y */
+        for (int j = 0; j < p->nu1; ++j)
+            lowrank_gibbs(p, l, 0, x, Lf->f, Lf->dv, (uint32_t)(2 * j), NULL, NULL, p->noise);
+        for (int j = 0; j < p->nu2; ++j)
+            lowrank_gibbs(p, l, 1, x, Lf->f, Lf->dv, (uint32_t)(2 * j + 1), NULL, NULL, p->noise);
+        if (qoi_out) qoi_out[s] = qoi_of(p, x);
+    }
+    return 0;
+}
+
 double oracle_rel_residual(const oracle_problem* p, const double* x)
 {
     const olevel* L = &p->lev[p->n_levels - 1];

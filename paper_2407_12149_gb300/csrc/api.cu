@@ -402,6 +402,24 @@ void enqueue_cycle(mgmc_ctx* h, cudaStream_t s, int& launches)
     const int Lf = h->L - 1;
     const DevProblem& P = h->P;
     const bool prof = h->profile && h->top < Lf;
+    if (h->cfg.gibbs) {
+        // plain Gibbs sampler (Sec. 5.2): the finest grid's sweeps of the V-cycle, no coarse correction
+        const DevLevel<T>& D = lv[Lf];
+        for (int j = 0; j < h->cfg.nu1; ++j) {
+            if (prof && j == 0) cudaEventRecordWithFlags(h->ev[0], s, cudaEventRecordExternal);
+            launch_sweep<T>(D, P, 0, (unsigned)(2 * j), s, launches);
+            if (prof && j == 0) cudaEventRecordWithFlags(h->ev[1], s, cudaEventRecordExternal);
+            launch_lowrank<T>(D, P, 0, (unsigned)(2 * j), false, s, launches);
+        }
+        for (int j = 0; j < h->cfg.nu2; ++j) {
+            if (prof && j == 0) cudaEventRecordWithFlags(h->ev[2], s, cudaEventRecordExternal);
+            launch_sweep<T>(D, P, 1, (unsigned)(2 * j + 1), s, launches);
+            if (prof && j == 0) cudaEventRecordWithFlags(h->ev[3], s, cudaEventRecordExternal);
+            launch_lowrank<T>(D, P, 1, (unsigned)(2 * j + 1), false, s, launches);
+        }
+        launch_qoi<T>(D, h->n_qoi, h->q_site, h->q_w, P, s, launches);
+        return;
+    }
     for (int l = Lf; l > h->top; --l) {
         const DevLevel<T>& D = lv[l];
         if (l < Lf) cudaMemsetAsync(D.x, 0, (size_t)D.alloc * sizeof(T), s);
@@ -490,6 +508,7 @@ mgmc_status mgmc_config_default(mgmc_config* cfg, int dim, int n)
     cfg->precision = MGMC_FP64;
     cfg->scale_hd = 1;
     cfg->coarse_max_n = 0;
+    cfg->gibbs = 0;
     return MGMC_OK;
 }
 
@@ -559,6 +578,8 @@ mgmc_status mgmc_create(const mgmc_config* cfg_in, const mgmc_allocator* alloc, 
     for (int nn = cfg.n; nn >= 3; nn = (nn - 1) / 2) ++max_levels;
     if (cfg.n_levels == 0) cfg.n_levels = max_levels;
     if (cfg.n_levels < 1 || cfg.n_levels > max_levels) return fail(MGMC_ERR_ARG, "n_levels out of range");
+    if (cfg.gibbs != 0 && cfg.gibbs != 1) return fail(MGMC_ERR_ARG, "gibbs must be 0 or 1");
+    if (cfg.gibbs && cfg.n_levels < 2) return fail(MGMC_ERR_ARG, "the Gibbs sampler needs n_levels >= 2");
     for (int t = 0; t < n_qoi; ++t)
         if (qoi_site[t] < 0 || qoi_site[t] >= N || !std::isfinite(qoi_w[t]))
             return fail(MGMC_ERR_ARG, "QoI site out of range or weight not finite");
@@ -595,9 +616,11 @@ mgmc_status mgmc_create(const mgmc_config* cfg_in, const mgmc_allocator* alloc, 
             if (hp.lev[l].n <= cmax && bytes + 16384 <= budget) h->top = l;
         }
     }
+    // the Gibbs sampler sweeps the finest grid with the unfused kernels, outside the coarse kernel
+    if (cfg.gibbs) h->top = 0;
     h->n0 = hp.n0;
     h->f_norm = hp.f_norm;
-    h->fused = cfg.dim == 2 && cfg.nu1 == 1 && cfg.nu2 == 1;
+    h->fused = cfg.dim == 2 && cfg.nu1 == 1 && cfg.nu2 == 1 && !cfg.gibbs;
     auto cleanup = [&](mgmc_status s) {
         h->buf.release();
         delete h;
@@ -975,6 +998,7 @@ mgmc_status mgmc_create_batch(int n_chains, const mgmc_config* cfgs, const mgmc_
     };
     for (int c = 0; c < n_chains; ++c) {
         mgmc_config cfg = cfgs[c];
+        if (cfg.gibbs) return cleanup(fail(MGMC_ERR_ARG, "batches run the MGMC V-cycle only (gibbs = 0)"));
         if (cfg.coarse_max_n == 0) cfg.coarse_max_n = 31;
         const mgmc_problem& p = problems[c];
         mgmc_handle sh = nullptr;

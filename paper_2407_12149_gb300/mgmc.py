@@ -35,7 +35,7 @@ class MGMCError(RuntimeError):
 class mgmc_config(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("n_levels", ctypes.c_int), ("nu1", ctypes.c_int),
                 ("nu2", ctypes.c_int), ("precision", ctypes.c_int), ("scale_hd", ctypes.c_int),
-                ("coarse_max_n", ctypes.c_int)]
+                ("coarse_max_n", ctypes.c_int), ("gibbs", ctypes.c_int)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -192,9 +192,9 @@ def mgmc_point_obs_rows(dim: int, n: int, xyz: np.ndarray):
 
 def mgmc_create(dim, n, *, n_levels=0, nu1=1, nu2=1, precision=MGMC_FP64, scale_hd=1, coarse_max_n=0,
                 kappa2=None, kappa2_const=10.0, obs_site=None, obs_w=None, Gamma=None, y=None,
-                qoi_site=None, qoi_w=None, allocator: Optional[TorchAllocator] = None, stream=None):
+                qoi_site=None, qoi_w=None, allocator: Optional[TorchAllocator] = None, stream=None, gibbs=0):
     L = load()
-    cfg = mgmc_config(dim, n, n_levels, nu1, nu2, precision, scale_hd, coarse_max_n)
+    cfg = mgmc_config(dim, n, n_levels, nu1, nu2, precision, scale_hd, coarse_max_n, gibbs)
     k2 = None if kappa2 is None else np.ascontiguousarray(kappa2, dtype=np.float64).ravel()
     if obs_site is None:
         m, nnz, os_, ow_, G_, y_ = 0, 1, None, None, None, None
@@ -296,10 +296,11 @@ def mgmc_destroy(h):
 # --------------------------------------------------------------------------
 
 class Sampler:
-    """MGMC sampler of one posterior problem (paper_2407_12149_gb300.inputs.Problem)."""
+    """MGMC sampler of one posterior problem (paper_2407_12149_gb300.inputs.Problem);
+    gibbs=True gives the plain Gibbs sampler of the same posterior (finest-grid sweeps only)."""
 
     def __init__(self, problem, precision: str = "fp64", nu1: int = 1, nu2: int = 1, coarse_max_n: int = 0,
-                 device: int = 0, use_torch_allocator: bool = True):
+                 device: int = 0, use_torch_allocator: bool = True, gibbs: bool = False):
         torch = _torch()
         if not torch.cuda.is_available():
             raise MGMCError(2, "no CUDA device available (the sampler has no CPU fallback)")
@@ -312,7 +313,8 @@ class Sampler:
         self.h = mgmc_create(p.dim, p.n, n_levels=p.n_levels, nu1=nu1, nu2=nu2, precision=self.precision,
                              scale_hd=p.scale_hd, coarse_max_n=coarse_max_n, kappa2=p.kappa2,
                              kappa2_const=p.kappa2_const, obs_site=p.obs_site, obs_w=p.obs_w, Gamma=p.Gamma,
-                             y=p.y, qoi_site=p.qoi_site, qoi_w=p.qoi_w, allocator=self._alloc)
+                             y=p.y, qoi_site=p.qoi_site, qoi_w=p.qoi_w, allocator=self._alloc,
+                             gibbs=1 if gibbs else 0)
 
     def zeros(self):
         torch = _torch()
