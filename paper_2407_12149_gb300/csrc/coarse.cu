@@ -462,13 +462,21 @@ __device__ __forceinline__ void coarse_body(const DevLevel<T>* __restrict__ leve
             } else {
                 for (int t = 0; t < nco; ++t) CS[t * sz + s] = L.coef[(long long)t * L.alloc + e];
             }
-            if (l == top) {
-                const bool interior = i >= 0 && i < n && j >= 0 && j < n && (DIM == 2 || (k >= 0 && k < n));
-                if (interior) {
-                    if (is_finest) blk(l, 0)[s] = L.x[e];
-                    if (L.f) blk(l, 1)[s] = L.f[e];
-                }
-            }
+        }
+    }
+    // the descriptors and operators above never change after set-up; the top grid's
+    // right-hand side and state (and the cycle state) come from the preceding launches
+    pdl_wait();
+    {
+        const DevLevel<T>& L = lv[top];
+        const int n = L.n, S = n + 2;
+        const int N = n * n * (DIM == 3 ? n : 1);
+        for (int s = threadIdx.x; s < N; s += blockDim.x) {
+            const int i = s % n, j = (s / n) % n, k = DIM == 3 ? s / (n * n) : 0;
+            const long long e = site_offset(DIM, L.pitch, L.plane, L.base, i, j, k);
+            const int ls = sidx<DIM>(S, i, j, k);
+            if (is_finest) blk(top, 0)[ls] = L.x[e];
+            if (L.f) blk(top, 1)[ls] = L.f[e];
         }
     }
     __syncthreads();
@@ -529,8 +537,7 @@ __global__ void __launch_bounds__(kCoarseBatchMaxThreads) k_coarse_cycle_batch(c
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     pdl_launch_dependents();
-    pdl_wait();
-    const CoarseJob<T>& J = jobs[blockIdx.x];
+    const CoarseJob<T>& J = jobs[blockIdx.x];   // static table; coarse_body waits for the predecessor
     coarse_body<T, 2>(J.levels, J.top, J.is_finest, *J.P, J.chol, J.n0, 1, 1, smem_raw);
 }
 

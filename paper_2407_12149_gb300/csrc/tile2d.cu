@@ -839,8 +839,19 @@ __global__ void __launch_bounds__(TileGeom<T, FINE, BWD>::NT, 3)
         jid[0] = jid[1] = -1;
     }
     __syncthreads();
+    // a CTA of a per-chain group loads its job descriptor (static) before the wait on the
+    // preceding launch; the cycle state is read after it
+    const int pre = (cpj > 0 && tb < te) ? (int)(blockIdx.x / cpj) : -1;
+    if (pre >= 0) load_job(*hdr(0), jobs + pre);
     pdl_wait();
     if (tb >= te) return;
+    if (pre >= 0) {
+        if (threadIdx.x == 0) {
+            cs_s[0] = *hdr(0)->P.cs;
+            jid[0] = pre;
+        }
+        __syncthreads();
+    }
 
     // header and cycle state of tile t's chain into slot hs
     auto fetch = [&](int t, int hs) {
@@ -944,8 +955,11 @@ __global__ void __launch_bounds__(TileGeom<T, FINE, BWD>::NT, 3)
 // The same step when m <= kLrReg and every thread holds at most one row of G
 // (and of H): all loads that do not depend on v -- the thread's G/H row, its
 // site and the value there, B^T G, d, the Cholesky diagonal -- are issued before
-// z and v are formed, so the step costs about three round trips to memory.  The
-// sums run in the same order as the general path.
+// z and v are formed.  The static ones (G/H rows, sites, B^T G, column pointers,
+// L_Gamma) are issued before the wait on the preceding launch (pdl_wait), so
+// after it only the state, f, d and the z partials are fetched: one round trip.
+// The sums run in the same order as the general path.  Both forms call
+// pdl_wait themselves.
 constexpr int kLrReg = 16;
 
 template <typename T>
@@ -972,15 +986,17 @@ __device__ __forceinline__ void lowrank_fused_short(const DevLevel<T>& L, const 
     }
     const long long gs = hg ? L.g_site[dir][r0] : 0;
     const long long hs = hh ? L.h_site[r0] : 0;
-    const CycleState cs = *P.cs;
     int t0 = 0, t1 = 0;
-    double dk = 0.0, lgk = 0.0;
+    double lgk = 0.0;
     if (hk) {
         t0 = L.bcol_ptr[k0];
         t1 = L.bcol_ptr[k0 + 1];
-        dk = L.d[k0];
         if (P.gamma_diag) lgk = P.LG[k0 * m + k0];
     }
+    // everything below depends on the preceding launches
+    pdl_wait();
+    const CycleState cs = *P.cs;
+    const double dk = hk ? L.d[k0] : 0.0;
     const T xv = hg ? x[gs] : T(0);
     const T fv = hh ? C.f[hs] : T(0);
     if (hk) {
@@ -1039,6 +1055,7 @@ __device__ __forceinline__ void lowrank_fused_body(const DevLevel<T>& L, const D
         lowrank_fused_short<T>(L, C, P, down, blk, z, zp, v);
         return;
     }
+    pdl_wait();
     const CycleState cs = *P.cs;
     for (int k = threadIdx.x; k < m; k += blockDim.x) {
         double acc = 0.0;
@@ -1088,8 +1105,7 @@ __global__ void k_lowrank_fused_batch(const LowrankJob<T>* __restrict__ jobs, in
     __shared__ __align__(16) LowrankJob<T> J;
     pdl_launch_dependents();
     load_job(J, jobs + find_job(jobs, njobs, per, blockIdx.x));   // static table
-    pdl_wait();
-    lowrank_fused_body<T>(J.L, J.C, J.P, down, blockIdx.x - J.block0, J.nblocks);
+    lowrank_fused_body<T>(J.L, J.C, J.P, down, blockIdx.x - J.block0, J.nblocks);   // waits inside
 }
 
 // ---------------------------------------------------------------------------
