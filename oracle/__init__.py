@@ -64,7 +64,6 @@ def lib():
         L.oracle_sample.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64,
                                     ctypes.c_uint32, ctypes.c_int, _c_dbl_p, _c_dbl_p]
         L.oracle_sample_gibbs.argtypes = L.oracle_sample.argtypes
-        L.oracle_set_draws32.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.oracle_mean_solve.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, _c_dbl_p,
                                         ctypes.POINTER(ctypes.c_int), _c_dbl_p]
         L.oracle_fine_rhs.argtypes = [ctypes.c_void_p, _c_dbl_p]
@@ -99,8 +98,7 @@ class Oracle:
 
     def __init__(self, dim, n, n_levels, *, kappa2=None, kappa2_const=10.0, scale_hd=1,
                  nu1=1, nu2=1, obs_site=None, obs_w=None, Gamma=None, y=None,
-                 qoi_site=None, qoi_w=None, draws32=False):
-        """draws32=True: site noise as the library's FP32 handles draw it (oracle_set_draws32)."""
+                 qoi_site=None, qoi_w=None):
         L = lib()
         self.dim, self.n, self.n_levels = dim, n, n_levels
         self.N = n ** dim
@@ -128,9 +126,6 @@ class Oracle:
         if rc != 0:
             raise OracleError(f"oracle_create failed with code {rc}")
         self._h = h
-        self.draws32 = bool(draws32)
-        if draws32:
-            L.oracle_set_draws32(self._h, 1)
 
     def close(self):
         if getattr(self, "_h", None):

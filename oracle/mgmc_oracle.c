@@ -122,7 +122,6 @@ struct oracle_problem {
     uint64_t cycle;
     uint32_t chain;
     int noise;
-    int draws32;           /* site noise of FP32 handles (kind 3), see draw32 */
 };
 
 /* ------------------------------------------------------------------ */
@@ -185,39 +184,6 @@ static double draw(const oracle_problem* p, uint32_t kind, int level, uint32_t s
     double z0, z1;
     oracle_normal_pair(p->seed, pair, c1, c2, c3, &z0, &z1);
     return member ? z1 : z0;
-}
-
-/* The site noise of FP32 handles (kind 3): one Philox block per span of 8
- * sites of a grid row and one parity, counter word
- *   c0 = ((k n + j) ceil(n/8) + floor(i/8)) * 2 + (i mod 2);
- * words (w0, w1) serve the 4-site group floor(i/4) even, (w2, w3) the odd one,
- * each as one Box-Muller pair with u = (w + 1/2) 2^-32 from a single 32-bit
- * word; the group's two sites of the parity take z0 (floor(i/2) even) and z1. */
-static double draw32(const oracle_problem* p, int level, uint32_t slot, const int c[3], int n)
-{
-    if (!p->noise) return 0.0;
-    const int i = c[0];
-    const uint32_t nsp = (uint32_t)((n + 7) / 8);
-    const uint32_t block = (uint32_t)((((int64_t)c[2] * n + c[1]) * nsp + (uint32_t)(i >> 3)) * 2 + (i & 1));
-    uint32_t ctr[4] = {block, (uint32_t)p->cycle,
-                       ((uint32_t)(p->cycle >> 32) & 0xFFFFu) | (p->chain << 16),
-                       (3u << 24) | ((uint32_t)level << 16) | slot};
-    uint32_t key[2] = {(uint32_t)p->seed, (uint32_t)(p->seed >> 32)};
-    uint32_t w[4];
-    oracle_philox4x32_10(ctr, key, w);
-    const int h = (i >> 2) & 1;
-    const double u1 = ((double)w[2 * h] + 0.5) * 0x1p-32;
-    const double u2 = ((double)w[2 * h + 1] + 0.5) * 0x1p-32;
-    const double r = sqrt(-2.0 * log(u1));
-    const double phi = 2.0 * M_PI * u2;
-    return ((i >> 1) & 1) ? r * sin(phi) : r * cos(phi);
-}
-
-int oracle_set_draws32(oracle_problem* p, int on)
-{
-    if (!p) return ERR_ARG;
-    p->draws32 = on ? 1 : 0;
-    return 0;
 }
 
 /* ------------------------------------------------------------------ */
@@ -429,8 +395,6 @@ static void gs_sweep(const oracle_problem* p, int l, const olevel* L, int dir, d
             if (use_noise) {
                 if (zdiag) {
                     z = zdiag[s];
-                } else if (p->draws32) {
-                    z = draw32(p, l, slot, c, n);
                 } else {
                     uint32_t pair = (uint32_t)((((int64_t)c[2] * n + c[1]) * nq + (c[0] >> 2)) * 2
                                                + (c[0] & 1));

@@ -78,13 +78,6 @@ int oracle_sample(oracle_problem* p, int64_t n_steps, uint64_t seed, uint64_t st
 int oracle_sample_gibbs(oracle_problem* p, int64_t n_steps, uint64_t seed, uint64_t step_offset,
                         uint32_t chain, int noise, double* x, double* qoi_out);
 
-/* on = 1: site noise drawn as the FP32 handles of the CUDA library draw it
- * (kind 3: one Philox block per 8-site span and parity, one 32-bit word per
- * uniform; see draw32 in mgmc_oracle.c); on = 0 (default): the FP64 draws
- * (kind 0, one block per 4-site group and parity, 53-bit uniforms).  The
- * low-rank and coarsest-grid noise are the same in both. */
-int oracle_set_draws32(oracle_problem* p, int on);
-
 /* Noise-free V-cycles from the given x until ||f - A~ x|| <= rtol ||f||. */
 int oracle_mean_solve(oracle_problem* p, double rtol, int max_cycles, double* x,
                       int* cycles_done, double* rel_residual);
