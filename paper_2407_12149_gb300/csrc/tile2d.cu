@@ -839,17 +839,48 @@ __global__ void __launch_bounds__(TileGeom<T, FINE, BWD>::NT, 3)
         jid[0] = jid[1] = -1;
     }
     __syncthreads();
-    // a CTA of a per-chain group loads its job descriptor (static) before the wait on the
-    // preceding launch; the cycle state is read after it
+    // the TMA copies of tile t (header in slot hs) into stage buffer ds, its state into xd
+    // (thread 0).  part 0: all fields; 1: the expected bytes of all and the operator
+    // coefficients alone (they never change after set-up); 2: the rest (state, dense
+    // right-hand side, coarse psi), which the preceding launches write.
+    auto issue = [&](int t, int hs, int ds, T* xd, int part) {
+        const TileJob<T>& J = *hdr(hs);
+        const int lt = t - J.tile0;
+        const int x0 = (lt % J.L.ntx) * G::TX, y0 = (lt / J.L.ntx) * G::TY;
+        const int cx = x0 - G::RX + 4, cy = y0 - G::R + 1;  // padded coordinates of the box corner
+        const CUtensorMap* M = maps[jid[hs]].m;
+        T* b = buf + ds * G::STAGE;
+        const bool loadx = BWD || !x_zero;
+        if (part != 2) {
+            const unsigned bytes =
+                (unsigned)(G::NFLD - (loadx ? 0 : 1)) * G::BOX_BYTES + (BWD ? G::PSI_BYTES : 0u);
+            mbar_expect_tx(&bar[ds], bytes);
+            for (int f = 1; f <= G::NCOEF; ++f) tma_load_2d(b + f * G::FS, &M[f], cx, cy, &bar[ds]);
+        }
+        if (part == 1) return;
+        if (loadx) tma_load_2d(xd, &M[0], cx, cy, &bar[ds]);
+        for (int f = G::NCOEF + 1; f < G::NFLD; ++f) tma_load_2d(b + f * G::FS, &M[f], cx, cy, &bar[ds]);
+        if (BWD) {
+            const int gx0 = x0 - G::RX, gy0 = y0 - G::R;
+            tma_load_2d(b + G::NFLD * G::FS, &M[G::NFLD], ((gx0 >> 1) - 1 - G::POFF) + 4, ((gy0 >> 1) - 1) + 1,
+                        &bar[ds]);
+        }
+    };
+    // a CTA of a per-chain group loads its job descriptor (static) and starts the copies
+    // of its first tile's operator coefficients before the wait on the preceding launch;
+    // the cycle state and the other fields follow it
     const int pre = (cpj > 0 && tb < te) ? (int)(blockIdx.x / cpj) : -1;
-    if (pre >= 0) load_job(*hdr(0), jobs + pre);
+    if (pre >= 0) {
+        load_job(*hdr(0), jobs + pre);
+        if (threadIdx.x == 0) {
+            jid[0] = pre;
+            issue(tb, 0, 0, buf, 1);
+        }
+    }
     pdl_wait();
     if (tb >= te) return;
     if (pre >= 0) {
-        if (threadIdx.x == 0) {
-            cs_s[0] = *hdr(0)->P.cs;
-            jid[0] = pre;
-        }
+        if (threadIdx.x == 0) cs_s[0] = *hdr(0)->P.cs;
         __syncthreads();
     }
 
@@ -875,32 +906,12 @@ __global__ void __launch_bounds__(TileGeom<T, FINE, BWD>::NT, 3)
     // state buffer of the k-th tile: field 0 of its stage, or the second state buffer
     // for odd k of a single-stage backward kernel
     auto xbuf = [&](int k, int ds) { return (G::XALT && (k & 1)) ? buf + G::STAGE : buf + ds * G::STAGE; };
-    // the TMA copies of tile t (header in slot hs) into stage buffer ds, its state into xd (thread 0)
-    auto issue = [&](int t, int hs, int ds, T* xd) {
-        const TileJob<T>& J = *hdr(hs);
-        const int lt = t - J.tile0;
-        const int x0 = (lt % J.L.ntx) * G::TX, y0 = (lt / J.L.ntx) * G::TY;
-        const int cx = x0 - G::RX + 4, cy = y0 - G::R + 1;  // padded coordinates of the box corner
-        const CUtensorMap* M = maps[jid[hs]].m;
-        T* b = buf + ds * G::STAGE;
-        const bool loadx = BWD || !x_zero;
-        unsigned bytes = (unsigned)(G::NFLD - (loadx ? 0 : 1)) * G::BOX_BYTES + (BWD ? G::PSI_BYTES : 0u);
-        mbar_expect_tx(&bar[ds], bytes);
-        if (loadx) tma_load_2d(xd, &M[0], cx, cy, &bar[ds]);
-        for (int f = 1; f < G::NFLD; ++f) tma_load_2d(b + f * G::FS, &M[f], cx, cy, &bar[ds]);
-        if (BWD) {
-            const int gx0 = x0 - G::RX, gy0 = y0 - G::R;
-            tma_load_2d(b + G::NFLD * G::FS, &M[G::NFLD], ((gx0 >> 1) - 1 - G::POFF) + 4, ((gy0 >> 1) - 1) + 1,
-                        &bar[ds]);
-        }
-    };
-
     // single-stage kernels issue the next tile's copies as soon as the current tile no
     // longer reads its operator fields (the state is not copied forward from psi = 0,
     // and has its own second buffer backward)
     const bool early = G::NSTAGE == 1 && (BWD || x_zero);
     fetch(tb, 0);
-    if (threadIdx.x == 0) issue(tb, 0, 0, xbuf(0, 0));
+    if (threadIdx.x == 0) issue(tb, 0, 0, xbuf(0, 0), pre >= 0 ? 2 : 0);
     for (int t = tb, k = 0; t < te; t += step, ++k) {
         const int hs = k & 1;
         const int ds = G::NSTAGE == 2 ? (k & 1) : 0;
@@ -908,7 +919,7 @@ __global__ void __launch_bounds__(TileGeom<T, FINE, BWD>::NT, 3)
         const bool more = t + step < te;
         if (G::NSTAGE == 2 && more) {
             fetch(t + step, hs ^ 1);
-            if (threadIdx.x == 0) issue(t + step, hs ^ 1, ds ^ 1, xbuf(k + 1, ds ^ 1));
+            if (threadIdx.x == 0) issue(t + step, hs ^ 1, ds ^ 1, xbuf(k + 1, ds ^ 1), 0);
         }
         const bool ok = mbar_wait(&bar[ds], parity);
         if (__syncthreads_or(!ok)) {
@@ -930,7 +941,7 @@ __global__ void __launch_bounds__(TileGeom<T, FINE, BWD>::NT, 3)
             fence_proxy_async();
             fetch(t + step, hs ^ 1);
             __syncthreads();
-            if (threadIdx.x == 0) issue(t + step, hs ^ 1, 0, xbuf(k + 1, 0));
+            if (threadIdx.x == 0) issue(t + step, hs ^ 1, 0, xbuf(k + 1, 0), 0);
         };
         if constexpr (BWD)
             tile_bwd_compute<T, FINE>(J.L, cs_s[hs], bx, by, xbuf(k, ds), b + G::FS, b + (1 + G::NCOEF) * G::FS,
@@ -942,7 +953,7 @@ __global__ void __launch_bounds__(TileGeom<T, FINE, BWD>::NT, 3)
         __syncthreads();
         if (G::NSTAGE == 1 && !early && more) {
             fetch(t + step, hs ^ 1);
-            if (threadIdx.x == 0) issue(t + step, hs ^ 1, 0, xbuf(k + 1, 0));
+            if (threadIdx.x == 0) issue(t + step, hs ^ 1, 0, xbuf(k + 1, 0), 0);
         }
     }
 }
