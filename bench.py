@@ -301,6 +301,12 @@ def run_mine(args):
             s.get_state(x)
     xh = [x.cpu().pin_memory() for x in xs]
     qh = torch.zeros(nch, dtype=torch.float64).pin_memory()
+    # batch: the chains' states live in one contiguous buffer on each side (the per-chain
+    # tensors handed to the API are views of it), so each direction is one copy
+    sizes = [p.N for p in ps]
+    flat_dev = torch.cat([x.view(-1) for x in xs]) if batch else None
+    views = list(torch.split(flat_dev, sizes)) if batch else None
+    flat_host = flat_dev.cpu().pin_memory() if batch else None
     n_e2e = max(3, min(args.steps, 20))
     if dist:
         dist.barrier()
@@ -308,11 +314,9 @@ def run_mine(args):
     t0 = time.perf_counter()
     for k in range(n_e2e):
         if batch:
-            for x, h in zip(xs, xh):
-                x.copy_(h, non_blocking=True)                     # H2D of every chain's state
-            s.sample(xs, 1, 2024 + 7919 * rank, step_offset=offset, qoi=qstep)
-            for x, h in zip(xs, xh):
-                h.copy_(x, non_blocking=True)                     # D2H of the new states
+            flat_dev.copy_(flat_host, non_blocking=True)             # H2D of every chain's state
+            s.sample(views, 1, 2024 + 7919 * rank, step_offset=offset, qoi=qstep)
+            flat_host.copy_(flat_dev, non_blocking=True)             # D2H of the new states
             qh.copy_(qstep, non_blocking=True)
             torch.cuda.synchronize()
         else:
