@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 # (k_tile_batch<float, 1, 0>) on the 32 x 1023^2 batch, from the ncu capture
 # summarised in profiles/k_tile_batch_fine_fwd_batch32_bayes2d_1023.md; None
 # for other workloads and whenever that kernel changes before it is re-captured.
-FINE_SWEEP_TRAFFIC_BYTES = 412.7e6
+FINE_SWEEP_TRAFFIC_BYTES = 412.6e6
 
 TAU_CALIBRATION = 2000     # default untimed cycles used for tau_int on the device
 CPU_SAMPLE_CYCLES = 12     # bounded oracle sample for the CPU baseline
