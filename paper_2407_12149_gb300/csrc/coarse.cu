@@ -547,10 +547,25 @@ __global__ void k_qoi_batch(const QoiJob<T>* __restrict__ jobs)
 {
     __shared__ double part[256];
     pdl_launch_dependents();
+    // the QoI sites and weights never change: the first kQoiPre of each thread are loaded
+    // before the wait on the preceding launch, the state after it (same summation order)
+    constexpr int kQoiPre = 8;
+    const QoiJob<T> J = jobs[blockIdx.x];
+    long long site[kQoiPre];
+    double w[kQoiPre];
+#pragma unroll
+    for (int r = 0; r < kQoiPre; ++r) {
+        const int t = threadIdx.x + r * blockDim.x;
+        site[r] = t < J.n_qoi ? J.q_site[t] : 0;
+        w[r] = t < J.n_qoi ? J.q_w[t] : 0.0;
+    }
     pdl_wait();
-    const QoiJob<T>& J = jobs[blockIdx.x];
     double acc = 0.0;
-    for (int t = threadIdx.x; t < J.n_qoi; t += blockDim.x) acc += J.q_w[t] * (double)J.x[J.q_site[t]];
+#pragma unroll
+    for (int r = 0; r < kQoiPre; ++r)
+        if (threadIdx.x + r * blockDim.x < J.n_qoi) acc += w[r] * (double)J.x[site[r]];
+    for (int t = threadIdx.x + kQoiPre * blockDim.x; t < J.n_qoi; t += blockDim.x)
+        acc += J.q_w[t] * (double)J.x[J.q_site[t]];
     part[threadIdx.x] = acc;
     __syncthreads();
     for (int st = blockDim.x / 2; st > 0; st >>= 1) {

@@ -623,8 +623,11 @@ __device__ __forceinline__ void tile_fwd_compute(const DevLevel<T>& L, const Dev
                 acc1 += (0.5f * wb) * e[b];
             }
             long long o = site_offset(2, C.pitch, C.plane, C.base, I, J, 0);
-            C.f[o] = (T)acc0;
-            if (I + 1 < C.n) C.f[o + 1] = (T)acc1;
+            // o is even (I, the padded base and the pitch are): both sites in one 8-byte store
+            if (I + 1 < C.n)
+                *reinterpret_cast<float2*>(C.f + o) = make_float2(acc0, acc1);
+            else
+                C.f[o] = (T)acc0;
         }
     } else {
         constexpr int RW = G::TX + 1;
