@@ -14,8 +14,10 @@ sampler is timed in the same run for comparison (config.plain_fp64_single_chain)
 
 --impl reference times the plain FP64 CPU oracle on the host cores (the only
 baseline this method has: the paper's code is a sequential CPU program).
-Multi-GPU: replicas only -- every rank advances its own independent chain
-(Philox stream = rank) of the same problem; no collective on the data path.
+Multi-GPU: replicas only -- every rank advances its own independent chains of
+the same problem (one chain: Philox chain id = rank; a batch: its own seed per
+rank); no collective on the data path, only the max over ranks of the timed
+region.
 """
 from __future__ import annotations
 
@@ -58,6 +60,28 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def replica_stream(rank, nch):
+    """(seed, chain id) of this rank's chains: the ranks are independent replicas.  One
+    chain per rank: seed 2024, Philox chain id = rank; a batch: its chains keep the ids
+    0 .. nch - 1 and each rank has its own seed."""
+    return (2024, rank) if nch == 1 else (2024 + 7919 * rank, None)
+
+
+def max_over_ranks(value, dist, device):
+    """The largest value of all ranks (the timed region of the slowest rank)."""
+    if not dist:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(ws, units_per_rank, seconds):
+    """Whole-job rate: the units every rank processed over the slowest rank's time."""
+    return ws * units_per_rank / seconds
 
 
 class ClockSampler:
@@ -225,15 +249,16 @@ def run_mine(args):
     stream = torch.cuda.current_stream()
     sites = sum(p.N for p in ps)
     launches = s.launches_per_cycle()
-    # chains of this rank: Philox chain ids rank * nch + c (independent replicas across ranks)
+    # this rank's chains: an independent replica (own seed, or own Philox chain id)
+    seed, chain_id = replica_stream(rank, nch)
     xs = s.zeros() if batch else [s.zeros()]
 
     def cycle(n_steps, offset, qoi=None, resume=False):
         # resume: continue from the states the handle holds (no copy of the chains in or out)
         if batch:
-            s.sample(None if resume else xs, n_steps, 2024 + 7919 * rank, step_offset=offset, qoi=qoi)
+            s.sample(None if resume else xs, n_steps, seed, step_offset=offset, qoi=qoi)
         else:
-            s.sample(None if resume else xs[0], n_steps, 2024, step_offset=offset, chain=rank, qoi=qoi)
+            s.sample(None if resume else xs[0], n_steps, seed, step_offset=offset, chain=chain_id, qoi=qoi)
 
     # --- untimed calibration chains: burn-in 100, then tau_int on the device ---
     ncal = args.tau_cycles
@@ -285,13 +310,10 @@ def run_mine(args):
     torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     clk = clocks.stop()
-    total_ms = sum(step_ms)
+    total_ms = max_over_ranks(sum(step_ms), dist, dev)
     if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
-    cps = ws * nch * args.steps / (total_ms / 1e3)       # chain V-cycles per second, whole job
+    cps = job_throughput(ws, nch * args.steps, total_ms / 1e3)   # chain V-cycles per second, whole job
     value = cps / tau
 
     # --- end-to-end through the public API with pinned host buffers -----------
@@ -319,7 +341,7 @@ def run_mine(args):
                 "s": sg, "stream": torch.cuda.Stream(device=dev) if ng > 1 else stream,
                 "dev": flat_dev, "views": list(torch.split(flat_dev, [p.N for p in part])),
                 "host": flat_dev.cpu().pin_memory(), "q": torch.zeros(gsz, dtype=torch.float64, device=dev),
-                "qh": qh[g * gsz:(g + 1) * gsz], "seed": 2024 + 7919 * rank + (104729 * g if ng > 1 else 0)})
+                "qh": qh[g * gsz:(g + 1) * gsz], "seed": seed + (104729 * g if ng > 1 else 0)})
     n_e2e = max(3, min(args.steps, 20))
     for G in groups:          # untimed first call of each group handle (graph capture)
         if G["s"] is not s:
@@ -339,14 +361,10 @@ def run_mine(args):
                     G["qh"].copy_(G["q"], non_blocking=True)
             torch.cuda.synchronize()
         else:
-            s.sample(xh[0], 1, 2024, step_offset=offset, chain=rank, qoi=qh[:1])   # host buffers: H2D, cycle, D2H
+            s.sample(xh[0], 1, seed, step_offset=offset, chain=chain_id, qoi=qh[:1])   # host buffers: H2D, cycle, D2H
         offset += 1
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = ws * nch * n_e2e / e2e_s / tau
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
+    e2e_value = job_throughput(ws, nch * n_e2e, e2e_s) / tau
 
     # --- plain FP64 single-chain GPU MGMC on the same posterior (comparison) ---
     plain = None
