@@ -327,7 +327,7 @@ __device__ void s_prolong(const DevLevel<T>& Cl, const T* XC, const DevLevel<T>&
 
 template <typename T, int DIM>
 __device__ void s_coarsest(const DevLevel<T>& L, const DevProblem& P, const CycleState& cs, T* X, const T* F,
-                           const double* chol, int n0)
+                           const double* chol, const double* Ls, int n0)
 {
     __shared__ double r[MGMC_MAX_COARSEST];
     const int n = L.n, S = n + 2;
@@ -347,27 +347,57 @@ __device__ void s_coarsest(const DevLevel<T>& L, const DevProblem& P, const Cycl
         for (int kk = 0; kk < P.m; ++kk)
             for (int t = L.bcol_ptr[kk]; t < L.bcol_ptr[kk + 1]; ++t) r[L.bcol_dense[t]] += L.bcol_w[t] * g[kk];
     __syncthreads();
-    for (int i = 0; i < n0; ++i) {
-        if (threadIdx.x == 0) r[i] = r[i] / chol[(long long)i * n0 + i];
-        __syncthreads();
-        const double yi = r[i];
-        for (int t = i + 1 + threadIdx.x; t < n0; t += blockDim.x) r[t] -= chol[(long long)t * n0 + i] * yi;
-        __syncthreads();
-    }
-    if (cs.noise) {
-        for (int s = threadIdx.x; s < n0; s += blockDim.x) {
-            double z0, z1;
-            draw_pair<double>(cs, (unsigned)(s >> 1), 2u, 0, 0u, z0, z1);
-            r[s] += (s & 1) ? z1 : z0;
+    if (n0 <= kCoarsestWarp) {
+        // one warp, lane t holding r_t, the factor staged in shared memory (Ls): the same
+        // operations in the same order as the CTA-wide solves below, without CTA barriers
+        if (threadIdx.x < 32) {
+            const int t = threadIdx.x;
+            double rt = t < n0 ? r[t] : 0.0;
+            for (int i = 0; i < n0; ++i) {
+                const double ri = __shfl_sync(0xffffffffu, rt, i) / Ls[i * n0 + i];
+                if (t == i)
+                    rt = ri;
+                else if (t > i && t < n0)
+                    rt -= Ls[t * n0 + i] * ri;
+            }
+            if (cs.noise && t < n0) {
+                double z0, z1;
+                draw_pair<double>(cs, (unsigned)(t >> 1), 2u, 0, 0u, z0, z1);
+                rt += (t & 1) ? z1 : z0;
+            }
+            for (int i = n0 - 1; i >= 0; --i) {
+                const double xi = __shfl_sync(0xffffffffu, rt, i) / Ls[i * n0 + i];
+                if (t == i)
+                    rt = xi;
+                else if (t < i)
+                    rt -= Ls[i * n0 + t] * xi;
+            }
+            if (t < n0) r[t] = rt;
         }
-    }
-    __syncthreads();
-    for (int i = n0 - 1; i >= 0; --i) {
-        if (threadIdx.x == 0) r[i] = r[i] / chol[(long long)i * n0 + i];
         __syncthreads();
-        const double xi = r[i];
-        for (int t = threadIdx.x; t < i; t += blockDim.x) r[t] -= chol[(long long)i * n0 + t] * xi;
+    } else {
+        for (int i = 0; i < n0; ++i) {
+            if (threadIdx.x == 0) r[i] = r[i] / chol[(long long)i * n0 + i];
+            __syncthreads();
+            const double yi = r[i];
+            for (int t = i + 1 + threadIdx.x; t < n0; t += blockDim.x) r[t] -= chol[(long long)t * n0 + i] * yi;
+            __syncthreads();
+        }
+        if (cs.noise) {
+            for (int s = threadIdx.x; s < n0; s += blockDim.x) {
+                double z0, z1;
+                draw_pair<double>(cs, (unsigned)(s >> 1), 2u, 0, 0u, z0, z1);
+                r[s] += (s & 1) ? z1 : z0;
+            }
+        }
         __syncthreads();
+        for (int i = n0 - 1; i >= 0; --i) {
+            if (threadIdx.x == 0) r[i] = r[i] / chol[(long long)i * n0 + i];
+            __syncthreads();
+            const double xi = r[i];
+            for (int t = threadIdx.x; t < i; t += blockDim.x) r[t] -= chol[(long long)i * n0 + t] * xi;
+            __syncthreads();
+        }
     }
     for (int s = threadIdx.x; s < n0; s += blockDim.x) {
         const int i = s % n, j = (s / n) % n, k = DIM == 3 ? s / (n * n) : 0;
@@ -398,6 +428,11 @@ long long coarse_smem_elems(int dim, const int* n_of_level, int top, bool top_is
     // normals of one sweep of the largest grid: 2 per Philox pair
     long long n = n_of_level[top], nq = (n + 3) / 4;
     tot += 4 * nq * n * (dim == 3 ? n : 1);
+    // the coarsest grid's Cholesky factor when one warp solves with it (doubles, at
+    // most two elements each, plus alignment)
+    long long n0 = n_of_level[0];
+    n0 = dim == 3 ? n0 * n0 * n0 : n0 * n0;
+    if (n0 <= kCoarsestWarp) tot += 2 * n0 * n0 + 2;
     return tot;
 }
 
@@ -464,6 +499,14 @@ __device__ __forceinline__ void coarse_body(const DevLevel<T>* __restrict__ leve
             }
         }
     }
+    // the coarsest grid's Cholesky factor, for the one-warp solves
+    double* Ls = nullptr;
+    if (n0 <= kCoarsestWarp) {
+        const int nt = lv[top].n;
+        const int zsz = 4 * ((nt + 3) / 4) * nt * (DIM == 3 ? nt : 1);
+        Ls = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(Z + zsz) + 7) & ~uintptr_t(7));
+        for (int i = threadIdx.x; i < n0 * n0; i += blockDim.x) Ls[i] = chol[i];
+    }
     // the descriptors and operators above never change after set-up; the top grid's
     // right-hand side and state (and the cycle state) come from the preceding launches
     pdl_wait();
@@ -493,7 +536,7 @@ __device__ __forceinline__ void coarse_body(const DevLevel<T>* __restrict__ leve
         if (nu1 == 0) s_lowrank<T>(L, P, cs, X, -1, 0u, true);
         s_restrict<T, DIM>(L, X, F, CS, lv[l - 1], blk(l - 1, 1));
     }
-    s_coarsest<T, DIM>(lv[0], P, cs, blk(0, 0), blk(0, 1), chol, n0);
+    s_coarsest<T, DIM>(lv[0], P, cs, blk(0, 0), blk(0, 1), chol, Ls, n0);
     for (int l = 1; l <= top; ++l) {
         const DevLevel<T>& L = lv[l];
         T* X = blk(l, 0);

@@ -47,6 +47,9 @@ void launch_set_cycle_batch(CycleState* const* cs, int n, unsigned long long see
 // the V-cycle of grids 0..top in one CTA with shared-memory state (coarse.cu)
 // grids a coarse kernel holds at most (their descriptors are staged in shared memory)
 constexpr int kCoarseMaxLevels = 8;
+// coarsest grids with at most this many unknowns are solved by one warp from a factor
+// staged in shared memory
+constexpr int kCoarsestWarp = 32;
 long long coarse_smem_elems(int dim, const int* n_of_level, int top, bool top_is_finest);
 template <typename T>
 cudaError_t coarse_prepare(int dim, size_t smem_bytes);
