@@ -342,7 +342,7 @@ def run_mine(args):
                 "dev": flat_dev, "views": list(torch.split(flat_dev, [p.N for p in part])),
                 "host": flat_dev.cpu().pin_memory(), "q": torch.zeros(gsz, dtype=torch.float64, device=dev),
                 "qh": qh[g * gsz:(g + 1) * gsz], "seed": seed + (104729 * g if ng > 1 else 0)})
-    n_e2e = max(3, min(args.steps, 20))
+    n_e2e = max(3, min(args.steps, 100))
     for G in groups:          # untimed first call of each group handle (graph capture)
         if G["s"] is not s:
             G["s"].sample(G["views"], 1, G["seed"], step_offset=offset, qoi=G["q"])
