@@ -521,12 +521,18 @@ __device__ __forceinline__ void tile_sweep(const DevLevel<T>& L, const CycleStat
 }
 
 // w_t * theta(site_t) of the observation entries inside the tile
-template <typename T, typename G>
-__device__ __forceinline__ void tile_zparts(const DevLevel<T>& L, const T* X, int tile)
+// [first, last) of the tile's observation entries; loaded at the start of a tile so
+// that the round trip overlaps the sweep
+template <typename T>
+__device__ __forceinline__ int2 tile_entries(const DevLevel<T>& L, int tile)
 {
-    if (!L.tile_ptr) return;
-    const int t0 = L.tile_ptr[tile], t1 = L.tile_ptr[tile + 1];
-    for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+    return L.tile_ptr ? make_int2(L.tile_ptr[tile], L.tile_ptr[tile + 1]) : make_int2(0, 0);
+}
+
+template <typename T, typename G>
+__device__ __forceinline__ void tile_zparts(const DevLevel<T>& L, const T* X, int2 range)
+{
+    for (int t = range.x + threadIdx.x; t < range.y; t += blockDim.x) {
         int loc = L.tile_loc[t];
         int lx = (loc & 0xFFFF) + G::RX, ly = (loc >> 16) + G::R;
         int ent = L.tile_ent[t];
@@ -564,13 +570,12 @@ __device__ __forceinline__ void tile_fwd_compute(const DevLevel<T>& L, const Dev
     using G = TileGeom<T, FINE, false>;
     const int x0 = bx * G::TX, y0 = by * G::TY;
     const int gx0 = x0 - G::RX, gy0 = y0 - G::R;
+    const int2 zr = tile_entries(L, by * L.ntx + bx);
     if (x_zero) {
         for (int idx = threadIdx.x; idx < G::SX * G::SY; idx += G::NT) X[idx] = T(0);
         __syncthreads();
     }
     tile_sweep<T, FINE, false, G>(L, cs, X, Cf, F, x0, y0, 0u);
-    const int tile = by * L.ntx + bx;
-    tile_zparts<T, G>(L, X, tile);
     // residual r = fdense - A theta*_s on [x0, x0+TX] x [y0, y0+TY] (inside the grid)
     const int I0 = x0 >> 1, J0 = y0 >> 1;
     if constexpr (sizeof(T) == 4) {
@@ -659,6 +664,10 @@ __device__ __forceinline__ void tile_fwd_compute(const DevLevel<T>& L, const Dev
             C.f[site_offset(2, C.pitch, C.plane, C.base, I, J, 0)] = acc;
         }
     }
+    // w_t theta*_s at the tile's observation entries (theta*_s is still in X: the
+    // residual and the restriction do not write it, and the next tile's copies that may
+    // already be in flight do not target it)
+    tile_zparts<T, G>(L, X, zr);
     tile_store<T, G>(L, L.x2, X, x0, y0);
 }
 
@@ -675,6 +684,7 @@ __device__ __forceinline__ void tile_bwd_compute(const DevLevel<T>& L, const Cyc
     const int x0 = bx * G::TX, y0 = by * G::TY;
     const int gx0 = x0 - G::RX, gy0 = y0 - G::R;
     const int Ilo = (gx0 >> 1) - 1 - G::POFF, Jlo = (gy0 >> 1) - 1;
+    const int2 zr = tile_entries(L, by * L.ntx + bx);
     // theta' + P psi on the staged region (interior sites only)
     if constexpr (sizeof(T) == 4) {
         // FP32: one 4-site group (i = gx0 + 4v even) per item; fine site i + c takes
@@ -740,7 +750,7 @@ __device__ __forceinline__ void tile_bwd_compute(const DevLevel<T>& L, const Cyc
     __syncthreads();
     tile_sweep<T, FINE, true, G>(L, cs, X, Cf, F, x0, y0, 1u);
     fields_free();
-    tile_zparts<T, G>(L, X, by * L.ntx + bx);
+    tile_zparts<T, G>(L, X, zr);
     tile_store<T, G>(L, L.x, X, x0, y0);
 }
 
