@@ -36,7 +36,7 @@ sys.path.insert(0, ROOT)
 # (k_tile_batch<float, 1, 0>) on the 32 x 1023^2 batch, from the ncu capture
 # summarised in profiles/k_tile_batch_fine_fwd_batch32_bayes2d_1023.md; None
 # for other workloads and whenever that kernel changes before it is re-captured.
-FINE_SWEEP_TRAFFIC_BYTES = 412.6e6
+FINE_SWEEP_TRAFFIC_BYTES = 412.8e6
 # the e2e measurement of a batch runs it as this many batches on their own streams
 E2E_GROUPS = 4
 
