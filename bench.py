@@ -32,11 +32,10 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# DRAM bytes (read + write) per launch of the finest-grid forward tile kernel
-# (k_tile_batch<float, 1, 0>) on the 32 x 1023^2 batch, from the ncu capture
-# summarised in profiles/k_tile_batch_fine_fwd_batch32_bayes2d_1023.md; None
+# DRAM bytes (read + write) per launch of the finest-grid forward kernel (k_stream_fwd)
+# on the 32 x 1023^2 batch, from an ncu capture of that kernel on this workload; None
 # for other workloads and whenever that kernel changes before it is re-captured.
-FINE_SWEEP_TRAFFIC_BYTES = 412.8e6
+FINE_SWEEP_TRAFFIC_BYTES = None
 # the e2e measurement of a batch runs it as this many batches on their own streams
 E2E_GROUPS = 4
 
@@ -402,7 +401,7 @@ def run_mine(args):
         # and s*kappa^2 (4 + 4 B/site), write theta*_s (4 B/site) and the restricted residual (4 B per
         # coarse site = 1 B per fine site); the noise is generated, never stored
         sweep_bytes = 13 * fine_sites
-        kernel = "k_tile_fwd_batch<float,1>: finest-grid forward Gibbs sweep + residual + restriction, all chains"
+        kernel = "k_stream_fwd: finest-grid forward Gibbs sweep + residual + restriction, all chains"
     achieved = sweep_bytes / (fwd_avg * 1e-3) / 1e9
     if wl.get("dim") == 3:
         desc = (f"{ps[0].n}^3 Bayesian posterior: kappa^2 = 25, 32 point obs, Gamma = 1e-4 I, "

@@ -5,11 +5,13 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
 #include "kernels.cuh"
 #include "setup.hpp"
+#include "stream2d.cuh"
 #include "tile2d.cuh"
 
 using namespace mgmc;
@@ -110,6 +112,14 @@ struct mgmc_ctx {
     std::vector<void*> maps_fwd, maps_bwd;   // TileMaps per tile job, per depth
     std::vector<int> njob_tile, nblk_tile, njob_lrd, nblk_lrd, njob_lru, nblk_lru;
     std::vector<int> per_tile, per_lrd, per_lru;
+    // FP32 finest grids: the streaming kernels (stream2d.cu) instead of depth-0 tiles
+    bool stream_fine = false;
+    void* jobs_stream = nullptr;
+    void* maps_sfwd = nullptr;
+    void* maps_sbwd = nullptr;
+    int njob_stream = 0;
+    long long stream_strips = 0;
+    int stream_ctas = 0;
     void* jobs_coarse = nullptr;
     void* jobs_qoi = nullptr;
     void* jobs_pack = nullptr;    // PackJob<T> per chain (2D fused path)
@@ -368,8 +378,12 @@ void enqueue_cycle_batch(mgmc_ctx* h, cudaStream_t s, int& launches)
     const bool prof = h->profile && h->n_depth > 0;
     for (int d = 0; d < h->n_depth; ++d) {
         if (prof && d == 0) cudaEventRecordWithFlags(h->ev[0], s, cudaEventRecordExternal);
-        launch_tile_batch<T>((const TileJob<T>*)h->jobs_tile[d], (const TileMaps*)h->maps_fwd[d], h->njob_tile[d],
-                             h->per_tile[d], h->nblk_tile[d], d == 0, false, d > 0, s, launches);
+        if (d == 0 && h->stream_fine)
+            launch_stream_fine((const StreamJob*)h->jobs_stream, (const StreamMaps*)h->maps_sfwd, h->njob_stream,
+                               h->stream_strips, h->stream_ctas, false, s, launches);
+        else
+            launch_tile_batch<T>((const TileJob<T>*)h->jobs_tile[d], (const TileMaps*)h->maps_fwd[d],
+                                 h->njob_tile[d], h->per_tile[d], h->nblk_tile[d], d == 0, false, d > 0, s, launches);
         if (prof && d == 0) cudaEventRecordWithFlags(h->ev[1], s, cudaEventRecordExternal);
         launch_lowrank_batch<T>((const LowrankJob<T>*)h->jobs_lrd[d], h->njob_lrd[d], h->per_lrd[d], h->nblk_lrd[d],
                                 true, s, launches);
@@ -382,8 +396,12 @@ void enqueue_cycle_batch(mgmc_ctx* h, cudaStream_t s, int& launches)
     launch_coarse_batch<T>((const CoarseJob<T>*)h->jobs_coarse, nc, coarse_threads, h->batch_coarse_smem, s, launches);
     for (int d = h->n_depth - 1; d >= 0; --d) {
         if (prof && d == 0) cudaEventRecordWithFlags(h->ev[2], s, cudaEventRecordExternal);
-        launch_tile_batch<T>((const TileJob<T>*)h->jobs_tile[d], (const TileMaps*)h->maps_bwd[d], h->njob_tile[d],
-                             h->per_tile[d], h->nblk_tile[d], d == 0, true, false, s, launches);
+        if (d == 0 && h->stream_fine)
+            launch_stream_fine((const StreamJob*)h->jobs_stream, (const StreamMaps*)h->maps_sbwd, h->njob_stream,
+                               h->stream_strips, h->stream_ctas, true, s, launches);
+        else
+            launch_tile_batch<T>((const TileJob<T>*)h->jobs_tile[d], (const TileMaps*)h->maps_bwd[d],
+                                 h->njob_tile[d], h->per_tile[d], h->nblk_tile[d], d == 0, true, false, s, launches);
         if (prof && d == 0) cudaEventRecordWithFlags(h->ev[3], s, cudaEventRecordExternal);
         launch_lowrank_batch<T>((const LowrankJob<T>*)h->jobs_lru[d], h->njob_lru[d], h->per_lru[d], h->nblk_lru[d],
                                 false, s, launches);
@@ -888,6 +906,45 @@ mgmc_status build_batch_tables(mgmc_ctx* h)
     int depth = 0;
     for (mgmc_ctx* c : chains) depth = std::max(depth, c->L - 1 - c->top);
     h->n_depth = depth;
+    // FP32 finest grids run in the streaming kernels; their low-rank steps then read
+    // the state at the observation entries (no z partials)
+    h->stream_fine = false;
+    if constexpr (std::is_same<T, float>::value) {
+        if (depth > 0) {
+            cudaError_t e = stream_prepare();
+            if (e != cudaSuccess)
+                return fail(MGMC_ERR_CUDA, std::string("stream kernel set-up: ") + cudaGetErrorString(e));
+            std::vector<StreamJob> sj;
+            std::vector<StreamMaps> sf, sb;
+            long long strips = 0;
+            for (mgmc_ctx* c : chains) {
+                const int l = c->L - 1;
+                if (l <= c->top) continue;
+                const auto& lv = levels_of<float>(c);
+                StreamJob J{};
+                J.L = lv[l];
+                J.C = lv[l - 1];
+                J.cs = c->cs;
+                J.strip0 = strips;
+                J.spb = (J.L.n + kStreamRows - 1) / kStreamRows;
+                J.nbands = (J.L.n + kStreamBand - 1) / kStreamBand;
+                strips += (long long)J.spb * J.nbands;
+                sj.push_back(J);
+                sf.emplace_back();
+                sb.emplace_back();
+                if (!make_stream_maps(J.L, J.C, false, &sf.back()) || !make_stream_maps(J.L, J.C, true, &sb.back()))
+                    return fail(MGMC_ERR_CUDA, "TMA descriptor encoding failed");
+            }
+            h->jobs_stream = upload(h, sj, st);
+            h->maps_sfwd = upload(h, sf, st);
+            h->maps_sbwd = upload(h, sb, st);
+            if (st != MGMC_OK) return fail(st, "stream table upload failed");
+            h->njob_stream = (int)sj.size();
+            h->stream_strips = strips;
+            h->stream_ctas = stream_grid(strips);
+            h->stream_fine = true;
+        }
+    }
     for (int d = 0; d < depth; ++d) {
         std::vector<TileJob<T>> tj;
         std::vector<TileMaps> mf, mb;
@@ -909,9 +966,11 @@ mgmc_status build_batch_tables(mgmc_ctx* h)
                 return fail(MGMC_ERR_CUDA, "TMA descriptor encoding failed");
             if (c->m > 0) {
                 int rd = std::max(Lh.g_rows[0], Lh.h_rows);
-                ld.push_back({Lh, Ch, c->P, bd, lowrank_blocks(rd)});
+                DevLevel<T> Lz = Lh;
+                if (d == 0 && h->stream_fine) Lz.zparts = nullptr;
+                ld.push_back({Lz, Ch, c->P, bd, lowrank_blocks(rd)});
                 bd += lowrank_blocks(rd);
-                lu.push_back({Lh, Ch, c->P, bu, lowrank_blocks(Lh.g_rows[1])});
+                lu.push_back({Lz, Ch, c->P, bu, lowrank_blocks(Lh.g_rows[1])});
                 bu += lowrank_blocks(Lh.g_rows[1]);
             }
         }

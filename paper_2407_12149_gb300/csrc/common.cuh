@@ -118,10 +118,11 @@ __device__ __forceinline__ uint4 philox10(uint4 c, unsigned k0, unsigned k1)
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        unsigned lo0 = 0xD2511F53u * c.x;
-        unsigned hi0 = __umulhi(0xD2511F53u, c.x);
-        unsigned lo1 = 0xCD9E8D57u * c.z;
-        unsigned hi1 = __umulhi(0xCD9E8D57u, c.z);
+        // one 32 x 32 -> 64-bit product per multiplier (both halves from one wide multiply)
+        const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+        const unsigned lo0 = (unsigned)p0, hi0 = (unsigned)(p0 >> 32);
+        const unsigned lo1 = (unsigned)p1, hi1 = (unsigned)(p1 >> 32);
         c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
@@ -160,12 +161,15 @@ __device__ __forceinline__ void normal_pair(const uint4 w, double& z0, double& z
 // reduced to phi = 2 pi (u2 - 1/2) in (-pi, pi], where the hardware sine/cosine
 // is accurate to ~4e-7 absolute; cos(2 pi u2) = -cos(phi), sin(2 pi u2) = -sin(phi).
 // The logarithm keeps full single precision: near u1 = 1 the radius is small
-// and an absolute-error logarithm would be too coarse.
+// and an absolute-error logarithm would be too coarse.  The radius is t / sqrt(t)
+// from the reciprocal square root (t = 0 when u1 rounds to 1 is held at 1e-37:
+// a radius of ~3e-19 instead of 0).
 __device__ __forceinline__ void normal_pair(const uint4 w, float& z0, float& z1)
 {
     float u1 = fmaf((float)w.x, 0x1p-32f, fmaf((float)(w.y & 0xFFFFF800u), 0x1p-64f, 0x1p-54f));
     float u2 = fmaf((float)w.z, 0x1p-32f, fmaf((float)(w.w & 0xFFFFF800u), 0x1p-64f, 0x1p-54f));
-    float r = sqrtf(-2.0f * logf(u1));
+    const float t = fmaxf(-2.0f * logf(u1), 1e-37f);
+    float r = t * rsqrtf(t);
     float s, c;
     __sincosf(6.28318530717958648f * (u2 - 0.5f), &s, &c);
     z0 = -r * c;

@@ -117,6 +117,27 @@ __device__ __forceinline__ float coarse_update(const DevLevel<float>& L, long lo
     return xi + (rhs - Ax) * ia;
 }
 
+// One FP32 Gibbs update of a 5-point site from its value xi, its four neighbours,
+// the row-sum part c = s kappa^2_i and the off-diagonal magnitude w (dense
+// right-hand side 0: the finest grid), the same operations as fine_update.
+__device__ __forceinline__ float fine_site(float xi, float up, float lf, float rt, float dn, float c, float w, float z)
+{
+    float lap = (xi - up) + (xi - lf) + (xi - rt) + (xi - dn);
+    float aii = fmaf(4.0f, w, c);
+    float Ax = fmaf(c, xi, w * lap);
+    float ia, sa;
+    inv_and_sqrt(aii, ia, sa);
+    float rhs = 0.0f + sa * z;
+    return xi + (rhs - Ax) * ia;
+}
+
+// (A x)_i of a 5-point FP32 site (dense part), the same operations as apply_A
+__device__ __forceinline__ float fine_ax(float xi, float up, float lf, float rt, float dn, float c, float w)
+{
+    float lap = (xi - up) + (xi - lf) + (xi - rt) + (xi - dn);
+    return fmaf(c, xi, w * lap);
+}
+
 // (A x)_e of the level (dense part of the operator)
 template <int DIM>
 __device__ __forceinline__ double apply_A(const DevLevel<double>& L, long long e)

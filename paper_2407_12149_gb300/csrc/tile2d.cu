@@ -240,16 +240,6 @@ __device__ __forceinline__ float cmp(const float4& v, float e, int k)
 {
     return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : k == 3 ? v.w : e;
 }
-__device__ __forceinline__ float fine_site(float xi, float up, float lf, float rt, float dn, float c, float w, float z)
-{
-    float lap = (xi - up) + (xi - lf) + (xi - rt) + (xi - dn);
-    float aii = fmaf(4.0f, w, c);
-    float Ax = fmaf(c, xi, w * lap);
-    float ia, sa;
-    inv_and_sqrt(aii, ia, sa);
-    float rhs = 0.0f + sa * z;
-    return xi + (rhs - Ax) * ia;
-}
 
 template <int SX>
 __device__ __forceinline__ void pair_fine(float* X, const float* C0, int lb, int px, float w, float z0, float z1,
@@ -985,6 +975,22 @@ __global__ void __launch_bounds__(TileGeom<T, FINE, BWD>::NT, 3)
 // The sums run in the same order as the general path.  Both forms call
 // pdl_wait themselves.
 constexpr int kLrReg = 16;
+// entries of a column of B whose sites are loaded before the wait (point observations have 4)
+constexpr int kLrEnt = 4;
+
+// z_k = (B^T theta)_k from the z partials of the tile kernels, or (streamed finest
+// grid, no partials) from the state itself: the same products w_t theta(site_t),
+// rounded before they are summed, in the same order
+template <typename T>
+__device__ __forceinline__ double lowrank_z(const DevLevel<T>& L, const T* x, int k)
+{
+    double acc = 0.0;
+    if (L.zparts)
+        for (int t = L.bcol_ptr[k]; t < L.bcol_ptr[k + 1]; ++t) acc += L.zparts[t];
+    else
+        for (int t = L.bcol_ptr[k]; t < L.bcol_ptr[k + 1]; ++t) acc += __dmul_rn(L.bcol_w[t], (double)x[L.bcol_site[t]]);
+    return acc;
+}
 
 template <typename T>
 __device__ __forceinline__ void lowrank_fused_short(const DevLevel<T>& L, const DevLevel<T>& C, const DevProblem& P,
@@ -1017,6 +1023,17 @@ __device__ __forceinline__ void lowrank_fused_short(const DevLevel<T>& L, const 
         t1 = L.bcol_ptr[k0 + 1];
         if (P.gamma_diag) lgk = P.LG[k0 * m + k0];
     }
+    // without z partials (streamed finest grid) the state is read at the entries of
+    // column k0 of B: their sites and weights are static
+    const bool zst = L.zparts == nullptr;
+    long long es[kLrEnt];
+    double ew[kLrEnt];
+#pragma unroll
+    for (int u = 0; u < kLrEnt; ++u) {
+        const bool has = hk && zst && t0 + u < t1;
+        es[u] = has ? L.bcol_site[t0 + u] : 0;
+        ew[u] = has ? L.bcol_w[t0 + u] : 0.0;
+    }
     // everything below depends on the preceding launches
     pdl_wait();
     const CycleState cs = *P.cs;
@@ -1025,7 +1042,14 @@ __device__ __forceinline__ void lowrank_fused_short(const DevLevel<T>& L, const 
     const T fv = hh ? C.f[hs] : T(0);
     if (hk) {
         double acc = 0.0;
-        for (int t = t0; t < t1; ++t) acc += L.zparts[t];
+        if (zst) {
+#pragma unroll
+            for (int u = 0; u < kLrEnt; ++u)
+                if (t0 + u < t1) acc += __dmul_rn(ew[u], (double)x[es[u]]);
+            for (int t = t0 + kLrEnt; t < t1; ++t) acc += __dmul_rn(L.bcol_w[t], (double)x[L.bcol_site[t]]);
+        } else {
+            for (int t = t0; t < t1; ++t) acc += L.zparts[t];
+        }
         z[k0] = acc;
         zp[k0] = cs.noise ? lowrank_normal<T>(cs, L.level, slot, k0) : 0.0;
     }
@@ -1081,10 +1105,9 @@ __device__ __forceinline__ void lowrank_fused_body(const DevLevel<T>& L, const D
     }
     pdl_wait();
     const CycleState cs = *P.cs;
+    T* x = down ? L.x2 : L.x;
     for (int k = threadIdx.x; k < m; k += blockDim.x) {
-        double acc = 0.0;
-        for (int t = L.bcol_ptr[k]; t < L.bcol_ptr[k + 1]; ++t) acc += L.zparts[t];
-        z[k] = acc;
+        z[k] = lowrank_z<T>(L, x, k);
         zp[k] = cs.noise ? lowrank_normal<T>(cs, L.level, slot, k) : 0.0;
     }
     __syncthreads();
@@ -1099,7 +1122,6 @@ __device__ __forceinline__ void lowrank_fused_body(const DevLevel<T>& L, const D
         v[k] = z[k] - L.d[k] - lz;
     }
     __syncthreads();
-    T* x = down ? L.x2 : L.x;
     const T* Gm = L.gT[dir];
     for (int r = blk * blockDim.x + threadIdx.x; r < L.g_rows[dir]; r += stride) {
         T acc = T(0);
