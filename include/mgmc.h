@@ -171,10 +171,11 @@ mgmc_status mgmc_qoi_stats(const double* qoi, int64_t n, int64_t burn_in, double
  * allocation or free of any kind is made.  All lags t <= (n - burn_in)/2 are
  * evaluated in one pass, so n - burn_in may be at most
  * MGMC_NOALLOC_MAX_SERIES (else MGMC_ERR_ARG).  The first call on a device
- * looks up the scratch address for that device; make that first call before
- * any stream capture.  All calls share the one scratch array: calls that may
- * overlap on the GPU (other streams, other threads) race and must be
- * serialised by the caller.  Synchronous on the stream. */
+ * also looks up the scratch address for that device.  The call copies its
+ * result to host memory and synchronises the stream, so it must not be made
+ * while that stream is being captured into a CUDA graph.  All calls share the
+ * one scratch array: calls that may overlap on the GPU (other streams, other
+ * threads) race and must be serialised by the caller. */
 mgmc_status mgmc_qoi_stats_noalloc(const double* qoi, int64_t n, int64_t burn_in, double S, mgmc_stats* out,
                                    void* stream);
 
@@ -212,9 +213,14 @@ mgmc_status mgmc_create_batch(int n_chains, const mgmc_config* cfgs, const mgmc_
                               const mgmc_allocator* alloc, void* stream, mgmc_handle* out);
 
 /* n_steps V-cycles of every chain of a batch handle.  x_inout: host array of
- * n_chains device pointers, chain c's dense n_c^2 state, or NULL to continue
- * from the states the handle holds (as in mgmc_sample); qoi_out: NULL or
- * device [n_chains * n_steps] (row c = chain c).  Asynchronous on stream. */
+ * n_chains pointers to chain c's dense n_c^2 state -- all in device memory, or
+ * all in host memory (copied in and out through the device inside the call, one
+ * copy per chain and direction) -- or NULL to continue from the states the
+ * handle holds (as in mgmc_sample); qoi_out: NULL, or device or host
+ * [n_chains * n_steps] (row c = chain c).  Asynchronous on stream when every
+ * buffer is device memory; with any host buffer the call synchronises the stream
+ * and reports the chains' sticky status bits (as mgmc_check_status).
+ * MGMC_ERR_ARG when host and device states are mixed. */
 mgmc_status mgmc_sample_batch(mgmc_handle h, int64_t n_steps, uint64_t seed, uint64_t step_offset,
                               void* const* x_inout, double* qoi_out, void* stream);
 
@@ -223,6 +229,23 @@ mgmc_status mgmc_sample_batch(mgmc_handle h, int64_t n_steps, uint64_t seed, uin
  * precision, device or host memory (host: the call synchronises the stream).
  * MGMC_ERR_ARG for a bad chain index or NULL x_out. */
 mgmc_status mgmc_get_state(mgmc_handle h, int chain, void* x_out, void* stream);
+
+/* The sticky status of every chain of a handle: the kernels set a bit when a
+ * bounded wait for a staging copy gave up or a QoI was not finite, and the bits
+ * stay set (across calls) until reported.  Synchronises the stream, returns
+ * MGMC_ERR_TIMEOUT (a wait gave up; the chain's state is not a valid sample) or
+ * MGMC_ERR_NUMERIC (non-finite QoI), else MGMC_OK, and clears the bits.
+ * mgmc_sample, mgmc_sample_batch with host buffers and mgmc_mean_solve report
+ * them the same way whenever they synchronise. */
+mgmc_status mgmc_check_status(mgmc_handle h, void* stream);
+
+/* Bound of the kernels' staging waits of every chain of a handle, for tests of
+ * the timeout path: 0 restores the default (1 s), a positive value is that many
+ * nanoseconds, a negative value makes every staging wait give up at once (the
+ * kernel then flags MGMC_ERR_TIMEOUT, lets its copies in flight land within the
+ * default bound and ends; the chain's state is garbage until it is re-set).
+ * Synchronises the device. */
+mgmc_status mgmc_set_wait_limit(mgmc_handle h, int64_t limit_ns);
 
 /* Benchmark timing: with enable != 0 the captured cycle records CUDA events
  * around the finest grid's forward sweep and its backward sweep (finest grid

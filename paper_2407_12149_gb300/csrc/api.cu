@@ -508,11 +508,50 @@ mgmc_status check_device()
     return MGMC_OK;
 }
 
+// The sticky status bits of every chain of a handle (the work queued on `s` is
+// waited for first): reported as a status and cleared, so that the handle can be
+// used again.  Timeouts are reported before non-finite values.
+mgmc_status take_status(mgmc_ctx* h, cudaStream_t s)
+{
+    CUDA_TRY(cudaStreamSynchronize(s));
+    std::vector<mgmc_ctx*> chains = h->is_batch() ? h->sub : std::vector<mgmc_ctx*>{h};
+    int bits = 0, first = -1;
+    for (size_t c = 0; c < chains.size(); ++c) {
+        int v = 0;
+        CUDA_TRY(cudaMemcpy(&v, &chains[c]->cs->status, sizeof(int), cudaMemcpyDeviceToHost));
+        if (v && first < 0) first = (int)c;
+        bits |= v;
+        if (v) CUDA_TRY(cudaMemset(&chains[c]->cs->status, 0, sizeof(int)));
+    }
+    const std::string who = h->is_batch() ? " (chain " + std::to_string(first) + " first)" : std::string();
+    if (bits & kStatusTimeout) return fail(MGMC_ERR_TIMEOUT, "a kernel's bounded staging wait gave up" + who);
+    if (bits & kStatusNumeric) return fail(MGMC_ERR_NUMERIC, "non-finite QoI produced" + who);
+    return MGMC_OK;
+}
+
 }  // namespace
 
 extern "C" {
 
 const char* mgmc_last_error(void) { return g_last_error.c_str(); }
+
+mgmc_status mgmc_check_status(mgmc_handle h, void* stream)
+{
+    if (!h) return fail(MGMC_ERR_ARG, "handle is NULL");
+    CUDA_TRY(cudaSetDevice(h->device));
+    return take_status(h, (cudaStream_t)stream);
+}
+
+mgmc_status mgmc_set_wait_limit(mgmc_handle h, int64_t limit_ns)
+{
+    if (!h) return fail(MGMC_ERR_ARG, "handle is NULL");
+    CUDA_TRY(cudaSetDevice(h->device));
+    CUDA_TRY(cudaDeviceSynchronize());
+    std::vector<mgmc_ctx*> chains = h->is_batch() ? h->sub : std::vector<mgmc_ctx*>{h};
+    const long long v = (long long)limit_ns;
+    for (mgmc_ctx* c : chains) CUDA_TRY(cudaMemcpy(&c->cs->wait_ns, &v, sizeof(v), cudaMemcpyHostToDevice));
+    return MGMC_OK;
+}
 
 mgmc_status mgmc_config_default(mgmc_config* cfg, int dim, int n)
 {
@@ -808,13 +847,7 @@ mgmc_status mgmc_sample(mgmc_handle h, int64_t n_steps, uint64_t seed, uint64_t 
         CUDA_TRY(cudaFreeAsync(qdev, s));
     }
     CUDA_TRY(cudaGetLastError());
-    if (xhost || qhost) {
-        CUDA_TRY(cudaStreamSynchronize(s));
-        CycleState csh;
-        CUDA_TRY(cudaMemcpy(&csh, h->cs, sizeof(csh), cudaMemcpyDeviceToHost));
-        if (csh.status == 2) return fail(MGMC_ERR_TIMEOUT, "a tile kernel's staging wait gave up");
-        if (csh.status) return fail(MGMC_ERR_NUMERIC, "non-finite QoI produced");
-    }
+    if (xhost || qhost) return take_status(h, s);
     return MGMC_OK;
 }
 
@@ -858,7 +891,8 @@ mgmc_status mgmc_mean_solve(mgmc_handle h, double rtol, int max_cycles, void* me
     }
     st = pack_out(h, mean_out, xhost, s, N);
     if (st != MGMC_OK) return st;
-    CUDA_TRY(cudaStreamSynchronize(s));
+    st = take_status(h, s);
+    if (st != MGMC_OK) return st;
     if (cycles_done) *cycles_done = c;
     if (rel_residual) *rel_residual = rr;
     return MGMC_OK;
@@ -1086,26 +1120,55 @@ mgmc_status mgmc_sample_batch(mgmc_handle h, int64_t n_steps, uint64_t seed, uin
     if (n_steps == 0) return MGMC_OK;
     const int nc = (int)h->sub.size();
     const bool resume = x_inout == nullptr;
-    if (!resume)
-        for (int c = 0; c < nc; ++c)
-            if (!x_inout[c] || !is_device_ptr(x_inout[c]))
-                return fail(MGMC_ERR_ARG, "batch states must be device memory");
-    if (qoi_out && !is_device_ptr(qoi_out)) return fail(MGMC_ERR_ARG, "batch QoI buffer must be device memory");
+    // states: all in device memory, or all in host memory (staged through the device)
+    int on_host = 0;
+    if (!resume) {
+        for (int c = 0; c < nc; ++c) {
+            if (!x_inout[c]) return fail(MGMC_ERR_ARG, "NULL state pointer");
+            on_host += is_device_ptr(x_inout[c]) ? 0 : 1;
+        }
+        if (on_host != 0 && on_host != nc) return fail(MGMC_ERR_ARG, "batch states must be all device or all host memory");
+    }
+    const bool xhost = on_host == nc && !resume;
+    const bool qhost = qoi_out && !is_device_ptr(qoi_out);
     cudaStream_t s = (cudaStream_t)stream;
     CUDA_TRY(cudaSetDevice(h->device));
     mgmc_status st = ensure_graph(h);
     if (st != MGMC_OK) return st;
+    const size_t esz = h->fp32() ? 4 : 8;
+    std::vector<size_t> bytes((size_t)nc), off((size_t)nc + 1, 0);
+    for (int c = 0; c < nc; ++c) {
+        const long long n = h->sub[c]->cfg.n;
+        bytes[c] = (size_t)(n * n) * esz;
+        off[c + 1] = off[c] + bytes[c];
+    }
+    // host buffers: one stream-ordered staging allocation for the states and the QoI
+    const size_t qbytes = qhost ? sizeof(double) * (size_t)nc * (size_t)n_steps : 0;
+    char* stage = nullptr;
+    if (xhost || qhost) CUDA_TRY(cudaMallocAsync((void**)&stage, (xhost ? off[nc] : 0) + qbytes, s));
+    std::vector<void*> dev((size_t)nc, nullptr);
+    for (int c = 0; c < nc && !resume; ++c) dev[c] = xhost ? (void*)(stage + off[c]) : x_inout[c];
+    double* qdev = qhost ? (double*)(stage + (xhost ? off[nc] : 0)) : qoi_out;
     auto pack = [&](bool in) {
         if (h->fp32())
-            launch_pack_batch<float>((const PackJob<float>*)h->jobs_pack, x_inout, nc, h->pack_max_n, in, s);
+            launch_pack_batch<float>((const PackJob<float>*)h->jobs_pack, dev.data(), nc, h->pack_max_n, in, s);
         else
-            launch_pack_batch<double>((const PackJob<double>*)h->jobs_pack, x_inout, nc, h->pack_max_n, in, s);
+            launch_pack_batch<double>((const PackJob<double>*)h->jobs_pack, dev.data(), nc, h->pack_max_n, in, s);
     };
+    if (xhost)
+        for (int c = 0; c < nc; ++c)
+            CUDA_TRY(cudaMemcpyAsync(dev[c], x_inout[c], bytes[c], cudaMemcpyHostToDevice, s));
     if (!resume) pack(true);
-    launch_set_cycle_batch(h->cs_list, nc, seed, step_offset, 1, qoi_out, n_steps, s);
+    launch_set_cycle_batch(h->cs_list, nc, seed, step_offset, 1, qdev, n_steps, s);
     for (int64_t t = 0; t < n_steps; ++t) CUDA_TRY(cudaGraphLaunch(h->exec, s));
     if (!resume) pack(false);
+    if (xhost)
+        for (int c = 0; c < nc; ++c)
+            CUDA_TRY(cudaMemcpyAsync(x_inout[c], dev[c], bytes[c], cudaMemcpyDeviceToHost, s));
+    if (qhost) CUDA_TRY(cudaMemcpyAsync(qoi_out, qdev, qbytes, cudaMemcpyDeviceToHost, s));
+    if (stage) CUDA_TRY(cudaFreeAsync(stage, s));
     CUDA_TRY(cudaGetLastError());
+    if (xhost || qhost) return take_status(h, s);
     return MGMC_OK;
 }
 

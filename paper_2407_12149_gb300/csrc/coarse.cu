@@ -619,7 +619,7 @@ __global__ void k_qoi_batch(const QoiJob<T>* __restrict__ jobs)
         CycleState* cs = J.cs;
         double q = part[0];
         if (cs->qoi) cs->qoi[cs->step] = q;
-        if (!isfinite(q)) cs->status = 1;
+        if (!isfinite(q)) atomicOr(&cs->status, kStatusNumeric);
         cs->step += 1;
         cs->cycle += 1;
     }
@@ -637,7 +637,6 @@ __global__ void k_set_cycle_batch(CycleState* const* cs, int n, unsigned long lo
     s->noise = noise;
     s->qoi = qoi ? qoi + (long long)c * n_steps : nullptr;
     s->step = 0;
-    s->status = 0;
 }
 
 template <typename T>

@@ -28,8 +28,14 @@ struct CycleState {
     int noise;                  // 0: deterministic multigrid (mean solve)
     double* qoi;                // NULL or [n_steps] QoI series
     long long step;             // index into qoi of the running cycle
-    int status;                 // sticky error flag (non-finite value seen)
+    int status;                 // sticky error bits, kept until the host reports them:
+                                // 1 a non-finite QoI, 2 a bounded wait gave up
+    long long wait_ns;          // bound of the kernels' staging waits: 0 the default
+                                // (1 s), > 0 that many ns, < 0 give up at once (tests)
 };
+
+constexpr int kStatusNumeric = 1;
+constexpr int kStatusTimeout = 2;
 
 // One grid level on the device.  T = float or double.
 template <typename T>

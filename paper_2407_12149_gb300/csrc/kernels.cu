@@ -255,7 +255,7 @@ __global__ void k_qoi_advance(DevLevel<T> L, int n_qoi, const long long* q_site,
         CycleState* cs = P.cs;
         double q = part[0];
         if (cs->qoi) cs->qoi[cs->step] = q;
-        if (!isfinite(q)) cs->status = 1;
+        if (!isfinite(q)) atomicOr(&cs->status, kStatusNumeric);
         cs->step += 1;
         cs->cycle += 1;
     }
@@ -270,7 +270,6 @@ __global__ void k_set_cycle(CycleState* cs, unsigned long long seed, unsigned lo
     cs->noise = noise;
     cs->qoi = qoi;
     cs->step = 0;
-    cs->status = 0;
 }
 
 // dense user field <-> padded finest-level state

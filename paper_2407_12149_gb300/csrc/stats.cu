@@ -115,14 +115,15 @@ __global__ void k_stats_final(const WolffState* st, long long n, mgmc_stats* out
     *out = r;
 }
 
-thread_local std::string g_stats_error;
-
 }  // namespace
 
 extern "C" mgmc_status mgmc_qoi_stats(const double* qoi, int64_t n, int64_t burn_in, double S, mgmc_stats* out,
                                       void* stream)
 {
-    if (!qoi || !out || burn_in < 0 || n - burn_in < 2) return MGMC_ERR_ARG;
+    if (!qoi || !out || burn_in < 0 || n - burn_in < 2) {
+        mgmc::set_last_error("mgmc_qoi_stats: NULL pointer or fewer than 2 samples after burn-in");
+        return MGMC_ERR_ARG;
+    }
     if (!(S > 0.0)) S = 1.5;
     cudaStream_t s = (cudaStream_t)stream;
     const double* a = qoi + burn_in;
@@ -131,33 +132,50 @@ extern "C" mgmc_status mgmc_qoi_stats(const double* qoi, int64_t n, int64_t burn
     WolffState* st = nullptr;
     double* G = nullptr;
     mgmc_stats* dout = nullptr;
-    if (cudaMallocAsync((void**)&st, sizeof(WolffState), s) != cudaSuccess) return MGMC_ERR_CUDA;
-    if (cudaMallocAsync((void**)&G, sizeof(double) * kLagChunk, s) != cudaSuccess) return MGMC_ERR_CUDA;
-    if (cudaMallocAsync((void**)&dout, sizeof(mgmc_stats), s) != cudaSuccess) return MGMC_ERR_CUDA;
-    k_stats_init<<<1, kThreads, 0, s>>>(a, nn, st);
-    long long t0 = 1;
     mgmc_status rc = MGMC_OK;
-    while (t0 <= tmax) {
-        long long t1 = t0 + kLagChunk < tmax + 1 ? t0 + kLagChunk : tmax + 1;
-        k_autocov<<<(unsigned)(t1 - t0), kThreads, 0, s>>>(a, nn, st, t0, t1, G);
-        k_wolff_scan<<<1, 1, 0, s>>>(G, t0, t1, tmax, nn, S, st);
-        WolffState hs;
-        if (cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-            cudaStreamSynchronize(s) != cudaSuccess) {
-            rc = MGMC_ERR_CUDA;
-            break;
+    const char* msg = nullptr;
+    // every exit below frees what was allocated (stream-ordered)
+    if (cudaMallocAsync((void**)&st, sizeof(WolffState), s) != cudaSuccess ||
+        cudaMallocAsync((void**)&G, sizeof(double) * kLagChunk, s) != cudaSuccess ||
+        cudaMallocAsync((void**)&dout, sizeof(mgmc_stats), s) != cudaSuccess) {
+        rc = MGMC_ERR_CUDA;
+        msg = "mgmc_qoi_stats: stream-ordered allocation failed";
+    }
+    if (rc == MGMC_OK) {
+        k_stats_init<<<1, kThreads, 0, s>>>(a, nn, st);
+        long long t0 = 1;
+        while (t0 <= tmax) {
+            long long t1 = t0 + kLagChunk < tmax + 1 ? t0 + kLagChunk : tmax + 1;
+            k_autocov<<<(unsigned)(t1 - t0), kThreads, 0, s>>>(a, nn, st, t0, t1, G);
+            k_wolff_scan<<<1, 1, 0, s>>>(G, t0, t1, tmax, nn, S, st);
+            WolffState hs;
+            if (cudaGetLastError() != cudaSuccess ||
+                cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess) {
+                rc = MGMC_ERR_CUDA;
+                msg = "mgmc_qoi_stats: kernel launch or copy failed";
+                break;
+            }
+            if (hs.done) break;
+            t0 = t1;
         }
-        if (hs.done) break;
-        t0 = t1;
     }
     if (rc == MGMC_OK) {
         k_stats_final<<<1, 1, 0, s>>>(st, nn, dout);
-        if (cudaMemcpyAsync(out, dout, sizeof(mgmc_stats), cudaMemcpyDeviceToHost, s) != cudaSuccess) rc = MGMC_ERR_CUDA;
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(out, dout, sizeof(mgmc_stats), cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+            rc = MGMC_ERR_CUDA;
+            msg = "mgmc_qoi_stats: kernel launch or copy failed";
+        }
     }
-    cudaFreeAsync(st, s);
-    cudaFreeAsync(G, s);
-    cudaFreeAsync(dout, s);
-    if (cudaStreamSynchronize(s) != cudaSuccess) rc = MGMC_ERR_CUDA;
+    if (st) cudaFreeAsync(st, s);
+    if (G) cudaFreeAsync(G, s);
+    if (dout) cudaFreeAsync(dout, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess && rc == MGMC_OK) {
+        rc = MGMC_ERR_CUDA;
+        msg = "mgmc_qoi_stats: stream synchronisation failed";
+    }
+    if (msg) mgmc::set_last_error(msg);
     return rc;
 }
 

@@ -171,11 +171,12 @@ __device__ __forceinline__ void colour_rows(float* xa, float* xb, const float* x
 }
 
 // wait (bounded) for blocks (waited, upto] of the ring; false if a wait gave up
-__device__ __forceinline__ bool wait_blocks(unsigned long long* bar, unsigned& ph, int& waited, int upto)
+__device__ __forceinline__ bool wait_blocks(unsigned long long* bar, unsigned& ph, int& waited, int upto,
+                                            long long limit_ns)
 {
     while (waited < upto) {
         const int q = (waited + 1) & (kNB - 1);
-        if (!mbar_wait(&bar[q], (ph >> q) & 1u)) return false;
+        if (!mbar_wait(&bar[q], (ph >> q) & 1u, limit_ns)) return false;
         ph ^= 1u << q;
         ++waited;
     }
@@ -185,7 +186,7 @@ __device__ __forceinline__ bool wait_blocks(unsigned long long* bar, unsigned& p
 // a wait gave up: flag the chain (MGMC_ERR_TIMEOUT) and let the copies in flight land
 __device__ __forceinline__ void give_up(CycleState* cs, unsigned long long* bar, unsigned ph, int waited, int issued)
 {
-    cs->status = 2;
+    atomicOr(&cs->status, kStatusTimeout);
     __threadfence();
     for (int k = waited + 1; k <= issued; ++k) {
         const int q = k & (kNB - 1);
@@ -325,7 +326,7 @@ __global__ void __launch_bounds__(kNT, 2)
         for (int s = 0; s < S; ++s) {
             const int R = ya - 2 + kK * s;
             // blocks up to 2s + 2 (rows up to R + 16) are in shared memory
-            const bool ok = wait_blocks(bar, ph, waited, min(2 * s + 2, KB));
+            const bool ok = wait_blocks(bar, ph, waited, min(2 * s + 2, KB), cs.wait_ns);
             if (__syncthreads_or(!ok)) {
                 if (tid == 0) give_up(J->cs, bar, ph, waited, issued);
                 __syncthreads();
@@ -460,7 +461,7 @@ __global__ void __launch_bounds__(kNT, 2)
         for (int s = 0; s < S; ++s) {
             const int R = ya - 2 + kK * s;
             // blocks up to 2s + 2 (psi of row R + 15) are in shared memory
-            const bool ok = wait_blocks(bar, ph, waited, min(2 * s + 2, KB));
+            const bool ok = wait_blocks(bar, ph, waited, min(2 * s + 2, KB), cs.wait_ns);
             if (__syncthreads_or(!ok)) {
                 if (tid == 0) give_up(J->cs, bar, ph, waited, issued);
                 __syncthreads();

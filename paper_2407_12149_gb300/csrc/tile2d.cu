@@ -924,10 +924,10 @@ __global__ void __launch_bounds__(TileGeom<T, FINE, BWD>::NT, 3)
             fetch(t + step, hs ^ 1);
             if (threadIdx.x == 0) issue(t + step, hs ^ 1, ds ^ 1, xbuf(k + 1, ds ^ 1), 0);
         }
-        const bool ok = mbar_wait(&bar[ds], parity);
+        const bool ok = mbar_wait(&bar[ds], parity, cs_s[hs].wait_ns);
         if (__syncthreads_or(!ok)) {
             if (threadIdx.x == 0) {
-                hdr(hs)->P.cs->status = 2;
+                atomicOr(&hdr(hs)->P.cs->status, kStatusTimeout);
                 __threadfence();
                 mbar_wait(&bar[ds], parity);
                 if (G::NSTAGE == 2 && more) mbar_wait(&bar[ds ^ 1], (unsigned)(((k + 1) >> 1) & 1));

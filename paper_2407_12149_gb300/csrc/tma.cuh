@@ -39,15 +39,19 @@ __device__ __forceinline__ unsigned long long global_ns()
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// wait for the completion of the barrier phase of the given parity; false after 1 s
+// wait for the completion of the barrier phase of the given parity; false once the
+// bound has passed (limit_ns: 0 the default 1 s, > 0 that many ns, < 0 give up at
+// once -- a test of the give-up path; the drains after a give-up use the default)
 constexpr unsigned long long kWaitNs = 1000000000ull;
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity)
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, long long limit_ns = 0)
 {
+    if (limit_ns < 0) return false;
+    const unsigned long long bound = limit_ns > 0 ? (unsigned long long)limit_ns : kWaitNs;
     if (mbar_test(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (unsigned it = 1; it < (1u << 30); ++it) {
         if (mbar_test(bar, parity)) return true;
-        if ((it & 63) == 0 && global_ns() - t0 > kWaitNs) return false;
+        if ((it & 63) == 0 && global_ns() - t0 > bound) return false;
     }
     return false;
 }

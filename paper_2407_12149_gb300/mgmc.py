@@ -73,7 +73,8 @@ EXPORTS = ("mgmc_config_default", "mgmc_create", "mgmc_point_obs_rows", "mgmc_sa
            "mgmc_profile_times", "mgmc_create_batch", "mgmc_sample_batch", "mgmc_get_state", "mgmc_destroy",
            "mgmc_tc_gemm", "mgmc_unet_create", "mgmc_unet_n_params", "mgmc_unet_get_params",
            "mgmc_unet_set_params", "mgmc_unet_inputs", "mgmc_unet_gradient", "mgmc_unet_train",
-           "mgmc_unet_predict", "mgmc_unet_destroy", "mgmc_last_error")
+           "mgmc_unet_predict", "mgmc_unet_destroy", "mgmc_check_status", "mgmc_set_wait_limit",
+           "mgmc_last_error")
 
 
 def load():
@@ -126,6 +127,8 @@ def load():
     L.mgmc_unet_predict.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
     L.mgmc_unet_destroy.argtypes = [ctypes.c_void_p]
     L.mgmc_destroy.argtypes = [ctypes.c_void_p]
+    L.mgmc_check_status.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    L.mgmc_set_wait_limit.argtypes = [ctypes.c_void_p, ctypes.c_int64]
     for name in EXPORTS:
         if name != "mgmc_last_error":
             getattr(L, name).restype = ctypes.c_int
@@ -179,6 +182,14 @@ class TorchAllocator:
 # --------------------------------------------------------------------------
 # functions with the C names
 # --------------------------------------------------------------------------
+
+def mgmc_check_status(h, stream=None):
+    _check(load().mgmc_check_status(h, _stream_handle(stream)))
+
+
+def mgmc_set_wait_limit(h, limit_ns: int):
+    _check(load().mgmc_set_wait_limit(h, int(limit_ns)))
+
 
 def mgmc_point_obs_rows(dim: int, n: int, xyz: np.ndarray):
     xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, dim)
@@ -341,6 +352,14 @@ class Sampler:
     def mean_solve(self, x, rtol=1e-10, max_cycles=200, stream=None):
         return mgmc_mean_solve(self.h, rtol, max_cycles, x.data_ptr(), stream)
 
+    def check_status(self, stream=None):
+        """Raise MGMCError if a kernel flagged the chain (wait gave up, non-finite QoI)."""
+        mgmc_check_status(self.h, stream)
+
+    def set_wait_limit(self, limit_ns: int):
+        """Bound of the kernels' staging waits (0 default, < 0 give up at once: tests)."""
+        mgmc_set_wait_limit(self.h, limit_ns)
+
     def launches_per_cycle(self):
         return mgmc_launches_per_cycle(self.h)
 
@@ -406,16 +425,29 @@ class BatchSampler:
         return [torch.zeros(p.N, dtype=self.dtype, device=f"cuda:{self.device}") for p in self.problems]
 
     def sample(self, xs, n_steps, seed, step_offset=0, qoi=None, stream=None):
-        """xs: one device tensor per chain (modified in place), or None to continue
-        from the states the handle holds (see get_state)."""
+        """xs: one tensor per chain (modified in place), all on the device or all in
+        host memory (the library copies them in and out and synchronises), or None
+        to continue from the states the handle holds (see get_state)."""
         n = len(self.problems)
+        if xs is not None:
+            for x, p in zip(xs, self.problems):
+                if x.dtype != self.dtype or not x.is_contiguous() or x.numel() != p.N:
+                    raise ValueError("each state must be a contiguous tensor of N_c entries in the precision")
         ptrs = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs]) if xs is not None else None
         if qoi is not None and (qoi.dtype != _torch().float64 or qoi.numel() < n * n_steps):
-            raise ValueError("qoi must be a float64 device tensor with n_chains * n_steps entries")
+            raise ValueError("qoi must be a float64 tensor with n_chains * n_steps entries")
         _check(load().mgmc_sample_batch(self.h, int(n_steps), int(seed) & (2**64 - 1), int(step_offset), ptrs,
                                         ctypes.c_void_p(qoi.data_ptr()) if qoi is not None else None,
                                         _stream_handle(stream)))
         return xs
+
+    def check_status(self, stream=None):
+        """Raise MGMCError if a kernel flagged a chain (wait gave up, non-finite QoI)."""
+        mgmc_check_status(self.h, stream)
+
+    def set_wait_limit(self, limit_ns: int):
+        """Bound of the kernels' staging waits (0 default, < 0 give up at once: tests)."""
+        mgmc_set_wait_limit(self.h, limit_ns)
 
     def get_state(self, c, x, stream=None):
         """Copy chain c's state into x (device or host tensor of N_c entries)."""

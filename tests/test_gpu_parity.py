@@ -120,6 +120,105 @@ def test_config3_full_size_parity(torch_mod):
         s.close()
 
 
+def test_config2_fp32_after_100_cycles_single_chain_and_batch_chain(torch_mod):
+    """The tolerance as stated for the FP32 path (2e-4 of the field RMS after 100
+    V-cycles) on the benchmarked problem (1023^2, 16 observations, 10 grids): one
+    chain, and chain 5 of a batch of 32 chains of it (the benchmark's launch
+    configuration); both use Philox chain id 5, so one oracle run serves both."""
+    torch = torch_mod
+    from paper_2407_12149_gb300.mgmc import BatchSampler
+    p = inputs.config2()
+    xo, qo = _orc(p).sample(100, 31, chain=5)
+    rms = np.sqrt(np.mean(xo ** 2))
+    s = _gpu(p, precision="fp32")
+    xg, qg = _run_gpu(torch, s, p, 100, 31, chain=5)
+    s.close()
+    _check32(xg, xo)
+    assert np.abs(qg - qo).max() <= TOL32 * rms
+    b = BatchSampler([p] * 32, precision="fp32")
+    xs = b.zeros()
+    q = torch.zeros(32 * 100, dtype=torch.float64, device="cuda")
+    b.sample(xs, 100, 31, qoi=q)
+    torch.cuda.synchronize()
+    _check32(xs[5].double().cpu().numpy(), xo)
+    assert np.abs(q[5 * 100:6 * 100].cpu().numpy() - qo).max() <= TOL32 * rms
+    b.close()
+
+
+@pytest.mark.slow
+def test_config3_fp32_after_100_cycles(torch_mod):
+    """127^3, kappa^2 = 25, 32 observations, coarsest 3^3: FP32 after 100 V-cycles
+    (the oracle needs about 2.8 s per cycle here)."""
+    p = inputs.config3()
+    xo, qo = _orc(p).sample(100, 55)
+    s = _gpu(p, precision="fp32")
+    xg, qg = _run_gpu(torch_mod, s, p, 100, 55)
+    s.close()
+    _check32(xg, xo)
+    assert np.abs(qg - qo).max() <= TOL32 * np.sqrt(np.mean(xo ** 2))
+
+
+def test_config1_fp64_parity_over_10000_cycles(torch_mod):
+    """Config 1 (31^2, 4 grids, seed 1234, x0 = 0): every site within 1e-11 after
+    10^4 V-cycles, and the whole QoI series."""
+    p = inputs.config1()
+    xo, qo = _orc(p).sample(10000, 1234)
+    s = _gpu(p)
+    xg, qg = _run_gpu(torch_mod, s, p, 10000, 1234)
+    s.close()
+    _check64(xg, xo)
+    _check64(qg, qo)
+
+
+def _mean_qoi(torch, p):
+    """F . mu with mu = A~^-1 f from the FP64 noise-free V-cycle (the exact posterior mean of the QoI)."""
+    s = _gpu(p)
+    x = s.zeros()
+    _, rr = s.mean_solve(x, rtol=1e-12, max_cycles=200)
+    s.close()
+    assert rr <= 1e-12
+    mu = x.cpu().numpy()
+    return float(np.dot(p.qoi_w, mu[p.qoi_site]))
+
+
+def test_fp32_batch_qoi_mean_matches_mean_solve(torch_mod):
+    """Config 2 has no closed form: the FP32 chains' QoI mean must match F . mu from the
+    FP64 mean solve within 3 standard errors (32 independent chains x 1000 cycles after
+    100 of burn-in; the standard error from the spread of the 32 chain means)."""
+    torch = torch_mod
+    from paper_2407_12149_gb300.mgmc import BatchSampler
+    p = inputs.config2()
+    fmu = _mean_qoi(torch, p)
+    nc, n = 32, 1100
+    b = BatchSampler([p] * nc, precision="fp32")
+    xs = b.zeros()
+    q = torch.zeros(nc * n, dtype=torch.float64, device="cuda")
+    b.sample(xs, n, 808, qoi=q)
+    torch.cuda.synchronize()
+    b.close()
+    means = q.view(nc, n)[:, 100:].mean(1).cpu().numpy()
+    se = means.std(ddof=1) / np.sqrt(nc)
+    assert abs(means.mean() - fmu) <= 3.0 * se, (means.mean(), fmu, se)
+
+
+def test_fp32_3d_qoi_mean_matches_mean_solve(torch_mod):
+    """Config 3 (127^3): one FP32 chain of 4000 cycles; standard error from the device
+    Wolff estimate of its integrated autocorrelation time; within 3 SE of F . mu."""
+    torch = torch_mod
+    from paper_2407_12149_gb300.mgmc import mgmc_qoi_stats
+    p = inputs.config3()
+    fmu = _mean_qoi(torch, p)
+    s = _gpu(p, precision="fp32")
+    x = s.zeros()
+    n = 4000
+    q = torch.zeros(n, dtype=torch.float64, device="cuda")
+    s.sample(x, n, 909, qoi=q)
+    st = mgmc_qoi_stats(q.data_ptr(), n, 100, 1.5)
+    s.close()
+    se = np.sqrt(st["var"] * st["tau_int"] / st["n_used"])
+    assert abs(st["mean"] - fmu) <= 3.0 * se, (st["mean"], fmu, se)
+
+
 def test_restart_is_bit_exact(torch_mod):
     """Counter-based noise: 2 x 50 cycles == 1 x 100 cycles, bit for bit."""
     p = inputs.make_problem("t", 2, 63, kappa2_seed=3, m=6, obs_seed=1)
@@ -207,7 +306,8 @@ def test_qoi_stats_on_device_match_oracle(torch_mod):
 
 
 def test_fp32_config1_moments(torch_mod):
-    """FP32 chain of config 1: QoI mean 0 and variance F^T A^-1 F = 0.18241764732 within 4 SE."""
+    """FP32 chain of config 1: QoI mean 0 and variance F^T A^-1 F = 0.18241764732 within 3 SE
+    (the closed-form integrated autocorrelation time 1.228612 of this chain)."""
     torch = torch_mod
     from paper_2407_12149_gb300.mgmc import mgmc_qoi_stats
     p = inputs.config1()
@@ -219,5 +319,5 @@ def test_fp32_config1_moments(torch_mod):
     st = mgmc_qoi_stats(q.data_ptr(), n, 100, 1.5)
     var, tau = 0.18241764732, 1.228612
     nn = n - 100
-    assert abs(st["mean"]) < 4 * np.sqrt(var * tau / nn)
-    assert abs(st["var"] - var) < 4 * var * np.sqrt(2 * tau / nn)
+    assert abs(st["mean"]) < 3 * np.sqrt(var * tau / nn)
+    assert abs(st["var"] - var) < 3 * var * np.sqrt(2 * tau / nn)

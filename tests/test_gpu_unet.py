@@ -80,6 +80,33 @@ def test_gradient_matches_oracle(torch_mod, batch):
         o += nw + co
 
 
+def test_forward_and_gradient_at_warm_start_size(torch_mod):
+    """The network the warm-start workload runs: 255^2 grid, c0 = 32 (about 2M
+    parameters, the bottom convolutions on N = 256 GEMM tiles), batch 2."""
+    torch = torch_mod
+    n, c0, batch = 255, 32, 2
+    net, theta, xr, xbits, t = _setup(torch, n, c0, batch=batch, seed=3)
+    got = net.predict(xbits, precision="fp64").cpu().numpy().reshape(batch, n, n)
+    ref, _ = U.forward(theta, xr, c0, bf16=True)
+    ref = ref[:, :n, :n]
+    rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert rel <= 1e-2, rel
+    assert np.abs(got - ref).max() <= 5e-2 * np.sqrt(np.mean(ref ** 2))
+    tg = torch.tensor(t.reshape(batch, n * n), dtype=torch.float32).cuda()
+    loss, g = net.gradient(xbits, tg, batch)
+    lo, go = U.loss_and_grad(theta, xr, t, c0, bf16=True)
+    assert abs(loss - lo) <= 1e-2 * lo
+    o = 0
+    for name, _, ci, co in U.layer_table(c0) + [("out", 0, c0, 1)]:
+        nw = co * 9 * ci if name != "out" else c0
+        for sl in (slice(o, o + nw), slice(o + nw, o + nw + co)):
+            ref_g = go[sl]
+            err = np.linalg.norm(g[sl] - ref_g) / max(np.linalg.norm(ref_g), 1e-12)
+            assert err <= 5e-2, (name, err)
+        o += nw + co
+    net.close()
+
+
 def test_one_adam_step_matches_oracle(torch_mod):
     """one step over a single batch (the shuffle cannot change it) against Adam on the
     oracle's gradient: the first step moves each parameter by about lr sign(g)"""
