@@ -45,7 +45,7 @@ def lib():
         L = ctypes.CDLL(_LIB)
         L.oracle_create.restype = ctypes.c_int
         L.oracle_create.argtypes = [
-            ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+            ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
             _c_dbl_p, ctypes.c_double,
             ctypes.c_int, _c_int_p, _c_dbl_p, ctypes.c_int,
             _c_dbl_p, _c_dbl_p,
@@ -98,7 +98,8 @@ class Oracle:
 
     def __init__(self, dim, n, n_levels, *, kappa2=None, kappa2_const=10.0, scale_hd=1,
                  nu1=1, nu2=1, obs_site=None, obs_w=None, Gamma=None, y=None,
-                 qoi_site=None, qoi_w=None):
+                 qoi_site=None, qoi_w=None, disc=0):
+        """disc: 0 finite-difference fine operator, 1 Q1 finite elements (constant kappa^2)."""
         L = lib()
         self.dim, self.n, self.n_levels = dim, n, n_levels
         self.N = n ** dim
@@ -120,7 +121,7 @@ class Oracle:
             qw = np.ascontiguousarray(qoi_w, dtype=np.float64)
             nq = qs.size
         h = ctypes.c_void_p()
-        rc = L.oracle_create(dim, n, n_levels, scale_hd, nu1, nu2, _dp(k2), float(kappa2_const),
+        rc = L.oracle_create(dim, n, n_levels, scale_hd, int(disc), nu1, nu2, _dp(k2), float(kappa2_const),
                              m, _ip(os_), _dp(ow_), nnz, _dp(G_), _dp(y_),
                              nq, _ip(qs), _dp(qw), ctypes.byref(h))
         if rc != 0:

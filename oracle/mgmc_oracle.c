@@ -102,6 +102,7 @@ struct oracle_problem {
     int d, NS, centre;
     int n_levels;
     int scale_hd;
+    int disc;              /* fine-grid discretisation: 0 finite differences, 1 Q1 finite elements */
     int nu1, nu2;
     int m;                 /* beta: number of observations */
     olevel* lev;           /* lev[0] coarsest ... lev[n_levels-1] finest */
@@ -550,6 +551,51 @@ static void build_fine_operator(oracle_problem* p, olevel* L, const double* kapp
     }
 }
 
+/* Fine-level lowest-order conforming Q1 (multilinear) finite-element matrix of
+ * kappa^2 I - Delta with zero Dirichlet values (Sec. 5.1.1, FE discretisation):
+ * a_ij = int grad phi_i . grad phi_j + kappa^2 phi_i phi_j over the unit
+ * square / cube for the nodal hat functions phi of the uniform grid, constant
+ * kappa^2.  A hat function is a product of 1D hats, so each entry is a sum of
+ * products of the 1D integrals
+ *   stiffness  int phi_a' phi_b'  = (2 / h, -1 / h)  for |a - b| = (0, 1),
+ *   mass       int phi_a  phi_b   = (4 h / 6, h / 6),
+ * one derivative factor per axis: a(o) = sum_ax K(o_ax) prod_{t != ax} M(o_t)
+ * + kappa^2 prod_t M(o_t).  scale_hd = 0 divides by h^d (the literal scaling
+ * of the finite-difference option). */
+static void build_fine_operator_q1(oracle_problem* p, olevel* L, double kappa2_const)
+{
+    int d = p->d, n = L->n;
+    double h = 1.0 / (double)(n + 1);
+    double scale = 1.0;
+    if (!p->scale_hd)
+        for (int a = 0; a < d; ++a) scale /= h;
+    for (int s = 0; s < L->N; ++s) {
+        int c[3];
+        site_coords(d, n, s, c);
+        double* a = L->a + (size_t)s * p->NS;
+        for (int o = 0; o < p->NS; ++o) {
+            int off[3], cc[3] = {0, 0, 0};
+            offset_of(d, o, off);
+            for (int t = 0; t < d; ++t) cc[t] = c[t] + off[t];
+            if (site_index(d, n, cc) < 0) continue;
+            double K[3], M[3];
+            for (int t = 0; t < d; ++t) {
+                K[t] = off[t] == 0 ? 2.0 / h : -1.0 / h;
+                M[t] = off[t] == 0 ? 4.0 * h / 6.0 : h / 6.0;
+            }
+            double stiff = 0.0, mass = 1.0;
+            for (int ax = 0; ax < d; ++ax) {
+                double term = K[ax];
+                for (int t = 0; t < d; ++t)
+                    if (t != ax) term *= M[t];
+                stiff += term;
+                mass *= M[ax];
+            }
+            a[o] = scale * (stiff + kappa2_const * mass);
+        }
+    }
+}
+
 /* Galerkin triple product A_c = P^T A_f P (Eq. A_ell_1_B_ell_1). */
 static void build_galerkin(oracle_problem* p, const olevel* F, olevel* C)
 {
@@ -747,7 +793,7 @@ static int build_lowrank(oracle_problem* p, int l, int dir)
     return 0;
 }
 
-int oracle_create(int dim, int n, int n_levels, int scale_hd, int nu1, int nu2,
+int oracle_create(int dim, int n, int n_levels, int scale_hd, int disc, int nu1, int nu2,
                   const double* kappa2, double kappa2_const,
                   int m, const int32_t* obs_site, const double* obs_w, int nnz_per_obs,
                   const double* Gamma, const double* y,
@@ -756,6 +802,8 @@ int oracle_create(int dim, int n, int n_levels, int scale_hd, int nu1, int nu2,
 {
     if (!out || (dim != 2 && dim != 3) || n < 1 || n_levels < 1 || m < 0 || nu1 < 0 || nu2 < 0)
         return ERR_ARG;
+    /* the Q1 option takes a constant kappa^2 */
+    if (disc != 0 && (disc != 1 || kappa2)) return ERR_ARG;
     /* n_levels grids: n_{l-1} = (n_l - 1) / 2 must stay >= 1 and exact */
     {
         int nn = n;
@@ -772,6 +820,7 @@ int oracle_create(int dim, int n, int n_levels, int scale_hd, int nu1, int nu2,
     p->centre = (p->NS - 1) / 2;
     p->n_levels = n_levels;
     p->scale_hd = scale_hd;
+    p->disc = disc;
     p->nu1 = nu1;
     p->nu2 = nu2;
     p->m = m;
@@ -810,7 +859,10 @@ int oracle_create(int dim, int n, int n_levels, int scale_hd, int nu1, int nu2,
         }
     }
     olevel* Lf = &p->lev[n_levels - 1];
-    build_fine_operator(p, Lf, kappa2, kappa2_const);
+    if (p->disc == 1)
+        build_fine_operator_q1(p, Lf, kappa2_const);
+    else
+        build_fine_operator(p, Lf, kappa2, kappa2_const);
     /* fine B from the given rows (duplicates are summed) */
     {
         int nnz = 0;

@@ -27,8 +27,10 @@ typedef struct oracle_problem oracle_problem;
  * coarsest Cholesky factor.  kappa2 may be NULL (then kappa2_const is used).
  * obs_site/obs_w hold m rows of nnz_per_obs (fine site, weight); site -1 is
  * an ignored (boundary) entry.  Gamma is m x m row-major SPD, y has m
- * entries.  qoi_site/qoi_w: n_qoi entries of the QoI vector F_L. */
-int oracle_create(int dim, int n, int n_levels, int scale_hd, int nu1, int nu2,
+ * entries.  qoi_site/qoi_w: n_qoi entries of the QoI vector F_L.
+ * disc: fine-grid discretisation of kappa^2 - Delta, 0 the finite-difference
+ * stencil, 1 the Q1 finite-element matrix (constant kappa^2: kappa2 = NULL). */
+int oracle_create(int dim, int n, int n_levels, int scale_hd, int disc, int nu1, int nu2,
                   const double* kappa2, double kappa2_const,
                   int m, const int32_t* obs_site, const double* obs_w, int nnz_per_obs,
                   const double* Gamma, const double* y,

@@ -3,7 +3,8 @@
 Everything here is built from the problem definition with dense linear
 algebra (numpy solves / Cholesky) rather than sweeps or stencils, so that it
 shares no code path with the oracle:
-  - A_L from the finite-difference formula s (kappa^2 I - Delta_h);
+  - A_L from the finite-difference formula s (kappa^2 I - Delta_h), or the Q1
+    finite-element matrix assembled by quadrature over the cells;
   - P from the coarse hat functions evaluated at the fine vertices (Sec. 5.1.3);
   - A_{l-1} = P^T A_l P and B_{l-1} = P^T B_l (Eq. A_ell_1_B_ell_1);
   - the forward/backward low-rank Gibbs splittings M~ = D + L + B Gamma^-1 B^T
@@ -26,6 +27,46 @@ def fd_operator(n, d, kappa2, scale_hd=1):
     else:
         lap = np.kron(np.kron(I, I), T) + np.kron(np.kron(I, T), I) + np.kron(np.kron(T, I), I)
     return s * (lap + np.diag(k2))
+
+
+def q1_operator(n, d, kappa2, scale_hd=1):
+    """Q1 finite-element matrix of kappa^2 - Delta (constant kappa^2, zero Dirichlet
+    values) assembled cell by cell with a 3-point Gauss-Legendre rule per axis (exact
+    for the products of multilinear functions), from the nodal hat functions of the
+    (n+1)^d cells of the unit square / cube; boundary vertices are dropped."""
+    h = 1.0 / (n + 1)
+    gx, gw = np.polynomial.legendre.leggauss(3)
+    qx, qw = 0.5 * (gx + 1.0), 0.5 * gw                     # on [0, 1]
+    corners = np.array(np.meshgrid(*[[0, 1]] * d, indexing="ij")).reshape(d, -1).T   # (2^d, d)
+    pts = np.array(np.meshgrid(*[qx] * d, indexing="ij")).reshape(d, -1).T
+    wts = np.prod(np.array(np.meshgrid(*[qw] * d, indexing="ij")).reshape(d, -1).T, axis=1)
+    # local basis values and reference gradients at the quadrature points
+    val = np.ones((len(corners), len(pts)))
+    grad = np.ones((len(corners), len(pts), d))
+    for c, cor in enumerate(corners):
+        for a in range(d):
+            f = pts[:, a] if cor[a] else 1.0 - pts[:, a]
+            df = 1.0 if cor[a] else -1.0
+            val[c] *= f
+            for b in range(d):
+                grad[c, :, b] *= df if b == a else f
+    K_loc = np.einsum("ipk,jpk,p->ij", grad, grad, wts) * h ** (d - 2)
+    M_loc = np.einsum("ip,jp,p->ij", val, val, wts) * h ** d
+    loc = K_loc + kappa2 * M_loc
+    N = n ** d
+    A = np.zeros((N, N))
+    for cell in np.ndindex(*([n + 1] * d)):
+        gidx = []
+        for cor in corners:
+            v = [cell[a] + cor[a] - 1 for a in range(d)]     # interior index of the corner vertex
+            gidx.append(-1 if min(v) < 0 or max(v) >= n else sum(v[a] * n ** a for a in range(d)))
+        for i, gi in enumerate(gidx):
+            if gi < 0:
+                continue
+            for j, gj in enumerate(gidx):
+                if gj >= 0:
+                    A[gi, gj] += loc[i, j]
+    return A if scale_hd else A / h ** d
 
 
 def prolongation_1d(nc):
@@ -75,13 +116,13 @@ def B_dense(N, obs_site, obs_w):
 class Hierarchy:
     """Dense operators of every level, index 0 = coarsest."""
 
-    def __init__(self, n, d, n_levels, kappa2, B=None, Gamma=None, scale_hd=1):
+    def __init__(self, n, d, n_levels, kappa2, B=None, Gamma=None, scale_hd=1, disc=0):
         self.d = d
         self.A = [None] * n_levels
         self.B = [None] * n_levels
         self.P = [None] * n_levels     # P[l]: level l-1 -> l
         self.n = [None] * n_levels
-        A = fd_operator(n, d, kappa2, scale_hd)
+        A = q1_operator(n, d, kappa2, scale_hd) if disc == 1 else fd_operator(n, d, kappa2, scale_hd)
         self.A[-1] = A
         self.B[-1] = B if B is not None else np.zeros((n ** d, 0))
         self.n[-1] = n
