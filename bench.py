@@ -172,6 +172,7 @@ WORKLOADS = {
     "bayes3d-127": {"n": 127, "chains": 1, "dim": 3},     # 127^3, kappa^2 = 25, 32 obs, coarsest 3^3
     "warmstart-255": {"n": 255, "chains": 64, "warm": True},       # learned warm start (U-Net), 255^2
     "gibbs-vs-mgmc-2d": {"n": 511, "chains": 1, "table": True},   # Table 1 comparison, 31^2 .. 511^2
+    "gibbs-vs-mgmc-2d-q1": {"n": 511, "chains": 1, "table": True, "q1": True},   # Table 1a setting (Q1 elements)
 }
 
 
@@ -617,9 +618,11 @@ def run_gibbs_table(args):
         ms = e0.elapsed_time(e1) / n_time
         return st["tau_int"], st["tau_err"], ms
 
+    q1 = bool(WORKLOADS[args.workload].get("q1"))
+    make = inputs.table1a if q1 else inputs.config2
     rows = []
     for n in (31, 63, 127, 255, 511):
-        p = inputs.config2(n=n)
+        p = make(n=n)
         row = {"n": n}
         # Gibbs: tau grows like h^-2 (about 100 at 31^2 for kappa^2 = 10); chains of up to 400 000 steps
         n_g = min(400000, 20000 * ((n + 1) // 32) ** 2)
@@ -633,7 +636,7 @@ def run_gibbs_table(args):
                     "ms_per_indep_gibbs": msg * tg, "tau_mgmc": tm, "tau_mgmc_err": em, "ms_per_step_mgmc": msm,
                     "ms_per_indep_mgmc": msm * tm})
         if n == 31:
-            pc = inputs.config2(n=31, n_levels=1)
+            pc = make(n=31, n_levels=1)
             s = M.Sampler(pc, precision="fp64", device=local)
             x = s.zeros()
             s.sample(x, 5, 1)
@@ -651,9 +654,12 @@ def run_gibbs_table(args):
         "metric": "time per independent QoI sample (MGMC, 511^2)", "value": big["ms_per_indep_mgmc"], "unit": "ms",
         "n_gpus": 1, "steps": 200, "warmup": 5, "ms_per_step": big["ms_per_step_mgmc"], "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "gibbs-vs-mgmc-2d: the Sec. 5.2 / Table 1 comparison on the 2D posterior "
-                               "(kappa^2 = 10 exp(g), 16 point obs, Gamma = 1e-4 I), 31^2 .. 511^2, one FP32 "
-                               "chain per sampler and grid; Cholesky = single-grid exact sampler (FP64, one CTA)",
+        "config": {"workload": (("gibbs-vs-mgmc-2d-q1: the Table 1a setting (Q1 finite elements, kappa^-1 = 0.1, "
+                                 "8 point obs, Gamma diagonal in [1e-6, 2e-6])") if q1 else
+                                ("gibbs-vs-mgmc-2d: the Sec. 5.2 / Table 1 comparison on the 2D posterior "
+                                 "(kappa^2 = 10 exp(g), 16 point obs, Gamma = 1e-4 I)")) +
+                               ", 31^2 .. 511^2, one FP32 chain per sampler and grid; Cholesky = single-grid "
+                               "exact sampler (FP64, one CTA)",
                    "table": rows,
                    "tau_from": "device Wolff estimate (S = 1.5) of each chain after its burn-in (Gibbs 2000, MGMC 100)",
                    "timing": "CUDA events over 200 back-to-back steps, state resident (grids up to 511^2 are "

@@ -90,7 +90,16 @@ typedef struct {
                          coarse-grid correction.  Needs n_levels >= 2 (the finest grid's
                          low-rank data are those of MGMC); single-chain handles only
                          (mgmc_create_batch returns MGMC_ERR_ARG). */
+    int disc;         /* discretisation of kappa^2 - Delta on the finest grid (Sec. 5.1.1):
+                         MGMC_FD (default): the 5/7-point finite-difference stencil;
+                         MGMC_Q1: the lowest-order conforming multilinear finite-element
+                         matrix, a_ij = int grad phi_i . grad phi_j + kappa^2 phi_i phi_j
+                         (9/27-point; constant kappa^2 only: kappa2 must be NULL), divided
+                         by h^d when scale_hd = 0.  The coarse grids are Galerkin products
+                         either way (for Q1 they are the Q1 matrices of the coarse grids). */
 } mgmc_config;
+
+enum { MGMC_FD = 0, MGMC_Q1 = 1 };
 
 /* Fill cfg with the paper's defaults for a dim-dimensional n^dim grid. */
 mgmc_status mgmc_config_default(mgmc_config* cfg, int dim, int n);

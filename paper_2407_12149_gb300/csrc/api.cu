@@ -114,6 +114,7 @@ struct mgmc_ctx {
     std::vector<int> per_tile, per_lrd, per_lru;
     // FP32 finest grids: the streaming kernels (stream2d.cu) instead of depth-0 tiles
     bool stream_fine = false;
+    bool fine0 = true;    // the depth-0 grids have the 5-point finite-difference form
     void* jobs_stream = nullptr;
     void* maps_sfwd = nullptr;
     void* maps_sbwd = nullptr;
@@ -185,12 +186,15 @@ mgmc_status build_device_levels(mgmc_ctx* h, const HostProblem& hp)
         if (!D.x) return fail(MGMC_ERR_OOM, "allocator returned NULL");
         CUDA_TRY(cudaMemsetAsync(D.x, 0, fbytes, h->buf.stream));
         const bool finest = l == hp.n_levels - 1;
-        if (!finest) {
+        // the finite-difference finest grid keeps its 5/7-point form; a Q1 finest grid is
+        // stored like the Galerkin grids (stencil fields and a zero dense right-hand side)
+        const bool fd_fine = finest && hp.disc == 0;
+        if (!fd_fine) {
             D.f = (T*)h->buf.get(fbytes);
             if (!D.f) return fail(MGMC_ERR_OOM, "allocator returned NULL");
             CUDA_TRY(cudaMemsetAsync(D.f, 0, fbytes, h->buf.stream));
         }
-        if (finest) {
+        if (fd_fine) {
             D.fine = 1;
             std::vector<T> diag((size_t)D.alloc, T(0));
             for (long long s = 0; s < HL.N; ++s)
@@ -297,7 +301,8 @@ mgmc_status build_device_levels(mgmc_ctx* h, const HostProblem& hp)
     {
         std::vector<int> nl;
         for (int l = 0; l < hp.n_levels; ++l) nl.push_back(hp.lev[l].n);
-        h->coarse_smem = (size_t)coarse_smem_elems(d, nl.data(), h->top, h->top == hp.n_levels - 1) * sizeof(T);
+        h->coarse_smem =
+            (size_t)coarse_smem_elems(d, nl.data(), h->top, h->top == hp.n_levels - 1 && hp.disc == 0) * sizeof(T);
         cudaError_t e = coarse_prepare<T>(d, h->coarse_smem);
         if (e != cudaSuccess)
             return fail(MGMC_ERR_CUDA, std::string("coarse kernel set-up: ") + cudaGetErrorString(e));
@@ -383,7 +388,8 @@ void enqueue_cycle_batch(mgmc_ctx* h, cudaStream_t s, int& launches)
                                h->stream_strips, h->stream_ctas, false, s, launches);
         else
             launch_tile_batch<T>((const TileJob<T>*)h->jobs_tile[d], (const TileMaps*)h->maps_fwd[d],
-                                 h->njob_tile[d], h->per_tile[d], h->nblk_tile[d], d == 0, false, d > 0, s, launches);
+                                 h->njob_tile[d], h->per_tile[d], h->nblk_tile[d], d == 0 && h->fine0, false, d > 0,
+                                 s, launches);
         if (prof && d == 0) cudaEventRecordWithFlags(h->ev[1], s, cudaEventRecordExternal);
         launch_lowrank_batch<T>((const LowrankJob<T>*)h->jobs_lrd[d], h->njob_lrd[d], h->per_lrd[d], h->nblk_lrd[d],
                                 true, s, launches);
@@ -401,7 +407,8 @@ void enqueue_cycle_batch(mgmc_ctx* h, cudaStream_t s, int& launches)
                                h->stream_strips, h->stream_ctas, true, s, launches);
         else
             launch_tile_batch<T>((const TileJob<T>*)h->jobs_tile[d], (const TileMaps*)h->maps_bwd[d],
-                                 h->njob_tile[d], h->per_tile[d], h->nblk_tile[d], d == 0, true, false, s, launches);
+                                 h->njob_tile[d], h->per_tile[d], h->nblk_tile[d], d == 0 && h->fine0, true, false, s,
+                                 launches);
         if (prof && d == 0) cudaEventRecordWithFlags(h->ev[3], s, cudaEventRecordExternal);
         launch_lowrank_batch<T>((const LowrankJob<T>*)h->jobs_lru[d], h->njob_lru[d], h->per_lru[d], h->nblk_lru[d],
                                 false, s, launches);
@@ -524,6 +531,8 @@ mgmc_status take_status(mgmc_ctx* h, cudaStream_t s)
         if (v) CUDA_TRY(cudaMemset(&chains[c]->cs->status, 0, sizeof(int)));
     }
     const std::string who = h->is_batch() ? " (chain " + std::to_string(first) + " first)" : std::string();
+    if (bits & kStatusLayout)
+        return fail(MGMC_ERR_CUDA, "a kernel's shared-memory layout exceeded its launch (not run)" + who);
     if (bits & kStatusTimeout) return fail(MGMC_ERR_TIMEOUT, "a kernel's bounded staging wait gave up" + who);
     if (bits & kStatusNumeric) return fail(MGMC_ERR_NUMERIC, "non-finite QoI produced" + who);
     return MGMC_OK;
@@ -645,7 +654,7 @@ mgmc_status mgmc_create(const mgmc_config* cfg_in, const mgmc_allocator* alloc, 
 
     HostProblem hp;
     int code = MGMC_OK;
-    std::string err = build_hierarchy(hp, cfg.dim, cfg.n, cfg.n_levels, cfg.scale_hd, kappa2, kappa2_const, m,
+    std::string err = build_hierarchy(hp, cfg.dim, cfg.n, cfg.n_levels, cfg.scale_hd, cfg.disc, kappa2, kappa2_const, m,
                                       obs_site, obs_w, nnz_per_obs, Gamma, y, &code);
     if (!err.empty()) return fail((mgmc_status)code, err);
 
@@ -669,7 +678,7 @@ mgmc_status mgmc_create(const mgmc_config* cfg_in, const mgmc_allocator* alloc, 
         std::vector<int> nl;
         for (int l = 0; l < h->L; ++l) nl.push_back(hp.lev[l].n);
         for (int l = 0; l < h->L && l < kCoarseMaxLevels; ++l) {
-            size_t bytes = (size_t)coarse_smem_elems(cfg.dim, nl.data(), l, l == h->L - 1) * esz;
+            size_t bytes = (size_t)coarse_smem_elems(cfg.dim, nl.data(), l, l == h->L - 1 && cfg.disc == 0) * esz;
             if (hp.lev[l].n <= cmax && bytes + 16384 <= budget) h->top = l;
         }
     }
@@ -940,11 +949,16 @@ mgmc_status build_batch_tables(mgmc_ctx* h)
     int depth = 0;
     for (mgmc_ctx* c : chains) depth = std::max(depth, c->L - 1 - c->top);
     h->n_depth = depth;
-    // FP32 finest grids run in the streaming kernels; their low-rank steps then read
-    // the state at the observation entries (no z partials)
+    // depth 0: the finest grids (5-point finite differences, or Q1 -- stored like the
+    // Galerkin grids); a batch holds one discretisation
+    h->fine0 = true;
+    for (mgmc_ctx* c : chains)
+        if (c->L - 1 > c->top && !levels_of<T>(c)[c->L - 1].fine) h->fine0 = false;
+    // FP32 5-point finest grids run in the streaming kernels; their low-rank steps then
+    // read the state at the observation entries (no z partials)
     h->stream_fine = false;
     if constexpr (std::is_same<T, float>::value) {
-        if (depth > 0) {
+        if (depth > 0 && h->fine0) {
             cudaError_t e = stream_prepare();
             if (e != cudaSuccess)
                 return fail(MGMC_ERR_CUDA, std::string("stream kernel set-up: ") + cudaGetErrorString(e));
@@ -1001,7 +1015,7 @@ mgmc_status build_batch_tables(mgmc_ctx* h)
             if (c->m > 0) {
                 int rd = std::max(Lh.g_rows[0], Lh.h_rows);
                 DevLevel<T> Lz = Lh;
-                if (d == 0 && h->stream_fine) Lz.zparts = nullptr;
+                if (d == 0 && h->stream_fine) Lz.zparts = nullptr;   // (stream_fine implies 5-point)
                 ld.push_back({Lz, Ch, c->P, bd, lowrank_blocks(rd)});
                 bd += lowrank_blocks(rd);
                 lu.push_back({Lz, Ch, c->P, bu, lowrank_blocks(Lh.g_rows[1])});
@@ -1071,6 +1085,7 @@ mgmc_status mgmc_create_batch(int n_chains, const mgmc_config* cfgs, const mgmc_
         if (cfgs[c].dim != 2 || cfgs[c].nu1 != 1 || cfgs[c].nu2 != 1)
             return fail(MGMC_ERR_ARG, "batched chains must be 2D with nu1 = nu2 = 1");
         if (cfgs[c].precision != cfgs[0].precision) return fail(MGMC_ERR_ARG, "batched chains share one precision");
+        if (cfgs[c].disc != cfgs[0].disc) return fail(MGMC_ERR_ARG, "batched chains share one discretisation");
     }
     mgmc_status dst = check_device();
     if (dst != MGMC_OK) return dst;

@@ -417,12 +417,12 @@ constexpr int coarse_threads()
 // Shared-memory elements of grids 0..top: state, right-hand side and
 // coefficient blocks (1 coefficient block for the 5/7-point finest grid,
 // (3^d + 1)/2 for a Galerkin grid), plus the normals of one sweep of grid top.
-long long coarse_smem_elems(int dim, const int* n_of_level, int top, bool top_is_finest)
+long long coarse_smem_elems(int dim, const int* n_of_level, int top, bool top_is_fd_finest)
 {
     long long tot = 0;
     for (int l = 0; l <= top; ++l) {
         long long S = n_of_level[l] + 2;
-        int ncoef = (l == top && top_is_finest) ? 1 : (dim == 2 ? 5 : 14);
+        int ncoef = (l == top && top_is_fd_finest) ? 1 : (dim == 2 ? 5 : 14);
         tot += (2 + ncoef) * (dim == 3 ? S * S * S : S * S);
     }
     // normals of one sweep of the largest grid: 2 per Philox pair
@@ -472,6 +472,20 @@ __device__ __forceinline__ void coarse_body(const DevLevel<T>* __restrict__ leve
         }
     }
     __syncthreads();
+    // the layout must fit the launch's dynamic shared memory: a mismatch between the
+    // host's sizing and this layout is reported (status bit), never run
+    {
+        unsigned dsz;
+        asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsz));
+        const long long nt = lv[top].n;
+        long long need = (long long)blk_off[top] + (long long)nblocks(top) * grid_sz(top) +
+                         4LL * ((nt + 3) / 4) * nt * (DIM == 3 ? nt : 1);
+        if (n0 <= kCoarsestWarp) need += 2LL * n0 * n0 + 2;
+        if (need * (long long)sizeof(T) > (long long)dsz) {
+            if (threadIdx.x == 0) atomicOr(&Pg.cs->status, kStatusLayout);
+            return;
+        }
+    }
     T* base = reinterpret_cast<T*>(smem_raw);
     // block layout per grid: X, F, coefficient slots (in that order)
     auto blk = [&](int l, int which) -> T* { return base + blk_off[l] + which * grid_sz(l); };

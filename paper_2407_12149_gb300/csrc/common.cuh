@@ -36,6 +36,7 @@ struct CycleState {
 
 constexpr int kStatusNumeric = 1;
 constexpr int kStatusTimeout = 2;
+constexpr int kStatusLayout = 4;   // a kernel's shared-memory layout exceeded its launch (not run)
 
 // One grid level on the device.  T = float or double.
 template <typename T>

@@ -50,7 +50,9 @@ constexpr int kCoarseMaxLevels = 8;
 // coarsest grids with at most this many unknowns are solved by one warp from a factor
 // staged in shared memory
 constexpr int kCoarsestWarp = 32;
-long long coarse_smem_elems(int dim, const int* n_of_level, int top, bool top_is_finest);
+// elements of the coarse kernel's dynamic shared memory; top_is_fd_finest: the top
+// grid is the finest grid in its 5/7-point finite-difference form (one operator field)
+long long coarse_smem_elems(int dim, const int* n_of_level, int top, bool top_is_fd_finest);
 template <typename T>
 cudaError_t coarse_prepare(int dim, size_t smem_bytes);
 template <typename T>

@@ -30,6 +30,7 @@ struct HostProblem {
     int n_levels = 1;
     int m = 0;
     int scale_hd = 1;
+    int disc = 0;                     // 0: finite differences on the finest grid, 1: Q1 elements
     double woff_fine = 0.0;           // s / h^2 of the finest grid
     std::vector<double> kappa_part;  // s * kappa^2 at the fine sites
     std::vector<HostLevel> lev;      // 0 = coarsest
@@ -42,7 +43,7 @@ struct HostProblem {
 
 // Returns an empty string on success, otherwise an error message; *code gets
 // the mgmc_status to return.
-std::string build_hierarchy(HostProblem& hp, int dim, int n, int n_levels, int scale_hd, const double* kappa2,
+std::string build_hierarchy(HostProblem& hp, int dim, int n, int n_levels, int scale_hd, int disc, const double* kappa2,
                             double kappa2_const, int m, const int32_t* obs_site, const double* obs_w,
                             int nnz_per_obs, const double* Gamma, const double* y, int* code);
 

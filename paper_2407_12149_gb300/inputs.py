@@ -142,6 +142,7 @@ class Problem:
     qoi_site: Optional[np.ndarray] = None
     qoi_w: Optional[np.ndarray] = None
     scale_hd: int = 1
+    disc: int = 0                         # 0 finite differences, 1 Q1 finite elements (constant kappa^2)
     meta: dict = field(default_factory=dict)
 
     @property
@@ -169,17 +170,25 @@ def levels_for(n: int, coarsest: int = 1) -> int:
 def make_problem(name: str, dim: int, n: int, *, n_levels: Optional[int] = None,
                  coarsest: int = 1, kappa2_seed: Optional[int] = None, kappa2_const: float = 10.0,
                  m: int = 0, obs_seed: int = 1, sigma2: float = 1e-4, qoi_cells: Optional[int] = None,
-                 scale_hd: int = 1) -> Problem:
-    """Assemble a seeded problem.  kappa2_seed=None gives constant kappa^2."""
+                 scale_hd: int = 1, disc: int = 0, gamma_range: Optional[tuple] = None) -> Problem:
+    """Assemble a seeded problem.  kappa2_seed=None gives constant kappa^2.  disc = 1: Q1
+    finite elements (constant kappa^2 only).  gamma_range = (lo, hi): Gamma diagonal with
+    seeded entries uniform in [lo, hi] instead of sigma2 I."""
+    if disc == 1 and kappa2_seed is not None:
+        raise ValueError("the Q1 discretisation takes a constant kappa^2")
     if n_levels is None:
         n_levels = levels_for(n, coarsest)
     k2 = None if kappa2_seed is None else kappa2_field(n, dim, kappa2_seed)
     p = Problem(name=name, dim=dim, n=n, n_levels=n_levels, kappa2=k2, kappa2_const=kappa2_const,
-                scale_hd=scale_hd)
+                scale_hd=scale_hd, disc=disc)
     if m > 0:
         xyz = obs_locations(m, dim, obs_seed)
         p.obs_site, p.obs_w = point_obs_rows(n, dim, xyz)
-        p.Gamma = sigma2 * np.eye(m)
+        if gamma_range is None:
+            p.Gamma = sigma2 * np.eye(m)
+        else:
+            g = np.random.default_rng(1_000_003 + obs_seed).uniform(gamma_range[0], gamma_range[1], m)
+            p.Gamma = np.diag(g)
         p.y = obs_values(m, obs_seed)
         p.meta["obs_xyz"] = xyz
     if qoi_cells is not None:
@@ -198,6 +207,16 @@ def config2(n: int = 1023, n_levels: Optional[int] = None) -> Problem:
     """Bayesian 2D, non-stationary kappa^2, 16 point observations, Gamma = 1e-4 I."""
     return make_problem(f"bayes-2d-{n}", 2, n, n_levels=n_levels, kappa2_seed=2024, m=16, obs_seed=1,
                         qoi_cells=max(2, (46 * (n + 1)) // 1024))
+
+
+def table1a(n: int, n_levels: Optional[int] = None) -> Problem:
+    """The setting of the paper's Table 1a (Sec. 5.1): the Q1 finite-element shifted
+    Laplacian with correlation length kappa^-1 = 0.1, 8 observations whose variances are
+    uniform in [1e-6, 2e-6], observed values in [1, 4]; point observations (bilinear rows)
+    stand in for the paper's ball averages, and the QoI is the central box of about the
+    area of the paper's ball of radius 0.025."""
+    return make_problem(f"table1a-q1-{n}", 2, n, n_levels=n_levels, kappa2_const=100.0, m=8, obs_seed=11,
+                        disc=1, gamma_range=(1e-6, 2e-6), qoi_cells=max(2, (46 * (n + 1)) // 1024))
 
 
 def config3(n: int = 127, n_levels: Optional[int] = None) -> Problem:

@@ -19,6 +19,8 @@ LIB_PATH = os.path.join(HERE, "libmgmc.so")
 
 MGMC_FP64 = 0
 MGMC_FP32 = 1
+MGMC_FD = 0
+MGMC_Q1 = 1
 MGMC_MAX_OBS = 64
 MGMC_NOALLOC_MAX_SERIES = 65536
 
@@ -35,7 +37,7 @@ class MGMCError(RuntimeError):
 class mgmc_config(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("n_levels", ctypes.c_int), ("nu1", ctypes.c_int),
                 ("nu2", ctypes.c_int), ("precision", ctypes.c_int), ("scale_hd", ctypes.c_int),
-                ("coarse_max_n", ctypes.c_int), ("gibbs", ctypes.c_int)]
+                ("coarse_max_n", ctypes.c_int), ("gibbs", ctypes.c_int), ("disc", ctypes.c_int)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -203,9 +205,10 @@ def mgmc_point_obs_rows(dim: int, n: int, xyz: np.ndarray):
 
 def mgmc_create(dim, n, *, n_levels=0, nu1=1, nu2=1, precision=MGMC_FP64, scale_hd=1, coarse_max_n=0,
                 kappa2=None, kappa2_const=10.0, obs_site=None, obs_w=None, Gamma=None, y=None,
-                qoi_site=None, qoi_w=None, allocator: Optional[TorchAllocator] = None, stream=None, gibbs=0):
+                qoi_site=None, qoi_w=None, allocator: Optional[TorchAllocator] = None, stream=None, gibbs=0,
+                disc=MGMC_FD):
     L = load()
-    cfg = mgmc_config(dim, n, n_levels, nu1, nu2, precision, scale_hd, coarse_max_n, gibbs)
+    cfg = mgmc_config(dim, n, n_levels, nu1, nu2, precision, scale_hd, coarse_max_n, gibbs, disc)
     k2 = None if kappa2 is None else np.ascontiguousarray(kappa2, dtype=np.float64).ravel()
     if obs_site is None:
         m, nnz, os_, ow_, G_, y_ = 0, 1, None, None, None, None
@@ -325,7 +328,7 @@ class Sampler:
                              scale_hd=p.scale_hd, coarse_max_n=coarse_max_n, kappa2=p.kappa2,
                              kappa2_const=p.kappa2_const, obs_site=p.obs_site, obs_w=p.obs_w, Gamma=p.Gamma,
                              y=p.y, qoi_site=p.qoi_site, qoi_w=p.qoi_w, allocator=self._alloc,
-                             gibbs=1 if gibbs else 0)
+                             gibbs=1 if gibbs else 0, disc=getattr(p, "disc", MGMC_FD))
 
     def zeros(self):
         torch = _torch()
@@ -396,7 +399,8 @@ class BatchSampler:
         probs = (mgmc_problem * n)()
         self._keep = []
         for c, p in enumerate(self.problems):
-            cfgs[c] = mgmc_config(p.dim, p.n, p.n_levels, 1, 1, self.precision, p.scale_hd, coarse_max_n)
+            cfgs[c] = mgmc_config(p.dim, p.n, p.n_levels, 1, 1, self.precision, p.scale_hd, coarse_max_n, 0,
+                                  p.disc)
             arrs = {}
             arrs["k2"] = None if p.kappa2 is None else np.ascontiguousarray(p.kappa2, dtype=np.float64)
             if p.obs_site is not None:

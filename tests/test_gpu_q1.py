@@ -1,0 +1,145 @@
+"""GPU parity of the Q1 finite-element option (mgmc_config.disc = MGMC_Q1,
+Sec. 5.1.1) against the oracle's Q1 hierarchy: the finest grid then has the
+9/27-point stencil and runs in the Galerkin-grid kernels (fused 2D tiles, the
+single-CTA coarse kernel, the 3D general path)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2407_12149_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    import torch
+    from paper_2407_12149_gb300 import build
+    build.build()
+    return torch
+
+
+def _q1(dim, n, m, kappa2=100.0, seed=2, qoi=None, **kw):
+    return inputs.make_problem("q1", dim, n, kappa2_const=kappa2, m=m, obs_seed=seed, disc=1,
+                               qoi_cells=qoi if qoi is not None else (n + 1) // 4, **kw)
+
+
+def _orc(p):
+    return oracle.Oracle(p.dim, p.n, p.n_levels, kappa2_const=p.kappa2_const, scale_hd=p.scale_hd,
+                         obs_site=p.obs_site, obs_w=p.obs_w, Gamma=p.Gamma, y=p.y, qoi_site=p.qoi_site,
+                         qoi_w=p.qoi_w, disc=1)
+
+
+def _run(torch, s, n_steps, seed):
+    x = s.zeros()
+    q = torch.zeros(n_steps, dtype=torch.float64, device="cuda")
+    s.sample(x, n_steps, seed, qoi=q)
+    torch.cuda.synchronize()
+    return x.double().cpu().numpy(), q.cpu().numpy()
+
+
+@pytest.mark.parametrize("dim,n,m,coarse_max_n", [(2, 63, 8, 0), (2, 127, 8, 7), (2, 255, 8, 31),
+                                                  (3, 15, 8, 0), (3, 31, 12, 3)])
+def test_q1_fp64_parity(torch_mod, dim, n, m, coarse_max_n):
+    from paper_2407_12149_gb300.mgmc import Sampler
+    p = _q1(dim, n, m)
+    xo, qo = _orc(p).sample(12, 5)
+    s = Sampler(p, precision="fp64", coarse_max_n=coarse_max_n)
+    xg, qg = _run(torch_mod, s, 12, 5)
+    s.close()
+    rms = np.sqrt(np.mean(xo ** 2))
+    assert np.all(np.abs(xg - xo) <= 1e-11 * np.maximum(np.abs(xo), rms))
+    assert np.all(np.abs(qg - qo) <= 1e-11 * np.maximum(np.abs(qo), rms))
+
+
+@pytest.mark.parametrize("dim,n,coarse_max_n", [(2, 255, 31), (3, 31, 3)])
+def test_q1_fp32_parity_after_100_cycles(torch_mod, dim, n, coarse_max_n):
+    from paper_2407_12149_gb300.mgmc import Sampler
+    p = _q1(dim, n, 8)
+    xo, qo = _orc(p).sample(100, 9)
+    s = Sampler(p, precision="fp32", coarse_max_n=coarse_max_n)
+    xg, qg = _run(torch_mod, s, 100, 9)
+    s.close()
+    rms = np.sqrt(np.mean(xo ** 2))
+    assert np.abs(xg - xo).max() <= 2e-4 * rms
+    assert np.abs(qg - qo).max() <= 2e-4 * rms
+
+
+@pytest.mark.parametrize("precision,n,levels", [("fp32", 63, None), ("fp32", 31, None), ("fp32", 31, 1),
+                                               ("fp64", 31, 1), ("fp64", 31, None)])
+def test_q1_finest_grid_inside_the_coarse_kernel(torch_mod, precision, n, levels):
+    """Small Q1 chains run whole in the single-CTA kernel (default threshold 63): the
+    9-point finest grid with its five coefficient fields in shared memory; levels = 1 is
+    the exact (Cholesky) sampler of the Q1 posterior."""
+    from paper_2407_12149_gb300.mgmc import Sampler
+    p = _q1(2, n, 6, **({"n_levels": levels} if levels else {}))
+    xo, qo = _orc(p).sample(20, 13)
+    s = Sampler(p, precision=precision)
+    xg, qg = _run(torch_mod, s, 20, 13)
+    s.close()
+    rms = np.sqrt(np.mean(xo ** 2))
+    if precision == "fp64":
+        assert np.all(np.abs(xg - xo) <= 1e-11 * np.maximum(np.abs(xo), rms))
+    else:
+        assert np.abs(xg - xo).max() <= 2e-4 * rms
+        assert np.abs(qg - qo).max() <= 2e-4 * rms
+
+
+@pytest.mark.parametrize("precision,dim,n", [("fp64", 2, 63), ("fp32", 2, 127), ("fp64", 3, 15)])
+def test_q1_gibbs_sampler(torch_mod, precision, dim, n):
+    """The plain Gibbs sampler (Sec. 5.1.3) on the Q1 posterior against the oracle's."""
+    from paper_2407_12149_gb300.mgmc import Sampler
+    p = _q1(dim, n, 6)
+    steps = 15 if precision == "fp64" else 100
+    xo, qo = _orc(p).sample(steps, 17, gibbs=True)
+    s = Sampler(p, precision=precision, gibbs=True)
+    xg, qg = _run(torch_mod, s, steps, 17)
+    s.close()
+    rms = np.sqrt(np.mean(xo ** 2))
+    if precision == "fp64":
+        assert np.all(np.abs(xg - xo) <= 1e-11 * np.maximum(np.abs(xo), rms))
+    else:
+        assert np.abs(xg - xo).max() <= 2e-4 * rms
+
+
+def test_q1_batch_equals_solo_runs(torch_mod):
+    torch = torch_mod
+    from paper_2407_12149_gb300.mgmc import BatchSampler, Sampler
+    ps = [_q1(2, n, 6 + c, seed=10 + c) for c, n in enumerate((63, 127, 255))]
+    b = BatchSampler(ps, precision="fp32")
+    xs = b.zeros()
+    b.sample(xs, 10, 21)
+    for c, p in enumerate(ps):
+        s = Sampler(p, precision="fp32", coarse_max_n=31)
+        x = s.zeros()
+        s.sample(x, 10, 21, chain=c)
+        assert torch.equal(x, xs[c])
+        s.close()
+    b.close()
+
+
+def test_q1_mean_solve_matches_oracle(torch_mod):
+    from paper_2407_12149_gb300.mgmc import Sampler
+    p = _q1(2, 127, 8)
+    # both solves stop on the relative residual; with Gamma = 1e-4 I the posterior
+    # precision is ill-conditioned, so both are driven to 1e-12 before the iterates
+    # are compared at 1e-8
+    xo, _, _ = _orc(p).mean_solve(rtol=1e-12, max_cycles=300)
+    s = Sampler(p)
+    x = s.zeros()
+    _, rr = s.mean_solve(x, rtol=1e-12, max_cycles=300)
+    s.close()
+    assert rr <= 1e-12
+    assert np.abs(x.cpu().numpy() - xo).max() <= 1e-8 * np.abs(xo).max()
+
+
+def test_q1_rejects_variable_kappa_and_mixed_batches(torch_mod):
+    from paper_2407_12149_gb300.mgmc import BatchSampler, MGMCError, Sampler
+    p = inputs.make_problem("v", 2, 31, kappa2_seed=3)
+    p.disc = 1
+    with pytest.raises(MGMCError) as e:
+        Sampler(p)
+    assert e.value.code == 1
+    with pytest.raises(MGMCError) as e:
+        BatchSampler([_q1(2, 63, 4), inputs.make_problem("fd", 2, 63, m=4)])
+    assert e.value.code == 1
