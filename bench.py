@@ -39,8 +39,9 @@ FINE_SWEEP_TRAFFIC_BYTES = None
 # the e2e measurement of a batch runs it as this many batches on their own streams
 E2E_GROUPS = 4
 
-TAU_CALIBRATION = 2000     # default untimed cycles used for tau_int on the device
-CPU_SAMPLE_CYCLES = 12     # bounded oracle sample for the CPU baseline
+TAU_CALIBRATION = 20000    # default untimed cycles per chain used for tau_int on the device
+CPU_SAMPLE_CYCLES = 12     # bounded oracle sample for the CPU baseline (per core)
+ESS_TARGET = 1.0e6         # equal-accuracy comparison: QoI mean with standard error 1e-3 of its sd
 REF_MAX_STEPS = 60         # cap on timed oracle cycles in the reference arm
 
 
@@ -139,21 +140,62 @@ def gpu_id_for_smi(torch, dev):
         return vis.split(",")[dev] if vis else str(dev)
 
 
-def cpu_baseline(problem, tau_ref):
-    """Time the FP64 CPU oracle on the same workload (bounded sample, one core)."""
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def _oracle_chain_seconds(job):
+    """One independent oracle chain of the 1023^2 posterior (a spawned worker): seconds
+    for n_cycles V-cycles after one untimed cycle, set-up excluded."""
+    n_cycles, chain = job
+    sys.path.insert(0, ROOT)
+    from paper_2407_12149_gb300 import inputs
     import oracle
-    o = oracle.Oracle(problem.dim, problem.n, problem.n_levels, kappa2=problem.kappa2, obs_site=problem.obs_site,
-                      obs_w=problem.obs_w, Gamma=problem.Gamma, y=problem.y, qoi_site=problem.qoi_site,
-                      qoi_w=problem.qoi_w)
-    x = o.sample(1, 2024, qoi=False)
+    p = inputs.config2()
+    o = oracle.Oracle(p.dim, p.n, p.n_levels, kappa2=p.kappa2, obs_site=p.obs_site, obs_w=p.obs_w, Gamma=p.Gamma,
+                      y=p.y, qoi_site=p.qoi_site, qoi_w=p.qoi_w)
+    x = o.sample(1, 2024, chain=chain, qoi=False)
     t = time.perf_counter()
-    o.sample(CPU_SAMPLE_CYCLES, 2024, x=x, step_offset=1, qoi=False)
-    dt = time.perf_counter() - t
-    cps = CPU_SAMPLE_CYCLES / dt
-    return {"value": cps / tau_ref, "unit": "QoI ESS/s", "cores": 1, "kind": "oracle",
-            "sample": f"{CPU_SAMPLE_CYCLES} V-cycles of the same 1023^2 problem after 1 untimed cycle, set-up "
-                      f"excluded; {cps:.3f} V-cycles/s divided by the oracle's own tau_int = {tau_ref:.4f} "
-                      f"(oracle/tau_bayes_2d_1023.json)"}
+    o.sample(n_cycles, 2024, x=x, step_offset=1, chain=chain, qoi=False)
+    return time.perf_counter() - t
+
+
+def cpu_baseline(problem, tau_ref):
+    """CPU baseline (oracle), not a target: the FP64 CPU oracle on the same workload,
+    single-threaded, and with one independent chain per host core on all cores
+    (spawned processes; each times its own cycles, set-up excluded; the all-core rate
+    is cores x cycles / the slowest core's time)."""
+    import multiprocessing
+    cores = os.cpu_count() or 1
+    t1 = _oracle_chain_seconds((CPU_SAMPLE_CYCLES, 0))
+    cps1 = CPU_SAMPLE_CYCLES / t1
+    ctx = multiprocessing.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        times = pool.map(_oracle_chain_seconds, [(CPU_SAMPLE_CYCLES, c) for c in range(cores)])
+    cps_all = cores * CPU_SAMPLE_CYCLES / max(times)
+    return {"value": cps_all / tau_ref, "unit": "QoI ESS/s", "cores": cores, "kind": "oracle",
+            "label": "CPU baseline (oracle), not a target", "cpu_model": cpu_model(),
+            "single_core_value": cps1 / tau_ref, "v_cycles_per_s_single_core": cps1,
+            "v_cycles_per_s_all_cores": cps_all,
+            "sample": f"{CPU_SAMPLE_CYCLES} V-cycles of the same 1023^2 problem per chain after 1 untimed cycle, "
+                      f"set-up excluded: one chain on one core ({cps1:.3f} V-cycles/s), then one independent chain "
+                      f"per core on all {cores} cores ({cps_all:.2f} V-cycles/s); divided by the oracle's own "
+                      f"tau_int = {tau_ref:.4f} (oracle/tau_bayes_2d_1023.json)"}
 
 
 def load_tau_ref():
@@ -166,6 +208,7 @@ def load_tau_ref():
 WORKLOADS = {
     "batch32-bayes2d-1023": {"n": 1023, "chains": 32},   # headline: batched FP32 chains of the 1023^2 posterior
     "bayes2d-1023": {"n": 1023, "chains": 1},
+    "bayes2d-1023-fp64": {"n": 1023, "chains": 1, "prec": "fp64"},   # plain FP64 GPU MGMC, first-class line
     "bayes2d-4095": {"n": 4095, "chains": 1},            # HBM-resident single-grid variants (roofline)
     "bayes2d-8191": {"n": 8191, "chains": 1},
     "batch512-mixed": {"n": 511, "chains": 512, "mixed": True},   # 128 chains each of 63^2 .. 511^2
@@ -173,6 +216,7 @@ WORKLOADS = {
     "warmstart-255": {"n": 255, "chains": 64, "warm": True},       # learned warm start (U-Net), 255^2
     "gibbs-vs-mgmc-2d": {"n": 511, "chains": 1, "table": True},   # Table 1 comparison, 31^2 .. 511^2
     "gibbs-vs-mgmc-2d-q1": {"n": 511, "chains": 1, "table": True, "q1": True},   # Table 1a setting (Q1 elements)
+    "convergence-2d": {"n": 255, "chains": 512, "conv": True},   # Sec. 5.3: R, Z, rates, RMSE (Q1, 31^2..255^2)
 }
 
 
@@ -231,6 +275,7 @@ def make_sampler(M, inputs, wl, precision, local):
 
 
 def run_mine(args):
+    import numpy as np
     import torch
     ws, rank, local = dist_env()
     from paper_2407_12149_gb300 import build, inputs
@@ -243,7 +288,8 @@ def run_mine(args):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     wl = WORKLOADS[args.workload]
-    s, ps = make_sampler(M, inputs, wl, "fp32", local)
+    prec = wl.get("prec", "fp32")
+    s, ps = make_sampler(M, inputs, wl, prec, local)
     nch = len(ps)
     batch = nch > 1
     stream = torch.cuda.current_stream()
@@ -272,6 +318,23 @@ def run_mine(args):
     tau = statistics.mean(taus)
     tau_err = (statistics.stdev(taus) / len(taus) ** 0.5) if len(taus) > 1 else errs[0]
     offset = ncal + 100
+    # cold-start burn-in of the calibration chains (all from 0): the first cycle at which the
+    # chains' mean QoI is within one Monte Carlo standard error of F . mu (FP64 mean solve)
+    burn = None
+    fmu = None
+    if not wl.get("mixed"):
+        p0 = single_problem(inputs, wl)
+        sm = M.Sampler(p0, precision="fp64", device=local)
+        xm = sm.zeros()
+        sm.mean_solve(xm, rtol=1e-12, max_cycles=300)
+        fmu = float(np.dot(p0.qoi_w, xm.cpu().numpy()[p0.qoi_site]))
+        sm.close()
+        qm = qcal.view(nch, ncal + 100).cpu().numpy()
+        sd = float(np.sqrt(np.mean(qm[:, 100:].var(axis=1))))
+        se = sd / np.sqrt(nch)
+        trace = qm.mean(axis=0)
+        hit = np.nonzero(np.abs(trace - fmu) <= se)[0]
+        burn = int(hit[0]) if hit.size else None
 
     # --- CPU baseline (rank 0, one GPU only), before the GPU timing ------------
     cpu = None
@@ -317,6 +380,11 @@ def run_mine(args):
     value = cps / tau
 
     # --- end-to-end through the public API with pinned host buffers -----------
+    # every step: each chain's state host -> device, one V-cycle, device -> host, and the
+    # QoI to the host, all inside the library call (mgmc_sample / mgmc_sample_batch with
+    # host buffers, which synchronise).  A batch runs as E2E_GROUPS batch handles, each on
+    # its own stream and driven from its own host thread, so that one group's copies
+    # overlap the others' cycles; each group has its own seed (independent Philox streams)
     M.mgmc_set_profiling(s.h, False)
     for c, x in enumerate(xs):                      # the chains' current states
         if batch:
@@ -324,64 +392,85 @@ def run_mine(args):
         else:
             s.get_state(x)
     xh = [x.cpu().pin_memory() for x in xs]
-    qh = torch.zeros(nch, dtype=torch.float64).pin_memory()
-    # batch: the chains run as E2E_GROUPS batches, each on its own stream with its states in
-    # one contiguous buffer per side (the per-chain tensors handed to the API are views of
-    # it), so that one group's host copies overlap the other groups' cycles; each group
-    # has its own seed (independent Philox streams)
     groups = []
     if batch:
         ng = E2E_GROUPS if nch % E2E_GROUPS == 0 and nch >= 2 * E2E_GROUPS else 1
         gsz = nch // ng
         for g in range(ng):
             part = ps[g * gsz:(g + 1) * gsz]
-            sg = s if ng == 1 else M.BatchSampler(part, precision="fp32", device=local)
-            flat_dev = torch.cat([x.view(-1) for x in xs[g * gsz:(g + 1) * gsz]])
-            groups.append({
-                "s": sg, "stream": torch.cuda.Stream(device=dev) if ng > 1 else stream,
-                "dev": flat_dev, "views": list(torch.split(flat_dev, [p.N for p in part])),
-                "host": flat_dev.cpu().pin_memory(), "q": torch.zeros(gsz, dtype=torch.float64, device=dev),
-                "qh": qh[g * gsz:(g + 1) * gsz], "seed": seed + (104729 * g if ng > 1 else 0)})
+            sg = s if ng == 1 else M.BatchSampler(part, precision=prec, device=local)
+            groups.append({"s": sg, "stream": torch.cuda.Stream(device=dev) if ng > 1 else stream,
+                           "host": xh[g * gsz:(g + 1) * gsz],
+                           "qh": torch.zeros(gsz, dtype=torch.float64).pin_memory(),
+                           "seed": seed + (104729 * g if ng > 1 else 0)})
+    qh1 = torch.zeros(1, dtype=torch.float64).pin_memory()
     n_e2e = max(3, min(args.steps, 100))
     for G in groups:          # untimed first call of each group handle (graph capture)
-        if G["s"] is not s:
-            G["s"].sample(G["views"], 1, G["seed"], step_offset=offset, qoi=G["q"])
+        G["s"].sample(G["host"], 1, G["seed"], step_offset=offset, qoi=G["qh"], stream=G["stream"])
     offset += 1
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+
+    def drive(G, first):
+        for k in range(n_e2e):
+            G["s"].sample(G["host"], 1, G["seed"], step_offset=first + k, qoi=G["qh"], stream=G["stream"])
+
     t0 = time.perf_counter()
-    for k in range(n_e2e):
-        if batch:
-            for G in groups:
-                with torch.cuda.stream(G["stream"]):
-                    G["dev"].copy_(G["host"], non_blocking=True)       # H2D of the group's states
-                    G["s"].sample(G["views"], 1, G["seed"], step_offset=offset, qoi=G["q"], stream=G["stream"])
-                    G["host"].copy_(G["dev"], non_blocking=True)       # D2H of the new states
-                    G["qh"].copy_(G["q"], non_blocking=True)
-            torch.cuda.synchronize()
-        else:
-            s.sample(xh[0], 1, seed, step_offset=offset, chain=chain_id, qoi=qh[:1])   # host buffers: H2D, cycle, D2H
-        offset += 1
+    if batch:
+        import threading
+        th = [threading.Thread(target=drive, args=(G, offset)) for G in groups]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+    else:
+        for k in range(n_e2e):
+            s.sample(xh[0], 1, seed, step_offset=offset + k, chain=chain_id, qoi=qh1)
     e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
+    offset += n_e2e
     e2e_value = job_throughput(ws, nch * n_e2e, e2e_s) / tau
 
-    # --- plain FP64 single-chain GPU MGMC on the same posterior (comparison) ---
+    # --- plain FP64 single-chain GPU MGMC on the same posterior, the same protocol ---
     plain = None
-    if rank == 0 and not wl.get("mixed") and wl["n"] <= 1023:
+    if rank == 0 and not wl.get("mixed") and wl["n"] <= 1023 and wl.get("dim", 2) == 2 and prec == "fp32":
         s64 = M.Sampler(single_problem(inputs, wl), precision="fp64", device=local)
         x64 = s64.zeros()
-        s64.sample(x64, 20, 99)
+        q64 = torch.zeros(ncal + 100, dtype=torch.float64, device=dev)
+        s64.sample(x64, ncal + 100, seed + 1, qoi=q64)                 # its own tau, from 0
+        st64 = M.mgmc_qoi_stats(q64.data_ptr(), ncal + 100, 100, 1.5)
+        off64 = ncal + 100
+        for w in range(args.warmup):
+            flush.fill_(float(w))
+            s64.sample(None, 1, seed + 1, step_offset=off64)
+            off64 += 1
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        s64.sample(x64, 200, 99, step_offset=20)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        cps64 = 200 / (e0.elapsed_time(e1) / 1e3)
-        plain = {"v_cycles_per_s": cps64, "ess_per_s": cps64 / tau,
-                 "note": "plain FP64 GPU MGMC, one chain, same posterior, 200 back-to-back cycles (L2-warm); "
-                         "same law as the measured chains, so the same tau_int"}
+        ms64 = []
+        for k in range(min(args.steps, 200)):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s64.sample(None, 1, seed + 1, step_offset=off64)
+            e1.record(stream)
+            off64 += 1
+            torch.cuda.synchronize()
+            ms64.append(e0.elapsed_time(e1))
+        cps64 = 1e3 / statistics.mean(ms64)
+        tau64 = st64["tau_int"]
+        plain = {"v_cycles_per_s": cps64, "ess_per_s": cps64 / tau64, "tau_int": tau64, "tau_err": st64["tau_err"],
+                 "tau_cycles": ncal, "ms_per_step": statistics.mean(ms64),
+                 "note": "plain FP64 GPU MGMC, one chain, same posterior, the same protocol as the headline "
+                         "(state resident, 256 MB L2 flush between steps, CUDA events); its own tau_int from a "
+                         f"{ncal}-cycle chain"}
+        if burn is not None:
+            # equal accuracy: the QoI mean to a standard error of 1e-3 of its sd needs ESS_TARGET
+            # effective samples; wall time including the cold-start burn-in (the same burn-in for
+            # both: the same law from the same start)
+            t_plain = (burn + ESS_TARGET * tau64) / cps64
+            t_batch = (burn + ESS_TARGET * tau / nch) * (total_ms / args.steps) / 1e3
+            plain["equal_accuracy"] = {"target_ess": ESS_TARGET, "burn_in_cycles": burn,
+                                       "seconds_plain_fp64": t_plain, "seconds_batched_fp32": t_batch,
+                                       "multiple": t_plain / t_batch}
         s64.close()
 
     if rank != 0:
@@ -403,6 +492,10 @@ def run_mine(args):
         # coarse site = 1 B per fine site); the noise is generated, never stored
         sweep_bytes = 13 * fine_sites
         kernel = "k_stream_fwd: finest-grid forward Gibbs sweep + residual + restriction, all chains"
+        if prec == "fp64":
+            # FP64: read theta and a_ii (8 + 8 B/site), write theta*_s (8) and the restricted residual (2)
+            sweep_bytes = 26 * fine_sites
+            kernel = "k_tile_batch<double,1,0>: finest-grid forward Gibbs sweep + residual + restriction (FP64)"
     achieved = sweep_bytes / (fwd_avg * 1e-3) / 1e9
     if wl.get("dim") == 3:
         desc = (f"{ps[0].n}^3 Bayesian posterior: kappa^2 = 25, 32 point obs, Gamma = 1e-4 I, "
@@ -415,18 +508,21 @@ def run_mine(args):
     line = {
         "metric": "QoI ESS/s", "value": value, "unit": "QoI ESS/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: {desc}; FP32 sweeps, FP64 low-rank/coarsest/QoI",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {desc}; " + ("FP32 sweeps, FP64 low-rank/coarsest/QoI"
+                                                                if prec == "fp32" else "FP64 throughout (plain MGMC)"),
                    "chains_per_gpu": nch, "sites_per_gpu": sites,
                    "v_cycles_per_s": cps, "site_updates_per_s": cps * sites / nch * 2,
-                   "tau_int": tau, "tau_err": tau_err,
+                   "tau_int": tau, "tau_err": tau_err, "burn_in_cycles_from_0": burn, "qoi_posterior_mean": fmu,
                    "tau_from": f"device Wolff estimates of {nch} untimed {ncal}-cycle chains (mean)",
                    "l2": "256 MB buffer written between timed steps",
                    "step": "one V-cycle of every chain, states resident on the device (mgmc_sample[_batch] "
                            "with x = NULL); e2e copies them in and out through host memory every step",
                    "parallelism": "replicas" if ws > 1 else "single GPU",
                    "launches_per_cycle": launches,
-                   "plain_fp64_single_chain": plain},
+                   "plain_fp64_single_chain": plain,
+                   "burn_in_rule": "first cycle at which the mean QoI of the chains (all from 0) is within one "
+                                   "Monte Carlo standard error of F . mu from the FP64 mean solve"},
         "roofline": {"bound": "hbm",
                      "kernel": kernel,
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -435,11 +531,12 @@ def run_mine(args):
                      "algorithmic_bytes": sweep_bytes, "avg_ms": fwd_avg,
                      "bwd_sweep_avg_ms": statistics.mean(bwd_ms)},
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": "QoI ESS/s", "h2d_bytes_per_step": 4 * sites,
-                "d2h_bytes_per_step": 4 * sites + 8 * nch,
-                "note": (f"{len(groups)} batches of {nch // max(len(groups), 1)} chains on their own streams, "
-                         "host copies of one overlapping the others' cycles") if batch else
-                        "mgmc_sample with host buffers (copies inside the call)"},
+        "e2e": {"value": e2e_value, "unit": "QoI ESS/s", "h2d_bytes_per_step": (4 if prec == "fp32" else 8) * sites,
+                "d2h_bytes_per_step": (4 if prec == "fp32" else 8) * sites + 8 * nch,
+                "note": (f"mgmc_sample_batch with pinned host buffers (copies inside the call, one per chain and "
+                         f"direction): {len(groups)} batch handles of {nch // max(len(groups), 1)} chains, each on "
+                         "its own stream and host thread") if batch else
+                        "mgmc_sample with pinned host buffers (copies inside the call)"},
         "gpu_launches": args.steps * (launches + 1),
         "clocks": clk,
     }
@@ -670,6 +767,89 @@ def run_gibbs_table(args):
     print(json.dumps(line), flush=True)
 
 
+def run_convergence(args):
+    """The experiments of Sec. 5.3 on the Table 1a posterior (Q1 elements, kappa^-1 = 0.1,
+    8 point observations), FP32: many independent chains from theta^(0) = 0 -- MGMC as
+    batches of 512 chains (one seed per batch: independent Philox streams), the plain
+    Gibbs sampler one chain per call -- give R^(m), Z^(m) over the first 16 steps and
+    the rates rho, zeta (Sec. 5.3.1), and 100 chains per sampler the RMSE Delta^(M) of
+    the running QoI mean (Sec. 5.3.3).  Exact mu_L, sigma_L^2 by a sparse direct solve."""
+    import numpy as np
+    import torch
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    from paper_2407_12149_gb300 import build, experiments as E, inputs
+    from paper_2407_12149_gb300 import mgmc as M
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    clocks = ClockSampler(gpu_id_for_smi(torch, local))
+    steps, B = 16, 512
+    n_batches = max(1, args.conv_chains // B)
+    M_values = [2 ** k for k in range(13)]          # 1 .. 4096
+    rows = []
+    t_start = time.perf_counter()
+    for n in (31, 63, 127, 255):
+        p = inputs.table1a(n)
+        mu, s2 = E.exact_qoi_moments(p)
+        # MGMC: batches of B chains, each batch its own seed
+        bs = M.BatchSampler([p] * B, precision="fp32", device=local)
+        z = []
+        for k in range(n_batches):
+            xs = bs.zeros()
+            q = torch.zeros(B * steps, dtype=torch.float64, device=dev)
+            bs.sample(xs, steps, 1000 + k, qoi=q)
+            z.append(q.view(B, steps).cpu().numpy())
+        zm = np.concatenate(z)
+        zm = np.concatenate([np.zeros((zm.shape[0], 1)), zm], axis=1)     # step 0: F . 0
+        # RMSE: 100 MGMC chains of 4096 steps from 0
+        b100 = M.BatchSampler([p] * 100, precision="fp32", device=local)
+        q = torch.zeros(100 * 4096, dtype=torch.float64, device=dev)
+        b100.sample(b100.zeros(), 4096, 7, qoi=q)
+        zr_m = np.concatenate([np.zeros((100, 1)), q.view(100, 4096).cpu().numpy()[:, :-1]], axis=1)
+        b100.close()
+        bs.close()
+        # Gibbs: one chain per call (batches run the V-cycle only)
+        sg = M.Sampler(p, precision="fp32", gibbs=True, device=local)
+        ng = args.conv_gibbs_chains
+        qg = torch.zeros(ng * steps, dtype=torch.float64, device=dev)
+        for c in range(ng):
+            sg.sample(sg.zeros(), steps, 2000 + c // 65536, chain=c % 65536, qoi=qg[c * steps:(c + 1) * steps])
+        zg = np.concatenate([np.zeros((ng, 1)), qg.view(ng, steps).cpu().numpy()], axis=1)
+        qr = torch.zeros(100 * 4096, dtype=torch.float64, device=dev)
+        for c in range(100):
+            sg.sample(sg.zeros(), 4096, 3000, chain=c, qoi=qr[c * 4096:(c + 1) * 4096])
+        zr_g = np.concatenate([np.zeros((100, 1)), qr.view(100, 4096).cpu().numpy()[:, :-1]], axis=1)
+        sg.close()
+        row = {"n": n, "mu_L": mu, "sigma2_L": s2, "chains_mgmc": zm.shape[0], "chains_gibbs": ng}
+        for name, zz in (("mgmc", zm), ("gibbs", zg)):
+            r = E.convergence_ratios(zz, mu, s2)
+            rho, mr = E.rate(r["R"], r["R_err"])
+            zeta, mz = E.rate(r["Z"], r["Z_err"])
+            row[name] = {"R": r["R"].tolist(), "R_err": r["R_err"].tolist(), "Z": r["Z"].tolist(),
+                         "Z_err": r["Z_err"].tolist(), "rho": rho, "m_star_rho": mr, "zeta": zeta, "m_star_zeta": mz}
+        row["rmse_M"] = M_values
+        row["rmse_mgmc"] = E.rmse(zr_m, mu, M_values).tolist()
+        row["rmse_gibbs"] = E.rmse(zr_g, mu, M_values).tolist()
+        rows.append(row)
+    clk = clocks.stop()
+    line = {
+        "metric": "MGMC convergence rate of the QoI mean (rho, 127^2)", "value": rows[2]["mgmc"]["rho"], "unit": "1",
+        "n_gpus": 1, "steps": steps, "warmup": 0, "ms_per_step": None, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "convergence-2d: Sec. 5.3 on the Table 1a posterior (Q1, kappa^-1 = 0.1, 8 point obs, "
+                               "Gamma diagonal in [1e-6, 2e-6]), 31^2 .. 255^2; MGMC chains in batches of 512 "
+                               f"({n_batches} seeds), Gibbs one chain per call; all chains from theta^(0) = 0",
+                   "table": rows, "wall_s": time.perf_counter() - t_start,
+                   "estimators": "R, Z of Eq. convergence_rate_definition with sample mean / variance over the "
+                                 "chains; rho, zeta at the last step whose statistical error is <= 10 %; RMSE of "
+                                 "the running mean of the first M QoI values (steps 0 .. M-1) over 100 chains"},
+        "roofline": None, "cpu_baseline": None, "e2e": None, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -684,6 +864,8 @@ def main():
     ap.add_argument("--warm-train", type=int, default=512, help="warmstart-255: training problems")
     ap.add_argument("--warm-epochs", type=int, default=20, help="warmstart-255: training epochs")
     ap.add_argument("--warm-cycles", type=int, default=40, help="warmstart-255: chain length of the burn-in test")
+    ap.add_argument("--conv-chains", type=int, default=16384, help="convergence-2d: MGMC chains per grid")
+    ap.add_argument("--conv-gibbs-chains", type=int, default=2048, help="convergence-2d: Gibbs chains per grid")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -694,6 +876,8 @@ def main():
         run_warmstart(args)
     elif WORKLOADS[args.workload].get("table"):
         run_gibbs_table(args)
+    elif WORKLOADS[args.workload].get("conv"):
+        run_convergence(args)
     else:
         run_mine(args)
 

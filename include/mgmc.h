@@ -188,6 +188,14 @@ mgmc_status mgmc_qoi_stats(const double* qoi, int64_t n, int64_t burn_in, double
 mgmc_status mgmc_qoi_stats_noalloc(const double* qoi, int64_t n, int64_t burn_in, double S, mgmc_stats* out,
                                    void* stream);
 
+/* The finest grid's operator A_L (without the observation term) exactly as
+ * mgmc_create assembles it from cfg->dim, n, scale_hd and disc (Sec. 2.3 /
+ * 5.1.1): out = host [n^dim * 3^dim], the coupling of site s to site s + o at
+ * out[s * 3^dim + o], offset o = (dx+1) + 3 (dy+1) [+ 9 (dz+1)], 0 where the
+ * neighbour is a boundary vertex.  kappa2: host [n^dim] or NULL (kappa2_const).
+ * Host only: needs no device.  MGMC_ERR_ARG for bad sizes or values. */
+mgmc_status mgmc_fine_operator(const mgmc_config* cfg, const double* kappa2, double kappa2_const, double* out);
+
 /* Number of grids, unknowns per axis of grid l (0 = coarsest) and the
  * precision of a handle. */
 mgmc_status mgmc_info(mgmc_handle h, int* n_levels, int* precision, int* dim);

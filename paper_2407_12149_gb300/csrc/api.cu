@@ -755,6 +755,35 @@ mgmc_status mgmc_create(const mgmc_config* cfg_in, const mgmc_allocator* alloc, 
     return MGMC_OK;
 }
 
+mgmc_status mgmc_fine_operator(const mgmc_config* cfg, const double* kappa2, double kappa2_const, double* out)
+{
+    if (!cfg || !out || (cfg->dim != 2 && cfg->dim != 3) || cfg->n < 1)
+        return fail(MGMC_ERR_ARG, "mgmc_fine_operator: bad arguments");
+    {
+        int k = cfg->n + 1;
+        while (k % 2 == 0) k /= 2;
+        if (k != 1) return fail(MGMC_ERR_ARG, "n must be 2^k - 1");
+    }
+    HostProblem hp;
+    hp.dim = cfg->dim;
+    hp.NS = cfg->dim == 2 ? 9 : 27;
+    hp.C = (hp.NS - 1) / 2;
+    hp.n_levels = 1;
+    hp.scale_hd = cfg->scale_hd;
+    hp.disc = cfg->disc;
+    hp.lev.assign(1, HostLevel());
+    hp.lev[0].n = cfg->n;
+    hp.lev[0].N = cfg->dim == 2 ? (long long)cfg->n * cfg->n : (long long)cfg->n * cfg->n * cfg->n;
+    if (cfg->disc != 0 && cfg->disc != 1) return fail(MGMC_ERR_ARG, "disc must be MGMC_FD or MGMC_Q1");
+    if (cfg->disc == 1 && kappa2)
+        return fail(MGMC_ERR_ARG, "the Q1 discretisation takes a constant kappa^2 (kappa2 = NULL)");
+    std::string err = fine_operator(hp, cfg->dim, cfg->n, cfg->scale_hd, cfg->disc, kappa2, kappa2_const);
+    if (!err.empty()) return fail(MGMC_ERR_ARG, err);
+    const std::vector<double>& st = hp.lev[0].st;
+    std::memcpy(out, st.data(), st.size() * sizeof(double));
+    return MGMC_OK;
+}
+
 mgmc_status mgmc_info(mgmc_handle h, int* n_levels, int* precision, int* dim)
 {
     if (!h) return fail(MGMC_ERR_ARG, "handle is NULL");

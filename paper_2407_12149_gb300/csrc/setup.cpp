@@ -358,6 +358,65 @@ std::vector<double> row_sums(const HostProblem& hp, int l)
     return out;
 }
 
+// The finest grid's operator into hp.lev[top].st (and, finite differences, the
+// s kappa^2 part and s / h^2 of the FP32 form); empty string on success.
+std::string fine_operator(HostProblem& hp, int dim, int n, int scale_hd, int disc, const double* kappa2,
+                          double kappa2_const)
+{
+    HostLevel& Fl = hp.lev[hp.n_levels - 1];
+    Grid gf{dim, n};
+    const double h = 1.0 / (double)(n + 1);
+    double scale = 1.0;
+    if (scale_hd)
+        for (int a = 0; a < dim; ++a) scale *= h;
+    const double inv_h2 = 1.0 / (h * h);
+    hp.woff_fine = scale * inv_h2;
+    Fl.st.assign((size_t)Fl.N * hp.NS, 0.0);
+    hp.kappa_part.assign((size_t)Fl.N, 0.0);
+    // Q1 elements: per offset o the 1D integrals of hat functions, one derivative pair per
+    // axis -- stiffness (2, -1) / h, mass (4, 1) h / 6 for |o_t| = 0, 1 -- multiplied out
+    std::vector<double> q1(hp.NS, 0.0);
+    if (disc == 1) {
+        if (!std::isfinite(kappa2_const) || kappa2_const < 0.0) return "kappa^2 must be finite and non-negative";
+        double hd = 1.0;
+        for (int a = 0; a < dim; ++a) hd *= h;
+        const double q1scale = scale_hd ? 1.0 : 1.0 / hd;   // literal scaling: the FE matrix divided by h^d
+        for (int o = 0; o < hp.NS; ++o) {
+            const int off[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
+            double stiff = 0.0, mass = 1.0;
+            for (int ax = 0; ax < dim; ++ax) {
+                double tk = off[ax] == 0 ? 2.0 / h : -1.0 / h;
+                for (int t = 0; t < dim; ++t)
+                    if (t != ax) tk *= off[t] == 0 ? 4.0 * h / 6.0 : h / 6.0;
+                stiff += tk;
+                mass *= off[ax] == 0 ? 4.0 * h / 6.0 : h / 6.0;
+            }
+            q1[(size_t)o] = q1scale * (stiff + kappa2_const * mass);
+        }
+    }
+    for (long long s = 0; s < Fl.N; ++s) {
+        double k2 = kappa2 ? kappa2[s] : kappa2_const;
+        if (!std::isfinite(k2) || k2 < 0.0) return "kappa^2 must be finite and non-negative";
+        int i, j, k;
+        gf.coords(s, i, j, k);
+        double* a = &Fl.st[(size_t)s * hp.NS];
+        if (disc == 1) {
+            for (int o = 0; o < hp.NS; ++o) {
+                const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
+                if (gf.inside(i + ox, j + oy, dim == 3 ? k + oz : k)) a[o] = q1[(size_t)o];
+            }
+            continue;
+        }
+        a[hp.C] = scale * (k2 + 2.0 * dim * inv_h2);
+        hp.kappa_part[(size_t)s] = scale * k2;
+        const int dd[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
+        for (int t = 0; t < 2 * dim; ++t)
+            if (gf.inside(i + dd[t][0], j + dd[t][1], k + dd[t][2]))
+                a[oidx(dim, dd[t][0], dd[t][1], dd[t][2])] = -scale * inv_h2;
+    }
+    return std::string();
+}
+
 std::string build_hierarchy(HostProblem& hp, int dim, int n, int n_levels, int scale_hd, int disc, const double* kappa2,
                             double kappa2_const, int m, const int32_t* obs_site, const double* obs_w,
                             int nnz_per_obs, const double* Gamma, const double* y, int* code)
@@ -415,54 +474,9 @@ std::string build_hierarchy(HostProblem& hp, int dim, int n, int n_levels, int s
         hp.y.assign(y, y + m);
     }
     // finest operator
-    const double h = 1.0 / (double)(n + 1);
-    double scale = 1.0;
-    if (scale_hd)
-        for (int a = 0; a < dim; ++a) scale *= h;
-    const double inv_h2 = 1.0 / (h * h);
-    hp.woff_fine = scale * inv_h2;
-    Fl.st.assign((size_t)Fl.N * hp.NS, 0.0);
-    hp.kappa_part.assign((size_t)Fl.N, 0.0);
-    // Q1 elements: per offset o the 1D integrals of hat functions, one derivative pair per
-    // axis -- stiffness (2, -1) / h, mass (4, 1) h / 6 for |o_t| = 0, 1 -- multiplied out
-    std::vector<double> q1(hp.NS, 0.0);
-    if (disc == 1) {
-        if (!std::isfinite(kappa2_const) || kappa2_const < 0.0) return "kappa^2 must be finite and non-negative";
-        double hd = 1.0;
-        for (int a = 0; a < dim; ++a) hd *= h;
-        const double q1scale = scale_hd ? 1.0 : 1.0 / hd;   // literal scaling: the FE matrix divided by h^d
-        for (int o = 0; o < hp.NS; ++o) {
-            const int off[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
-            double stiff = 0.0, mass = 1.0;
-            for (int ax = 0; ax < dim; ++ax) {
-                double tk = off[ax] == 0 ? 2.0 / h : -1.0 / h;
-                for (int t = 0; t < dim; ++t)
-                    if (t != ax) tk *= off[t] == 0 ? 4.0 * h / 6.0 : h / 6.0;
-                stiff += tk;
-                mass *= off[ax] == 0 ? 4.0 * h / 6.0 : h / 6.0;
-            }
-            q1[(size_t)o] = q1scale * (stiff + kappa2_const * mass);
-        }
-    }
-    for (long long s = 0; s < Fl.N; ++s) {
-        double k2 = kappa2 ? kappa2[s] : kappa2_const;
-        if (!std::isfinite(k2) || k2 < 0.0) return "kappa^2 must be finite and non-negative";
-        int i, j, k;
-        gf.coords(s, i, j, k);
-        double* a = &Fl.st[(size_t)s * hp.NS];
-        if (disc == 1) {
-            for (int o = 0; o < hp.NS; ++o) {
-                const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
-                if (gf.inside(i + ox, j + oy, dim == 3 ? k + oz : k)) a[o] = q1[(size_t)o];
-            }
-            continue;
-        }
-        a[hp.C] = scale * (k2 + 2.0 * dim * inv_h2);
-        hp.kappa_part[(size_t)s] = scale * k2;
-        const int dd[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
-        for (int t = 0; t < 2 * dim; ++t)
-            if (gf.inside(i + dd[t][0], j + dd[t][1], k + dd[t][2]))
-                a[oidx(dim, dd[t][0], dd[t][1], dd[t][2])] = -scale * inv_h2;
+    {
+        std::string e = fine_operator(hp, dim, n, scale_hd, disc, kappa2, kappa2_const);
+        if (!e.empty()) return e;
     }
     // fine B from the caller's rows
     Fl.bptr.assign(m + 1, 0);

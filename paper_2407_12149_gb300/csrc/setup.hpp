@@ -47,6 +47,11 @@ std::string build_hierarchy(HostProblem& hp, int dim, int n, int n_levels, int s
                             double kappa2_const, int m, const int32_t* obs_site, const double* obs_w,
                             int nnz_per_obs, const double* Gamma, const double* y, int* code);
 
+// The finest grid's operator alone: hp.dim, NS, C, n_levels and lev[] must be set
+// (build_hierarchy does this); fills lev[n_levels - 1].st.
+std::string fine_operator(HostProblem& hp, int dim, int n, int scale_hd, int disc, const double* kappa2,
+                          double kappa2_const);
+
 // H = P^T A_l G_l(forward) and B_l^T G_l(forward) for level l >= 1.
 void fused_extras(HostLevel& L, const HostProblem& hp, int l);
 

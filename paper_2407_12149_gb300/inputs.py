@@ -93,6 +93,50 @@ def point_obs_rows(n: int, dim: int, xyz: np.ndarray):
     return site, wts
 
 
+def ball_rows(n: int, dim: int, centres: np.ndarray, radius: float, sub: int = 8):
+    """Rows of B for averages of the field over balls (Sec. 5.1.2, Eq. observations):
+    (1/|B|) int_B phi_i dx for the multilinear hat functions phi_i of the interior
+    vertices, by the midpoint rule on a sub-grid of spacing h / sub, normalised by the
+    rule's own area inside the ball so that constants are averaged exactly (points
+    outside the domain count: the field is 0 there).  Returns (site int32 [m, nnz],
+    weight float64 [m, nnz]); rows are padded with site -1, weight 0."""
+    centres = np.atleast_2d(np.asarray(centres, dtype=np.float64))
+    h = 1.0 / (n + 1)
+    d = h / sub
+    rows = []
+    for c in centres:
+        lo = np.floor((c - radius) / d).astype(int)
+        hi = np.ceil((c + radius) / d).astype(int)
+        axes = [(np.arange(lo[a], hi[a]) + 0.5) * d for a in range(dim)]
+        pts = np.stack(np.meshgrid(*axes, indexing="ij"), axis=-1).reshape(-1, dim)
+        pts = pts[np.sum((pts - c) ** 2, axis=1) <= radius ** 2]
+        npts = len(pts)
+        pts = pts[np.all((pts > 0.0) & (pts < 1.0), axis=1)]
+        acc = {}
+        for q in pts:
+            cell = np.floor(q / h).astype(np.int64)
+            t = q / h - cell
+            for corner in range(1 << dim):
+                w, idx, ok = 1.0, 0, True
+                for a in range(dim):
+                    up = (corner >> a) & 1
+                    w *= t[a] if up else 1.0 - t[a]
+                    v = cell[a] + up - 1          # interior index of the vertex
+                    ok = ok and 0 <= v < n
+                    idx += v * n ** a
+                if ok and w > 0.0:
+                    acc[idx] = acc.get(idx, 0.0) + w
+        rows.append({i: w / npts for i, w in acc.items()})
+    nnz = max(1, max(len(r) for r in rows))
+    site = np.full((len(rows), nnz), -1, dtype=np.int32)
+    wts = np.zeros((len(rows), nnz), dtype=np.float64)
+    for k, acc in enumerate(rows):
+        for t, (i, w) in enumerate(sorted(acc.items())):
+            site[k, t] = i
+            wts[k, t] = w
+    return site, wts
+
+
 def qoi_box(n: int, dim: int, c0: int, c1: int):
     """F_L for the average of the multilinear interpolant over the box
     [c0 h, c1 h]^dim (c0 < c1 are vertex indices of grid lines).
@@ -170,10 +214,13 @@ def levels_for(n: int, coarsest: int = 1) -> int:
 def make_problem(name: str, dim: int, n: int, *, n_levels: Optional[int] = None,
                  coarsest: int = 1, kappa2_seed: Optional[int] = None, kappa2_const: float = 10.0,
                  m: int = 0, obs_seed: int = 1, sigma2: float = 1e-4, qoi_cells: Optional[int] = None,
-                 scale_hd: int = 1, disc: int = 0, gamma_range: Optional[tuple] = None) -> Problem:
+                 scale_hd: int = 1, disc: int = 0, gamma_range: Optional[tuple] = None,
+                 ball_radius: Optional[float] = None) -> Problem:
     """Assemble a seeded problem.  kappa2_seed=None gives constant kappa^2.  disc = 1: Q1
     finite elements (constant kappa^2 only).  gamma_range = (lo, hi): Gamma diagonal with
-    seeded entries uniform in [lo, hi] instead of sigma2 I."""
+    seeded entries uniform in [lo, hi] instead of sigma2 I.  ball_radius: observations
+    and QoI are averages over balls of that radius (the QoI centred in the domain)
+    instead of point values and the central box."""
     if disc == 1 and kappa2_seed is not None:
         raise ValueError("the Q1 discretisation takes a constant kappa^2")
     if n_levels is None:
@@ -183,7 +230,10 @@ def make_problem(name: str, dim: int, n: int, *, n_levels: Optional[int] = None,
                 scale_hd=scale_hd, disc=disc)
     if m > 0:
         xyz = obs_locations(m, dim, obs_seed)
-        p.obs_site, p.obs_w = point_obs_rows(n, dim, xyz)
+        if ball_radius is None:
+            p.obs_site, p.obs_w = point_obs_rows(n, dim, xyz)
+        else:
+            p.obs_site, p.obs_w = ball_rows(n, dim, xyz, ball_radius)
         if gamma_range is None:
             p.Gamma = sigma2 * np.eye(m)
         else:
@@ -191,7 +241,12 @@ def make_problem(name: str, dim: int, n: int, *, n_levels: Optional[int] = None,
             p.Gamma = np.diag(g)
         p.y = obs_values(m, obs_seed)
         p.meta["obs_xyz"] = xyz
-    if qoi_cells is not None:
+    if ball_radius is not None:
+        qs, qw = ball_rows(n, dim, np.full((1, dim), 0.5), ball_radius)
+        keep = qs[0] >= 0
+        p.qoi_site, p.qoi_w = qs[0][keep], qw[0][keep]
+        p.meta["qoi_ball"] = ball_radius
+    elif qoi_cells is not None:
         c0, c1 = central_box(n, qoi_cells)
         p.qoi_site, p.qoi_w = qoi_box(n, dim, c0, c1)
         p.meta["qoi_box"] = (c0, c1)
@@ -212,11 +267,12 @@ def config2(n: int = 1023, n_levels: Optional[int] = None) -> Problem:
 def table1a(n: int, n_levels: Optional[int] = None) -> Problem:
     """The setting of the paper's Table 1a (Sec. 5.1): the Q1 finite-element shifted
     Laplacian with correlation length kappa^-1 = 0.1, 8 observations whose variances are
-    uniform in [1e-6, 2e-6], observed values in [1, 4]; point observations (bilinear rows)
-    stand in for the paper's ball averages, and the QoI is the central box of about the
-    area of the paper's ball of radius 0.025."""
+    uniform in [1e-6, 2e-6], observed values in [1, 4]; the observations are averages over
+    balls of radius 0.025 at seeded locations, and the QoI is the
+    average over the ball of the same radius at the centre of the domain (Eq.
+    measurement_definition)."""
     return make_problem(f"table1a-q1-{n}", 2, n, n_levels=n_levels, kappa2_const=100.0, m=8, obs_seed=11,
-                        disc=1, gamma_range=(1e-6, 2e-6), qoi_cells=max(2, (46 * (n + 1)) // 1024))
+                        disc=1, gamma_range=(1e-6, 2e-6), ball_radius=0.025)
 
 
 def config3(n: int = 127, n_levels: Optional[int] = None) -> Problem:

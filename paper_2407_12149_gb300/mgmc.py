@@ -76,6 +76,7 @@ EXPORTS = ("mgmc_config_default", "mgmc_create", "mgmc_point_obs_rows", "mgmc_sa
            "mgmc_tc_gemm", "mgmc_unet_create", "mgmc_unet_n_params", "mgmc_unet_get_params",
            "mgmc_unet_set_params", "mgmc_unet_inputs", "mgmc_unet_gradient", "mgmc_unet_train",
            "mgmc_unet_predict", "mgmc_unet_destroy", "mgmc_check_status", "mgmc_set_wait_limit",
+           "mgmc_fine_operator",
            "mgmc_last_error")
 
 
@@ -130,6 +131,7 @@ def load():
     L.mgmc_unet_destroy.argtypes = [ctypes.c_void_p]
     L.mgmc_destroy.argtypes = [ctypes.c_void_p]
     L.mgmc_check_status.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    L.mgmc_fine_operator.argtypes = [ctypes.POINTER(mgmc_config), _F64P, ctypes.c_double, _F64P]
     L.mgmc_set_wait_limit.argtypes = [ctypes.c_void_p, ctypes.c_int64]
     for name in EXPORTS:
         if name != "mgmc_last_error":
@@ -184,6 +186,18 @@ class TorchAllocator:
 # --------------------------------------------------------------------------
 # functions with the C names
 # --------------------------------------------------------------------------
+
+def mgmc_fine_operator(problem) -> np.ndarray:
+    """The finest grid's operator A_L of a problem as the library assembles it:
+    float64 [N, 3^dim] stencil (host only)."""
+    p = problem
+    cfg = mgmc_config(p.dim, p.n, p.n_levels, 1, 1, MGMC_FP64, p.scale_hd, 0, 0, getattr(p, "disc", MGMC_FD))
+    k2 = None if p.kappa2 is None else np.ascontiguousarray(p.kappa2, dtype=np.float64).ravel()
+    out = np.empty((p.N, 3 ** p.dim), dtype=np.float64)
+    _check(load().mgmc_fine_operator(ctypes.byref(cfg), _ptr(k2, ctypes.c_double), float(p.kappa2_const),
+                                     _ptr(out, ctypes.c_double)))
+    return out
+
 
 def mgmc_check_status(h, stream=None):
     _check(load().mgmc_check_status(h, _stream_handle(stream)))

@@ -77,3 +77,28 @@ def test_sample_rejects_null_handle(lib):
 def test_stats_rejects_short_series(lib):
     out = mgmc.mgmc_stats()
     assert lib.mgmc_qoi_stats(None, 10, 0, 1.5, ctypes.byref(out), None) == 1
+
+
+@pytest.mark.parametrize("dim,n,disc,scale_hd,var", [(2, 15, 0, 1, True), (2, 7, 0, 0, False), (3, 7, 0, 1, True),
+                                                     (2, 15, 1, 1, False), (2, 7, 1, 0, False), (3, 7, 1, 1, False)])
+def test_fine_operator_matches_oracle(lib, dim, n, disc, scale_hd, var):
+    """mgmc_fine_operator (host only) returns the oracle's finest stencil (FD and Q1)."""
+    import oracle
+    p = inputs.make_problem("op", dim, n, kappa2_seed=4 if var else None, kappa2_const=37.0, scale_hd=scale_hd,
+                            disc=disc)
+    got = mgmc.mgmc_fine_operator(p)
+    o = oracle.Oracle(dim, n, 1, kappa2=p.kappa2, kappa2_const=37.0, scale_hd=scale_hd, disc=disc)
+    ref = o.stencil(0)
+    assert got.shape == ref.shape
+    assert np.allclose(got, ref, rtol=1e-14, atol=1e-14 * np.abs(ref).max())
+
+
+def test_fine_operator_rejects_bad_input(lib):
+    p = inputs.make_problem("op", 2, 7, kappa2_seed=4)
+    p.disc = 1
+    with pytest.raises(mgmc.MGMCError):
+        mgmc.mgmc_fine_operator(p)
+    p = inputs.make_problem("op", 2, 7)
+    p.n = 8
+    with pytest.raises(mgmc.MGMCError):
+        mgmc.mgmc_fine_operator(p)

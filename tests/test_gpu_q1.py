@@ -143,3 +143,52 @@ def test_q1_rejects_variable_kappa_and_mixed_batches(torch_mod):
     with pytest.raises(MGMCError) as e:
         BatchSampler([_q1(2, 63, 4), inputs.make_problem("fd", 2, 63, m=4)])
     assert e.value.code == 1
+
+
+def test_q1_gpu_chains_follow_the_closed_form_law(torch_mod):
+    """Sec. 5.3 estimators on GPU chains: 8192 FP32 chains of the 15^2 Q1 posterior from
+    theta^(0) = 0 (16 batches of 512, one seed each); their QoI mean and variance at
+    steps 1..6 match the exact law (I - X^m) mu, A~^-1 - X^m A~^-1 X^mT within 3 SE."""
+    torch = torch_mod
+    from paper_2407_12149_gb300 import experiments as E
+    from paper_2407_12149_gb300.mgmc import BatchSampler
+    from tests.test_experiments import _dense, _law
+    from tests.test_oracle_pins import _z_ok
+    p = _q1(2, 15, 4, qoi=4)
+    H, At, f, F = _dense(p)
+    steps, B, K = 6, 512, 16
+    mean, var, _, mu, s2 = _law(H, At, f, F, steps)
+    b = BatchSampler([p] * B, precision="fp32")
+    z = []
+    for k in range(K):
+        q = torch.zeros(B * steps, dtype=torch.float64, device="cuda")
+        b.sample(b.zeros(), steps, 500 + k, qoi=q)
+        z.append(q.view(B, steps).cpu().numpy())
+    b.close()
+    z = np.concatenate([np.zeros((B * K, 1)), np.concatenate(z)], axis=1)
+    n = z.shape[0]
+    r = E.convergence_ratios(z, mu, s2)
+    m = np.arange(1, steps + 1)
+    assert _z_ok(r["mean"][m], mean[m], np.sqrt(var[m] / n))
+    assert _z_ok(r["var"][m], var[m], var[m] * np.sqrt(2.0 / (n - 1)))
+    mu_s, s2_s = E.exact_qoi_moments(p)
+    assert mu_s == pytest.approx(mu, rel=1e-10) and s2_s == pytest.approx(s2, rel=1e-10)
+
+
+@pytest.mark.parametrize("n,precision", [(63, "fp64"), (127, "fp64"), (255, "fp32")])
+def test_table1a_ball_observations_parity(torch_mod, n, precision):
+    """The Table 1a problem (Q1, ball-average observations and QoI, Gamma ~ 1e-6):
+    observation rows with tens to hundreds of entries through the fused path."""
+    from paper_2407_12149_gb300.mgmc import Sampler
+    p = inputs.table1a(n)
+    steps = 12 if precision == "fp64" else 100
+    xo, qo = _orc(p).sample(steps, 23)
+    s = Sampler(p, precision=precision, coarse_max_n=31)
+    xg, qg = _run(torch_mod, s, steps, 23)
+    s.close()
+    rms = np.sqrt(np.mean(xo ** 2))
+    if precision == "fp64":
+        assert np.all(np.abs(xg - xo) <= 1e-11 * np.maximum(np.abs(xo), rms))
+        assert np.all(np.abs(qg - qo) <= 1e-11 * np.maximum(np.abs(qo), rms))
+    else:
+        assert np.abs(xg - xo).max() <= 2e-4 * rms
