@@ -682,7 +682,7 @@ def run_warmstart(args):
 
 
 def run_gibbs_table(args):
-    """The comparison of the paper's Table 1 (Sec. 5.2) on the 2D posterior of the headline
+    """The comparison of the paper's Table 1 (Sec. 5.2; samplers of Sec. 5.1.3) on the 2D posterior of the headline
     workload (kappa^2 = 10 exp(g), 16 point observations), FP32, one chain per sampler and
     grid: IACT of the QoI (device Wolff estimate after a burn-in), time per step (CUDA
     events over back-to-back steps, state resident) and time per independent sample for

@@ -13,7 +13,7 @@
  * forward sweeps before the coarse-grid correction, nu2 backward sweeps
  * after it), Galerkin coarse operators (Eq. galerkin_triple_product),
  * restriction = transpose of the multilinear prolongation, and an exact
- * Cholesky sampler on the coarsest grid (Sec. 2.5).
+ * Cholesky sampler on the coarsest grid (Sec. 3.5).
  *
  * Conventions used by every entry point:
  *   - Grids are cubes: n interior points per axis, n = 2^k - 1; level
@@ -84,7 +84,7 @@ typedef struct {
     int coarse_max_n; /* grids with n <= coarse_max_n run inside one single-CTA kernel;
                          0 selects the default (63 in 2D, 15 in 3D) */
     int gibbs;        /* 0: the MGMC V-cycle (Alg. 1).  1: the plain Gibbs sampler the
-                         paper compares against (Sec. 5.2): one step is nu1 forward and
+                         paper compares against (Sec. 5.1.3): one step is nu1 forward and
                          nu2 backward sweeps of the low-rank Gibbs smoother (Alg. 3) on
                          the finest grid alone, with the MGMC cycle's noise slots and no
                          coarse-grid correction.  Needs n_levels >= 2 (the finest grid's
@@ -141,7 +141,7 @@ mgmc_status mgmc_point_obs_rows(int dim, int n, int m, const double* xyz, int32_
 mgmc_status mgmc_sample(mgmc_handle h, int64_t n_steps, uint64_t seed, uint64_t step_offset,
                         uint32_t chain, void* x_inout, double* qoi_out, void* stream);
 
-/* Posterior mean by noise-free V-cycles (deterministic multigrid, Sec. 3.2):
+/* Posterior mean by noise-free V-cycles (deterministic multigrid; the multigrid / MGMC equivalence of Sec. 4):
  * iterates from mean_out (dense n^dim field, handle precision, device or
  * host) until ||f - A~ x||_2 <= rtol ||f||_2 or max_cycles.  Synchronous.
  * cycles_done / rel_residual may be NULL. */
@@ -280,7 +280,7 @@ mgmc_status mgmc_destroy(mgmc_handle h);
  * on the (n+1) x (n+1) grid -- log(kappa^2 / 10), the summed observation row
  * weights sum_k B_{k,i} and the weighted data sum_k B_{k,i} y_k, with the last
  * row and column zero -- to an estimate of the posterior mean mu = A~^-1 f
- * (Sec. 3.2), to be used ONLY as a chain's initial state: the chain's law is
+ * (Sec. 2.2), to be used ONLY as a chain's initial state: the chain's law is
  * that of the sampler whatever x_0 is; a good x_0 shortens burn-in.
  * Channels-last BF16 activations and weights, FP32 accumulation on the tcgen05
  * tensor cores.  c0 channels at full resolution, doubling at each of three

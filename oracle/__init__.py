@@ -196,7 +196,7 @@ class Oracle:
         return x
 
     def sample(self, n_steps, seed, x=None, step_offset=0, chain=0, noise=True, qoi=True, gibbs=False):
-        """n_steps MGMC V-cycles, or with gibbs=True steps of the plain Gibbs sampler (Sec. 5.2)."""
+        """n_steps MGMC V-cycles, or with gibbs=True steps of the plain Gibbs sampler (Sec. 5.1.3)."""
         x = np.zeros(self.N) if x is None else np.array(x, dtype=np.float64, copy=True).ravel()
         q = np.zeros(max(n_steps, 1)) if qoi else None
         fn = lib().oracle_sample_gibbs if gibbs else lib().oracle_sample

@@ -421,7 +421,7 @@ static void gs_sweep(const oracle_problem* p, int l, const olevel* L, int dir, d
     }
 }
 
-/* Gamma xi_LR = L_Gamma z' (z' standard normal), the low-rank noise of Sec. 2.4
+/* Gamma xi_LR = L_Gamma z' (z' standard normal), the low-rank noise of Sec. 3.4
  * in the units of the data vector. */
 static void lowrank_noise(const oracle_problem* p, int l, uint32_t slot, const double* zgiven, double* gxi)
 {
@@ -1099,7 +1099,7 @@ int oracle_sample(oracle_problem* p, int64_t n_steps, uint64_t seed, uint64_t st
     return 0;
 }
 
-/* Sec. 5.2, "Gibbs sampler": the symmetric low-rank Gibbs sweeps of the finest
+/* Sec. 5.1.3, "Gibbs sampler": the symmetric low-rank Gibbs sweeps of the finest
  * level alone (Alg. 3 forward nu1 times, then backward nu2 times). */
 int oracle_sample_gibbs(oracle_problem* p, int64_t n_steps, uint64_t seed, uint64_t step_offset,
                         uint32_t chain, int noise, double* x, double* qoi_out)

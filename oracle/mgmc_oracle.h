@@ -71,7 +71,7 @@ int oracle_smoother_step_given(const oracle_problem* p, int l, int dir,
 int oracle_sample(oracle_problem* p, int64_t n_steps, uint64_t seed, uint64_t step_offset,
                   uint32_t chain, int noise, double* x, double* qoi_out);
 
-/* The plain Gibbs sampler the paper compares MGMC with (Sec. 5.2, "Gibbs
+/* The plain Gibbs sampler the paper compares MGMC with (Sec. 5.1.3, "Gibbs
  * sampler"): each step is nu1 forward then nu2 backward sweeps of the
  * low-rank Gibbs smoother (Alg. 3) on the finest level, with the right-hand
  * side f_L = B Gamma^-1 y held as fd = 0, d = y, and the noise slots of the

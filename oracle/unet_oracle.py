@@ -3,7 +3,7 @@ only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline leg may use it.
 
 The warm start maps three input channels on the (n+1) x (n+1) grid -- the
 interior n x n sites padded with one zero row and column -- to an estimate of
-the posterior mean mu = A~^-1 f (Sec. 3.2; the chain's law does not depend on
+the posterior mean mu = A~^-1 f (Sec. 2.2; the chain's law does not depend on
 its starting state, so the estimate only shortens burn-in):
   channel 0: log(kappa^2 / 10) at each site,
   channel 1: sum over observations k of the row weight B_{k,i} (the bilinear

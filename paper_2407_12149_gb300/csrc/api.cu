@@ -428,7 +428,7 @@ void enqueue_cycle(mgmc_ctx* h, cudaStream_t s, int& launches)
     const DevProblem& P = h->P;
     const bool prof = h->profile && h->top < Lf;
     if (h->cfg.gibbs) {
-        // plain Gibbs sampler (Sec. 5.2): the finest grid's sweeps of the V-cycle, no coarse correction
+        // plain Gibbs sampler (Sec. 5.1.3): the finest grid's sweeps of the V-cycle, no coarse correction
         const DevLevel<T>& D = lv[Lf];
         for (int j = 0; j < h->cfg.nu1; ++j) {
             if (prof && j == 0) cudaEventRecordWithFlags(h->ev[0], s, cudaEventRecordExternal);

@@ -1,6 +1,6 @@
 // coarse.cu -- the V-cycle below and including grid `top` in one CTA (Alg. 1
 // recursion for the small grids, ending in the exact coarsest Cholesky sample
-// of Sec. 2.5).
+// of Sec. 3.5).
 //
 // The state theta_l, the dense right-hand side fdense_l and the operator
 // coefficients of every grid l <= top live in shared memory for the whole

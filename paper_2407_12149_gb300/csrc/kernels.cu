@@ -7,7 +7,7 @@
 //   k_residual, k_restrict                 : r = f_l - A_l theta' on the fine grid, then
 //                                            f_{l-1} = P^T r and d_{l-1} = d_l - B_l^T theta'
 // the grids with n <= coarse_max_n run as one k_coarse_cycle (coarse.cu),
-// which ends in the exact coarsest Cholesky sample (Sec. 2.5), and back up:
+// which ends in the exact coarsest Cholesky sample (Sec. 3.5), and back up:
 //   k_prolong                              : theta += P psi_{l-1}
 //   k_sweep_colour  (reverse colours), k_lowrank_v + k_lowrank_apply (backward G)
 // and k_qoi_advance records F^T theta and advances the cycle counter.

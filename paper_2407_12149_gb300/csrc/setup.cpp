@@ -12,7 +12,7 @@
 //    neighbours, so the substitution runs on the bounding box of supp(b_k)
 //    grown by the number of colours, which gives the full-grid result;
 //  - the coarsest posterior operator A~_0 = A_0 + B_0 Gamma^-1 B_0^T and its
-//    Cholesky factor (exact coarse sampler, Sec. 2.5);
+//    Cholesky factor (exact coarse sampler, Sec. 3.5);
 //  - the finest data vector d_L = y, so that f_L = B_L Gamma^-1 d_L (Eq. f_ell_definition).
 #include "setup.hpp"
 

@@ -1,6 +1,6 @@
 // unet.cu -- learned warm start for the sampler: a U-Net maps (log kappa^2, the
 // observation weights B^T 1, the weighted data B^T y) on the (n+1)^2 grid to an
-// estimate of the posterior mean mu = A~^-1 f (Sec. 3.2), used only as a
+// estimate of the posterior mean mu = A~^-1 f (Sec. 2.2), used only as a
 // chain's initial state x_0: the MGMC chain's law does not depend on x_0, the
 // estimate only shortens burn-in.
 //

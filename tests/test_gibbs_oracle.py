@@ -1,4 +1,4 @@
-"""Pins of the oracle's plain Gibbs sampler (Sec. 5.2, "Gibbs sampler"): one step is
+"""Pins of the oracle's plain Gibbs sampler (Sec. 5.1.3, "Gibbs sampler"): one step is
 the forward then the backward low-rank Gibbs sweep (Alg. 3) of the finest grid.
 
 Checked against dense linear algebra built from the definitions (tests/dense_ref.py):

@@ -1,4 +1,4 @@
-"""The plain Gibbs sampler (mgmc_config.gibbs = 1, Sec. 5.2) on the GPU against the
+"""The plain Gibbs sampler (mgmc_config.gibbs = 1, Sec. 5.1.3) on the GPU against the
 oracle's Gibbs sampler, per site, with the tolerances of the MGMC parity tests."""
 import numpy as np
 import pytest

@@ -137,7 +137,7 @@ def test_alg3_equals_generic_random_smoother(dim, n, levels, direction):
 
 def test_smoother_noise_covariance_identity_and_naive_split():
     """M~ + M~^T - A~ = D + B Gamma^-1 B^T (Eq. low_rank_smoother_covariance) and the naive
-    D + L splitting gives the indefinite D - B Gamma^-1 B^T (end of Sec. 2.4)."""
+    D + L splitting gives the indefinite D - B Gamma^-1 B^T (end of Sec. 3.4)."""
     p = inputs.make_problem("t", 2, 15, n_levels=3, kappa2_const=10.0, m=8, obs_seed=1)
     H = _hier(p)
     l = 2
