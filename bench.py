@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 # DRAM bytes (read + write) per launch of the finest-grid forward kernel (k_stream_fwd)
 # on the 32 x 1023^2 batch, from an ncu capture of that kernel on this workload; None
 # for other workloads and whenever that kernel changes before it is re-captured.
-FINE_SWEEP_TRAFFIC_BYTES = None
+FINE_SWEEP_TRAFFIC_BYTES = 482_450_432
 # the e2e measurement of a batch runs it as this many batches on their own streams
 E2E_GROUPS = 4
 
@@ -217,7 +217,59 @@ WORKLOADS = {
     "gibbs-vs-mgmc-2d": {"n": 511, "chains": 1, "table": True},   # Table 1 comparison, 31^2 .. 511^2
     "gibbs-vs-mgmc-2d-q1": {"n": 511, "chains": 1, "table": True, "q1": True},   # Table 1a setting (Q1 elements)
     "convergence-2d": {"n": 255, "chains": 512, "conv": True},   # Sec. 5.3: R, Z, rates, RMSE (Q1, 31^2..255^2)
+    "tc-gemm-8192": {"n": 8192, "chains": 1, "gemm": True},      # the U-Net's tensor-core GEMM, 8192^3 BF16
 }
+
+
+def run_tc_gemm(args):
+    """C = A B^T, A and B 8192 x 8192 BF16, FP32 accumulate and output, on the
+    tcgen05 GEMM of the learned warm start (k_tc_gemm): CUDA events per launch."""
+    import torch
+    from paper_2407_12149_gb300 import build
+    from paper_2407_12149_gb300 import mgmc as M
+    build.build()
+    dev = torch.device("cuda", 0)
+    n = 8192
+    g = torch.Generator(device=dev).manual_seed(1)
+    A = torch.randn(n, n, generator=g, device=dev).bfloat16()
+    B = torch.randn(n, n, generator=g, device=dev).bfloat16()
+    C = torch.empty(n, n, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        M.tc_gemm(A, B, out=C)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(gpu_id_for_smi(torch, 0))
+    time.sleep(0.3)
+    for a, b in ev:
+        a.record()
+        M.tc_gemm(A, B, out=C)
+        b.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    avg = statistics.mean(ms)
+    tflops = 2.0 * n ** 3 / (avg * 1e-3) / 1e12
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except Exception:
+        pass
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    # spot check against an FP64 product of the same BF16 values
+    rows = torch.arange(0, n, 997, device=dev)
+    ref = A[rows].double() @ B.double().T
+    err = float(((C[rows].double() - ref).abs().max() / ref.abs().max()).item())
+    line = {"metric": "TFLOP/s", "value": tflops, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": avg, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "tc-gemm-8192: C = A B^T, 8192^3, BF16 inputs, FP32 accumulate and output "
+                                   "(k_tc_gemm, tcgen05 + TMA + TMEM)", "max_rel_err_vs_fp64": err},
+            "roofline": {"bound": "tensor", "kernel": "k_tc_gemm", "achieved": tflops, "peak": peak,
+                         "unit": "TFLOP/s", "frac": tflops / peak,
+                         "peak_kind": "measured cuBLAS bf16 burst" if peaks else "fallback", "traffic": None},
+            "clocks": clk, "gpu_launches": args.steps}
+    print(json.dumps(line), flush=True)
 
 
 def run_reference(args):
@@ -336,6 +388,27 @@ def run_mine(args):
         hit = np.nonzero(np.abs(trace - fmu) <= se)[0]
         burn = int(hit[0]) if hit.size else None
 
+    # --- band threshold of the 9-point depths, timed on this handle (autotune) ---
+    tuned = None
+    if prec == "fp32" and wl.get("dim", 2) == 2:
+        from paper_2407_12149_gb300 import autotune
+        cands = autotune.band_candidates(ps, 31)
+        if len(cands) > 1:
+            best, tms = autotune.tune_band_min_n(
+                s, cands, timer=lambda smp: autotune.time_cycles(smp, cycles=20, warm=3, seed=seed + 7,
+                                                               device=local))
+            cache = autotune.TuneCache()
+            cache.put(autotune.cache_key(ps, prec), {"coarse_max_n": 31, "band_min_n": best}, tms)
+            try:
+                cache.save()
+            except OSError:
+                pass
+            tuned = {"coarse_max_n": 31, "band_min_n": best,
+                     "ms_per_cycle": {("tiles only" if k == autotune.TILES_ONLY else str(k)): round(v, 4)
+                                      for k, v in tms.items()},
+                     "how": "band_min_n candidates timed on this handle, 20 back-to-back cycles each "
+                            "(CUDA events), the fastest kept and cached"}
+
     # --- CPU baseline (rank 0, one GPU only), before the GPU timing ------------
     cpu = None
     if rank == 0 and ws == 1 and wl["n"] == 1023 and not wl.get("mixed") and wl.get("dim", 2) == 2:
@@ -398,7 +471,8 @@ def run_mine(args):
         gsz = nch // ng
         for g in range(ng):
             part = ps[g * gsz:(g + 1) * gsz]
-            sg = s if ng == 1 else M.BatchSampler(part, precision=prec, device=local)
+            sg = s if ng == 1 else M.BatchSampler(part, precision=prec, device=local,
+                                                  band_min_n=tuned["band_min_n"] if tuned else None)
             groups.append({"s": sg, "stream": torch.cuda.Stream(device=dev) if ng > 1 else stream,
                            "host": xh[g * gsz:(g + 1) * gsz],
                            "qh": torch.zeros(gsz, dtype=torch.float64).pin_memory(),
@@ -520,6 +594,7 @@ def run_mine(args):
                            "with x = NULL); e2e copies them in and out through host memory every step",
                    "parallelism": "replicas" if ws > 1 else "single GPU",
                    "launches_per_cycle": launches,
+                   "tuned": tuned,
                    "plain_fp64_single_chain": plain,
                    "burn_in_rule": "first cycle at which the mean QoI of the chains (all from 0) is within one "
                                    "Monte Carlo standard error of F . mu from the FP64 mean solve"},
@@ -878,6 +953,8 @@ def main():
         run_gibbs_table(args)
     elif WORKLOADS[args.workload].get("conv"):
         run_convergence(args)
+    elif WORKLOADS[args.workload].get("gemm"):
+        run_tc_gemm(args)
     else:
         run_mine(args)
 

@@ -97,6 +97,12 @@ typedef struct {
                          (9/27-point; constant kappa^2 only: kappa2 must be NULL), divided
                          by h^d when scale_hd = 0.  The coarse grids are Galerkin products
                          either way (for Q1 they are the Q1 matrices of the coarse grids). */
+    int band_min_n;   /* 2D FP32 V-cycles (nu1 = nu2 = 1): the 9-point grids below the finest
+                         with n >= band_min_n (and above coarse_max_n) run in the streaming
+                         band kernels, the smaller ones in shared-memory tile kernels.  0 selects
+                         the default (255); a value above n keeps every grid on the tiles.  Both
+                         kernel families give bitwise identical states; a batch takes the value
+                         of its first configuration. */
 } mgmc_config;
 
 enum { MGMC_FD = 0, MGMC_Q1 = 1 };
@@ -263,6 +269,14 @@ mgmc_status mgmc_check_status(mgmc_handle h, void* stream);
  * default bound and ends; the chain's state is garbage until it is re-set).
  * Synchronises the device. */
 mgmc_status mgmc_set_wait_limit(mgmc_handle h, int64_t limit_ns);
+
+/* Change band_min_n (see mgmc_config) of a handle after creation: the job tables
+ * of both kernel families exist from mgmc_create / mgmc_create_batch on, so this
+ * only selects, per grid depth, which one the captured cycle launches (the graph is
+ * captured again on the next call that samples).  The states do not depend on the
+ * choice.  Synchronises the device when the choice changes.  MGMC_ERR_ARG for a
+ * negative value.  (An autotuner uses it to time the settings on one handle.) */
+mgmc_status mgmc_set_band_min_n(mgmc_handle h, int band_min_n);
 
 /* Benchmark timing: with enable != 0 the captured cycle records CUDA events
  * around the finest grid's forward sweep and its backward sweep (finest grid

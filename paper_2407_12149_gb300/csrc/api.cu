@@ -1,6 +1,7 @@
 // api.cu -- the C ABI (include/mgmc.h): handle life cycle, device upload of
 // the hierarchy, CUDA-graph capture of one V-cycle and the sampling loop.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -12,6 +13,7 @@
 #include "kernels.cuh"
 #include "setup.hpp"
 #include "stream2d.cuh"
+#include "stream9.cuh"
 #include "tile2d.cuh"
 
 using namespace mgmc;
@@ -121,6 +123,13 @@ struct mgmc_ctx {
     int njob_stream = 0;
     long long stream_strips = 0;
     int stream_ctas = 0;
+    // FP32 9-point grids below the finest: the streaming band kernels (stream9.cu) at the
+    // depths whose grids all have n >= band_min_n, per depth
+    std::vector<char> s9_ok, s9_use;
+    std::vector<int> s9_minn;   // smallest grid of the depth
+    std::vector<void*> jobs_s9, maps_s9;
+    std::vector<int> njob_s9, s9_grid;
+    std::vector<long long> s9_strips;
     void* jobs_coarse = nullptr;
     void* jobs_qoi = nullptr;
     void* jobs_pack = nullptr;    // PackJob<T> per chain (2D fused path)
@@ -137,6 +146,7 @@ namespace {
 
 template <typename T>
 mgmc_status build_batch_tables(mgmc_ctx* h);
+void apply_band_min(mgmc_ctx* h);
 
 template <typename T>
 std::vector<DevLevel<T>>& levels_of(mgmc_ctx* h);
@@ -386,6 +396,9 @@ void enqueue_cycle_batch(mgmc_ctx* h, cudaStream_t s, int& launches)
         if (d == 0 && h->stream_fine)
             launch_stream_fine((const StreamJob*)h->jobs_stream, (const StreamMaps*)h->maps_sfwd, h->njob_stream,
                                h->stream_strips, h->stream_ctas, false, s, launches);
+        else if (h->s9_use[d])
+            launch_stream9((const StreamJob*)h->jobs_s9[d], (const Stream9Maps*)h->maps_s9[d], h->njob_s9[d],
+                           h->s9_strips[d], h->s9_grid[d], false, s, launches);
         else
             launch_tile_batch<T>((const TileJob<T>*)h->jobs_tile[d], (const TileMaps*)h->maps_fwd[d],
                                  h->njob_tile[d], h->per_tile[d], h->nblk_tile[d], d == 0 && h->fine0, false, d > 0,
@@ -405,6 +418,9 @@ void enqueue_cycle_batch(mgmc_ctx* h, cudaStream_t s, int& launches)
         if (d == 0 && h->stream_fine)
             launch_stream_fine((const StreamJob*)h->jobs_stream, (const StreamMaps*)h->maps_sbwd, h->njob_stream,
                                h->stream_strips, h->stream_ctas, true, s, launches);
+        else if (h->s9_use[d])
+            launch_stream9((const StreamJob*)h->jobs_s9[d], (const Stream9Maps*)h->maps_s9[d], h->njob_s9[d],
+                           h->s9_strips[d], h->s9_grid[d], true, s, launches);
         else
             launch_tile_batch<T>((const TileJob<T>*)h->jobs_tile[d], (const TileMaps*)h->maps_bwd[d],
                                  h->njob_tile[d], h->per_tile[d], h->nblk_tile[d], d == 0 && h->fine0, true, false, s,
@@ -575,6 +591,7 @@ mgmc_status mgmc_config_default(mgmc_config* cfg, int dim, int n)
     cfg->scale_hd = 1;
     cfg->coarse_max_n = 0;
     cfg->gibbs = 0;
+    cfg->band_min_n = 0;
     return MGMC_OK;
 }
 
@@ -631,6 +648,7 @@ mgmc_status mgmc_create(const mgmc_config* cfg_in, const mgmc_allocator* alloc, 
     if (cfg.n < 1 || ((cfg.n + 1) & cfg.n) != 0) return fail(MGMC_ERR_ARG, "n must be 2^k - 1");
     if (cfg.precision != MGMC_FP32 && cfg.precision != MGMC_FP64) return fail(MGMC_ERR_ARG, "bad precision");
     if (cfg.nu1 < 0 || cfg.nu2 < 0 || cfg.nu1 > 16 || cfg.nu2 > 16) return fail(MGMC_ERR_ARG, "nu1/nu2 out of range");
+    if (cfg.band_min_n < 0) return fail(MGMC_ERR_ARG, "band_min_n must be >= 0");
     if (m < 0 || m > MGMC_MAX_OBS) return fail(MGMC_ERR_ARG, "number of observations out of range");
     if (m > 0 && (!obs_site || !obs_w || !Gamma || !y || nnz_per_obs < 1))
         return fail(MGMC_ERR_ARG, "observation arrays missing");
@@ -953,6 +971,22 @@ mgmc_status mgmc_set_profiling(mgmc_handle h, int enable)
     return MGMC_OK;
 }
 
+mgmc_status mgmc_set_band_min_n(mgmc_handle h, int band_min_n)
+{
+    if (!h) return fail(MGMC_ERR_ARG, "handle is NULL");
+    if (band_min_n < 0) return fail(MGMC_ERR_ARG, "band_min_n must be >= 0");
+    CUDA_TRY(cudaSetDevice(h->device));
+    h->cfg.band_min_n = band_min_n;
+    const std::vector<char> before = h->s9_use;
+    apply_band_min(h);
+    if (h->exec && h->s9_use != before) {
+        CUDA_TRY(cudaDeviceSynchronize());
+        cudaGraphExecDestroy(h->exec);
+        h->exec = nullptr;
+    }
+    return MGMC_OK;
+}
+
 mgmc_status mgmc_profile_times(mgmc_handle h, float* ms, int n, void* stream)
 {
     if (!h || !ms || n < 2) return fail(MGMC_ERR_ARG, "bad arguments");
@@ -968,6 +1002,16 @@ mgmc_status mgmc_profile_times(mgmc_handle h, float* ms, int n, void* stream)
 }  // extern "C"
 
 namespace {
+
+// which depths run in the streaming band kernels: the eligible ones (FP32 9-point
+// grids below the finest) whose smallest grid has n >= band_min_n (default 255)
+constexpr int kBandMinDefault = 255;
+void apply_band_min(mgmc_ctx* h)
+{
+    const int band_min = h->cfg.band_min_n > 0 ? h->cfg.band_min_n : kBandMinDefault;
+    h->s9_use.assign(h->s9_ok.size(), 0);
+    for (size_t d = 0; d < h->s9_ok.size(); ++d) h->s9_use[d] = h->s9_ok[d] && h->s9_minn[d] >= band_min;
+}
 
 template <typename T>
 mgmc_status build_batch_tables(mgmc_ctx* h)
@@ -1027,6 +1071,64 @@ mgmc_status build_batch_tables(mgmc_ctx* h)
         std::vector<TileMaps> mf, mb;
         std::vector<LowrankJob<T>> ld, lu;
         int tiles = 0, bd = 0, bu = 0;
+        // FP32 9-point grids below the finest: the streaming band kernels can take this
+        // depth (which of the two kernel families runs is set by band_min_n, see
+        // apply_band_min); the low-rank steps then read the state at the observation
+        // entries, whichever family wrote it
+        bool s9 = false;
+        int s9_minn = 0;
+        if constexpr (std::is_same<T, float>::value) {
+            if (d > 0) {
+                s9 = true;
+                s9_minn = INT_MAX;
+                for (mgmc_ctx* c : chains) {
+                    const int l = c->L - 1 - d;
+                    if (l <= c->top) continue;
+                    const DevLevel<T>& Lh = levels_of<T>(c)[l];
+                    if (Lh.fine) s9 = false;
+                    s9_minn = std::min(s9_minn, Lh.n);
+                }
+            }
+        }
+        h->s9_ok.push_back(s9 ? 1 : 0);
+        h->s9_minn.push_back(s9_minn);
+        h->jobs_s9.push_back(nullptr);
+        h->maps_s9.push_back(nullptr);
+        h->njob_s9.push_back(0);
+        h->s9_strips.push_back(0);
+        h->s9_grid.push_back(0);
+        if constexpr (std::is_same<T, float>::value) {
+            if (s9) {
+                cudaError_t e = stream9_prepare();
+                if (e != cudaSuccess)
+                    return fail(MGMC_ERR_CUDA, std::string("band kernel set-up: ") + cudaGetErrorString(e));
+                std::vector<StreamJob> sj;
+                std::vector<Stream9Maps> sm;
+                long long strips = 0;
+                for (mgmc_ctx* c : chains) {
+                    const int l = c->L - 1 - d;
+                    if (l <= c->top) continue;
+                    const auto& lv = levels_of<float>(c);
+                    StreamJob J{};
+                    J.L = lv[l];
+                    J.C = lv[l - 1];
+                    J.cs = c->cs;
+                    J.strip0 = strips;
+                    J.spb = (J.L.n + kStream9Rows - 1) / kStream9Rows;
+                    J.nbands = (J.L.n + kStream9Band - 1) / kStream9Band;
+                    strips += (long long)J.spb * J.nbands;
+                    sj.push_back(J);
+                    sm.emplace_back();
+                    if (!make_stream9_maps(J.L, J.C, &sm.back()))
+                        return fail(MGMC_ERR_CUDA, "TMA descriptor encoding failed");
+                }
+                h->jobs_s9.back() = upload(h, sj, st);
+                h->maps_s9.back() = upload(h, sm, st);
+                h->njob_s9.back() = (int)sj.size();
+                h->s9_strips.back() = strips;
+                h->s9_grid.back() = stream9_grid(strips);
+            }
+        }
         for (mgmc_ctx* c : chains) {
             const int l = c->L - 1 - d;
             if (l <= c->top) continue;
@@ -1044,7 +1146,7 @@ mgmc_status build_batch_tables(mgmc_ctx* h)
             if (c->m > 0) {
                 int rd = std::max(Lh.g_rows[0], Lh.h_rows);
                 DevLevel<T> Lz = Lh;
-                if (d == 0 && h->stream_fine) Lz.zparts = nullptr;   // (stream_fine implies 5-point)
+                if ((d == 0 && h->stream_fine) || s9) Lz.zparts = nullptr;   // the low-rank kernel reads the state
                 ld.push_back({Lz, Ch, c->P, bd, lowrank_blocks(rd)});
                 bd += lowrank_blocks(rd);
                 lu.push_back({Lz, Ch, c->P, bu, lowrank_blocks(Lh.g_rows[1])});
@@ -1096,6 +1198,7 @@ mgmc_status build_batch_tables(mgmc_ctx* h)
     cudaError_t e = coarse_prepare_batch<T>(smem);
     if (e == cudaSuccess) e = tile_prepare_batch<T>();
     if (e != cudaSuccess) return fail(MGMC_ERR_CUDA, std::string("batch kernel set-up: ") + cudaGetErrorString(e));
+    apply_band_min(h);
     (void)nc;
     return MGMC_OK;
 }

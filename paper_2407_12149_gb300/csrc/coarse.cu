@@ -11,6 +11,7 @@
 // memory round trips.  The per-site arithmetic is that of stencil.cuh in the
 // same order of operations.
 #include "kernels.cuh"
+#include "tma.cuh"
 
 namespace mgmc {
 
@@ -518,7 +519,7 @@ __device__ __forceinline__ void coarse_body(const DevLevel<T>* __restrict__ leve
     if (n0 <= kCoarsestWarp) {
         const int nt = lv[top].n;
         const int zsz = 4 * ((nt + 3) / 4) * nt * (DIM == 3 ? nt : 1);
-        Ls = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(Z + zsz) + 7) & ~uintptr_t(7));
+        Ls = reinterpret_cast<double*>(smem_align_up<8>(reinterpret_cast<unsigned char*>(Z + zsz)));
         for (int i = threadIdx.x; i < n0 * n0; i += blockDim.x) Ls[i] = chol[i];
     }
     // the descriptors and operators above never change after set-up; the top grid's

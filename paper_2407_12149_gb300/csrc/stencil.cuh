@@ -188,6 +188,92 @@ __device__ __forceinline__ float apply_A(const DevLevel<float>& L, long long e)
     return fmaf(L.coef[e], xi, lap);
 }
 
+// --- FP32 9-point sites of a 4-site group (components 0..3), shared by the tile
+// and the streaming kernels so that both evaluate the same operations in the
+// same order (coarse_update / apply_A of the Galerkin grids).
+// component k of the row (k = -1 and k = 4 are the scalar e outside the group)
+__device__ __forceinline__ float cmp(const float4& v, float e, int k)
+{
+    return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : k == 3 ? v.w : e;
+}
+
+// rows of one 9-point group item: X rows -1, 0, +1; coefficient slot 0 and slots
+// 1..4 on row 0; slots 2..4 on row -1; the dense right-hand side
+struct Rows9 {
+    float4 xm, x0, xp, s0, c1, c2, c3, c4, c2m, c3m, c4m, f;
+    float exm, ex0, exp, c1e, c4me, c2me;  // the column outside the group (left or right, see cmp)
+};
+
+template <int Q>
+__device__ __forceinline__ float site9(const Rows9& r, float z)
+{
+    const float xi = cmp(r.x0, 0.f, Q);
+    float lap = 0.0f, offsum = 0.0f, a;
+    // o = 0: (-1,-1)
+    a = cmp(r.c4m, r.c4me, Q - 1);
+    lap = fmaf(a, cmp(r.xm, r.exm, Q - 1) - xi, lap);
+    offsum += a;
+    // o = 1: (0,-1)
+    a = cmp(r.c3m, 0.f, Q);
+    lap = fmaf(a, cmp(r.xm, r.exm, Q) - xi, lap);
+    offsum += a;
+    // o = 2: (+1,-1)
+    a = cmp(r.c2m, r.c2me, Q + 1);
+    lap = fmaf(a, cmp(r.xm, r.exm, Q + 1) - xi, lap);
+    offsum += a;
+    // o = 3: (-1,0)
+    a = cmp(r.c1, r.c1e, Q - 1);
+    lap = fmaf(a, cmp(r.x0, r.ex0, Q - 1) - xi, lap);
+    offsum += a;
+    // o = 5: (+1,0)
+    a = cmp(r.c1, 0.f, Q);
+    lap = fmaf(a, cmp(r.x0, r.ex0, Q + 1) - xi, lap);
+    offsum += a;
+    // o = 6: (-1,+1)
+    a = cmp(r.c2, 0.f, Q);
+    lap = fmaf(a, cmp(r.xp, r.exp, Q - 1) - xi, lap);
+    offsum += a;
+    // o = 7: (0,+1)
+    a = cmp(r.c3, 0.f, Q);
+    lap = fmaf(a, cmp(r.xp, r.exp, Q) - xi, lap);
+    offsum += a;
+    // o = 8: (+1,+1)
+    a = cmp(r.c4, 0.f, Q);
+    lap = fmaf(a, cmp(r.xp, r.exp, Q + 1) - xi, lap);
+    offsum += a;
+    const float s = cmp(r.s0, 0.f, Q);
+    const float aii = s - offsum;
+    const float Ax = fmaf(s, xi, lap);
+    float ia, sa;
+    inv_and_sqrt(aii, ia, sa);
+    const float rhs = cmp(r.f, 0.f, Q) + sa * z;
+    return xi + (rhs - Ax) * ia;
+}
+
+// rows for the 4-site residual: extras on both sides
+struct Rows9R {
+    Rows9 r;      // extras of r on the left (exm, ex0, exp, c1e, c4me)
+    float xmr, x0r, xpr, c2mr;  // right extras
+};
+
+template <int Q>
+__device__ __forceinline__ float ax9q(const Rows9R& R)
+{
+    const Rows9& r = R.r;
+    auto X = [&](const float4& v, float el, float er, int k) { return k < 0 ? el : k > 3 ? er : cmp(v, 0.f, k); };
+    const float xi = cmp(r.x0, 0.f, Q);
+    float lap = 0.0f;
+    lap = fmaf(cmp(r.c4m, r.c4me, Q - 1), X(r.xm, r.exm, R.xmr, Q - 1) - xi, lap);
+    lap = fmaf(cmp(r.c3m, 0.f, Q), X(r.xm, r.exm, R.xmr, Q) - xi, lap);
+    lap = fmaf(Q + 1 > 3 ? R.c2mr : cmp(r.c2m, 0.f, Q + 1), X(r.xm, r.exm, R.xmr, Q + 1) - xi, lap);
+    lap = fmaf(cmp(r.c1, r.c1e, Q - 1), X(r.x0, r.ex0, R.x0r, Q - 1) - xi, lap);
+    lap = fmaf(cmp(r.c1, 0.f, Q), X(r.x0, r.ex0, R.x0r, Q + 1) - xi, lap);
+    lap = fmaf(cmp(r.c2, 0.f, Q), X(r.xp, r.exp, R.xpr, Q - 1) - xi, lap);
+    lap = fmaf(cmp(r.c3, 0.f, Q), X(r.xp, r.exp, R.xpr, Q) - xi, lap);
+    lap = fmaf(cmp(r.c4, 0.f, Q), X(r.xp, r.exp, R.xpr, Q + 1) - xi, lap);
+    return fmaf(cmp(r.s0, 0.f, Q), xi, lap);
+}
+
 // 1D weight of the canonical prolongation for offset p in {-1, 0, 1}
 __device__ __forceinline__ double pw(int p) { return p == 0 ? 1.0 : 0.5; }
 

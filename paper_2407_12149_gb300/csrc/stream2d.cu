@@ -32,11 +32,14 @@
 
 #include "stencil.cuh"
 #include "stream2d.cuh"
+#include "stream_core.cuh"
 #include "tma.cuh"
 
 namespace mgmc {
 
 namespace {
+
+using namespace sc;
 
 constexpr int kBW = kStreamBand;
 constexpr int kK = kStreamRows;
@@ -64,61 +67,6 @@ static_assert(kRing == 64 && kRRing == 64 && kPRing == 32 && kNB == 8, "power-of
 static_assert(kBox % 128 == 0 && kPBox % 128 == 0, "TMA destinations on 128-byte boundaries");
 static_assert(kSX <= 256 && kPX <= 256 && (kSX * 4) % 16 == 0 && (kPX * 4) % 16 == 0, "TMA box");
 static_assert(kNB * 8 <= (int)kHead, "mbarriers");
-
-__device__ __forceinline__ int cdiv_pos(int a, int b) { return a > 0 ? (a + b - 1) / b : 0; }
-
-__device__ __forceinline__ int find_stream_job(const StreamJob* jobs, int njobs, long long s)
-{
-    int lo = 0, hi = njobs - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (jobs[mid].strip0 <= s)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
-}
-
-__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
-__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
-
-// the first 128-byte boundary of the dynamic shared memory, reached by pointer
-// arithmetic on the shared array so that every access stays a shared-memory access
-__device__ __forceinline__ unsigned char* smem_aligned(unsigned char* smem_dyn)
-{
-    return smem_dyn + ((128u - (smem_addr(smem_dyn) & 127u)) & 127u);
-}
-
-// Philox4x32-10 round keys of one key (Weyl schedule), computed once per run so that
-// the rounds do not recompute them; the same block as philox10 of common.cuh
-struct RoundKeys {
-    unsigned a[10], b[10];
-};
-__device__ __forceinline__ RoundKeys round_keys(unsigned k0, unsigned k1)
-{
-    RoundKeys K;
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        K.a[r] = k0;
-        K.b[r] = k1;
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-    return K;
-}
-__device__ __forceinline__ void draw_k(uint4 c, unsigned pair, const RoundKeys& K, float& z0, float& z1)
-{
-    c.x = pair;
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
-        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
-        c = make_uint4((unsigned)(p1 >> 32) ^ c.y ^ K.a[r], (unsigned)p1, (unsigned)(p0 >> 32) ^ c.w ^ K.b[r],
-                       (unsigned)p0);
-    }
-    normal_pair(c, z0, z1);
-}
 
 // The two same-colour sites (components PX and PX + 2) of a 4-site group r0, given
 // the group one row above (ru) and below (rd), s kappa^2 of the group (c) and the
@@ -170,57 +118,12 @@ __device__ __forceinline__ void colour_rows(float* xa, float* xb, const float* x
     st4(xb, gibbs_upd<1>(rb, ra, rd, cb, eb, w, z2 * zs, z3 * zs, b0, b1));
 }
 
-// wait (bounded) for blocks (waited, upto] of the ring; false if a wait gave up
-__device__ __forceinline__ bool wait_blocks(unsigned long long* bar, unsigned& ph, int& waited, int upto,
-                                            long long limit_ns)
-{
-    while (waited < upto) {
-        const int q = (waited + 1) & (kNB - 1);
-        if (!mbar_wait(&bar[q], (ph >> q) & 1u, limit_ns)) return false;
-        ph ^= 1u << q;
-        ++waited;
-    }
-    return true;
-}
-
-// a wait gave up: flag the chain (MGMC_ERR_TIMEOUT) and let the copies in flight land
-__device__ __forceinline__ void give_up(CycleState* cs, unsigned long long* bar, unsigned ph, int waited, int issued)
-{
-    atomicOr(&cs->status, kStatusTimeout);
-    __threadfence();
-    for (int k = waited + 1; k <= issued; ++k) {
-        const int q = k & (kNB - 1);
-        if (mbar_wait(&bar[q], (ph >> q) & 1u)) ph ^= 1u << q;
-    }
-}
-
-// the run of a CTA: strips [gs, ge) of one band of chain jb, rows [ya, yb)
-struct Run {
-    int jb, n, nc, x0, ya, yb;
-};
-__device__ __forceinline__ Run next_run(const StreamJob* jobs, int njobs, long long& gs, long long s_end)
-{
-    Run r;
-    r.jb = find_stream_job(jobs, njobs, gs);
-    const StreamJob* J = jobs + r.jb;
-    r.n = J->L.n;
-    r.nc = J->C.n;
-    const int ls = (int)(gs - J->strip0);
-    const int band = ls / J->spb, st0 = ls % J->spb;
-    const long long ge = min(s_end, J->strip0 + (long long)(band + 1) * J->spb);
-    r.ya = kK * st0;
-    r.yb = min(kK * (st0 + (int)(ge - gs)), r.n);
-    r.x0 = kBW * band;
-    gs = ge;
-    return r;
-}
-
 // Forward pass of the finest grids: one launch over all strips of all chains.
 __global__ void __launch_bounds__(kNT, 2)
     k_stream_fwd(const StreamJob* __restrict__ jobs, const StreamMaps* __restrict__ maps, int njobs, long long total)
 {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
-    unsigned char* sm = smem_aligned(smem_dyn);
+    unsigned char* sm = smem_align_up<128>(smem_dyn);
     unsigned long long* bar = reinterpret_cast<unsigned long long*>(sm);
     float* const Xr = reinterpret_cast<float*>(sm + kHead);
     float* const Kr = Xr + kRing * kSX;
@@ -237,7 +140,7 @@ __global__ void __launch_bounds__(kNT, 2)
     const long long s_beg = total * blockIdx.x / gridDim.x, s_end = total * (blockIdx.x + 1) / gridDim.x;
     unsigned ph = 0;  // bit q: parity of the next phase of mbarrier q
     for (long long gs = s_beg; gs < s_end;) {
-        const Run run = next_run(jobs, njobs, gs, s_end);
+        const Run run = next_run<kK, kBW>(jobs, njobs, gs, s_end);
         const StreamJob* J = jobs + run.jb;
         const int n = run.n, nc = run.nc, x0 = run.x0, ya = run.ya, yb = run.yb;
         // coarse rows J with centre row 2J + 1 in [ya, yb)
@@ -326,9 +229,9 @@ __global__ void __launch_bounds__(kNT, 2)
         for (int s = 0; s < S; ++s) {
             const int R = ya - 2 + kK * s;
             // blocks up to 2s + 2 (rows up to R + 16) are in shared memory
-            const bool ok = wait_blocks(bar, ph, waited, min(2 * s + 2, KB), cs.wait_ns);
+            const bool ok = wait_blocks<kNB>(bar, ph, waited, min(2 * s + 2, KB), cs.wait_ns);
             if (__syncthreads_or(!ok)) {
-                if (tid == 0) give_up(J->cs, bar, ph, waited, issued);
+                if (tid == 0) give_up<kNB>(J->cs, bar, ph, waited, issued);
                 __syncthreads();
                 return;
             }
@@ -392,7 +295,7 @@ __global__ void __launch_bounds__(kNT, 2)
     k_stream_bwd(const StreamJob* __restrict__ jobs, const StreamMaps* __restrict__ maps, int njobs, long long total)
 {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
-    unsigned char* sm = smem_aligned(smem_dyn);
+    unsigned char* sm = smem_align_up<128>(smem_dyn);
     unsigned long long* bar = reinterpret_cast<unsigned long long*>(sm);
     float* const Xr = reinterpret_cast<float*>(sm + kHead);
     float* const Kr = Xr + kRing * kSX;
@@ -409,7 +312,7 @@ __global__ void __launch_bounds__(kNT, 2)
     const long long s_beg = total * blockIdx.x / gridDim.x, s_end = total * (blockIdx.x + 1) / gridDim.x;
     unsigned ph = 0;
     for (long long gs = s_beg; gs < s_end;) {
-        const Run run = next_run(jobs, njobs, gs, s_end);
+        const Run run = next_run<kK, kBW>(jobs, njobs, gs, s_end);
         const StreamJob* J = jobs + run.jb;
         const int n = run.n, x0 = run.x0, ya = run.ya, yb = run.yb;
         // step s completes rows [ya - 4 + 16 s, ya + 12 + 16 s)
@@ -461,9 +364,9 @@ __global__ void __launch_bounds__(kNT, 2)
         for (int s = 0; s < S; ++s) {
             const int R = ya - 2 + kK * s;
             // blocks up to 2s + 2 (psi of row R + 15) are in shared memory
-            const bool ok = wait_blocks(bar, ph, waited, min(2 * s + 2, KB), cs.wait_ns);
+            const bool ok = wait_blocks<kNB>(bar, ph, waited, min(2 * s + 2, KB), cs.wait_ns);
             if (__syncthreads_or(!ok)) {
-                if (tid == 0) give_up(J->cs, bar, ph, waited, issued);
+                if (tid == 0) give_up<kNB>(J->cs, bar, ph, waited, issued);
                 __syncthreads();
                 return;
             }

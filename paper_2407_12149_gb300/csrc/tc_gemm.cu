@@ -111,8 +111,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr unsigned TCOLS = tmem_cols<BN>();
     extern __shared__ __align__(1024) unsigned char smem_dyn[];
     // 128-byte-swizzled operand tiles start on 1024-byte boundaries
-    unsigned char* sm =
-        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
+    unsigned char* sm = smem_align_up<1024>(smem_dyn);
     __shared__ unsigned long long full[kStages], empty[kStages], done;
     __shared__ unsigned tmem_base;
     __shared__ int aborted, issued, consumed;

@@ -14,6 +14,15 @@ using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, 
 EncodeTiled tensor_map_encoder();
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+// p advanced to the next multiple of A bytes (A a power of two), by pointer arithmetic
+// on the shared array itself: rounding the generic address as an integer would make
+// the compiler lose the address space and turn every access through the result into
+// a generic load or store
+template <unsigned A>
+__device__ __forceinline__ unsigned char* smem_align_up(unsigned char* p)
+{
+    return p + ((A - (smem_addr(p) & (A - 1u))) & (A - 1u));
+}
 __device__ __forceinline__ void mbar_init(unsigned long long* bar)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(bar)) : "memory");

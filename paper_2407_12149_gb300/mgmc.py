@@ -37,7 +37,8 @@ class MGMCError(RuntimeError):
 class mgmc_config(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("n_levels", ctypes.c_int), ("nu1", ctypes.c_int),
                 ("nu2", ctypes.c_int), ("precision", ctypes.c_int), ("scale_hd", ctypes.c_int),
-                ("coarse_max_n", ctypes.c_int), ("gibbs", ctypes.c_int), ("disc", ctypes.c_int)]
+                ("coarse_max_n", ctypes.c_int), ("gibbs", ctypes.c_int), ("disc", ctypes.c_int),
+                ("band_min_n", ctypes.c_int)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -72,7 +73,7 @@ _lib = None
 # every symbol include/mgmc.h declares
 EXPORTS = ("mgmc_config_default", "mgmc_create", "mgmc_point_obs_rows", "mgmc_sample", "mgmc_mean_solve",
            "mgmc_qoi_stats", "mgmc_qoi_stats_noalloc", "mgmc_info", "mgmc_level_n", "mgmc_launches_per_cycle", "mgmc_set_profiling",
-           "mgmc_profile_times", "mgmc_create_batch", "mgmc_sample_batch", "mgmc_get_state", "mgmc_destroy",
+           "mgmc_profile_times", "mgmc_set_band_min_n", "mgmc_create_batch", "mgmc_sample_batch", "mgmc_get_state", "mgmc_destroy",
            "mgmc_tc_gemm", "mgmc_unet_create", "mgmc_unet_n_params", "mgmc_unet_get_params",
            "mgmc_unet_set_params", "mgmc_unet_inputs", "mgmc_unet_gradient", "mgmc_unet_train",
            "mgmc_unet_predict", "mgmc_unet_destroy", "mgmc_check_status", "mgmc_set_wait_limit",
@@ -107,6 +108,7 @@ def load():
     L.mgmc_level_n.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     L.mgmc_launches_per_cycle.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]
     L.mgmc_set_profiling.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    L.mgmc_set_band_min_n.argtypes = [ctypes.c_void_p, ctypes.c_int]
     L.mgmc_profile_times.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_int, ctypes.c_void_p]
     L.mgmc_create_batch.argtypes = [ctypes.c_int, ctypes.POINTER(mgmc_config), ctypes.POINTER(mgmc_problem),
                                     ctypes.POINTER(mgmc_allocator), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
@@ -220,9 +222,9 @@ def mgmc_point_obs_rows(dim: int, n: int, xyz: np.ndarray):
 def mgmc_create(dim, n, *, n_levels=0, nu1=1, nu2=1, precision=MGMC_FP64, scale_hd=1, coarse_max_n=0,
                 kappa2=None, kappa2_const=10.0, obs_site=None, obs_w=None, Gamma=None, y=None,
                 qoi_site=None, qoi_w=None, allocator: Optional[TorchAllocator] = None, stream=None, gibbs=0,
-                disc=MGMC_FD):
+                disc=MGMC_FD, band_min_n=0):
     L = load()
-    cfg = mgmc_config(dim, n, n_levels, nu1, nu2, precision, scale_hd, coarse_max_n, gibbs, disc)
+    cfg = mgmc_config(dim, n, n_levels, nu1, nu2, precision, scale_hd, coarse_max_n, gibbs, disc, band_min_n)
     k2 = None if kappa2 is None else np.ascontiguousarray(kappa2, dtype=np.float64).ravel()
     if obs_site is None:
         m, nnz, os_, ow_, G_, y_ = 0, 1, None, None, None, None
@@ -308,6 +310,10 @@ def mgmc_set_profiling(h, enable):
     _check(load().mgmc_set_profiling(h, 1 if enable else 0))
 
 
+def mgmc_set_band_min_n(h, band_min_n):
+    _check(load().mgmc_set_band_min_n(h, int(band_min_n)))
+
+
 def mgmc_profile_times(h, stream=None):
     ms = (ctypes.c_float * 2)()
     _check(load().mgmc_profile_times(h, ms, 2, _stream_handle(stream)))
@@ -328,7 +334,7 @@ class Sampler:
     gibbs=True gives the plain Gibbs sampler of the same posterior (finest-grid sweeps only)."""
 
     def __init__(self, problem, precision: str = "fp64", nu1: int = 1, nu2: int = 1, coarse_max_n: int = 0,
-                 device: int = 0, use_torch_allocator: bool = True, gibbs: bool = False):
+                 device: int = 0, use_torch_allocator: bool = True, gibbs: bool = False, band_min_n: int = 0):
         torch = _torch()
         if not torch.cuda.is_available():
             raise MGMCError(2, "no CUDA device available (the sampler has no CPU fallback)")
@@ -342,7 +348,7 @@ class Sampler:
                              scale_hd=p.scale_hd, coarse_max_n=coarse_max_n, kappa2=p.kappa2,
                              kappa2_const=p.kappa2_const, obs_site=p.obs_site, obs_w=p.obs_w, Gamma=p.Gamma,
                              y=p.y, qoi_site=p.qoi_site, qoi_w=p.qoi_w, allocator=self._alloc,
-                             gibbs=1 if gibbs else 0, disc=getattr(p, "disc", MGMC_FD))
+                             gibbs=1 if gibbs else 0, disc=getattr(p, "disc", MGMC_FD), band_min_n=band_min_n)
 
     def zeros(self):
         torch = _torch()
@@ -377,6 +383,10 @@ class Sampler:
         """Bound of the kernels' staging waits (0 default, < 0 give up at once: tests)."""
         mgmc_set_wait_limit(self.h, limit_ns)
 
+    def set_band_min_n(self, band_min_n: int):
+        """Grids from which the 9-point depths run in the band kernels (mgmc_set_band_min_n)."""
+        mgmc_set_band_min_n(self.h, band_min_n)
+
     def launches_per_cycle(self):
         return mgmc_launches_per_cycle(self.h)
 
@@ -398,8 +408,11 @@ class BatchSampler:
     Chain c uses the Philox chain id c: it reproduces Sampler(problems[c],
     coarse_max_n=coarse_max_n).sample(..., chain=c)."""
 
-    def __init__(self, problems, precision: str = "fp32", coarse_max_n: int = 31, device: int = 0,
-                 use_torch_allocator: bool = True):
+    def __init__(self, problems, precision: str = "fp32", coarse_max_n: Optional[int] = None, device: int = 0,
+                 use_torch_allocator: bool = True, band_min_n: Optional[int] = None, tune_cache=None):
+        """coarse_max_n / band_min_n: explicit values win; else, with tune_cache (an
+        autotune.TuneCache or a path to its JSON file), the cached choice for this batch;
+        else the defaults (31, 0)."""
         torch = _torch()
         if not torch.cuda.is_available():
             raise MGMCError(2, "no CUDA device available (the sampler has no CPU fallback)")
@@ -408,13 +421,18 @@ class BatchSampler:
         self.precision = MGMC_FP32 if precision == "fp32" else MGMC_FP64
         self.dtype = torch.float32 if self.precision == MGMC_FP32 else torch.float64
         self._alloc = TorchAllocator(device) if use_torch_allocator else None
+        from . import autotune
+        if tune_cache is not None and not isinstance(tune_cache, autotune.TuneCache):
+            tune_cache = autotune.TuneCache(str(tune_cache))
+        self.settings = autotune.resolve_settings(self.problems, precision, coarse_max_n, band_min_n, tune_cache)
+        coarse_max_n, band_min_n = self.settings["coarse_max_n"], self.settings["band_min_n"]
         n = len(self.problems)
         cfgs = (mgmc_config * n)()
         probs = (mgmc_problem * n)()
         self._keep = []
         for c, p in enumerate(self.problems):
             cfgs[c] = mgmc_config(p.dim, p.n, p.n_levels, 1, 1, self.precision, p.scale_hd, coarse_max_n, 0,
-                                  p.disc)
+                                  p.disc, band_min_n)
             arrs = {}
             arrs["k2"] = None if p.kappa2 is None else np.ascontiguousarray(p.kappa2, dtype=np.float64)
             if p.obs_site is not None:
@@ -466,6 +484,10 @@ class BatchSampler:
     def set_wait_limit(self, limit_ns: int):
         """Bound of the kernels' staging waits (0 default, < 0 give up at once: tests)."""
         mgmc_set_wait_limit(self.h, limit_ns)
+
+    def set_band_min_n(self, band_min_n: int):
+        """Grids from which the 9-point depths run in the band kernels (mgmc_set_band_min_n)."""
+        mgmc_set_band_min_n(self.h, band_min_n)
 
     def get_state(self, c, x, stream=None):
         """Copy chain c's state into x (device or host tensor of N_c entries)."""

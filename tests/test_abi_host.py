@@ -50,9 +50,11 @@ def test_point_obs_rows_rejects_outside_points(lib):
 
 @pytest.mark.parametrize("kw,msg", [(dict(dim=4, n=7), "dim"), (dict(dim=2, n=30), "2^k - 1"),
                                     (dict(dim=2, n=7, n_levels=9), "n_levels"),
-                                    (dict(dim=2, n=7, precision=5), "precision")])
+                                    (dict(dim=2, n=7, precision=5), "precision"),
+                                    (dict(dim=2, n=7, band_min_n=-1), "band_min_n")])
 def test_create_rejects_bad_config(lib, kw, msg):
     cfg = mgmc.mgmc_config(kw.get("dim", 2), kw.get("n", 7), kw.get("n_levels", 0), 1, 1, kw.get("precision", 0), 1, 0)
+    cfg.band_min_n = kw.get("band_min_n", 0)
     h = ctypes.c_void_p()
     rc = lib.mgmc_create(ctypes.byref(cfg), None, None, None, 10.0, 0, None, None, 1, None, None, 0, None, None,
                          ctypes.byref(h))
