@@ -393,21 +393,21 @@ def run_mine(args):
     if prec == "fp32" and wl.get("dim", 2) == 2:
         from paper_2407_12149_gb300 import autotune
         cands = autotune.band_candidates(ps, 31)
-        if len(cands) > 1:
-            best, tms = autotune.tune_band_min_n(
-                s, cands, timer=lambda smp: autotune.time_cycles(smp, cycles=20, warm=3, seed=seed + 7,
-                                                               device=local))
-            cache = autotune.TuneCache()
-            cache.put(autotune.cache_key(ps, prec), {"coarse_max_n": 31, "band_min_n": best}, tms)
-            try:
-                cache.save()
-            except OSError:
-                pass
-            tuned = {"coarse_max_n": 31, "band_min_n": best,
-                     "ms_per_cycle": {("tiles only" if k == autotune.TILES_ONLY else str(k)): round(v, 4)
-                                      for k, v in tms.items()},
-                     "how": "band_min_n candidates timed on this handle, 20 back-to-back cycles each "
-                            "(CUDA events), the fastest kept and cached"}
+        timer = lambda smp: autotune.time_cycles(smp, cycles=20, warm=3, seed=seed + 7, device=local)  # noqa: E731
+        best, tms = autotune.tune_band_min_n(s, cands, timer=timer) if len(cands) > 1 else (0, {})
+        bt, tth = autotune.tune_coarse_threads(s, timer=timer)
+        cache = autotune.TuneCache()
+        cache.put(autotune.cache_key(ps, prec), {"coarse_max_n": 31, "band_min_n": best, "coarse_threads": bt})
+        try:
+            cache.save()
+        except OSError:
+            pass
+        tuned = {"coarse_max_n": 31, "band_min_n": best, "coarse_threads": bt,
+                 "ms_per_cycle_band_min_n": {("tiles only" if k == autotune.TILES_ONLY else str(k)): round(v, 4)
+                                             for k, v in tms.items()},
+                 "ms_per_cycle_coarse_threads": {("auto" if k == 0 else str(k)): round(v, 4) for k, v in tth.items()},
+                 "how": "candidates timed on this handle, 20 back-to-back cycles each (CUDA events), band "
+                        "threshold first, then the coarse kernel's threads; the fastest kept and cached"}
 
     # --- CPU baseline (rank 0, one GPU only), before the GPU timing ------------
     cpu = None
@@ -472,7 +472,8 @@ def run_mine(args):
         for g in range(ng):
             part = ps[g * gsz:(g + 1) * gsz]
             sg = s if ng == 1 else M.BatchSampler(part, precision=prec, device=local,
-                                                  band_min_n=tuned["band_min_n"] if tuned else None)
+                                                  band_min_n=tuned["band_min_n"] if tuned else None,
+                                                  coarse_threads=tuned["coarse_threads"] if tuned else None)
             groups.append({"s": sg, "stream": torch.cuda.Stream(device=dev) if ng > 1 else stream,
                            "host": xh[g * gsz:(g + 1) * gsz],
                            "qh": torch.zeros(gsz, dtype=torch.float64).pin_memory(),

@@ -278,6 +278,14 @@ mgmc_status mgmc_set_wait_limit(mgmc_handle h, int64_t limit_ns);
  * negative value.  (An autotuner uses it to time the settings on one handle.) */
 mgmc_status mgmc_set_band_min_n(mgmc_handle h, int band_min_n);
 
+/* Threads per CTA of the 2D coarse-grid kernel (one CTA per chain, all grids with
+ * n <= coarse_max_n in shared memory): 0 (default) chooses 1024 while the chains
+ * leave SMs free and 256 once several chains share an SM; else a multiple of 32 in
+ * [64, 1024].  The kernel's arithmetic does not depend on it (the states are bitwise
+ * the same); only the time of its barrier-bound phases does.  The graph is captured
+ * again on the next sampling call.  MGMC_ERR_ARG for other values. */
+mgmc_status mgmc_set_coarse_threads(mgmc_handle h, int threads);
+
 /* Benchmark timing: with enable != 0 the captured cycle records CUDA events
  * around the finest grid's forward sweep and its backward sweep (finest grid
  * above coarse_max_n only).  mgmc_profile_times synchronises the stream given

@@ -1,19 +1,22 @@
 """Run-time choice of a batch's kernel settings, with a cache.
 
-Two settings change how a cycle runs but not what it computes:
+Three settings change how a cycle runs but not what it computes:
   coarse_max_n  grids with n <= coarse_max_n run inside the shared-memory coarse
                 kernel (one CTA per chain, barrier-latency bound), the larger ones in
                 per-depth launches;
   band_min_n    of the 9-point grids below the finest (FP32), those with
                 n >= band_min_n run in the streaming band kernels, the others in the
-                tile kernels (bitwise identical states).
+                tile kernels (bitwise identical states);
+  coarse_threads threads per CTA of the coarse kernel (0: by the chain count; the
+                kernel's arithmetic does not depend on it).
 Which values are fastest depends on the chain count and the grid sizes, so each
 candidate's captured V-cycle is timed with CUDA events over back-to-back cycles
-(states resident on the device) and the fastest kept.  band_min_n candidates are
-timed on one handle (mgmc_set_band_min_n); coarse_max_n candidates each need their
-own handle.  The choice is stored in a JSON cache keyed by (dim, grid sizes,
-precision, chain count) and applied when a BatchSampler is created without explicit
-settings (mgmc.BatchSampler -> mgmc_create_batch).
+(states resident on the device) and the fastest kept.  band_min_n and coarse_threads
+candidates are timed on one handle (mgmc_set_band_min_n, mgmc_set_coarse_threads);
+coarse_max_n candidates each need their own handle.  The choice is stored in a JSON
+cache keyed by (dim, grid sizes, precision, chain count) and applied when a
+BatchSampler is created with that cache and without explicit settings
+(mgmc.BatchSampler -> mgmc_create_batch, then mgmc_set_coarse_threads).
 """
 from __future__ import annotations
 
@@ -24,7 +27,8 @@ from typing import Callable, Dict, Iterable, Optional, Sequence, Tuple
 
 # a band threshold above every grid: the tile kernels only
 TILES_ONLY = 1 << 20
-DEFAULTS = {"coarse_max_n": 31, "band_min_n": 0}
+DEFAULTS = {"coarse_max_n": 31, "band_min_n": 0, "coarse_threads": 0}
+COARSE_THREADS = (0, 128, 256, 512, 1024)
 
 
 def pick_fastest(timings: Dict[int, float]) -> int:
@@ -51,7 +55,8 @@ def default_cache_path() -> str:
 
 
 class TuneCache:
-    """JSON file of {key: {"coarse_max_n": int, "band_min_n": int, "ms": {...}}}."""
+    """JSON file of {key: {"coarse_max_n": int, "band_min_n": int, "coarse_threads": int,
+    "ms": {...}}}."""
 
     def __init__(self, path: Optional[str] = None):
         self.path = path or default_cache_path()
@@ -96,7 +101,8 @@ class TuneCache:
 
 
 def resolve_settings(problems: Sequence, precision: str, coarse_max_n: Optional[int] = None,
-                     band_min_n: Optional[int] = None, cache: Optional[TuneCache] = None) -> dict:
+                     band_min_n: Optional[int] = None, cache: Optional[TuneCache] = None,
+                     coarse_threads: Optional[int] = None) -> dict:
     """Explicit values win; otherwise the cached choice for this batch; otherwise the
     library defaults."""
     out = dict(DEFAULTS)
@@ -108,6 +114,8 @@ def resolve_settings(problems: Sequence, precision: str, coarse_max_n: Optional[
         out["coarse_max_n"] = int(coarse_max_n)
     if band_min_n is not None:
         out["band_min_n"] = int(band_min_n)
+    if coarse_threads is not None:
+        out["coarse_threads"] = int(coarse_threads)
     return out
 
 
@@ -154,6 +162,23 @@ def tune_band_min_n(sampler, candidates: Iterable[int], timer: Optional[Callable
     return best, timings
 
 
+def tune_coarse_threads(sampler, candidates: Iterable[int] = COARSE_THREADS,
+                        timer: Optional[Callable[[object], float]] = None) -> Tuple[int, Dict[int, float]]:
+    """(best thread count, {candidate: ms per cycle}) of the coarse kernel, timed on one
+    handle, which is left at the best value."""
+    cands = sorted({int(c) for c in candidates})
+    if not cands or cands[0] < 0:
+        raise ValueError("coarse thread candidates must be >= 0")
+    timer = timer or time_cycles
+    timings = {}
+    for c in cands:
+        sampler.set_coarse_threads(c)
+        timings[c] = float(timer(sampler))
+    best = pick_fastest(timings)
+    sampler.set_coarse_threads(best)
+    return best, timings
+
+
 def time_batch_cycle(problems: Sequence, coarse_max_n: int, precision: str = "fp32", cycles: int = 20,
                      warm: int = 3, device: int = 0, seed: int = 1, band_min_n: int = 0) -> float:
     """Milliseconds per V-cycle of a new batch with this coarse threshold."""
@@ -186,8 +211,9 @@ def autotune(problems: Sequence, precision: str = "fp32", coarse_candidates: Ite
              cache: Optional[TuneCache] = None, cycles: int = 20, warm: int = 3, device: int = 0,
              make_sampler: Optional[Callable] = None, timer: Optional[Callable[[object], float]] = None) -> dict:
     """Time every coarse_max_n candidate (its own handle) and, on each, every band
-    threshold (same handle); store the fastest pair in the cache (if given) and return
-    {"coarse_max_n", "band_min_n", "ms": {"c/b": ms}}.  make_sampler(problems, c)
+    threshold and then every coarse thread count (same handle); store the fastest
+    combination in the cache (if given) and return {"coarse_max_n", "band_min_n",
+    "coarse_threads", "ms": {...}}.  make_sampler(problems, c)
     and timer(sampler) replace the GPU parts (tests)."""
     if make_sampler is None:
         from .mgmc import BatchSampler
@@ -204,14 +230,18 @@ def autotune(problems: Sequence, precision: str = "fp32", coarse_candidates: Ite
         s = make_sampler(problems, c)
         try:
             b, ms = tune_band_min_n(s, band_candidates(problems, c), timer=timer)
+            t, tms = tune_coarse_threads(s, timer=timer)
         finally:
             s.close()
         for k, v in ms.items():
-            all_ms[f"{c}/{k}"] = v
-        if best is None or ms[b] < best[2]:
-            best = (c, b, ms[b])
-    out = {"coarse_max_n": best[0], "band_min_n": best[1], "ms": all_ms}
+            all_ms[f"{c}/band {k}"] = v
+        for k, v in tms.items():
+            all_ms[f"{c}/threads {k}"] = v
+        if best is None or tms[t] < best[3]:
+            best = (c, b, t, tms[t])
+    out = {"coarse_max_n": best[0], "band_min_n": best[1], "coarse_threads": best[2], "ms": all_ms}
     if cache is not None:
-        cache.put(cache_key(problems, precision), {"coarse_max_n": best[0], "band_min_n": best[1]}, all_ms)
+        cache.put(cache_key(problems, precision),
+                  {"coarse_max_n": best[0], "band_min_n": best[1], "coarse_threads": best[2]}, all_ms)
         cache.save()
     return out

@@ -125,6 +125,7 @@ struct mgmc_ctx {
     int stream_ctas = 0;
     // FP32 9-point grids below the finest: the streaming band kernels (stream9.cu) at the
     // depths whose grids all have n >= band_min_n, per depth
+    int coarse_threads = 0;   // threads of the batched coarse kernel (0: by the chain count)
     std::vector<char> s9_ok, s9_use;
     std::vector<int> s9_minn;   // smallest grid of the depth
     std::vector<void*> jobs_s9, maps_s9;
@@ -411,7 +412,8 @@ void enqueue_cycle_batch(mgmc_ctx* h, cudaStream_t s, int& launches)
     // grids), 256 once several chains share an SM
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-    const int coarse_threads = (!h->is_batch() || nc <= 2 * sms) ? 1024 : 256;
+    const int coarse_threads =
+        h->coarse_threads > 0 ? h->coarse_threads : ((!h->is_batch() || nc <= 2 * sms) ? 1024 : 256);
     launch_coarse_batch<T>((const CoarseJob<T>*)h->jobs_coarse, nc, coarse_threads, h->batch_coarse_smem, s, launches);
     for (int d = h->n_depth - 1; d >= 0; --d) {
         if (prof && d == 0) cudaEventRecordWithFlags(h->ev[2], s, cudaEventRecordExternal);
@@ -980,6 +982,22 @@ mgmc_status mgmc_set_band_min_n(mgmc_handle h, int band_min_n)
     const std::vector<char> before = h->s9_use;
     apply_band_min(h);
     if (h->exec && h->s9_use != before) {
+        CUDA_TRY(cudaDeviceSynchronize());
+        cudaGraphExecDestroy(h->exec);
+        h->exec = nullptr;
+    }
+    return MGMC_OK;
+}
+
+mgmc_status mgmc_set_coarse_threads(mgmc_handle h, int threads)
+{
+    if (!h) return fail(MGMC_ERR_ARG, "handle is NULL");
+    if (threads != 0 && (threads < 64 || threads > 1024 || threads % 32 != 0))
+        return fail(MGMC_ERR_ARG, "coarse threads must be 0 or a multiple of 32 in [64, 1024]");
+    CUDA_TRY(cudaSetDevice(h->device));
+    if (threads == h->coarse_threads) return MGMC_OK;
+    h->coarse_threads = threads;
+    if (h->exec) {
         CUDA_TRY(cudaDeviceSynchronize());
         cudaGraphExecDestroy(h->exec);
         h->exec = nullptr;

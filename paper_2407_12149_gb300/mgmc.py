@@ -73,7 +73,7 @@ _lib = None
 # every symbol include/mgmc.h declares
 EXPORTS = ("mgmc_config_default", "mgmc_create", "mgmc_point_obs_rows", "mgmc_sample", "mgmc_mean_solve",
            "mgmc_qoi_stats", "mgmc_qoi_stats_noalloc", "mgmc_info", "mgmc_level_n", "mgmc_launches_per_cycle", "mgmc_set_profiling",
-           "mgmc_profile_times", "mgmc_set_band_min_n", "mgmc_create_batch", "mgmc_sample_batch", "mgmc_get_state", "mgmc_destroy",
+           "mgmc_profile_times", "mgmc_set_band_min_n", "mgmc_set_coarse_threads", "mgmc_create_batch", "mgmc_sample_batch", "mgmc_get_state", "mgmc_destroy",
            "mgmc_tc_gemm", "mgmc_unet_create", "mgmc_unet_n_params", "mgmc_unet_get_params",
            "mgmc_unet_set_params", "mgmc_unet_inputs", "mgmc_unet_gradient", "mgmc_unet_train",
            "mgmc_unet_predict", "mgmc_unet_destroy", "mgmc_check_status", "mgmc_set_wait_limit",
@@ -109,6 +109,7 @@ def load():
     L.mgmc_launches_per_cycle.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]
     L.mgmc_set_profiling.argtypes = [ctypes.c_void_p, ctypes.c_int]
     L.mgmc_set_band_min_n.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    L.mgmc_set_coarse_threads.argtypes = [ctypes.c_void_p, ctypes.c_int]
     L.mgmc_profile_times.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_int, ctypes.c_void_p]
     L.mgmc_create_batch.argtypes = [ctypes.c_int, ctypes.POINTER(mgmc_config), ctypes.POINTER(mgmc_problem),
                                     ctypes.POINTER(mgmc_allocator), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
@@ -314,6 +315,10 @@ def mgmc_set_band_min_n(h, band_min_n):
     _check(load().mgmc_set_band_min_n(h, int(band_min_n)))
 
 
+def mgmc_set_coarse_threads(h, threads):
+    _check(load().mgmc_set_coarse_threads(h, int(threads)))
+
+
 def mgmc_profile_times(h, stream=None):
     ms = (ctypes.c_float * 2)()
     _check(load().mgmc_profile_times(h, ms, 2, _stream_handle(stream)))
@@ -387,6 +392,10 @@ class Sampler:
         """Grids from which the 9-point depths run in the band kernels (mgmc_set_band_min_n)."""
         mgmc_set_band_min_n(self.h, band_min_n)
 
+    def set_coarse_threads(self, threads: int):
+        """Threads per CTA of the coarse-grid kernel (mgmc_set_coarse_threads; 0 = automatic)."""
+        mgmc_set_coarse_threads(self.h, threads)
+
     def launches_per_cycle(self):
         return mgmc_launches_per_cycle(self.h)
 
@@ -409,10 +418,11 @@ class BatchSampler:
     coarse_max_n=coarse_max_n).sample(..., chain=c)."""
 
     def __init__(self, problems, precision: str = "fp32", coarse_max_n: Optional[int] = None, device: int = 0,
-                 use_torch_allocator: bool = True, band_min_n: Optional[int] = None, tune_cache=None):
-        """coarse_max_n / band_min_n: explicit values win; else, with tune_cache (an
-        autotune.TuneCache or a path to its JSON file), the cached choice for this batch;
-        else the defaults (31, 0)."""
+                 use_torch_allocator: bool = True, band_min_n: Optional[int] = None, tune_cache=None,
+                 coarse_threads: Optional[int] = None):
+        """coarse_max_n / band_min_n / coarse_threads: explicit values win; else, with
+        tune_cache (an autotune.TuneCache or a path to its JSON file), the cached choice for
+        this batch; else the defaults (31, 0, 0)."""
         torch = _torch()
         if not torch.cuda.is_available():
             raise MGMCError(2, "no CUDA device available (the sampler has no CPU fallback)")
@@ -424,7 +434,8 @@ class BatchSampler:
         from . import autotune
         if tune_cache is not None and not isinstance(tune_cache, autotune.TuneCache):
             tune_cache = autotune.TuneCache(str(tune_cache))
-        self.settings = autotune.resolve_settings(self.problems, precision, coarse_max_n, band_min_n, tune_cache)
+        self.settings = autotune.resolve_settings(self.problems, precision, coarse_max_n, band_min_n, tune_cache,
+                                                  coarse_threads=coarse_threads)
         coarse_max_n, band_min_n = self.settings["coarse_max_n"], self.settings["band_min_n"]
         n = len(self.problems)
         cfgs = (mgmc_config * n)()
@@ -455,6 +466,8 @@ class BatchSampler:
         _check(load().mgmc_create_batch(n, cfgs, probs, ctypes.byref(self._alloc.struct) if self._alloc else None,
                                         _stream_handle(None), ctypes.byref(h)))
         self.h = h
+        if self.settings.get("coarse_threads"):
+            mgmc_set_coarse_threads(self.h, self.settings["coarse_threads"])
 
     def zeros(self):
         torch = _torch()
@@ -488,6 +501,10 @@ class BatchSampler:
     def set_band_min_n(self, band_min_n: int):
         """Grids from which the 9-point depths run in the band kernels (mgmc_set_band_min_n)."""
         mgmc_set_band_min_n(self.h, band_min_n)
+
+    def set_coarse_threads(self, threads: int):
+        """Threads per CTA of the coarse-grid kernel (mgmc_set_coarse_threads; 0 = by chain count)."""
+        mgmc_set_coarse_threads(self.h, threads)
 
     def get_state(self, c, x, stream=None):
         """Copy chain c's state into x (device or host tensor of N_c entries)."""

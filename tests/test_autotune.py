@@ -46,6 +46,9 @@ class _FakeSampler:
         self.band = v
         self.seen.append(v)
 
+    def set_coarse_threads(self, v):
+        self.threads = v
+
     def close(self):
         self.closed = True
 
@@ -86,16 +89,21 @@ def test_autotune_stores_the_fastest_pair_and_resolve_applies_it(tmp_path):
         made.append(s)
         return s
 
+    # thread counts: 256 is 0.05 ms faster than the others
+    def timer(smp):
+        t = getattr(smp, "threads", None)
+        return smp.table[smp.band] - (0.05 if t == 256 else 0.0)
+
     cache = autotune.TuneCache(str(path))
-    out = autotune.autotune(ps, "fp32", coarse_candidates=(31, 15), cache=cache, make_sampler=make,
-                            timer=lambda smp: smp.table[smp.band])
-    assert (out["coarse_max_n"], out["band_min_n"]) == (31, 255)
-    assert all(s.closed for s in made) and len(out["ms"]) == 11
+    out = autotune.autotune(ps, "fp32", coarse_candidates=(31, 15), cache=cache, make_sampler=make, timer=timer)
+    assert (out["coarse_max_n"], out["band_min_n"], out["coarse_threads"]) == (31, 255, 256)
+    assert all(s.closed for s in made) and len(out["ms"]) == 11 + 2 * len(autotune.COARSE_THREADS)
     # a fresh cache object reads the file back; explicit values win over it
     c2 = autotune.TuneCache(str(path))
-    assert c2.get(autotune.cache_key(ps, "fp32")) == {"coarse_max_n": 31, "band_min_n": 255}
-    assert autotune.resolve_settings(ps, "fp32", cache=c2) == {"coarse_max_n": 31, "band_min_n": 255}
-    assert autotune.resolve_settings(ps, "fp32", band_min_n=0, cache=c2) == {"coarse_max_n": 31, "band_min_n": 0}
+    best = {"coarse_max_n": 31, "band_min_n": 255, "coarse_threads": 256}
+    assert c2.get(autotune.cache_key(ps, "fp32")) == best
+    assert autotune.resolve_settings(ps, "fp32", cache=c2) == best
+    assert autotune.resolve_settings(ps, "fp32", band_min_n=0, cache=c2) == dict(best, band_min_n=0)
     assert autotune.resolve_settings(ps, "fp64", cache=c2) == autotune.DEFAULTS
     assert autotune.resolve_settings(ps, "fp32") == autotune.DEFAULTS
 

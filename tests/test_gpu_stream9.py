@@ -103,3 +103,23 @@ def test_band_kernel_wait_that_gives_up_reports_timeout(torch_mod):
     s.close()
     xo, _ = _orc(p).sample(10, 7)
     assert np.abs(x.double().numpy() - xo).max() <= 2e-4 * np.sqrt(np.mean(xo ** 2))
+
+
+def test_coarse_kernel_thread_count_does_not_change_the_states(torch_mod):
+    """mgmc_set_coarse_threads (an autotuned launch setting) leaves the arithmetic alone."""
+    torch = torch_mod
+    from paper_2407_12149_gb300.mgmc import BatchSampler
+    ps = [inputs.make_problem(f"ct{c}", 2, n, kappa2_seed=900 + c, m=8, obs_seed=910 + c, qoi_cells=16)
+          for c, n in enumerate([127, 255, 127, 63])]
+    out = []
+    for threads in (0, 128, 256, 1024):
+        b = BatchSampler(ps, precision="fp32", coarse_threads=threads)
+        xs = b.zeros()
+        q = torch.zeros(len(ps) * 5, dtype=torch.float64, device="cuda")
+        b.sample(xs, 5, 13, qoi=q)
+        torch.cuda.synchronize()
+        out.append((xs, q))
+        b.close()
+    for xs, q in out[1:]:
+        assert all(torch.equal(a, c) for a, c in zip(xs, out[0][0]))
+        assert torch.equal(q, out[0][1])
