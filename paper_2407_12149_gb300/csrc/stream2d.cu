@@ -15,7 +15,10 @@
 //            sweep with ω = 1);
 //   backward theta += P psi on [R, R+16), black on [R-1, R+15), red on
 //            [R-2, R+14), store of the final rows [R-2, R+14) (Alg. 1
-//            prolongation and post-smoothing, colours in reverse order);
+//            prolongation and post-smoothing, colours in reverse order); the
+//            red phase of a step runs in the next step's first barrier
+//            interval, beside that step's prolongation (their rows are
+//            disjoint), so a step has two barriers;
 // so every value a phase reads is the one a global colour sweep gives.  Only
 // the first step of a run recomputes rows above the run, and across a band
 // edge each colour phase updates the halo one column further than the next
@@ -356,31 +359,52 @@ __global__ void __launch_bounds__(kNT, 2)
             tma_load_2d(Kr + q * kBK * kSX, mk, x0, prw, &bar[q]);
             tma_load_2d(Pr + q * kPK * kPX, mp, x0 >> 1, jcb + kPK * k + 1, &bar[q]);
         };
+        // red on step t's rows ja - 2 (even, parity 0) and ja - 1 (odd, parity 1) with the
+        // noise z; then their final states
+        auto red_step = [&](int t, float z0, float z1, float z2, float z3) {
+            const int ja = ya - 2 + kK * t + 2 * rp;
+            const int oZ = xrow(ja - 3), oA = xrow(ja - 2), oB = xrow(ja - 1), oC = xrow(ja);
+            const bool va = (unsigned)(ja - 2) < (unsigned)n, vb = (unsigned)(ja - 1) < (unsigned)n;
+            const float4 ra = ld4(Xr + oA), rb = ld4(Xr + oB), ru = ld4(Xr + oZ), rd = ld4(Xr + oC);
+            const float4 ca = ld4(Kr + oA), cb = ld4(Kr + oB);
+            const float ea = Xr[oA - 1], eb = Xr[oB + 4];
+            const float4 na = gibbs_upd<0>(ra, ru, rb, ca, ea, w, z0 * zs, z1 * zs, va && cr0, va && cr1);
+            const float4 nb = gibbs_upd<1>(rb, ra, rd, cb, eb, w, z2 * zs, z3 * zs, vb && cr2, vb && cr3);
+            st4(Xr + oA, na);
+            st4(Xr + oB, nb);
+            if (hasS && ja - 2 >= ya && ja - 2 < yb) st4(xout + pitch * (ja - 2), na);
+            if (hasS && ja - 1 >= ya && ja - 1 < yb) st4(xout + pitch * (ja - 1), nb);
+        };
         fence_proxy_async();
         __syncthreads();
         int issued = min(KB, 4), waited = -1;
         if (tid == 0)
             for (int k = 0; k <= issued; ++k) issue(k);
+        // noise drawn one barrier interval ahead of its use: the black blocks of step s in
+        // the first interval of step s (of step 0 here), the red blocks of step s in the
+        // black phase of step s
+        float zb0, zb1, zb2, zb3, zr0 = 0.f, zr1 = 0.f, zr2 = 0.f, zr3 = 0.f;
+        draw_k(ctr, pair, K, zb0, zb1);
+        draw_k(ctr, pair + drow + 1, K, zb2, zb3);
         for (int s = 0; s < S; ++s) {
             const int R = ya - 2 + kK * s;
-            // blocks up to 2s + 2 (psi of row R + 15) are in shared memory
+            // blocks up to 2s + 2 (psi of row R + 15) are in shared memory; the barrier also
+            // ends the black phase of step s - 1
             const bool ok = wait_blocks<kNB>(bar, ph, waited, min(2 * s + 2, KB), cs.wait_ns);
             if (__syncthreads_or(!ok)) {
                 if (tid == 0) give_up<kNB>(J->cs, bar, ph, waited, issued);
                 __syncthreads();
                 return;
             }
-            // blocks 2s - 3 and 2s - 2 are no longer read: blocks 2s + 5, 2s + 6 go into their slots
-            if (tid == 0)
-                for (int k = 2 * s + 5; k <= min(2 * s + 6, KB); ++k) issue(k);
-            issued = max(issued, min(2 * s + 6, KB));
             const int ja = R + 2 * rp;  // even row of the thread
-            const int oZ = xrow(ja - 3), oA = xrow(ja - 2), oB = xrow(ja - 1), oC = xrow(ja), oD = xrow(ja + 1);
+            const int oA = xrow(ja - 2), oB = xrow(ja - 1), oC = xrow(ja), oD = xrow(ja + 1);
             const bool vc = (unsigned)ja < (unsigned)n, vd = (unsigned)(ja + 1) < (unsigned)n,
-                       vb = (unsigned)(ja - 1) < (unsigned)n, va = (unsigned)(ja - 2) < (unsigned)n;
+                       vb = (unsigned)(ja - 1) < (unsigned)n;
             // theta' + P psi on rows ja (even: coarse rows ja/2 - 1, ja/2 with weight 1/2) and
             // ja + 1 (odd: coarse row ja/2, weight 1); fine site gx + c takes the coarse columns
-            // a - 1, a (c = 0), a (c = 1), a, a + 1 (c = 2), a + 1 (c = 3), a = gx / 2
+            // a - 1, a (c = 0), a (c = 1), a, a + 1 (c = 2), a + 1 (c = 3), a = gx / 2.
+            // Alongside, the red phase of step s - 1 (rows up to R - 3; its black neighbours are
+            // final since the barrier)
             if (hasP) {
                 const float* q0 = Pr + prow((ja >> 1) - 1);
                 const float* q1 = Pr + prow(ja >> 1);
@@ -424,28 +448,32 @@ __global__ void __launch_bounds__(kNT, 2)
                     st4(Xr + oD, x);
                 }
             }
-            __syncthreads();
-            // black on rows ja - 1 (odd, parity 0) and ja (even, parity 1)
-            colour_rows(Xr + oB, Xr + oC, Xr + oA, Xr + oD, Kr + oB, Kr + oC, w, zs, ctr, pair, pair + drow + 1, K, vb && cb0, vb && cb1, vc && cb2, vc && cb3);
-            __syncthreads();
-            // red on rows ja - 2 (even, parity 0) and ja - 1 (odd, parity 1); then their final states
-            {
-                float z0, z1, z2, z3;
-                draw_k(ctr, pair - drow, K, z0, z1);
-                draw_k(ctr, pair + 1, K, z2, z3);
-                const float4 ra = ld4(Xr + oA), rb = ld4(Xr + oB), ru = ld4(Xr + oZ), rd = ld4(Xr + oC);
-                const float4 ca = ld4(Kr + oA), cb = ld4(Kr + oB);
-                const float ea = Xr[oA - 1], eb = Xr[oB + 4];
-                const float4 na = gibbs_upd<0>(ra, ru, rb, ca, ea, w, z0 * zs, z1 * zs, va && cr0, va && cr1);
-                const float4 nb = gibbs_upd<1>(rb, ra, rd, cb, eb, w, z2 * zs, z3 * zs, vb && cr2, vb && cr3);
-                st4(Xr + oA, na);
-                st4(Xr + oB, nb);
-                if (hasS && ja - 2 >= ya && ja - 2 < yb) st4(xout + pitch * (ja - 2), na);
-                if (hasS && ja - 1 >= ya && ja - 1 < yb) st4(xout + pitch * (ja - 1), nb);
+            if (s > 0) {
+                red_step(s - 1, zr0, zr1, zr2, zr3);
+                draw_k(ctr, pair, K, zb0, zb1);
+                draw_k(ctr, pair + drow + 1, K, zb2, zb3);
             }
             fence_proxy_async();
+            __syncthreads();
+            // blocks 2s - 3 and 2s - 2 were last read by the red phase above: blocks 2s + 5,
+            // 2s + 6 go into their slots
+            if (tid == 0)
+                for (int k = 2 * s + 5; k <= min(2 * s + 6, KB); ++k) issue(k);
+            issued = max(issued, min(2 * s + 6, KB));
+            // black on rows ja - 1 (odd, parity 0) and ja (even, parity 1)
+            {
+                const float4 ra = ld4(Xr + oB), rb = ld4(Xr + oC), ru = ld4(Xr + oA), rd = ld4(Xr + oD);
+                const float4 ca = ld4(Kr + oB), cb = ld4(Kr + oC);
+                const float ea = Xr[oB - 1], eb = Xr[oC + 4];
+                st4(Xr + oB, gibbs_upd<0>(ra, ru, rb, ca, ea, w, zb0 * zs, zb1 * zs, vb && cb0, vb && cb1));
+                st4(Xr + oC, gibbs_upd<1>(rb, ra, rd, cb, eb, w, zb2 * zs, zb3 * zs, vc && cb2, vc && cb3));
+            }
+            draw_k(ctr, pair - drow, K, zr0, zr1);
+            draw_k(ctr, pair + 1, K, zr2, zr3);
             pair += dstep;
         }
+        __syncthreads();
+        red_step(S - 1, zr0, zr1, zr2, zr3);
     }
 }
 

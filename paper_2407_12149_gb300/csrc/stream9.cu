@@ -20,7 +20,8 @@
 //   backward (prolongation and post-smoothing, colours in reverse order)
 //     theta += P psi on [R, R+16), P0 colour (1,0) on the even rows of
 //     [R-1, R+15), P1 (0,1) and P2 (1,1) on the odd rows of [R-2, R+14), P3
-//     (0,0) on the even rows of [R-3, R+13).
+//     (0,0) on the even rows of [R-3, R+13); P3 of a step runs in the next
+//     step's first barrier interval, beside its prolongation (disjoint rows).
 // Thread (g, rp) owns the 4-site group g on the even row a = R + 2 rp (P0), the
 // odd row a - 1 (P1, P2) and the even row a - 2 (P3), and the residual rows
 // a - 3 and a - 2; it stores the final rows a - 1 and a - 2.
@@ -428,23 +429,34 @@ __global__ void __launch_bounds__(kNT, 2)
         if (tid == 0)
             for (int k = 0; k <= issued; ++k) issue(k);
         int r3 = 2 * rp;  // ring row of a - 3 for the thread's even row a of step 0
+        auto roff = [&](int r, int i) { return wrap(r + i, kRing) * kSX + 4 + 4 * g; };
+        // P3, colour (0,0), on row a - 2 of the step whose row a - 3 sits in ring row r;
+        // then its final state
+        auto p3_step = [&](int a, int r, float z0, float z1) {
+            const bool v2 = (unsigned)(a - 2) < (unsigned)n;
+            const int o3 = roff(r, 0), o2 = roff(r, 1), o1 = roff(r, 2);
+            Rows9 q;
+            load9<0>(q, Xr, Cr, Fr, o3, o2, o1);
+            const float4 o = upd9<0>(q, z0 * zs, z1 * zs, v2 && c30, v2 && c32);
+            st4(Xr + o2, o);
+            if (hasS && a - 2 >= ya && a - 2 < yb) st4(xout + pitch * (a - 2), o);
+        };
+        // noise drawn one barrier interval ahead of its use: P0 and P1 of step s in the first
+        // interval of step s, P2 in P0, P3 in P1
+        float z30 = 0.f, z31 = 0.f;
         for (int s = 0; s < S; ++s) {
             const int R = ya - 4 + kK * s;
+            // the barrier also ends P2 of step s - 1
             const bool ok = wait_blocks<kNB>(bar, ph, waited, min(2 * s + 2, KB), cs.wait_ns);
             if (__syncthreads_or(!ok)) {
                 if (tid == 0) give_up<kNB>(J->cs, bar, ph, waited, issued);
                 __syncthreads();
                 return;
             }
-            if (s > 0 && tid == 0)
-                for (int k = 2 * s + 3; k <= min(2 * s + 4, KB); ++k) issue(k);
-            if (s > 0) issued = max(issued, min(2 * s + 4, KB));
             const int a = R + 2 * rp;  // even row of the thread
-            const int o3 = r3 * kSX + 4 + 4 * g;
-            const int o2 = wrap(r3 + 1, kRing) * kSX + 4 + 4 * g, o1 = wrap(r3 + 2, kRing) * kSX + 4 + 4 * g;
-            const int o0 = wrap(r3 + 3, kRing) * kSX + 4 + 4 * g, op = wrap(r3 + 4, kRing) * kSX + 4 + 4 * g;
+            const int o2 = roff(r3, 1), o1 = roff(r3, 2), o0 = roff(r3, 3), op = roff(r3, 4);
             const bool vp = (unsigned)(a + 1) < (unsigned)n, v0 = (unsigned)a < (unsigned)n,
-                       v1 = (unsigned)(a - 1) < (unsigned)n, v2 = (unsigned)(a - 2) < (unsigned)n;
+                       v1 = (unsigned)(a - 1) < (unsigned)n;
             // theta' + P psi on rows a (even: coarse rows a/2 - 1, a/2 with weight 1/2) and
             // a + 1 (odd: coarse row a/2, weight 1); fine site gx + c takes the coarse columns
             // b - 1, b (c = 0), b (c = 1), b, b + 1 (c = 2), b + 1 (c = 3), b = gx / 2
@@ -491,10 +503,21 @@ __global__ void __launch_bounds__(kNT, 2)
                     st4(Xr + op, x);
                 }
             }
+            // alongside the prolongation: P3 of step s - 1 (rows up to R - 4; its neighbours are
+            // final since the barrier)
+            if (s > 0) p3_step(a - kK, wrap(r3 + kRing - kK, kRing), z30, z31);
+            float z00, z01, z10, z11;
+            draw2(ctr, pair + 1, pair - drow, K, z00, z01, z10, z11);
+            fence_proxy_async();
             __syncthreads();
-            // P0, colour (1,0), row a; the noise of P3 (colour (0,0), row a - 2) drawn alongside
-            float z00, z01, z30, z31;
-            draw2(ctr, pair + 1, pair - 2 * drow, K, z00, z01, z30, z31);
+            // blocks 2s - 2 and 2s - 1 were last read by P3 above: blocks 2s + 3, 2s + 4 take
+            // their slots
+            if (s > 0 && tid == 0)
+                for (int k = 2 * s + 3; k <= min(2 * s + 4, KB); ++k) issue(k);
+            if (s > 0) issued = max(issued, min(2 * s + 4, KB));
+            // P0, colour (1,0), row a
+            float z20, z21;
+            draw_k(ctr, pair - drow + 1, K, z20, z21);
             {
                 Rows9 r;
                 load9<1>(r, Xr, Cr, Fr, o1, o0, op);
@@ -502,8 +525,7 @@ __global__ void __launch_bounds__(kNT, 2)
             }
             __syncthreads();
             // P1, colour (0,1), and P2, colour (1,1), on row a - 1
-            float z10, z11, z20, z21;
-            draw2(ctr, pair - drow, pair - drow + 1, K, z10, z11, z20, z21);
+            draw_k(ctr, pair - 2 * drow, K, z30, z31);
             Rows9 r;
             load9<0>(r, Xr, Cr, Fr, o2, o1, o0);
             r.x0 = upd9<0>(r, z10 * zs, z11 * zs, v1 && c10, v1 && c12);
@@ -521,19 +543,11 @@ __global__ void __launch_bounds__(kNT, 2)
                 st4(Xr + o1, o);
                 if (hasS && a - 1 >= ya && a - 1 < yb) st4(xout + pitch * (a - 1), o);
             }
-            __syncthreads();
-            // P3, colour (0,0), row a - 2; then its final state
-            {
-                Rows9 q;
-                load9<0>(q, Xr, Cr, Fr, o3, o2, o1);
-                const float4 o = upd9<0>(q, z30 * zs, z31 * zs, v2 && c30, v2 && c32);
-                st4(Xr + o2, o);
-                if (hasS && a - 2 >= ya && a - 2 < yb) st4(xout + pitch * (a - 2), o);
-            }
-            fence_proxy_async();
             pair += dstep;
             r3 = wrap(r3 + kK, kRing);
         }
+        __syncthreads();
+        p3_step(ya - 4 + kK * (S - 1) + 2 * rp, wrap(r3 + kRing - kK, kRing), z30, z31);
     }
 }
 
