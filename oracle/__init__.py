@@ -75,6 +75,9 @@ def lib():
         L.oracle_normal_pair.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                          ctypes.c_uint32, _c_dbl_p, _c_dbl_p]
         L.oracle_normal_pair.restype = None
+        L.oracle_normal_quad.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                         ctypes.c_uint32, _c_dbl_p]
+        L.oracle_normal_quad.restype = None
         L.oracle_chain_stats.argtypes = [_c_dbl_p, ctypes.c_int64, ctypes.c_double, _c_dbl_p, _c_dbl_p,
                                          _c_dbl_p, _c_dbl_p, ctypes.POINTER(ctypes.c_int64)]
         _lib = L
@@ -230,6 +233,13 @@ def normal_pair(seed, c0, c1, c2, c3):
     z1 = ctypes.c_double()
     lib().oracle_normal_pair(int(seed) & (2**64 - 1), c0, c1, c2, c3, ctypes.byref(z0), ctypes.byref(z1))
     return z0.value, z1.value
+
+
+def normal_quad(seed, c0, c1, c2, c3):
+    """The four normals of one site-noise block (kind 0)."""
+    z = np.zeros(4)
+    lib().oracle_normal_quad(int(seed) & (2**64 - 1), c0, c1, c2, c3, z.ctypes.data_as(_c_dbl_p))
+    return tuple(float(v) for v in z)
 
 
 def chain_stats(series, S=1.5):

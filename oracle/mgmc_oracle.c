@@ -54,13 +54,17 @@
  *   - random numbers: Philox4x32-10 (Salmon et al., SC'11), key = seed,
  *     counter (c0 = pair, c1 = cycle low 32 bits,
  *     c2 = (cycle bits 32..47) | chain << 16, c3 = kind << 24 | level << 16 | slot);
- *     u = (k53 + 0.5) 2^-53 from the top 53 bits of (w0,w1) resp. (w2,w3);
- *     Box-Muller z0 = r cos(2 pi u2), z1 = r sin(2 pi u2).
- *     kind 0 (site noise): pair = ((k n + j) nq + (i >> 2)) * 2 + (i & 1),
- *       nq = (n + 3) / 4, member (i >> 1) & 1; slot = 2 j for the j-th pre
- *       sweep, 2 j + 1 for the j-th post sweep.
- *     kind 1 (low-rank noise z'): pair = k >> 1, member k & 1.
- *     kind 2 (coarsest sample): pair = s >> 1, member s & 1.
+ *     kind 0 (site noise): one block per 4-site group of a grid row,
+ *       c0 = (k n + j) nq + (i >> 2), nq = (n + 3) / 4; its four words give
+ *       two Box-Muller pairs from 32-bit uniforms u = (w + 0.5) 2^-32:
+ *       (w0, w1) for the sites with i even, (w2, w3) for i odd, member
+ *       (i >> 1) & 1, z0 = r cos(2 pi u2), z1 = r sin(2 pi u2),
+ *       r = sqrt(-2 ln u1); slot = 2 j for the j-th pre sweep, 2 j + 1 for
+ *       the j-th post sweep.
+ *     kinds 1 and 2: one Box-Muller pair per block from 53-bit uniforms
+ *       u = (k53 + 0.5) 2^-53 of the top 53 bits of (w0,w1) resp. (w2,w3);
+ *       kind 1 (low-rank noise z'): c0 = k >> 1, member k & 1;
+ *       kind 2 (coarsest sample): c0 = s >> 1, member s & 1.
  *
  * Compile with -ffp-contract=off so that x86 and Arm builds round alike.
  */
@@ -173,6 +177,34 @@ void oracle_normal_pair(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, ui
     double phi = 2.0 * M_PI * u2;
     *z0 = r * cos(phi);
     *z1 = r * sin(phi);
+}
+
+void oracle_normal_quad(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, double z[4])
+{
+    uint32_t ctr[4] = {c0, c1, c2, c3};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t w[4];
+    oracle_philox4x32_10(ctr, key, w);
+    for (int h = 0; h < 2; ++h) {
+        double u1 = ((double)w[2 * h] + 0.5) * 0x1p-32;
+        double u2 = ((double)w[2 * h + 1] + 0.5) * 0x1p-32;
+        double r = sqrt(-2.0 * log(u1));
+        double phi = 2.0 * M_PI * u2;
+        z[2 * h] = r * cos(phi);
+        z[2 * h + 1] = r * sin(phi);
+    }
+}
+
+/* site noise (kind 0) of column i in block c0 of level `level` */
+static double draw_site(const oracle_problem* p, int level, uint32_t slot, uint32_t block, int i)
+{
+    if (!p->noise) return 0.0;
+    uint32_t c1 = (uint32_t)p->cycle;
+    uint32_t c2 = ((uint32_t)(p->cycle >> 32) & 0xFFFFu) | (p->chain << 16);
+    uint32_t c3 = ((uint32_t)level << 16) | slot;
+    double z[4];
+    oracle_normal_quad(p->seed, block, c1, c2, c3, z);
+    return z[2 * (i & 1) + ((i >> 1) & 1)];
 }
 
 static double draw(const oracle_problem* p, uint32_t kind, int level, uint32_t slot,
@@ -397,9 +429,8 @@ static void gs_sweep(const oracle_problem* p, int l, const olevel* L, int dir, d
                 if (zdiag) {
                     z = zdiag[s];
                 } else {
-                    uint32_t pair = (uint32_t)((((int64_t)c[2] * n + c[1]) * nq + (c[0] >> 2)) * 2
-                                               + (c[0] & 1));
-                    z = draw(p, 0u, l, slot, pair, (c[0] >> 1) & 1);
+                    uint32_t block = (uint32_t)(((int64_t)c[2] * n + c[1]) * nq + (c[0] >> 2));
+                    z = draw_site(p, l, slot, block, c[0]);
                 }
             }
             double acc = rhs ? rhs[s] : 0.0;

@@ -93,6 +93,10 @@ double oracle_rel_residual(const oracle_problem* p, const double* x);
 void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 void oracle_normal_pair(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                         double* z0, double* z1);
+/* The four standard normals of one site-noise block (kind 0): two Box-Muller
+ * pairs from 32-bit uniforms u = (w + 0.5) 2^-32 of the Philox words
+ * (w0, w1) -> z[0], z[1] and (w2, w3) -> z[2], z[3]. */
+void oracle_normal_quad(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, double z[4]);
 
 /* Chain statistics: sample mean/variance, lagged autocovariance and the
  * integrated autocorrelation time with Wolff's automatic window (S given).

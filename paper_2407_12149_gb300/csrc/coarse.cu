@@ -167,17 +167,19 @@ __device__ void s_sweep(const DevLevel<T>& L, const CycleState& cs, T* X, const 
     const int n = L.n, S = n + 2;
     const int SZ = DIM == 3 ? S * S * S : S * S;
     const int nq = (n + 3) >> 2;
-    const int npairs = 2 * nq * n * (DIM == 3 ? n : 1);
+    const int nblocks = nq * n * (DIM == 3 ? n : 1);
     if (cs.noise) {
+        // one block per 4-site group of a row: Z[4 b .. 4 b + 3] = the even columns' pair,
+        // then the odd columns' pair
         const uint4 ctr = noise_counter(cs, 0u, 0u, L.level, slot);
         const unsigned k0 = (unsigned)cs.seed, k1 = (unsigned)(cs.seed >> 32);
-        for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
-            const int px = p & 1, q = (p >> 1) % nq;
-            if (4 * q + px >= n) continue;
-            T z0, z1;
-            draw_pair_ctr<T>(ctr, (unsigned)p, k0, k1, z0, z1);
-            Z[2 * p] = z0;
-            Z[2 * p + 1] = z1;
+        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+            T a0, a1, b0, b1;
+            draw_quad_ctr<T>(ctr, (unsigned)b, k0, k1, a0, a1, b0, b1);
+            Z[4 * b] = a0;
+            Z[4 * b + 1] = a1;
+            Z[4 * b + 2] = b0;
+            Z[4 * b + 3] = b1;
         }
         __syncthreads();
     }
@@ -197,9 +199,9 @@ __device__ void s_sweep(const DevLevel<T>& L, const CycleState& cs, T* X, const 
             const bool has1 = i0 + 2 < n;
             T z0 = T(0), z1 = T(0);
             if (cs.noise) {
-                const int pair = (int)((((long long)k * n + j) * nq + q) * 2 + px);
-                z0 = Z[2 * pair];
-                z1 = Z[2 * pair + 1];
+                const int blk = (int)(((long long)k * n + j) * nq + q);
+                z0 = Z[4 * blk + 2 * px];
+                z1 = Z[4 * blk + 2 * px + 1];
             }
             const int ls = sidx<DIM>(S, i0, j, k);
             X[ls] = upd_s<DIM>(L, X, F, CS, SZ, ls, S, z0);

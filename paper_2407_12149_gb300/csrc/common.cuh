@@ -183,6 +183,48 @@ __device__ __forceinline__ void normal_pair(const uint4 w, float& z0, float& z1)
     z1 = -r * s;
 }
 
+// The four normals of one site-noise block (kind 0, one block per 4-site group of a
+// grid row): two Box-Muller pairs from 32-bit uniforms u = (w + 1/2) 2^-32,
+// (w.x, w.y) -> z0, z1 for the even columns of the group, (w.z, w.w) -> z2, z3 for
+// the odd ones.  FP64: u exact; FP32: the FP32 rounding of u, the same reduced
+// angle, accurate logarithm and reciprocal-square-root radius as normal_pair.
+__device__ __forceinline__ void normal_quad(const uint4 w, double& z0, double& z1, double& z2, double& z3)
+{
+    const double r0 = sqrt(-2.0 * log(((double)w.x + 0.5) * 0x1p-32));
+    const double r1 = sqrt(-2.0 * log(((double)w.z + 0.5) * 0x1p-32));
+    double s, c;
+    sincospi(2.0 * (((double)w.y + 0.5) * 0x1p-32), &s, &c);
+    z0 = r0 * c;
+    z1 = r0 * s;
+    sincospi(2.0 * (((double)w.w + 0.5) * 0x1p-32), &s, &c);
+    z2 = r1 * c;
+    z3 = r1 * s;
+}
+__device__ __forceinline__ void normal_quad(const uint4 w, float& z0, float& z1, float& z2, float& z3)
+{
+    const float u1 = fmaf((float)w.x, 0x1p-32f, 0x1p-33f), u2 = fmaf((float)w.y, 0x1p-32f, 0x1p-33f);
+    const float u3 = fmaf((float)w.z, 0x1p-32f, 0x1p-33f), u4 = fmaf((float)w.w, 0x1p-32f, 0x1p-33f);
+    const float t0 = fmaxf(-2.0f * logf(u1), 1e-37f), t1 = fmaxf(-2.0f * logf(u3), 1e-37f);
+    const float r0 = t0 * rsqrtf(t0), r1 = t1 * rsqrtf(t1);
+    float s, c;
+    __sincosf(6.28318530717958648f * (u2 - 0.5f), &s, &c);
+    z0 = -r0 * c;
+    z1 = -r0 * s;
+    __sincosf(6.28318530717958648f * (u4 - 0.5f), &s, &c);
+    z2 = -r1 * c;
+    z3 = -r1 * s;
+}
+
+// the four site normals of block `block` with the counter words c1..c3 and the key in
+// registers (ctr.x is replaced by the block index)
+template <typename T>
+__device__ __forceinline__ void draw_quad_ctr(uint4 ctr, unsigned block, unsigned k0, unsigned k1, T& z0, T& z1,
+                                              T& z2, T& z3)
+{
+    ctr.x = block;
+    normal_quad(philox10(ctr, k0, k1), z0, z1, z2, z3);
+}
+
 // the same draw with the counter words c1..c3 and the key already in registers
 // (ctr.x is replaced by the pair index)
 template <typename T>

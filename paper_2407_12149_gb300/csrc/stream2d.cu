@@ -63,8 +63,10 @@ constexpr int kBoxW = kSX, kBoxH = kBK, kPBoxW = kPX, kPBoxH = kPK;
 constexpr unsigned kBox = kBoxW * kBoxH * 4;
 constexpr unsigned kPBox = kPBoxW * kPBoxH * 4;
 constexpr size_t kHead = 256;      // mbarriers; also keeps the reads one float left of the ring inside shared memory
-constexpr size_t kFwdSmem = 128 + kHead + 4 * (2 * (size_t)kRing * kSX + (size_t)kRRing * kRW);
-constexpr size_t kBwdSmem = 128 + kHead + 4 * (2 * (size_t)kRing * kSX + (size_t)kPRing * kPX);
+// hand-off of site normals between the threads of consecutive rows: [step parity][rp][g][2]
+constexpr int kZx = 2 * (kK / 2) * kNG * 2;
+constexpr size_t kFwdSmem = 128 + kHead + 4 * (2 * (size_t)kRing * kSX + (size_t)kRRing * kRW + kZx);
+constexpr size_t kBwdSmem = 128 + kHead + 4 * (2 * (size_t)kRing * kSX + (size_t)kPRing * kPX + kZx);
 static_assert(kNT <= 1024 && kNT >= 8 * 32, "thread layout: the restriction needs 8 x 32 threads");
 static_assert(kRing == 64 && kRRing == 64 && kPRing == 32 && kNB == 8, "power-of-two rings");
 static_assert(kBox % 128 == 0 && kPBox % 128 == 0, "TMA destinations on 128-byte boundaries");
@@ -103,24 +105,6 @@ __device__ __forceinline__ float4 residual4(float4 r0, float4 ru, float4 rd, flo
                        0.0f - fine_ax(r0.w, ru.w, r0.z, er, rd.w, c.w, w));
 }
 
-// The red (forward: phase A; backward: the second colour) or black phase of a
-// thread: its group on an even row a (sites of parity 0, Philox block pa) and the
-// odd row below it (parity 1, block pb).  xa/xb: the two rows, xu: the row above
-// a, xd: the row below b; ka/kb: their operator rows.  Both rows are read before
-// either is written: b reads only the other colour of row a.
-__device__ __forceinline__ void colour_rows(float* xa, float* xb, const float* xu, const float* xd, const float* ka,
-                                            const float* kb, float w, float zs, uint4 ctr, unsigned pa, unsigned pb,
-                                            const RoundKeys& K, bool a0, bool a1, bool b0, bool b1)
-{
-    float z0, z1, z2, z3;
-    draw_k(ctr, pa, K, z0, z1);
-    draw_k(ctr, pb, K, z2, z3);
-    const float4 ra = ld4(xa), rb = ld4(xb), ru = ld4(xu), rd = ld4(xd), ca = ld4(ka), cb = ld4(kb);
-    const float ea = xa[-1], eb = xb[4];
-    st4(xa, gibbs_upd<0>(ra, ru, rb, ca, ea, w, z0 * zs, z1 * zs, a0, a1));
-    st4(xb, gibbs_upd<1>(rb, ra, rd, cb, eb, w, z2 * zs, z3 * zs, b0, b1));
-}
-
 // Forward pass of the finest grids: one launch over all strips of all chains.
 __global__ void __launch_bounds__(kNT, 2)
     k_stream_fwd(const StreamJob* __restrict__ jobs, const StreamMaps* __restrict__ maps, int njobs, long long total)
@@ -131,6 +115,7 @@ __global__ void __launch_bounds__(kNT, 2)
     float* const Xr = reinterpret_cast<float*>(sm + kHead);
     float* const Kr = Xr + kRing * kSX;
     float* const Rr = Kr + kRing * kSX;
+    float* const Zx = Rr + kRRing * kRW;
     const int tid = threadIdx.x;
     const int g = tid % kNG, rp = tid / kNG;  // group g of rows R + 2 rp (even) and R + 2 rp + 1 of each step
     pdl_launch_dependents();
@@ -166,10 +151,14 @@ __global__ void __launch_bounds__(kNT, 2)
         const bool cr2 = col(gx + 1, x0 - 2, x0 + kBW + 2), cr3 = col(gx + 3, x0 - 2, x0 + kBW + 2);
         const bool cb0 = col(gx, x0 - 1, x0 + kBW + 1), cb1 = col(gx + 2, x0 - 1, x0 + kBW + 1);
         const bool cb2 = col(gx + 1, x0 - 1, x0 + kBW + 1), cb3 = col(gx + 3, x0 - 1, x0 + kBW + 1);
-        // Philox block of the red item of the even row in step 0 (row ya - 2 + 2 rp); the odd
-        // row's block is 2 nq + 1 further, the black items' rows are one above
-        unsigned pair = (unsigned)(((long long)(ya - 2 + 2 * rp) * nq + (gx >> 2)) * 2);
-        const unsigned dstep = (unsigned)(2 * kK * nq), drow = (unsigned)(2 * nq);
+        // site-noise block of the thread's even row in step 0 (row ya - 2 + 2 rp, group gx / 4);
+        // the block of the row below is nq further.  A block gives the even columns' pair
+        // (red on an even row, black on an odd one) and the odd columns' pair
+        unsigned blk = (unsigned)((long long)(ya - 2 + 2 * rp) * nq + (gx >> 2));
+        const unsigned dstep = (unsigned)(kK * nq), drow = (unsigned)nq;
+        // the even-column pair of the odd row below: black there, which is the next row
+        // pair's thread (rp + 1, or rp = 0 of the next step) -- handed over in Zx
+        auto zx = [&](int par, int r) { return Zx + ((par * (kK / 2) + r) * kNG + g) * 2; };
         const bool hasR = g >= 1;
         const bool rin = gx < n, r1 = gx + 1 < n, r2 = gx + 2 < n, r3 = gx + 3 < n;
         const bool hasS = g >= 1 && g <= kBW / 4 && gx < n;  // the band's own columns
@@ -247,14 +236,35 @@ __global__ void __launch_bounds__(kNT, 2)
                       oD = xrow(ja + 2);
             const bool va = (unsigned)ja < (unsigned)n, vb = (unsigned)(ja + 1) < (unsigned)n,
                        vu = (unsigned)(ja - 1) < (unsigned)n, vz = (unsigned)(ja - 2) < (unsigned)n;
-            // red on rows ja (parity 0) and ja + 1 (parity 1)
-            colour_rows(Xr + oB, Xr + oC, Xr + oA, Xr + oD, Kr + oB, Kr + oC, w, zs, ctr, pair, pair + drow + 1, K, va && cr0, va && cr1, vb && cr2, vb && cr3);
+            // red on rows ja (parity 0: the even columns' pair of its block) and ja + 1
+            // (parity 1: the odd columns' pair); the other halves are black's
+            const Quad qa = draw_q(ctr, blk, K), qb = draw_q(ctr, blk + drow, K);
+            {
+                float* z = zx(s & 1, rp);
+                z[0] = qb.a0;
+                z[1] = qb.a1;
+                const float4 ra = ld4(Xr + oB), rb = ld4(Xr + oC), ru = ld4(Xr + oA), rd = ld4(Xr + oD);
+                const float4 ca = ld4(Kr + oB), cb = ld4(Kr + oC);
+                const float ea = Xr[oB - 1], eb = Xr[oC + 4];
+                st4(Xr + oB, gibbs_upd<0>(ra, ru, rb, ca, ea, w, qa.a0 * zs, qa.a1 * zs, va && cr0, va && cr1));
+                st4(Xr + oC, gibbs_upd<1>(rb, ra, rd, cb, eb, w, qb.b0 * zs, qb.b1 * zs, vb && cr2, vb && cr3));
+            }
             __syncthreads();
             // black on rows ja - 1 (parity 0) and ja (parity 1); then their final states
             {
-                float z0, z1, z2, z3;
-                draw_k(ctr, pair - drow, K, z0, z1);
-                draw_k(ctr, pair + 1, K, z2, z3);
+                // row ja - 1's block: the thread above (rp - 1, or rp = 7 of the previous step)
+                // drew it; at the start of a run it is drawn here
+                float z0, z1;
+                if (rp > 0 || s > 0) {
+                    const float* z = rp > 0 ? zx(s & 1, rp - 1) : zx((s + 1) & 1, kK / 2 - 1);
+                    z0 = z[0];
+                    z1 = z[1];
+                } else {
+                    const Quad qu = draw_q(ctr, blk - drow, K);
+                    z0 = qu.a0;
+                    z1 = qu.a1;
+                }
+                const float z2 = qa.b0, z3 = qa.b1;
                 const float4 ra = ld4(Xr + oA), rb = ld4(Xr + oB), ru = ld4(Xr + oZ), rd = ld4(Xr + oC);
                 const float4 ca = ld4(Kr + oA), cb = ld4(Kr + oB);
                 const float ea = Xr[oA - 1], eb = Xr[oB + 4];
@@ -286,7 +296,7 @@ __global__ void __launch_bounds__(kNT, 2)
             // the coarse rows of the previous step (its residual rows are complete)
             if (s > 0) restrict_step(s - 1);
             fence_proxy_async();
-            pair += dstep;
+            blk += dstep;
         }
         __syncthreads();
         restrict_step(S - 1);
@@ -303,6 +313,7 @@ __global__ void __launch_bounds__(kNT, 2)
     float* const Xr = reinterpret_cast<float*>(sm + kHead);
     float* const Kr = Xr + kRing * kSX;
     float* const Pr = Kr + kRing * kSX;
+    float* const Zx = Pr + kPRing * kPX;
     const int tid = threadIdx.x;
     const int g = tid % kNG, rp = tid / kNG;
     pdl_launch_dependents();
@@ -334,10 +345,14 @@ __global__ void __launch_bounds__(kNT, 2)
         const bool cb2 = col(gx + 1, x0 - 1, x0 + kBW), cb3 = col(gx + 3, x0 - 1, x0 + kBW);
         const bool cr0 = col(gx, x0, x0 + kBW - 1), cr1 = col(gx + 2, x0, x0 + kBW - 1);
         const bool cr2 = col(gx + 1, x0, x0 + kBW - 1), cr3 = col(gx + 3, x0, x0 + kBW - 1);
-        // Philox block of the black item of the odd row ya - 3 + 2 rp in step 0 (parity 0);
-        // the even row below it (parity 1) is 2 nq + 1 further, the red items' rows are one above
-        unsigned pair = (unsigned)(((long long)(ya - 3 + 2 * rp) * nq + (gx >> 2)) * 2);
-        const unsigned dstep = (unsigned)(2 * kK * nq), drow = (unsigned)(2 * nq);
+        // site-noise block of the thread's odd row ja - 1 in step 0 (row ya - 3 + 2 rp, group
+        // gx / 4); the even row ja below it is nq further.  Black takes the even columns'
+        // pair of row ja - 1 and the odd columns' pair of row ja; red the odd columns' pair
+        // of row ja - 1 and the even columns' pair of row ja - 2, which the thread above
+        // (rp - 1, or rp = 7 of the previous step) drew as its row ja and hands over in Zx
+        unsigned blk = (unsigned)((long long)(ya - 3 + 2 * rp) * nq + (gx >> 2));
+        const unsigned dstep = (unsigned)(kK * nq), drow = (unsigned)nq;
+        auto zx = [&](int par, int r) { return Zx + ((par * (kK / 2) + r) * kNG + g) * 2; };
         const bool hasP = gx >= 0 && gx < n;
         const bool p1 = gx + 1 < n, p2 = gx + 2 < n, p3 = gx + 3 < n;
         const bool hasS = g >= 1 && g <= kBW / 4 && gx < n;
@@ -380,12 +395,22 @@ __global__ void __launch_bounds__(kNT, 2)
         int issued = min(KB, 4), waited = -1;
         if (tid == 0)
             for (int k = 0; k <= issued; ++k) issue(k);
-        // noise drawn one barrier interval ahead of its use: the black blocks of step s in
-        // the first interval of step s (of step 0 here), the red blocks of step s in the
-        // black phase of step s
+        // noise drawn one barrier interval ahead of its use: the two blocks of step s in the
+        // first interval of step s (of step 0 here); red's hand-over read in the black phase
         float zb0, zb1, zb2, zb3, zr0 = 0.f, zr1 = 0.f, zr2 = 0.f, zr3 = 0.f;
-        draw_k(ctr, pair, K, zb0, zb1);
-        draw_k(ctr, pair + drow + 1, K, zb2, zb3);
+        auto draw_step = [&](int s) {
+            const Quad qm = draw_q(ctr, blk, K), qo = draw_q(ctr, blk + drow, K);
+            zb0 = qm.a0;
+            zb1 = qm.a1;
+            zb2 = qo.b0;
+            zb3 = qo.b1;
+            zr2 = qm.b0;
+            zr3 = qm.b1;
+            float* z = zx(s & 1, rp);
+            z[0] = qo.a0;
+            z[1] = qo.a1;
+        };
+        draw_step(0);
         for (int s = 0; s < S; ++s) {
             const int R = ya - 2 + kK * s;
             // blocks up to 2s + 2 (psi of row R + 15) are in shared memory; the barrier also
@@ -450,8 +475,7 @@ __global__ void __launch_bounds__(kNT, 2)
             }
             if (s > 0) {
                 red_step(s - 1, zr0, zr1, zr2, zr3);
-                draw_k(ctr, pair, K, zb0, zb1);
-                draw_k(ctr, pair + drow + 1, K, zb2, zb3);
+                draw_step(s);
             }
             fence_proxy_async();
             __syncthreads();
@@ -468,9 +492,18 @@ __global__ void __launch_bounds__(kNT, 2)
                 st4(Xr + oB, gibbs_upd<0>(ra, ru, rb, ca, ea, w, zb0 * zs, zb1 * zs, vb && cb0, vb && cb1));
                 st4(Xr + oC, gibbs_upd<1>(rb, ra, rd, cb, eb, w, zb2 * zs, zb3 * zs, vc && cb2, vc && cb3));
             }
-            draw_k(ctr, pair - drow, K, zr0, zr1);
-            draw_k(ctr, pair + 1, K, zr2, zr3);
-            pair += dstep;
+            // red's even-column pair of row ja - 2 (written before the barrier above; the
+            // slot is written again two steps later, rp = 7's one step later)
+            if (rp > 0 || s > 0) {
+                const float* z = rp > 0 ? zx(s & 1, rp - 1) : zx((s + 1) & 1, kK / 2 - 1);
+                zr0 = z[0];
+                zr1 = z[1];
+            } else {
+                const Quad qu = draw_q(ctr, blk - drow, K);
+                zr0 = qu.a0;
+                zr1 = qu.a1;
+            }
+            blk += dstep;
         }
         __syncthreads();
         red_step(S - 1, zr0, zr1, zr2, zr3);

@@ -68,8 +68,10 @@ constexpr unsigned kBox = kBoxW * kBoxH * 4;
 constexpr unsigned kPBox = kPBoxW * kPBoxH * 4;
 constexpr size_t kHead = 256;  // mbarriers; also keeps the reads one float left of the rings inside shared memory
 constexpr int kTail = 8;       // floats after the last ring (the right-edge read of the last group)
-constexpr size_t kFwdSmem = 128 + kHead + 4 * ((size_t)kNF * kFS + (size_t)kRRing * kRW + kTail);
-constexpr size_t kBwdSmem = 128 + kHead + 4 * ((size_t)kNF * kFS + (size_t)kPRing * kPX + kTail);
+// hand-off of site normals between the threads of consecutive rows: [step parity][rp][g][2]
+constexpr int kZx = 2 * (kK / 2) * kNG * 2;
+constexpr size_t kFwdSmem = 128 + kHead + 4 * ((size_t)kNF * kFS + (size_t)kRRing * kRW + kZx + kTail);
+constexpr size_t kBwdSmem = 128 + kHead + 4 * ((size_t)kNF * kFS + (size_t)kPRing * kPX + kZx + kTail);
 static_assert(kNT >= 8 * 16, "thread layout: the restriction needs 8 x 16 threads");
 static_assert(kBox % 128 == 0 && kPBox % 128 == 0 && (kFS * 4) % 128 == 0, "TMA destinations on 128-byte boundaries");
 static_assert(kSX <= 256 && kPX <= 256 && (kSX * 4) % 16 == 0 && (kPX * 4) % 16 == 0, "TMA box");
@@ -142,14 +144,6 @@ __device__ __forceinline__ float4 res9(const float* X, const float* Cf, const fl
     return make_float4(r.f.x - ax9q<0>(R), r.f.y - ax9q<1>(R), r.f.z - ax9q<2>(R), r.f.w - ax9q<3>(R));
 }
 
-// two Philox blocks drawn together (independent instruction streams)
-__device__ __forceinline__ void draw2(uint4 ctr, unsigned pa, unsigned pb, const RoundKeys& K, float& a0, float& a1,
-                                      float& b0, float& b1)
-{
-    draw_k(ctr, pa, K, a0, a1);
-    draw_k(ctr, pb, K, b0, b1);
-}
-
 // Forward pass of the 9-point grids of one depth, from psi = 0: one launch over all
 // strips of all chains.
 __global__ void __launch_bounds__(kNT, 2)
@@ -163,6 +157,7 @@ __global__ void __launch_bounds__(kNT, 2)
     float* const Cr = Xr + kFS;  // operator slot t at Cr + t kFS
     float* const Fr = Cr + 5 * kFS;
     float* const Rr = Fr + kFS;
+    float* const Zx = Rr + kRRing * kRW;
     const int tid = threadIdx.x;
     const int g = tid % kNG, rp = tid / kNG;
     pdl_launch_dependents();
@@ -197,10 +192,13 @@ __global__ void __launch_bounds__(kNT, 2)
         const bool c11 = col(gx + 1, x0 - 3, x0 + kBW + 3), c13 = col(gx + 3, x0 - 3, x0 + kBW + 3);
         const bool c20 = col(gx, x0 - 2, x0 + kBW + 2), c22 = col(gx + 2, x0 - 2, x0 + kBW + 2);
         const bool c31 = col(gx + 1, x0 - 1, x0 + kBW + 1), c33 = col(gx + 3, x0 - 1, x0 + kBW + 1);
-        // Philox block of P0 in step 0 (row ya - 2 + 2 rp, parity 0); P1: one row up,
-        // parity 1; P2: one row up, parity 0; P3: two rows up, parity 1
-        unsigned pair = (unsigned)(((long long)(ya - 2 + 2 * rp) * nq + (gx >> 2)) * 2);
-        const unsigned dstep = (unsigned)(2 * kK * nq), drow = (unsigned)(2 * nq);
+        // site-noise block of the thread's row a in step 0 (row ya - 2 + 2 rp, group gx / 4);
+        // the row above is nq back.  P0 takes the even columns' pair of row a, P1 and P2 the
+        // odd and even pairs of row a - 1, P3 the odd pair of row a - 2, which the thread
+        // above (rp - 1, or rp = 7 of the previous step) drew as its row a and hands over in Zx
+unsigned blk = (unsigned)((long long)(ya - 2 + 2 * rp) * nq + (gx >> 2));
+        const unsigned dstep = (unsigned)(kK * nq), drow = (unsigned)nq;
+        auto zx = [&](int par, int r) { return Zx + ((par * (kK / 2) + r) * kNG + g) * 2; };
         const bool hasR = g >= 1;
         const bool rin = gx < n, r1 = gx + 1 < n, r2 = gx + 2 < n, r3 = gx + 3 < n;
         const bool hasS = g >= 1 && g <= kBW / 4 && gx < n;  // the band's own columns
@@ -291,18 +289,21 @@ __global__ void __launch_bounds__(kNT, 2)
             const int op = wrap(r4 + 5, kRing) * kSX + 4 + 4 * g;
             const bool v0 = (unsigned)a < (unsigned)n, v1 = (unsigned)(a - 1) < (unsigned)n,
                        v2 = (unsigned)(a - 2) < (unsigned)n, v3 = (unsigned)(a - 3) < (unsigned)n;
-            // P0, colour (0,0), row a; the noise of P3 (colour (1,0), row a - 2) drawn alongside
-            float z00, z01, z30, z31;
-            draw2(ctr, pair, pair - 2 * drow + 1, K, z00, z01, z30, z31);
+            // P0, colour (0,0), row a
             {
+                const Quad qa = draw_q(ctr, blk, K);
+                float* z = zx(s & 1, rp);
+                z[0] = qa.b0;
+                z[1] = qa.b1;
+                const float z00 = qa.a0, z01 = qa.a1;
                 Rows9 r;
                 load9<0>(r, Xr, Cr, Fr, o1, o0, op);
                 st4(Xr + o0, upd9<0>(r, z00 * zs, z01 * zs, v0 && c00, v0 && c02));
             }
             __syncthreads();
             // P1, colour (1,1), and P2, colour (0,1), on row a - 1
-            float z10, z11, z20, z21;
-            draw2(ctr, pair - drow + 1, pair - drow, K, z10, z11, z20, z21);
+            const Quad qm = draw_q(ctr, blk - drow, K);
+            const float z10 = qm.b0, z11 = qm.b1, z20 = qm.a0, z21 = qm.a1;
             Rows9 r;
             load9<1>(r, Xr, Cr, Fr, o2, o1, o0);
             r.x0 = upd9<1>(r, z10 * zs, z11 * zs, v1 && c11, v1 && c13);
@@ -324,6 +325,16 @@ __global__ void __launch_bounds__(kNT, 2)
             __syncthreads();
             // P3, colour (1,0), row a - 2; then its final state
             {
+                float z30, z31;
+                if (rp > 0 || s > 0) {
+                    const float* z = rp > 0 ? zx(s & 1, rp - 1) : zx((s + 1) & 1, kK / 2 - 1);
+                    z30 = z[0];
+                    z31 = z[1];
+                } else {
+                    const Quad qu = draw_q(ctr, blk - 2 * drow, K);
+                    z30 = qu.b0;
+                    z31 = qu.b1;
+                }
                 Rows9 q;
                 load9<1>(q, Xr, Cr, Fr, o3, o2, o1);
                 const float4 o = upd9<1>(q, z30 * zs, z31 * zs, v2 && c31, v2 && c33);
@@ -348,7 +359,7 @@ __global__ void __launch_bounds__(kNT, 2)
             // the coarse rows of the previous step (its residual rows are complete)
             if (s > 0) restrict_step(s - 1);
             fence_proxy_async();
-            pair += dstep;
+            blk += dstep;
             r4 = wrap(r4 + kK, kRing);
         }
         __syncthreads();
@@ -369,6 +380,7 @@ __global__ void __launch_bounds__(kNT, 2)
     float* const Cr = Xr + kFS;
     float* const Fr = Cr + 5 * kFS;
     float* const Pr = Fr + kFS;
+    float* const Zx = Pr + kPRing * kPX;
     const int tid = threadIdx.x;
     const int g = tid % kNG, rp = tid / kNG;
     pdl_launch_dependents();
@@ -402,10 +414,13 @@ __global__ void __launch_bounds__(kNT, 2)
         const bool c10 = col(gx, x0 - 2, x0 + kBW + 1), c12 = col(gx + 2, x0 - 2, x0 + kBW + 1);
         const bool c21 = col(gx + 1, x0 - 1, x0 + kBW), c23 = col(gx + 3, x0 - 1, x0 + kBW);
         const bool c30 = col(gx, x0, x0 + kBW - 1), c32 = col(gx + 2, x0, x0 + kBW - 1);
-        // Philox block of P0 in step 0 (row ya - 4 + 2 rp, parity 1); P1: one row up,
-        // parity 0; P2: one row up, parity 1; P3: two rows up, parity 0
-        unsigned pair = (unsigned)(((long long)(ya - 4 + 2 * rp) * nq + (gx >> 2)) * 2);
-        const unsigned dstep = (unsigned)(2 * kK * nq), drow = (unsigned)(2 * nq);
+        // site-noise block of the thread's row a in step 0 (row ya - 4 + 2 rp, group gx / 4);
+        // the row above is nq back.  P0 takes the odd columns' pair of row a, P1 and P2 the
+        // even and odd pairs of row a - 1, P3 the even pair of row a - 2, which the thread
+        // above (rp - 1, or rp = 7 of the previous step) drew as its row a and hands over in Zx
+        unsigned blk = (unsigned)((long long)(ya - 4 + 2 * rp) * nq + (gx >> 2));
+        const unsigned dstep = (unsigned)(kK * nq), drow = (unsigned)nq;
+        auto zx = [&](int par, int r) { return Zx + ((par * (kK / 2) + r) * kNG + g) * 2; };
         const bool hasP = gx >= 0 && gx < n;
         const bool p1 = gx + 1 < n, p2 = gx + 2 < n, p3 = gx + 3 < n;
         const bool hasS = g >= 1 && g <= kBW / 4 && gx < n;
@@ -441,8 +456,8 @@ __global__ void __launch_bounds__(kNT, 2)
             st4(Xr + o2, o);
             if (hasS && a - 2 >= ya && a - 2 < yb) st4(xout + pitch * (a - 2), o);
         };
-        // noise drawn one barrier interval ahead of its use: P0 and P1 of step s in the first
-        // interval of step s, P2 in P0, P3 in P1
+        // the two blocks of step s are drawn in its first interval; P3's hand-over is read
+        // in its second
         float z30 = 0.f, z31 = 0.f;
         for (int s = 0; s < S; ++s) {
             const int R = ya - 4 + kK * s;
@@ -506,8 +521,12 @@ __global__ void __launch_bounds__(kNT, 2)
             // alongside the prolongation: P3 of step s - 1 (rows up to R - 4; its neighbours are
             // final since the barrier)
             if (s > 0) p3_step(a - kK, wrap(r3 + kRing - kK, kRing), z30, z31);
-            float z00, z01, z10, z11;
-            draw2(ctr, pair + 1, pair - drow, K, z00, z01, z10, z11);
+            const Quad qa = draw_q(ctr, blk, K), qm = draw_q(ctr, blk - drow, K);
+            {
+                float* z = zx(s & 1, rp);
+                z[0] = qa.a0;
+                z[1] = qa.a1;
+            }
             fence_proxy_async();
             __syncthreads();
             // blocks 2s - 2 and 2s - 1 were last read by P3 above: blocks 2s + 3, 2s + 4 take
@@ -515,20 +534,28 @@ __global__ void __launch_bounds__(kNT, 2)
             if (s > 0 && tid == 0)
                 for (int k = 2 * s + 3; k <= min(2 * s + 4, KB); ++k) issue(k);
             if (s > 0) issued = max(issued, min(2 * s + 4, KB));
+            // P3's even-column pair of row a - 2 (written before the barrier above; the slot is
+            // written again two steps later, rp = 7's one step later)
+            if (rp > 0 || s > 0) {
+                const float* z = rp > 0 ? zx(s & 1, rp - 1) : zx((s + 1) & 1, kK / 2 - 1);
+                z30 = z[0];
+                z31 = z[1];
+            } else {
+                const Quad qu = draw_q(ctr, blk - 2 * drow, K);
+                z30 = qu.a0;
+                z31 = qu.a1;
+            }
             // P0, colour (1,0), row a
-            float z20, z21;
-            draw_k(ctr, pair - drow + 1, K, z20, z21);
             {
                 Rows9 r;
                 load9<1>(r, Xr, Cr, Fr, o1, o0, op);
-                st4(Xr + o0, upd9<1>(r, z00 * zs, z01 * zs, v0 && c01, v0 && c03));
+                st4(Xr + o0, upd9<1>(r, qa.b0 * zs, qa.b1 * zs, v0 && c01, v0 && c03));
             }
             __syncthreads();
             // P1, colour (0,1), and P2, colour (1,1), on row a - 1
-            draw_k(ctr, pair - 2 * drow, K, z30, z31);
             Rows9 r;
             load9<0>(r, Xr, Cr, Fr, o2, o1, o0);
-            r.x0 = upd9<0>(r, z10 * zs, z11 * zs, v1 && c10, v1 && c12);
+            r.x0 = upd9<0>(r, qm.a0 * zs, qm.a1 * zs, v1 && c10, v1 && c12);
             st4(Xr + o1, r.x0);
             __syncthreads();
             {
@@ -539,11 +566,11 @@ __global__ void __launch_bounds__(kNT, 2)
                 r.c1e = 0.f;
                 r.c4me = 0.f;
                 r.c2me = Cr[2 * kFS + o2 + 4];
-                const float4 o = upd9<1>(r, z20 * zs, z21 * zs, v1 && c21, v1 && c23);
+                const float4 o = upd9<1>(r, qm.b0 * zs, qm.b1 * zs, v1 && c21, v1 && c23);
                 st4(Xr + o1, o);
                 if (hasS && a - 1 >= ya && a - 1 < yb) st4(xout + pitch * (a - 1), o);
             }
-            pair += dstep;
+            blk += dstep;
             r3 = wrap(r3 + kK, kRing);
         }
         __syncthreads();

@@ -44,9 +44,9 @@ __device__ __forceinline__ RoundKeys round_keys(unsigned k0, unsigned k1)
     }
     return K;
 }
-__device__ __forceinline__ void draw_k(uint4 c, unsigned pair, const RoundKeys& K, float& z0, float& z1)
+__device__ __forceinline__ uint4 philox_k(uint4 c, unsigned block, const RoundKeys& K)
 {
-    c.x = pair;
+    c.x = block;
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
         const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
@@ -54,9 +54,18 @@ __device__ __forceinline__ void draw_k(uint4 c, unsigned pair, const RoundKeys& 
         c = make_uint4((unsigned)(p1 >> 32) ^ c.y ^ K.a[r], (unsigned)p1, (unsigned)(p0 >> 32) ^ c.w ^ K.b[r],
                        (unsigned)p0);
     }
-    normal_pair(c, z0, z1);
+    return c;
 }
-
+// the four site normals of one block (normal_quad of common.cuh)
+struct Quad {
+    float a0, a1, b0, b1;  // a: the even columns of the group, b: the odd ones
+};
+__device__ __forceinline__ Quad draw_q(uint4 c, unsigned block, const RoundKeys& K)
+{
+    Quad q;
+    normal_quad(philox_k(c, block, K), q.a0, q.a1, q.b0, q.b1);
+    return q;
+}
 // wait (bounded) for blocks (waited, upto] of a ring of NB slots (bit q of ph: the parity of
 // slot q's next phase); false if a wait gave up
 template <int NB>

@@ -391,8 +391,11 @@ __device__ __forceinline__ void tile_phase(const DevLevel<T>& L, const CycleStat
         if (!v0 && !v1) continue;
         T z0 = T(0), z1 = T(0);
         if (noise) {
-            const unsigned pair = (unsigned)(((long long)j * nq + (q0 + gq)) * 2 + px);
-            draw_pair_ctr<T>(ctr, pair, k0, k1, z0, z1);
+            // the block of the group's row gives both column parities: take this colour's half
+            T a0, a1, b0, b1;
+            draw_quad_ctr<T>(ctr, (unsigned)((long long)j * nq + (q0 + gq)), k0, k1, a0, a1, b0, b1);
+            z0 = px ? b0 : a0;
+            z1 = px ? b1 : a1;
         }
         if constexpr (sizeof(T) == 4) {
             // FP32: whole 4-site groups as float4 rows of the staged tile

@@ -68,6 +68,27 @@ def test_box_muller_normals():
     assert abs(np.corrcoef(z[0::2], z[1::2])[0, 1]) < 4 / np.sqrt(z.size / 2)
 
 
+def test_site_noise_quads_are_independent_standard_normals():
+    """The four normals of a site-noise block (two Box-Muller pairs from 32-bit
+    uniforms): each member N(0, 1) (moments, Kolmogorov-Smirnov), the six pairs of
+    members uncorrelated, and the squares uncorrelated (a wrong angle or a shared
+    radius between the two pairs would correlate them)."""
+    q = np.array([oracle.normal_quad(7, c, 11, 3 << 16, 2) for c in range(40000)])
+    m = q.shape[0]
+    for k in range(4):
+        z = q[:, k]
+        assert abs(z.mean()) < 4 / np.sqrt(m)
+        assert abs(z.var() - 1) < 4 * np.sqrt(2 / m)
+        assert stats.kstest(z, "norm").pvalue > 1e-3
+    for a in range(4):
+        for b in range(a + 1, 4):
+            assert abs(np.corrcoef(q[:, a], q[:, b])[0, 1]) < 4 / np.sqrt(m)
+    assert abs(np.corrcoef(q[:, 0] ** 2, q[:, 2] ** 2)[0, 1]) < 4 / np.sqrt(m)
+    # a pair's radius is shared by its members: r^2 = z0^2 + z1^2 ~ chi^2_2 (exponential, mean 2)
+    r2 = q[:, 0] ** 2 + q[:, 1] ** 2
+    assert stats.kstest(r2, "expon", args=(0, 2)).pvalue > 1e-3
+
+
 # --------------------------------------------------------------------------
 # hierarchy (Eq. A_ell_1_B_ell_1, Sec. 5.1.3)
 # --------------------------------------------------------------------------
