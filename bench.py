@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 # DRAM bytes (read + write) per launch of the finest-grid forward kernel (k_stream_fwd)
 # on the 32 x 1023^2 batch, from an ncu capture of that kernel on this workload; None
 # for other workloads and whenever that kernel changes before it is re-captured.
-FINE_SWEEP_TRAFFIC_BYTES = None
+FINE_SWEEP_TRAFFIC_BYTES = 483_135_232
 # the e2e measurement of a batch runs it as this many batches on their own streams
 E2E_GROUPS = 4
 

@@ -215,6 +215,36 @@ __device__ __forceinline__ void normal_quad(const uint4 w, float& z0, float& z1,
     z3 = -r1 * s;
 }
 
+// One half of normal_quad: the pair of the even (px = 0) or odd (px = 1) columns,
+// transforming only the two words it needs (the same operations as normal_quad)
+__device__ __forceinline__ void normal_half(const uint4 w, int px, double& z0, double& z1)
+{
+    const unsigned wa = px ? w.z : w.x, wb = px ? w.w : w.y;
+    const double r = sqrt(-2.0 * log(((double)wa + 0.5) * 0x1p-32));
+    double s, c;
+    sincospi(2.0 * (((double)wb + 0.5) * 0x1p-32), &s, &c);
+    z0 = r * c;
+    z1 = r * s;
+}
+__device__ __forceinline__ void normal_half(const uint4 w, int px, float& z0, float& z1)
+{
+    const unsigned wa = px ? w.z : w.x, wb = px ? w.w : w.y;
+    const float u1 = fmaf((float)wa, 0x1p-32f, 0x1p-33f), u2 = fmaf((float)wb, 0x1p-32f, 0x1p-33f);
+    const float t = fmaxf(-2.0f * logf(u1), 1e-37f);
+    const float r = t * rsqrtf(t);
+    float s, c;
+    __sincosf(6.28318530717958648f * (u2 - 0.5f), &s, &c);
+    z0 = -r * c;
+    z1 = -r * s;
+}
+template <typename T>
+__device__ __forceinline__ void draw_half_ctr(uint4 ctr, unsigned block, int px, unsigned k0, unsigned k1, T& z0,
+                                              T& z1)
+{
+    ctr.x = block;
+    normal_half(philox10(ctr, k0, k1), px, z0, z1);
+}
+
 // the four site normals of block `block` with the counter words c1..c3 and the key in
 // registers (ctr.x is replaced by the block index)
 template <typename T>

@@ -67,15 +67,9 @@ __device__ __forceinline__ void sweep_item(const DevLevel<T>& L, const DevProble
     int i0 = 4 * q + px;
     bool has1 = i0 + 2 < n;
     T z0 = T(0), z1 = T(0);
-    if (cs.noise) {
-        // the block of the group's row gives both column parities: take this colour's half
-        T a0, a1, b0, b1;
-        const uint4 ctr = noise_counter(cs, 0u, 0u, L.level, slot);
-        draw_quad_ctr<T>(ctr, (unsigned)(((long long)k * n + j) * nq + q), (unsigned)cs.seed,
-                         (unsigned)(cs.seed >> 32), a0, a1, b0, b1);
-        z0 = px ? b0 : a0;
-        z1 = px ? b1 : a1;
-    }
+    if (cs.noise)  // the block of the group's row, this colour's half of it
+        draw_half_ctr<T>(noise_counter(cs, 0u, 0u, L.level, slot), (unsigned)(((long long)k * n + j) * nq + q), px,
+                         (unsigned)cs.seed, (unsigned)(cs.seed >> 32), z0, z1);
     long long e = site_offset(DIM, L.pitch, L.plane, L.base, i0, j, k);
     if (L.fine) {
         L.x[e] = fine_update<DIM>(L, e, z0);

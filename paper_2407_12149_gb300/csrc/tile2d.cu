@@ -390,13 +390,8 @@ __device__ __forceinline__ void tile_phase(const DevLevel<T>& L, const CycleStat
         const bool v1 = rowok && dx1 >= -rp && dx1 < G::TX + rp && i1 >= 0 && i1 < n;
         if (!v0 && !v1) continue;
         T z0 = T(0), z1 = T(0);
-        if (noise) {
-            // the block of the group's row gives both column parities: take this colour's half
-            T a0, a1, b0, b1;
-            draw_quad_ctr<T>(ctr, (unsigned)((long long)j * nq + (q0 + gq)), k0, k1, a0, a1, b0, b1);
-            z0 = px ? b0 : a0;
-            z1 = px ? b1 : a1;
-        }
+        if (noise)  // the block of the group's row, this colour's half of it
+            draw_half_ctr<T>(ctr, (unsigned)((long long)j * nq + (q0 + gq)), px, k0, k1, z0, z1);
         if constexpr (sizeof(T) == 4) {
             // FP32: whole 4-site groups as float4 rows of the staged tile
             const int lb = (dy + G::R) * SX + (4 * gq + G::RX);

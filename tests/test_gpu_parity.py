@@ -305,13 +305,15 @@ def test_qoi_stats_on_device_match_oracle(torch_mod):
     assert abs(st["tau_int"] - 1.228612) < 3 * st["tau_err"]
 
 
-def test_fp32_config1_moments(torch_mod):
-    """FP32 chain of config 1: QoI mean 0 and variance F^T A^-1 F = 0.18241764732 within 3 SE
-    (the closed-form integrated autocorrelation time 1.228612 of this chain)."""
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_config1_qoi_moments(torch_mod, precision):
+    """A chain of config 1 in either precision: QoI mean 0 and variance
+    F^T A^-1 F = 0.18241764732 within 3 SE (the closed-form integrated
+    autocorrelation time 1.228612 of this chain, which the iteration matrix fixes)."""
     torch = torch_mod
     from paper_2407_12149_gb300.mgmc import mgmc_qoi_stats
     p = inputs.config1()
-    s = _gpu(p, precision="fp32")
+    s = _gpu(p, precision=precision)
     x = s.zeros()
     n = 40000
     q = torch.zeros(n, dtype=torch.float64, device="cuda")
