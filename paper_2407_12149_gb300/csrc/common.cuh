@@ -255,15 +255,6 @@ __device__ __forceinline__ void draw_quad_ctr(uint4 ctr, unsigned block, unsigne
     normal_quad(philox10(ctr, k0, k1), z0, z1, z2, z3);
 }
 
-// the same draw with the counter words c1..c3 and the key already in registers
-// (ctr.x is replaced by the pair index)
-template <typename T>
-__device__ __forceinline__ void draw_pair_ctr(uint4 ctr, unsigned pair, unsigned k0, unsigned k1, T& z0, T& z1)
-{
-    ctr.x = pair;
-    normal_pair(philox10(ctr, k0, k1), z0, z1);
-}
-
 template <typename T>
 __device__ __forceinline__ void draw_pair(const CycleState& cs, unsigned pair, unsigned kind, int level,
                                           unsigned slot, T& z0, T& z1)
