@@ -652,7 +652,9 @@ def run_warmstart(args):
     from paper_2407_12149_gb300 import mgmc as M
     build.build()
     dev = torch.device("cuda", 0)
-    n, n_test, n_train = 255, 64, args.warm_train
+    n, n_test = 255, args.warm_test
+    curve = sorted({int(v) for v in args.warm_curve.split(",") if v.strip()}) if args.warm_curve else []
+    n_train = max(curve) if curve else args.warm_train
     t0 = time.perf_counter()
     train = warm_problems(n, n_train, 0)
     test = warm_problems(n, n_test, 1_000_000)
@@ -672,38 +674,59 @@ def run_warmstart(args):
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - t0
 
-    net = M.Unet(n, c0=32, max_batch=8, seed=1)
-    t1 = time.perf_counter()
-    losses = net.train(Xtr, Ttr, epochs=args.warm_epochs, batch=8, lr=1e-3, shuffle_seed=2)
-    torch.cuda.synchronize()
-    train_s = time.perf_counter() - t1
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    mu_hat = net.predict(Xte, precision="fp32")
-    e1.record()
-    torch.cuda.synchronize()
-    pred_ms = e0.elapsed_time(e1)
-    err = (mu_hat.double() - Tte).norm(dim=1) / Tte.norm(dim=1)
+    def train_net(count):
+        net = M.Unet(n, c0=32, max_batch=8, seed=1)
+        t1 = time.perf_counter()
+        losses = net.train(Xtr[:count], Ttr[:count], epochs=args.warm_epochs, batch=8, lr=1e-3, shuffle_seed=2)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t1
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        mu_hat = net.predict(Xte, precision="fp32")
+        e1.record()
+        torch.cuda.synchronize()
+        pred_ms = e0.elapsed_time(e1)
+        net_params = net.n_params
+        net.close()
+        return mu_hat, losses, train_s, pred_ms, net_params
 
-    # chains of the held-out problems from 0 and from the estimate, FP32 batched
+    # chains of the held-out problems from 0 and from the estimates, FP32 batched
     K = args.warm_cycles
-    runs = {}
-    for name, init in (("zero", None), ("unet", mu_hat)):
-        b = M.BatchSampler(test, precision="fp32")
-        xs = b.zeros()
-        if init is not None:
-            for k, x in enumerate(xs):
+    b = M.BatchSampler(test, precision="fp32")
+    xs = b.zeros()
+
+    def chains(init):
+        for k, x in enumerate(xs):
+            if init is None:
+                x.zero_()
+            else:
                 x.copy_(init[k])
         q = torch.zeros(n_test * K, dtype=torch.float64, device=dev)
         b.sample(xs, K, 77, qoi=q)
         torch.cuda.synchronize()
-        runs[name] = q.view(n_test, K).cpu().numpy()
-        b.close()
+        return q.view(n_test, K).cpu().numpy()
+
+    runs = {"zero": chains(None)}
+    points = []
+    for count in (curve or [n_train]):
+        mu_hat, losses, train_s, pred_ms, n_params = train_net(count)
+        err = (mu_hat.double() - Tte).norm(dim=1) / Tte.norm(dim=1)
+        runs[count] = chains(mu_hat)
+        points.append({"train_problems": count, "mu_rel_l2_error_mean": float(err.mean()),
+                       "mu_rel_l2_error_max": float(err.max()), "train_s": train_s,
+                       "train_loss_first_last": [float(losses[0]), float(losses[-1])]})
+    b.close()
+
     qmu = np.array([float(np.dot(p.qoi_w, Tte[k].cpu().numpy()[p.qoi_site])) for k, p in enumerate(test)])
-    tail = np.concatenate([runs["zero"][:, K // 2:], runs["unet"][:, K // 2:]], axis=1)
+    tail = np.concatenate([r[:, K // 2:] for r in runs.values()], axis=1)
     sig = tail.std(axis=1, ddof=1)
     b_zero, d_zero = burn_in(runs["zero"], qmu, sig)
-    b_unet, d_unet = burn_in(runs["unet"], qmu, sig)
+    for pt in points:
+        pt["burn_in_cycles"] = burn_in(runs[pt["train_problems"]], qmu, sig)[0]
+    b_unet, d_unet = burn_in(runs[n_train], qmu, sig)
+    err_mean, err_max = points[-1]["mu_rel_l2_error_mean"], points[-1]["mu_rel_l2_error_max"]
+    losses = points[-1]["train_loss_first_last"]
+    train_s = points[-1]["train_s"]
 
     # tensor-core roofline of the GEMM on the largest convolution shapes of a batch of 8
     peaks = {}
@@ -736,17 +759,18 @@ def run_warmstart(args):
         "metric": "burn-in V-cycles (learned warm start)", "value": b_unet, "unit": "V-cycles",
         "n_gpus": 1, "steps": K, "warmup": 0, "ms_per_step": None, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-        "config": {"workload": f"warmstart-255: U-Net (c0 = 32, {net.n_params} parameters) trained on {n_train} "
+        "config": {"workload": f"warmstart-255: U-Net (c0 = 32, {n_params} parameters) trained on {n_train} "
                                f"FP64 mean-solve targets of seeded 255^2 posteriors (kappa^2 = 10 exp(g), m ~ U{{8..32}}, "
                                f"Gamma = 1e-4 I), {n_test} held-out problems, FP32 batched chains",
                    "burn_in_from_zero": b_zero, "burn_in_from_unet": b_unet,
-                   "burn_in_rule": "first cycle with |mean_k (q_kt - F mu_k) / sd_k| <= 1 / sqrt(64)",
+                   "burn_in_rule": f"first cycle with |mean_k (q_kt - F mu_k) / sd_k| <= 1 / sqrt({n_test})",
                    "mean_error_trace_zero": [round(float(v), 3) for v in d_zero[:12]],
                    "mean_error_trace_unet": [round(float(v), 3) for v in d_unet[:12]],
-                   "mu_rel_l2_error_mean": float(err.mean()), "mu_rel_l2_error_max": float(err.max()),
-                   "train_epochs": args.warm_epochs, "train_loss_first_last": [float(losses[0]), float(losses[-1])],
+                   "mu_rel_l2_error_mean": err_mean, "mu_rel_l2_error_max": err_max,
+                   "train_epochs": args.warm_epochs, "train_loss_first_last": losses,
                    "train_s": train_s, "data_generation_s": gen_s,
-                   "predict_ms_per_problem": pred_ms / n_test},
+                   "predict_ms_per_problem": pred_ms / n_test,
+                   "learning_curve": points if curve else None},
         "roofline": {"bound": "tensor", "kernel": "k_tc_gemm<256>: bottom-level convolution GEMM of 64 samples "
                                                   "(M = 64 x 32^2 pixels, N = 256, K = 9 x 256)",
                      "achieved": bott, "peak": peak, "unit": "TFLOP/s", "frac": bott / peak,
@@ -937,9 +961,12 @@ def main():
                          "one chain; bayes2d-4095/8191: HBM-resident single grids; batch512-mixed: 512 chains")
     ap.add_argument("--tau-cycles", type=int, default=TAU_CALIBRATION,
                     help="length of the untimed chain that estimates tau_int (>= 200)")
-    ap.add_argument("--warm-train", type=int, default=512, help="warmstart-255: training problems")
+    ap.add_argument("--warm-train", type=int, default=1024, help="warmstart-255: training problems")
     ap.add_argument("--warm-epochs", type=int, default=20, help="warmstart-255: training epochs")
     ap.add_argument("--warm-cycles", type=int, default=40, help="warmstart-255: chain length of the burn-in test")
+    ap.add_argument("--warm-test", type=int, default=512, help="warmstart-255: held-out problems")
+    ap.add_argument("--warm-curve", default="", help="warmstart-255: comma-separated training-set sizes; each trains "
+                                                     "a fresh network on the first N problems (learning curve)")
     ap.add_argument("--conv-chains", type=int, default=16384, help="convergence-2d: MGMC chains per grid")
     ap.add_argument("--conv-gibbs-chains", type=int, default=2048, help="convergence-2d: Gibbs chains per grid")
     args = ap.parse_args()
