@@ -54,6 +54,7 @@ def lib():
         L.oracle_destroy.argtypes = [ctypes.c_void_p]
         L.oracle_destroy.restype = None
         L.oracle_level_n.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.oracle_set_gamma.argtypes = [ctypes.c_void_p, ctypes.c_int]
         for name in ("oracle_level_stencil", "oracle_level_B_dense"):
             getattr(L, name).argtypes = [ctypes.c_void_p, ctypes.c_int, _c_dbl_p]
         L.oracle_level_G_dense.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _c_dbl_p]
@@ -101,10 +102,13 @@ class Oracle:
 
     def __init__(self, dim, n, n_levels, *, kappa2=None, kappa2_const=10.0, scale_hd=1,
                  nu1=1, nu2=1, obs_site=None, obs_w=None, Gamma=None, y=None,
-                 qoi_site=None, qoi_w=None, disc=0):
-        """disc: 0 finite-difference fine operator, 1 Q1 finite elements (constant kappa^2)."""
+                 qoi_site=None, qoi_w=None, disc=0, gamma=1):
+        """disc: 0 finite-difference fine operator, 1 Q1 finite elements (constant kappa^2),
+        2 the 13-point finite-difference squared shifted Laplacian (2D, constant kappa^2).
+        gamma: cycle index of Alg. 1 (1 V-cycle, 2 W-cycle)."""
         L = lib()
         self.dim, self.n, self.n_levels = dim, n, n_levels
+        self.W = 5 if disc == 2 else 3
         self.N = n ** dim
         k2 = None if kappa2 is None else np.ascontiguousarray(kappa2, dtype=np.float64).ravel()
         if obs_site is None:
@@ -130,6 +134,9 @@ class Oracle:
         if rc != 0:
             raise OracleError(f"oracle_create failed with code {rc}")
         self._h = h
+        if gamma != 1 and L.oracle_set_gamma(h, int(gamma)) != 0:
+            self.close()
+            raise OracleError(f"oracle_set_gamma({gamma}) failed")
 
     def close(self):
         if getattr(self, "_h", None):
@@ -150,7 +157,7 @@ class Oracle:
         return self.level_n(l) ** self.dim
 
     def stencil(self, l):
-        NS = 3 ** self.dim
+        NS = self.W ** self.dim
         out = np.zeros((self.level_N(l), NS))
         lib().oracle_level_stencil(self._h, l, _dp(out))
         return out

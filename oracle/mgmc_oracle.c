@@ -12,7 +12,10 @@
  *  Sec. 2.3 / Eq. (def-A_ell), (A_ell_1_B_ell_1):
  *    finest A_L = s (kappa^2 I - Delta_h) on the interior vertices of the
  *    unit square/cube (zero Dirichlet), s = h^d (bilinear-form scaling,
- *    Phi(l) = h^{d/2}) or s = 1 (literal reading); A_{l-1} = P^T A_l P,
+ *    Phi(l) = h^{d/2}) or s = 1 (literal reading); or its Q1 finite-element
+ *    matrix; or (Sec. 5.1.1, Eq. squared_shifted_laplace) the 13-point
+ *    finite-difference matrix of (kappa^2 - Delta)^2 with u = du/dn = 0 in
+ *    2D (radius-2 stencils on every grid); A_{l-1} = P^T A_l P,
  *    B_{l-1} = P^T B_l with the canonical multilinear prolongation
  *    P = I_{l-1}^l (Eq. definition_prolongation), restriction = P^T unscaled.
  *  Eq. (f_ell_definition):  f_L = B Gamma^-1 y.
@@ -34,7 +37,10 @@
  *        theta' = theta*_s - G (B^T theta*_s - d - L_Gamma z').
  *    This is the same update; it avoids forming theta*, whose entries near
  *    an observation reach |Gamma^-1 y| w / a_ii and cancel in theta'.
- *  Alg. 1 with gamma = 1 (V-cycle), nu1 forward / nu2 backward sweeps,
+ *  Alg. 1 with gamma = 1 (V-cycle) or gamma = 2 (W-cycle: the finest grid
+ *    calls the next one once, every coarser grid calls its coarse grid
+ *    twice, the coarse state carried from one call to the next),
+ *    nu1 forward / nu2 backward sweeps,
  *    f_{l-1} = P^T (f_l - A~_l theta), coarse start psi = 0, theta += P psi.
  *    With the split: fd_{l-1} = P^T (fd_l - A_l theta) and
  *    d_{l-1} = d_l - B_l^T theta (because P^T B_l = B_{l-1}).
@@ -48,8 +54,9 @@
  * definition only, not by code):
  *   - unknown order: 2^d parity colours, 2D order (0,0),(1,1),(0,1),(1,0);
  *     3D the four even colours (i+j+k even) in lexicographic order of
- *     (i mod 2, j mod 2, k mod 2) then the four odd ones; lexicographic
- *     within a colour.  Backward sweep = reverse colour order.
+ *     (i mod 2, j mod 2, k mod 2) then the four odd ones; radius-2 stencils
+ *     the nine classes (i mod 3, j mod 3) by code (i mod 3) + 3 (j mod 3);
+ *     lexicographic within a colour.  Backward sweep = reverse colour order.
  *   - omega = 1.
  *   - random numbers: Philox4x32-10 (Salmon et al., SC'11), key = seed,
  *     counter (c0 = pair, c1 = cycle low 32 bits,
@@ -59,12 +66,14 @@
  *       two Box-Muller pairs from 32-bit uniforms u = (w + 0.5) 2^-32:
  *       (w0, w1) for the sites with i even, (w2, w3) for i odd, member
  *       (i >> 1) & 1, z0 = r cos(2 pi u2), z1 = r sin(2 pi u2),
- *       r = sqrt(-2 ln u1); slot = 2 j for the j-th pre sweep, 2 j + 1 for
- *       the j-th post sweep.
+ *       r = sqrt(-2 ln u1); slot = 2 (v S + j) for the j-th pre sweep and
+ *       2 (v S + j) + 1 for the j-th post sweep of the v-th visit of the
+ *       level within the cycle, S = max(nu1, nu2, 1) (v = 0 in a V-cycle).
  *     kinds 1 and 2: one Box-Muller pair per block from 53-bit uniforms
  *       u = (k53 + 0.5) 2^-53 of the top 53 bits of (w0,w1) resp. (w2,w3);
  *       kind 1 (low-rank noise z'): c0 = k >> 1, member k & 1;
- *       kind 2 (coarsest sample): c0 = s >> 1, member s & 1.
+ *       kind 2 (coarsest sample): c0 = s >> 1, member s & 1, slot = the
+ *       visit index v of the coarsest grid.
  *
  * Compile with -ffp-contract=off so that x86 and Arm builds round alike.
  */
@@ -104,6 +113,9 @@ typedef struct {
 
 struct oracle_problem {
     int d, NS, centre;
+    int R, W;              /* stencil radius (1, or 2 for the squared operator) and width 2R+1 */
+    int gamma;             /* recursive calls on the coarser grids below the finest (1 V, 2 W) */
+    int visit[32];         /* visits of each level within the current cycle */
     int n_levels;
     int scale_hd;
     int disc;              /* fine-grid discretisation: 0 finite differences, 1 Q1 finite elements */
@@ -304,11 +316,17 @@ static int site_index(int d, int n, const int c[3])
     return s;
 }
 
-static void offset_of(int d, int o, int off[3])
+static void offset_of(int d, int W, int o, int off[3])
 {
-    off[0] = o % 3 - 1;
-    off[1] = (d >= 2) ? (o / 3) % 3 - 1 : 0;
-    off[2] = (d >= 3) ? o / 9 - 1 : 0;
+    int R = W / 2;
+    off[0] = o % W - R;
+    off[1] = (d >= 2) ? (o / W) % W - R : 0;
+    off[2] = (d >= 3) ? o / (W * W) - R : 0;
+}
+
+static int offset_index(const oracle_problem* p, int dx, int dy, int dz)
+{
+    return (dx + p->R) + p->W * (dy + p->R) + (p->d == 3 ? p->W * p->W * (dz + p->R) : 0);
 }
 
 /* Entry of the 1D canonical prolongation: fine interior index i, coarse j.
@@ -321,9 +339,17 @@ static double p1d(int i, int j)
     return 0.0;
 }
 
-/* Colour (parity class) sequence; returns the number of colours. */
-static int colour_sequence(int d, int seq[8])
+/* Colour sequence; returns the number of colours.  Radius-2 stencils (2D): the
+ * nine classes (i mod 3, j mod 3) with code (i mod 3) + 3 (j mod 3) in increasing
+ * code order -- sites of one class are at least 3 apart along an axis and so
+ * never coupled by a 5 x 5 stencil. */
+static int colour_sequence(const oracle_problem* p, int seq[27])
 {
+    int d = p->d;
+    if (p->R == 2) {
+        for (int c = 0; c < 9; ++c) seq[c] = c;
+        return 9;
+    }
     if (d == 2) {
         /* (0,0), (1,1), (0,1), (1,0) with code px + 2 py */
         seq[0] = 0; seq[1] = 3; seq[2] = 2; seq[3] = 1;
@@ -336,8 +362,10 @@ static int colour_sequence(int d, int seq[8])
     return 8;
 }
 
-static int parity_code(int d, const int c[3])
+static int parity_code(const oracle_problem* p, const int c[3])
 {
+    int d = p->d;
+    if (p->R == 2) return c[0] % 3 + 3 * (c[1] % 3);
     int code = (c[0] & 1) + 2 * (c[1] & 1);
     if (d == 3) code += 4 * (c[2] & 1);
     return code;
@@ -355,7 +383,7 @@ static void apply_A(const oracle_problem* p, const olevel* L, const double* x, d
             double a = L->a[(size_t)s * p->NS + o];
             if (a == 0.0) continue;
             int off[3], nc[3];
-            offset_of(d, o, off);
+            offset_of(d, p->W, o, off);
             for (int t = 0; t < 3; ++t) nc[t] = c[t] + off[t];
             int j = site_index(d, n, nc);
             if (j < 0) continue;
@@ -413,15 +441,15 @@ static void gs_sweep(const oracle_problem* p, int l, const olevel* L, int dir, d
                      int use_noise)
 {
     int d = p->d, n = L->n;
-    int seq[8];
-    int nc = colour_sequence(d, seq);
+    int seq[27];
+    int nc = colour_sequence(p, seq);
     int nq = (n + 3) / 4;
     for (int ci = 0; ci < nc; ++ci) {
         int colour = dir == 0 ? seq[ci] : seq[nc - 1 - ci];
         for (int s = 0; s < L->N; ++s) {
             int c[3];
             site_coords(d, n, s, c);
-            if (parity_code(d, c) != colour) continue;
+            if (parity_code(p, c) != colour) continue;
             const double* a = L->a + (size_t)s * p->NS;
             double aii = a[p->centre];
             double z = 0.0;
@@ -441,7 +469,7 @@ static void gs_sweep(const oracle_problem* p, int l, const olevel* L, int dir, d
                 double aij = a[o];
                 if (aij == 0.0) continue;
                 int off[3], cc[3];
-                offset_of(d, o, off);
+                offset_of(d, p->W, o, off);
                 for (int t = 0; t < 3; ++t) cc[t] = c[t] + off[t];
                 int j = site_index(d, n, cc);
                 if (j < 0) continue;
@@ -575,7 +603,7 @@ static void build_fine_operator(oracle_problem* p, olevel* L, const double* kapp
                 if (site_index(d, n, cc) < 0) continue;
                 int off[3] = {0, 0, 0};
                 off[ax] = sg;
-                int o = (off[0] + 1) + 3 * (off[1] + 1) + (d == 3 ? 9 * (off[2] + 1) : 0);
+                int o = offset_index(p, off[0], off[1], off[2]);
                 a[o] = -scale * inv_h2;
             }
         }
@@ -606,7 +634,7 @@ static void build_fine_operator_q1(oracle_problem* p, olevel* L, double kappa2_c
         double* a = L->a + (size_t)s * p->NS;
         for (int o = 0; o < p->NS; ++o) {
             int off[3], cc[3] = {0, 0, 0};
-            offset_of(d, o, off);
+            offset_of(d, p->W, o, off);
             for (int t = 0; t < d; ++t) cc[t] = c[t] + off[t];
             if (site_index(d, n, cc) < 0) continue;
             double K[3], M[3];
@@ -627,6 +655,55 @@ static void build_fine_operator_q1(oracle_problem* p, olevel* L, double kappa2_c
     }
 }
 
+/* Fine-level finite-difference matrix of the squared shifted Laplacian
+ * (kappa^2 - Delta)^2 = Delta^2 - 2 kappa^2 Delta + kappa^4 (Eq.
+ * squared_shifted_laplace, Sec. 5.1.1, boundary conditions u = du/dn = 0), 2D,
+ * constant kappa^2:
+ *   Delta_h^2 -- the 13-point stencil h^-4 [20 at the centre, -8 at the four axis
+ *     neighbours, 2 at the four diagonal neighbours, 1 at distance 2 along the
+ *     axes]; a coupling that lands on a boundary vertex is dropped (u = 0 there),
+ *     one that lands on the ghost vertex behind it takes the value of its mirror
+ *     image across the boundary vertex (the centred difference of du/dn = 0);
+ *   -2 kappa^2 Delta_h -- the 5-point stencil 2 kappa^2 h^-2 [4 at the centre, -1 at
+ *     the axis neighbours] with u = 0 on the boundary;
+ *   kappa^4 on the diagonal;
+ * all times s = h^2 (scale_hd = 1) or 1. */
+static void build_fine_operator_ssl(oracle_problem* p, olevel* L, double kappa2)
+{
+    int n = L->n;
+    double h = 1.0 / (double)(n + 1);
+    double scale = p->scale_hd ? h * h : 1.0;
+    double ih2 = 1.0 / (h * h), ih4 = ih2 * ih2;
+    static const int bih[13][3] = {{0, 0, 20},  {-1, 0, -8}, {1, 0, -8}, {0, -1, -8}, {0, 1, -8},
+                                   {-1, -1, 2}, {1, -1, 2},  {-1, 1, 2}, {1, 1, 2},   {-2, 0, 1},
+                                   {2, 0, 1},   {0, -2, 1},  {0, 2, 1}};
+    for (int s = 0; s < L->N; ++s) {
+        int c[3];
+        site_coords(2, n, s, c);
+        double* a = L->a + (size_t)s * p->NS;
+        for (int t = 0; t < 13; ++t) {
+            int g[2] = {c[0] + bih[t][0], c[1] + bih[t][1]};
+            int drop = 0;
+            for (int ax = 0; ax < 2; ++ax) {
+                if (g[ax] == -1 || g[ax] == n)
+                    drop = 1;               /* boundary vertex */
+                else if (g[ax] == -2)
+                    g[ax] = 0;              /* ghost behind x = 0: mirror image */
+                else if (g[ax] == n + 1)
+                    g[ax] = n - 1;          /* ghost behind x = 1: mirror image */
+            }
+            if (drop) continue;
+            a[offset_index(p, g[0] - c[0], g[1] - c[1], 0)] += scale * (double)bih[t][2] * ih4;
+        }
+        a[p->centre] += scale * (2.0 * kappa2 * 4.0 * ih2 + kappa2 * kappa2);
+        for (int t = 1; t <= 4; ++t) {
+            int g0 = c[0] + bih[t][0], g1 = c[1] + bih[t][1];
+            if (g0 < 0 || g0 >= n || g1 < 0 || g1 >= n) continue;
+            a[offset_index(p, bih[t][0], bih[t][1], 0)] += -scale * 2.0 * kappa2 * ih2;
+        }
+    }
+}
+
 /* Galerkin triple product A_c = P^T A_f P (Eq. A_ell_1_B_ell_1). */
 static void build_galerkin(oracle_problem* p, const olevel* F, olevel* C)
 {
@@ -637,7 +714,7 @@ static void build_galerkin(oracle_problem* p, const olevel* F, olevel* C)
         double* ac = C->a + (size_t)J * p->NS;
         for (int po = 0; po < p->NS; ++po) {
             int pp[3];
-            offset_of(d, po, pp);
+            offset_of(d, p->W, po, pp);
             int ci[3] = {0, 0, 0};
             double wP = 1.0;
             for (int t = 0; t < d; ++t) {
@@ -651,12 +728,12 @@ static void build_galerkin(oracle_problem* p, const olevel* F, olevel* C)
                 double aij = af[o];
                 if (aij == 0.0) continue;
                 int off[3], cjf[3] = {0, 0, 0};
-                offset_of(d, o, off);
+                offset_of(d, p->W, o, off);
                 for (int t = 0; t < d; ++t) cjf[t] = ci[t] + off[t];
                 if (site_index(d, F->n, cjf) < 0) continue;
                 for (int q = 0; q < p->NS; ++q) {
                     int qq[3], ck[3] = {0, 0, 0};
-                    offset_of(d, q, qq);
+                    offset_of(d, p->W, q, qq);
                     double w = 1.0;
                     for (int t = 0; t < d; ++t) {
                         ck[t] = cj[t] + qq[t];
@@ -690,7 +767,7 @@ static int build_coarse_B(oracle_problem* p, const olevel* F, olevel* C)
             site_coords(d, F->n, F->b_site[e], cf);
             for (int q = 0; q < p->NS; ++q) {
                 int qq[3], ck[3] = {0, 0, 0};
-                offset_of(d, q, qq);
+                offset_of(d, p->W, q, qq);
                 double w = 1.0;
                 for (int t = 0; t < d; ++t) {
                     /* the coarse vertices whose hat function covers fine index cf */
@@ -833,8 +910,11 @@ int oracle_create(int dim, int n, int n_levels, int scale_hd, int disc, int nu1,
 {
     if (!out || (dim != 2 && dim != 3) || n < 1 || n_levels < 1 || m < 0 || nu1 < 0 || nu2 < 0)
         return ERR_ARG;
-    /* the Q1 option takes a constant kappa^2 */
-    if (disc != 0 && (disc != 1 || kappa2)) return ERR_ARG;
+    /* the Q1 and squared-operator options take a constant kappa^2; the squared
+       operator is two-dimensional */
+    if (disc != 0 && ((disc != 1 && disc != 2) || kappa2)) return ERR_ARG;
+    if (disc == 2 && dim != 2) return ERR_ARG;
+    if (n_levels > 32) return ERR_ARG;
     /* n_levels grids: n_{l-1} = (n_l - 1) / 2 must stay >= 1 and exact */
     {
         int nn = n;
@@ -847,8 +927,11 @@ int oracle_create(int dim, int n, int n_levels, int scale_hd, int disc, int nu1,
     oracle_problem* p = calloc(1, sizeof(oracle_problem));
     if (!p) return ERR_OOM;
     p->d = dim;
-    p->NS = dim == 2 ? 9 : 27;
+    p->R = disc == 2 ? 2 : 1;
+    p->W = 2 * p->R + 1;
+    p->NS = dim == 2 ? p->W * p->W : p->W * p->W * p->W;
     p->centre = (p->NS - 1) / 2;
+    p->gamma = 1;
     p->n_levels = n_levels;
     p->scale_hd = scale_hd;
     p->disc = disc;
@@ -892,6 +975,8 @@ int oracle_create(int dim, int n, int n_levels, int scale_hd, int disc, int nu1,
     olevel* Lf = &p->lev[n_levels - 1];
     if (p->disc == 1)
         build_fine_operator_q1(p, Lf, kappa2_const);
+    else if (p->disc == 2)
+        build_fine_operator_ssl(p, Lf, kappa2_const);
     else
         build_fine_operator(p, Lf, kappa2, kappa2_const);
     /* fine B from the given rows (duplicates are summed) */
@@ -957,7 +1042,7 @@ int oracle_create(int dim, int n, int n_levels, int scale_hd, int disc, int nu1,
             site_coords(p->d, L0->n, s, c);
             for (int o = 0; o < p->NS; ++o) {
                 int off[3], cc[3];
-                offset_of(p->d, o, off);
+                offset_of(p->d, p->W, o, off);
                 for (int t = 0; t < 3; ++t) cc[t] = c[t] + off[t];
                 int j = site_index(p->d, L0->n, cc);
                 if (j < 0) continue;
@@ -1002,7 +1087,7 @@ fail:
 /* coarsest exact sampler and the V-cycle (Alg. 1)                     */
 /* ------------------------------------------------------------------ */
 
-static void coarsest_sample(oracle_problem* p, double* x, const double* fd, const double* d)
+static void coarsest_sample(oracle_problem* p, double* x, const double* fd, const double* d, uint32_t slot)
 {
     int n0 = p->n0, m = p->m;
     olevel* L0 = &p->lev[0];
@@ -1022,7 +1107,7 @@ static void coarsest_sample(oracle_problem* p, double* x, const double* fd, cons
         yv[i] = acc / p->L0[(size_t)i * n0 + i];
     }
     /* y += z */
-    for (int i = 0; i < n0; ++i) yv[i] += draw(p, 2u, 0, 0u, (uint32_t)(i >> 1), i & 1);
+    for (int i = 0; i < n0; ++i) yv[i] += draw(p, 2u, 0, slot, (uint32_t)(i >> 1), i & 1);
     /* L^T x = y */
     for (int i = n0 - 1; i >= 0; --i) {
         double acc = yv[i];
@@ -1043,7 +1128,7 @@ static void restrict_to(const oracle_problem* p, const olevel* F, const olevel* 
         double acc = 0.0;
         for (int po = 0; po < p->NS; ++po) {
             int pp[3], ci[3] = {0, 0, 0};
-            offset_of(d, po, pp);
+            offset_of(d, p->W, po, pp);
             double w = 1.0;
             for (int t = 0; t < d; ++t) {
                 ci[t] = 2 * cj[t] + 1 + pp[t];
@@ -1067,7 +1152,7 @@ static void prolong_add(const oracle_problem* p, const olevel* C, const olevel* 
         double acc = 0.0;
         for (int q = 0; q < p->NS; ++q) {
             int qq[3], ck[3] = {0, 0, 0};
-            offset_of(d, q, qq);
+            offset_of(d, p->W, q, qq);
             double w = 1.0;
             for (int t = 0; t < d; ++t) {
                 ck[t] = (cf[t] >> 1) + qq[t];
@@ -1081,15 +1166,25 @@ static void prolong_add(const oracle_problem* p, const olevel* C, const olevel* 
     }
 }
 
+/* Alg. 1 on level l.  The v-th visit of level l within a cycle (v = 0, 1, ...
+ * in call order) draws with slots 2 (v S + j) for its j-th pre sweep and
+ * 2 (v S + j) + 1 for its j-th post sweep, S = max(nu1, nu2, 1), and the coarsest
+ * level's v-th visit with slot v; a V-cycle has v = 0 throughout.  The finest
+ * level makes one coarse call, every other level gamma (Alg. 1: gamma_L = 1,
+ * gamma_l = gamma below). */
 static void mgmc_level(oracle_problem* p, int l, double* x, const double* fd, const double* d)
 {
+    const int v = p->visit[l]++;
     if (l == 0) {
-        coarsest_sample(p, x, fd, d);
+        coarsest_sample(p, x, fd, d, (uint32_t)v);
         return;
     }
     olevel* L = &p->lev[l];
     olevel* C = &p->lev[l - 1];
-    for (int j = 0; j < p->nu1; ++j) lowrank_gibbs(p, l, 0, x, fd, d, (uint32_t)(2 * j), NULL, NULL, p->noise);
+    int S = p->nu1 > p->nu2 ? p->nu1 : p->nu2;
+    if (S < 1) S = 1;
+    for (int j = 0; j < p->nu1; ++j)
+        lowrank_gibbs(p, l, 0, x, fd, d, (uint32_t)(2 * (v * S + j)), NULL, NULL, p->noise);
     /* f_{l-1} = P^T (f_l - A~_l theta):  fd_{l-1} = P^T (fd_l - A_l theta),
        d_{l-1} = d_l - B_l^T theta */
     apply_A(p, L, x, L->r);
@@ -1100,9 +1195,11 @@ static void mgmc_level(oracle_problem* p, int l, double* x, const double* fd, co
         for (int k = 0; k < p->m; ++k) C->dv[k] = d[k] - C->dv[k];
     }
     memset(C->x, 0, sizeof(double) * C->N);
-    mgmc_level(p, l - 1, C->x, C->f, C->dv);
+    const int calls = l == p->n_levels - 1 ? 1 : p->gamma;
+    for (int g = 0; g < calls; ++g) mgmc_level(p, l - 1, C->x, C->f, C->dv);
     prolong_add(p, C, L, C->x, x);
-    for (int j = 0; j < p->nu2; ++j) lowrank_gibbs(p, l, 1, x, fd, d, (uint32_t)(2 * j + 1), NULL, NULL, p->noise);
+    for (int j = 0; j < p->nu2; ++j)
+        lowrank_gibbs(p, l, 1, x, fd, d, (uint32_t)(2 * (v * S + j) + 1), NULL, NULL, p->noise);
 }
 
 static double qoi_of(const oracle_problem* p, const double* x)
@@ -1124,6 +1221,7 @@ int oracle_sample(oracle_problem* p, int64_t n_steps, uint64_t seed, uint64_t st
         olevel* Lf = &p->lev[p->n_levels - 1];
         memset(Lf->f, 0, sizeof(double) * Lf->N);      /* fd_L = 0 */
         if (p->m > 0) memcpy(Lf->dv, p->y, sizeof(double) * p->m);   /* d_L = y */
+        memset(p->visit, 0, sizeof(p->visit));
         mgmc_level(p, p->n_levels - 1, x, Lf->f, Lf->dv);
         if (qoi_out) qoi_out[s] = qoi_of(p, x);
     }
@@ -1200,6 +1298,19 @@ int oracle_level_n(const oracle_problem* p, int l)
 {
     if (!p || l < 0 || l >= p->n_levels) return ERR_ARG;
     return p->lev[l].n;
+}
+
+int oracle_set_gamma(oracle_problem* p, int gamma)
+{
+    if (!p || gamma < 1 || gamma > 2) return ERR_ARG;
+    /* the slots of the last visit of the coarsest level must fit 16 bits */
+    double visits = 1.0;
+    for (int l = p->n_levels - 2; l >= 1; --l) visits *= gamma;
+    int S = p->nu1 > p->nu2 ? p->nu1 : p->nu2;
+    if (S < 1) S = 1;
+    if (2.0 * visits * S > 65536.0) return ERR_ARG;
+    p->gamma = gamma;
+    return 0;
 }
 
 int oracle_level_stencil(const oracle_problem* p, int l, double* out)

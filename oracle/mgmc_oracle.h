@@ -28,8 +28,11 @@ typedef struct oracle_problem oracle_problem;
  * obs_site/obs_w hold m rows of nnz_per_obs (fine site, weight); site -1 is
  * an ignored (boundary) entry.  Gamma is m x m row-major SPD, y has m
  * entries.  qoi_site/qoi_w: n_qoi entries of the QoI vector F_L.
- * disc: fine-grid discretisation of kappa^2 - Delta, 0 the finite-difference
- * stencil, 1 the Q1 finite-element matrix (constant kappa^2: kappa2 = NULL). */
+ * disc: fine-grid discretisation, 0 the finite-difference stencil of
+ * kappa^2 - Delta, 1 its Q1 finite-element matrix (constant kappa^2: kappa2 =
+ * NULL), 2 the 13-point finite-difference matrix of the squared operator
+ * (kappa^2 - Delta)^2 with u = du/dn = 0 (2D, constant kappa^2; radius-2
+ * stencils on every level). */
 int oracle_create(int dim, int n, int n_levels, int scale_hd, int disc, int nu1, int nu2,
                   const double* kappa2, double kappa2_const,
                   int m, const int32_t* obs_site, const double* obs_w, int nnz_per_obs,
@@ -38,11 +41,16 @@ int oracle_create(int dim, int n, int n_levels, int scale_hd, int disc, int nu1,
                   oracle_problem** out);
 void oracle_destroy(oracle_problem* p);
 
+/* Cycle index of Alg. 1: gamma = 1 (V-cycle, the default) or 2 (W-cycle: the
+ * finest level calls the next grid once, every coarser level calls its coarse
+ * grid twice). */
+int oracle_set_gamma(oracle_problem* p, int gamma);
+
 /* Level queries (l = 0 coarsest .. n_levels-1 finest). */
 int oracle_level_n(const oracle_problem* p, int l);
-/* Full 3^d stencil of level l: out[N * 3^d], offset index (3D form;
- * 2D drops the dz term)
- * (dx+1) + 3 (dy+1) + 9 (dz+1); out-of-domain couplings are 0. */
+/* Full W^d stencil of level l, W = 2R + 1 (R = 2 for disc 2, else 1):
+ * out[N * W^d], offset index (3D form; 2D drops the dz term)
+ * (dx+R) + W (dy+R) + W^2 (dz+R); out-of-domain couplings are 0. */
 int oracle_level_stencil(const oracle_problem* p, int l, double* out);
 /* Dense B_l (N x m, row-major). */
 int oracle_level_B_dense(const oracle_problem* p, int l, double* out);
@@ -63,7 +71,8 @@ int oracle_smoother_step_given(const oracle_problem* p, int l, int dir,
                                double* x, const double* fd, const double* d,
                                const double* zdiag, const double* zlr);
 
-/* Run n_steps MGMC V-cycles (Alg. 1, gamma = 1) on the finest level.
+/* Run n_steps MGMC cycles (Alg. 1 with the cycle index of oracle_set_gamma) on
+ * the finest level.
  * x (in/out) is the dense fine state.  Cycle m uses the Philox counters of
  * cycle index step_offset + m.  noise = 0 gives the deterministic
  * multigrid iteration.  qoi_out (may be NULL) receives F_L^T x after each

@@ -186,7 +186,8 @@ class Problem:
     qoi_site: Optional[np.ndarray] = None
     qoi_w: Optional[np.ndarray] = None
     scale_hd: int = 1
-    disc: int = 0                         # 0 finite differences, 1 Q1 finite elements (constant kappa^2)
+    disc: int = 0                         # 0 finite differences, 1 Q1 finite elements, 2 squared shifted
+                                          # Laplacian (13-point finite differences; 1 and 2 constant kappa^2)
     meta: dict = field(default_factory=dict)
 
     @property
@@ -221,8 +222,10 @@ def make_problem(name: str, dim: int, n: int, *, n_levels: Optional[int] = None,
     seeded entries uniform in [lo, hi] instead of sigma2 I.  ball_radius: observations
     and QoI are averages over balls of that radius (the QoI centred in the domain)
     instead of point values and the central box."""
-    if disc == 1 and kappa2_seed is not None:
-        raise ValueError("the Q1 discretisation takes a constant kappa^2")
+    if disc in (1, 2) and kappa2_seed is not None:
+        raise ValueError("the Q1 and squared-operator discretisations take a constant kappa^2")
+    if disc == 2 and dim != 2:
+        raise ValueError("the squared shifted Laplacian is two-dimensional")
     if n_levels is None:
         n_levels = levels_for(n, coarsest)
     k2 = None if kappa2_seed is None else kappa2_field(n, dim, kappa2_seed)
@@ -273,6 +276,16 @@ def table1a(n: int, n_levels: Optional[int] = None) -> Problem:
     measurement_definition)."""
     return make_problem(f"table1a-q1-{n}", 2, n, n_levels=n_levels, kappa2_const=100.0, m=8, obs_seed=11,
                         disc=1, gamma_range=(1e-6, 2e-6), ball_radius=0.025)
+
+
+def table1c(n: int, n_levels: Optional[int] = None) -> Problem:
+    """The setting of the paper's Table 1c (Sec. 5.1): the squared shifted Laplacian
+    (kappa^2 - Delta)^2 with kappa^-1 = 0.1 in 2D, 13-point finite differences with
+    u = du/dn = 0, and the observations and QoI of Table 1a (8 averages over balls of
+    radius 0.025, variances uniform in [1e-6, 2e-6], values in [1, 4]); the paper samples
+    it with a W-cycle."""
+    return make_problem(f"table1c-ssl-{n}", 2, n, n_levels=n_levels, kappa2_const=100.0, m=8, obs_seed=11,
+                        disc=2, gamma_range=(1e-6, 2e-6), ball_radius=0.025)
 
 
 def config3(n: int = 127, n_levels: Optional[int] = None) -> Problem:

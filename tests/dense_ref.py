@@ -9,7 +9,10 @@ shares no code path with the oracle:
   - A_{l-1} = P^T A_l P and B_{l-1} = P^T B_l (Eq. A_ell_1_B_ell_1);
   - the forward/backward low-rank Gibbs splittings M~ = D + L + B Gamma^-1 B^T
     (Eq. M_lowrank_gibbs) with L the strictly lower part in colour order;
-  - the deterministic V-cycle iteration matrix X_L (Lemma MG-iteration-rep).
+  - the squared shifted Laplacian as the matrix square of the shifted
+    5-point operator plus the diagonal boundary term of u = du/dn = 0;
+  - the deterministic V- and W-cycle iteration matrices X_L (Lemma
+    MG-iteration-rep).
 """
 import numpy as np
 
@@ -27,6 +30,22 @@ def fd_operator(n, d, kappa2, scale_hd=1):
     else:
         lap = np.kron(np.kron(I, I), T) + np.kron(np.kron(I, T), I) + np.kron(np.kron(T, I), I)
     return s * (lap + np.diag(k2))
+
+
+def ssl_operator(n, kappa2, scale_hd=1):
+    """Squared shifted Laplacian (kappa^2 - Delta)^2 in 2D with u = du/dn = 0, as a matrix
+    product: s [(kappa^2 I + L)^2 + 2 h^-4 E] with L = -Delta_h the 5-point Dirichlet matrix
+    and E the diagonal that counts, per vertex, the boundary sides it is adjacent to
+    (the clamped-plate correction of the 13-point stencil: the mirror ghost behind a
+    boundary vertex adds h^-4 where L^2 lacks h^-4 from the dropped boundary row)."""
+    h = 1.0 / (n + 1)
+    L = fd_operator(n, 2, 0.0, scale_hd=0)
+    K = kappa2 * np.eye(n * n) + L
+    idx = np.arange(n * n)
+    i, j = idx % n, idx // n
+    E = np.diag((i == 0).astype(float) + (i == n - 1) + (j == 0) + (j == n - 1))
+    s = h * h if scale_hd else 1.0
+    return s * (K @ K + 2.0 / h ** 4 * E)
 
 
 def q1_operator(n, d, kappa2, scale_hd=1):
@@ -86,13 +105,17 @@ def prolongation(nc, d):
     return np.kron(np.kron(P1, P1), P1)
 
 
-def colour_order(n, d):
-    """Sites in colour-major order (the parity-colour reading), lexicographic inside."""
+def colour_order(n, d, radius=1):
+    """Sites in colour-major order (the parity-colour reading; radius-2 stencils: the
+    nine classes (i mod 3, j mod 3) by code (i mod 3) + 3 (j mod 3)), lexicographic inside."""
+    idx = np.arange(n ** d)
+    if radius == 2:
+        code = (idx % n) % 3 + 3 * ((idx // n) % 3)
+        return np.concatenate([idx[code == c] for c in range(9)])
     if d == 2:
         seq = [(0, 0), (1, 1), (0, 1), (1, 0)]
     else:
         seq = [(0, 0, 0), (0, 1, 1), (1, 0, 1), (1, 1, 0), (0, 0, 1), (0, 1, 0), (1, 0, 0), (1, 1, 1)]
-    idx = np.arange(n ** d)
     coords = [idx % n, (idx // n) % n] + ([idx // (n * n)] if d == 3 else [])
     perm = []
     for c in seq:
@@ -116,13 +139,20 @@ def B_dense(N, obs_site, obs_w):
 class Hierarchy:
     """Dense operators of every level, index 0 = coarsest."""
 
-    def __init__(self, n, d, n_levels, kappa2, B=None, Gamma=None, scale_hd=1, disc=0):
+    def __init__(self, n, d, n_levels, kappa2, B=None, Gamma=None, scale_hd=1, disc=0, gamma=1):
         self.d = d
+        self.radius = 2 if disc == 2 else 1
+        self.gamma = gamma
         self.A = [None] * n_levels
         self.B = [None] * n_levels
         self.P = [None] * n_levels     # P[l]: level l-1 -> l
         self.n = [None] * n_levels
-        A = q1_operator(n, d, kappa2, scale_hd) if disc == 1 else fd_operator(n, d, kappa2, scale_hd)
+        if disc == 2:
+            A = ssl_operator(n, kappa2, scale_hd)
+        elif disc == 1:
+            A = q1_operator(n, d, kappa2, scale_hd)
+        else:
+            A = fd_operator(n, d, kappa2, scale_hd)
         self.A[-1] = A
         self.B[-1] = B if B is not None else np.zeros((n ** d, 0))
         self.n[-1] = n
@@ -146,7 +176,7 @@ class Hierarchy:
     def splitting(self, l, direction):
         """M~ of Eq. M_lowrank_gibbs (omega = 1) in natural site order."""
         A = self.A[l]
-        perm = colour_order(self.n[l], self.d)
+        perm = colour_order(self.n[l], self.d, self.radius)
         Ap = A[np.ix_(perm, perm)]
         Mp = np.tril(Ap) if direction == 0 else np.triu(Ap)
         M = np.zeros_like(A)
@@ -158,7 +188,10 @@ class Hierarchy:
         return np.eye(M.shape[0]) - np.linalg.solve(M, self.Atilde(l))
 
     def iteration_matrix(self, l=None):
-        """X_l of the noise-free V(1,1)-cycle with exact coarsest solve."""
+        """X_l of the noise-free (1,1)-cycle with exact coarsest solve: the coarse
+        correction of level l applies the coarse cycle gamma_l times from zero,
+        psi = (I - X_{l-1}^gamma_l) A~_{l-1}^-1 P^T r, with gamma_L = 1 on the finest
+        level and gamma_l = gamma below (Alg. 1)."""
         if l is None:
             l = len(self.A) - 1
         At = self.Atilde(l)
@@ -168,7 +201,9 @@ class Hierarchy:
         P = self.P[l]
         Ac = self.Atilde(l - 1)
         Xc = self.iteration_matrix(l - 1)
-        cgc = np.eye(N) - P @ (np.eye(Ac.shape[0]) - Xc) @ np.linalg.solve(Ac, P.T @ At)
+        reps = 1 if l == len(self.A) - 1 else self.gamma
+        Xg = np.linalg.matrix_power(Xc, reps)
+        cgc = np.eye(N) - P @ (np.eye(Ac.shape[0]) - Xg) @ np.linalg.solve(Ac, P.T @ At)
         return self.smoother_matrix(l, 1) @ cgc @ self.smoother_matrix(l, 0)
 
 

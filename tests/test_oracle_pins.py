@@ -31,12 +31,15 @@ def _hier(p):
 
 
 def _stencil_to_dense(st, n, d):
+    """Dense matrix of a full W^d stencil (W = 3, or 5 for radius-2 stencils)."""
     N = n ** d
+    W = int(round(st.shape[1] ** (1.0 / d)))
+    R = W // 2
     A = np.zeros((N, N))
     for s in range(N):
         c = [s % n, (s // n) % n] + ([s // (n * n)] if d == 3 else [])
-        for o in range(3 ** d):
-            off = [o % 3 - 1, (o // 3) % 3 - 1] + ([o // 9 - 1] if d == 3 else [])
+        for o in range(W ** d):
+            off = [o % W - R, (o // W) % W - R] + ([o // (W * W) - R] if d == 3 else [])
             cc = [c[a] + off[a] for a in range(d)]
             if all(0 <= v < n for v in cc):
                 t = cc[0] + n * cc[1] + (n * n * cc[2] if d == 3 else 0)
