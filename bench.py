@@ -216,6 +216,8 @@ WORKLOADS = {
     "warmstart-255": {"n": 255, "chains": 64, "warm": True},       # learned warm start (U-Net), 255^2
     "gibbs-vs-mgmc-2d": {"n": 511, "chains": 1, "table": True},   # Table 1 comparison, 31^2 .. 511^2
     "gibbs-vs-mgmc-2d-q1": {"n": 511, "chains": 1, "table": True, "q1": True},   # Table 1a setting (Q1 elements)
+    # Table 1c setting: squared shifted Laplacian (13-point FD), W-cycle, FP64
+    "gibbs-vs-mgmc-2d-ssl": {"n": 511, "chains": 1, "table": True, "ssl": True},
     "convergence-2d": {"n": 255, "chains": 512, "conv": True},   # Sec. 5.3: R, Z, rates, RMSE (Q1, 31^2..255^2)
     "tc-gemm-8192": {"n": 8192, "chains": 1, "gemm": True},      # the U-Net's tensor-core GEMM, 8192^3 BF16
 }
@@ -787,7 +789,8 @@ def run_gibbs_table(args):
     grid: IACT of the QoI (device Wolff estimate after a burn-in), time per step (CUDA
     events over back-to-back steps, state resident) and time per independent sample for
     the plain Gibbs sampler (one symmetric low-rank Gibbs sweep per step) and MGMC
-    (V(1,1)-cycle); the exact Cholesky sampler (single-grid hierarchy, FP64) on 31^2."""
+    (V(1,1)-cycle); the exact Cholesky sampler (single-grid hierarchy, FP64) on 31^2.  The
+    squared-operator form (Table 1c) runs FP64 with MGMC's W-cycle."""
     import torch
     ws, rank, local = dist_env()
     if rank != 0:
@@ -816,18 +819,22 @@ def run_gibbs_table(args):
         return st["tau_int"], st["tau_err"], ms
 
     q1 = bool(WORKLOADS[args.workload].get("q1"))
-    make = inputs.table1a if q1 else inputs.config2
+    ssl = bool(WORKLOADS[args.workload].get("ssl"))
+    make = inputs.table1c if ssl else (inputs.table1a if q1 else inputs.config2)
+    prec = "fp64" if ssl else "fp32"
     rows = []
     for n in (31, 63, 127, 255, 511):
         p = make(n=n)
         row = {"n": n}
         # Gibbs: tau grows like h^-2 (about 100 at 31^2 for kappa^2 = 10); chains of up to 400 000 steps
-        n_g = min(400000, 20000 * ((n + 1) // 32) ** 2)
-        s = M.Sampler(p, precision="fp32", gibbs=True, device=local)
+        # (the squared operator: up to 200 000, its Gibbs tau cannot be estimated reliably on the fine grids)
+        n_g = min(200000 if ssl else 400000, 20000 * ((n + 1) // 32) ** 2)
+        s = M.Sampler(p, precision=prec, gibbs=True, device=local)
         tg, eg, msg = measure(s, n_g, 2000, 200)
         s.close()
-        s = M.Sampler(p, precision="fp32", device=local)
-        tm, em, msm = measure(s, 5000, 100, 200)
+        s = M.Sampler(p, precision=prec, device=local)
+        tm, em, msm = measure(s, 3000 if ssl else 5000, 100, 50 if ssl else 200)
+        row["launches_per_cycle_mgmc"] = s.launches_per_cycle()
         s.close()
         row.update({"gibbs_steps": n_g, "tau_gibbs": tg, "tau_gibbs_err": eg, "ms_per_step_gibbs": msg,
                     "ms_per_indep_gibbs": msg * tg, "tau_mgmc": tm, "tau_mgmc_err": em, "ms_per_step_mgmc": msm,
@@ -850,17 +857,24 @@ def run_gibbs_table(args):
     line = {
         "metric": "time per independent QoI sample (MGMC, 511^2)", "value": big["ms_per_indep_mgmc"], "unit": "ms",
         "n_gpus": 1, "steps": 200, "warmup": 5, "ms_per_step": big["ms_per_step_mgmc"], "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": (("gibbs-vs-mgmc-2d-q1: the Table 1a setting (Q1 finite elements, kappa^-1 = 0.1, "
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if ssl else "f32", "data": "synthetic",
+        "config": {"workload": (("gibbs-vs-mgmc-2d-ssl: the Table 1c setting (squared shifted Laplacian, 13-point "
+                                 "finite differences with u = du/dn = 0, kappa^-1 = 0.1, 8 ball obs, Gamma diagonal "
+                                 "in [1e-6, 2e-6]), MGMC W-cycle") if ssl else
+                                ("gibbs-vs-mgmc-2d-q1: the Table 1a setting (Q1 finite elements, kappa^-1 = 0.1, "
                                  "8 point obs, Gamma diagonal in [1e-6, 2e-6])") if q1 else
                                 ("gibbs-vs-mgmc-2d: the Sec. 5.2 / Table 1 comparison on the 2D posterior "
                                  "(kappa^2 = 10 exp(g), 16 point obs, Gamma = 1e-4 I)")) +
-                               ", 31^2 .. 511^2, one FP32 chain per sampler and grid; Cholesky = single-grid "
-                               "exact sampler (FP64, one CTA)",
+                               f", 31^2 .. 511^2, one {prec.upper()} chain per sampler and grid; Cholesky = "
+                               "single-grid exact sampler (FP64, one CTA)",
                    "table": rows,
                    "tau_from": "device Wolff estimate (S = 1.5) of each chain after its burn-in (Gibbs 2000, MGMC 100)",
-                   "timing": "CUDA events over 200 back-to-back steps, state resident (grids up to 511^2 are "
-                             "L2-resident)"},
+                   "timing": ("CUDA events over 200 (Gibbs) / 50 (MGMC) back-to-back steps" if ssl else
+                              "CUDA events over 200 back-to-back steps") +
+                             ", state resident (grids up to 511^2 are L2-resident)",
+                   "paper_table": ("Table 1c (sequential C++ on a Xeon 8168): MGMC 0.36 .. 110.39 ms per sample, "
+                                   "IACT 2.22 .. 3.94, 0.81 .. 435.17 ms per independent sample (32^2 .. 512^2 "
+                                   "cells)") if ssl else None},
         "roofline": None, "cpu_baseline": None, "e2e": None,
         "clocks": clk,
     }

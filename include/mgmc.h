@@ -96,16 +96,33 @@ typedef struct {
                          matrix, a_ij = int grad phi_i . grad phi_j + kappa^2 phi_i phi_j
                          (9/27-point; constant kappa^2 only: kappa2 must be NULL), divided
                          by h^d when scale_hd = 0.  The coarse grids are Galerkin products
-                         either way (for Q1 they are the Q1 matrices of the coarse grids). */
+                         either way (for Q1 they are the Q1 matrices of the coarse grids).
+                         MGMC_SSL: the squared shifted Laplacian (kappa^2 - Delta)^2 of
+                         Eq. squared_shifted_laplace with u = du/dn = 0 (Sec. 5.1.1), the
+                         13-point finite-difference stencil h^-4 [20, -8, 2, 1] with mirror
+                         ghosts behind the boundary vertices, plus 2 kappa^2 (-Delta_h) and
+                         kappa^4, times h^2 (scale_hd = 1); 2D, constant kappa^2, FP64.  Every
+                         grid carries a radius-2 (5 x 5) stencil and is swept in the nine
+                         colours (i mod 3, j mod 3); the general (one launch per colour) path
+                         runs every grid but the coarsest, which is sampled exactly. */
     int band_min_n;   /* 2D FP32 V-cycles (nu1 = nu2 = 1): the 9-point grids below the finest
                          with n >= band_min_n (and above coarse_max_n) run in the streaming
                          band kernels, the smaller ones in shared-memory tile kernels.  0 selects
                          the default (255); a value above n keeps every grid on the tiles.  Both
                          kernel families give bitwise identical states; a batch takes the value
                          of its first configuration. */
+    int gamma;        /* cycle index of Alg. 1: 1 V-cycle, 2 W-cycle (the finest grid calls the
+                         next grid once, every coarser grid calls its coarse grid twice, the
+                         coarse state carried from one call to the next; Sec. 5.1.3 uses it
+                         for MGMC_SSL); 0 selects 2 for MGMC_SSL and 1 otherwise.  The v-th
+                         visit of a grid within a cycle draws its sweep noise with slots
+                         2 (v S + j) (pre) and 2 (v S + j) + 1 (post), S = max(nu1, nu2, 1),
+                         and the coarsest grid's v-th sample with slot v; a W-cycle runs on
+                         the general path with the coarsest grid alone in the coarse kernel.
+                         Single-chain handles only (mgmc_create_batch takes 0 or 1). */
 } mgmc_config;
 
-enum { MGMC_FD = 0, MGMC_Q1 = 1 };
+enum { MGMC_FD = 0, MGMC_Q1 = 1, MGMC_SSL = 2 };
 
 /* Fill cfg with the paper's defaults for a dim-dimensional n^dim grid. */
 mgmc_status mgmc_config_default(mgmc_config* cfg, int dim, int n);
@@ -196,9 +213,10 @@ mgmc_status mgmc_qoi_stats_noalloc(const double* qoi, int64_t n, int64_t burn_in
 
 /* The finest grid's operator A_L (without the observation term) exactly as
  * mgmc_create assembles it from cfg->dim, n, scale_hd and disc (Sec. 2.3 /
- * 5.1.1): out = host [n^dim * 3^dim], the coupling of site s to site s + o at
- * out[s * 3^dim + o], offset o = (dx+1) + 3 (dy+1) [+ 9 (dz+1)], 0 where the
- * neighbour is a boundary vertex.  kappa2: host [n^dim] or NULL (kappa2_const).
+ * 5.1.1): out = host [n^dim * W^dim], W = 2R + 1 with the stencil radius R (2 for
+ * MGMC_SSL, else 1), the coupling of site s to site s + o at out[s * W^dim + o],
+ * offset o = (dx+R) + W (dy+R) [+ W^2 (dz+R)], 0 where the neighbour is a
+ * boundary vertex.  kappa2: host [n^dim] or NULL (kappa2_const).
  * Host only: needs no device.  MGMC_ERR_ARG for bad sizes or values. */
 mgmc_status mgmc_fine_operator(const mgmc_config* cfg, const double* kappa2, double kappa2_const, double* out);
 

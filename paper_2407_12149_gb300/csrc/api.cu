@@ -35,10 +35,12 @@ mgmc_status fail(mgmc_status code, const std::string& msg)
             return fail(MGMC_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e));                     \
     } while (0)
 
-long long padded_pitch(int n, int elem_bytes)
+// elements per padded row: 4 leading elements, the n interior sites and R trailing
+// halo elements (R = stencil radius), rounded up to 128 bytes
+long long padded_pitch(int n, int elem_bytes, int R = 1)
 {
     int align = 128 / elem_bytes;
-    return ((long long)(n + 5) + align - 1) / align * align;
+    return ((long long)(n + 4 + R) + align - 1) / align * align;
 }
 
 struct Buffers {
@@ -106,6 +108,7 @@ struct mgmc_ctx {
     int launches = 0;
     size_t coarse_smem = 0;   // dynamic shared memory of the coarse-grid kernel
     bool fused = false;   // 2D, nu1 = nu2 = 1: fused tile kernels on the grids above coarse_max_n
+    bool recursive = false;   // W-cycle or radius-2 grids: general kernels, cycle enqueued recursively
     DevProblem* P_dev = nullptr;   // device copy of P (batched launches)
     // batch handle: per-chain handles and the job tables of the batched launches
     std::vector<mgmc_ctx*> sub;
@@ -184,9 +187,12 @@ mgmc_status build_device_levels(mgmc_ctx* h, const HostProblem& hp)
         D.level = l;
         D.dim = d;
         D.n = HL.n;
-        D.pitch = (int)padded_pitch(HL.n, sizeof(T));
-        D.plane = (long long)D.pitch * (HL.n + 2);
-        D.base = 4 + D.pitch + (d == 3 ? D.plane : 0);
+        // radius-R stencils read R halo rows and columns around the interior
+        const int R = hp.R;
+        D.rad = R;
+        D.pitch = (int)padded_pitch(HL.n, sizeof(T), R);
+        D.plane = (long long)D.pitch * (HL.n + 2 * R);
+        D.base = 4 + (long long)R * D.pitch + (d == 3 ? D.plane : 0);
         D.alloc = d == 3 ? D.plane * (HL.n + 2) : D.plane;
         auto off = [&](long long s) {
             int i = (int)(s % HL.n), j = (int)((s / HL.n) % HL.n), k = d == 3 ? (int)(s / ((long long)HL.n * HL.n)) : 0;
@@ -434,11 +440,56 @@ void enqueue_cycle_batch(mgmc_ctx* h, cudaStream_t s, int& launches)
     launch_qoi_batch<T>((const QoiJob<T>*)h->jobs_qoi, nc, s, launches);
 }
 
+// Alg. 1 on grid l of the general path, recursively: the v-th visit of the grid uses the
+// noise slots 2 (v S + j) / 2 (v S + j) + 1, the coarsest grid's v-th sample slot v; the
+// finest grid calls grid l-1 once, every other grid cfg.gamma times from psi = 0.
+template <typename T>
+void enqueue_level(mgmc_ctx* h, int l, std::vector<int>& visit, cudaStream_t s, int& launches)
+{
+    auto& lv = levels_of<T>(h);
+    const DevProblem& P = h->P;
+    const int Lf = h->L - 1;
+    const int v = visit[(size_t)l]++;
+    if (l == 0) {
+        launch_coarsest_slot<T>(lv[0], P, h->chol, h->n0, (unsigned)v, s, launches);
+        return;
+    }
+    const DevLevel<T>& D = lv[l];
+    const int S = std::max(1, std::max(h->cfg.nu1, h->cfg.nu2));
+    const bool prof = h->profile && l == Lf;
+    for (int j = 0; j < h->cfg.nu1; ++j) {
+        const unsigned slot = (unsigned)(2 * (v * S + j));
+        if (prof && j == 0) cudaEventRecordWithFlags(h->ev[0], s, cudaEventRecordExternal);
+        launch_sweep<T>(D, P, 0, slot, s, launches);
+        if (prof && j == 0) cudaEventRecordWithFlags(h->ev[1], s, cudaEventRecordExternal);
+        launch_lowrank<T>(D, P, 0, slot, j == h->cfg.nu1 - 1, s, launches);
+    }
+    if (h->cfg.nu1 == 0) launch_lowrank<T>(D, P, -1, 0u, true, s, launches);
+    launch_restrict<T>(D, lv[l - 1], s, launches);
+    cudaMemsetAsync(lv[l - 1].x, 0, (size_t)lv[l - 1].alloc * sizeof(T), s);
+    const int calls = l == Lf ? 1 : h->cfg.gamma;
+    for (int g = 0; g < calls; ++g) enqueue_level<T>(h, l - 1, visit, s, launches);
+    launch_prolong<T>(lv[l - 1], D, s, launches);
+    for (int j = 0; j < h->cfg.nu2; ++j) {
+        const unsigned slot = (unsigned)(2 * (v * S + j) + 1);
+        if (prof && j == 0) cudaEventRecordWithFlags(h->ev[2], s, cudaEventRecordExternal);
+        launch_sweep<T>(D, P, 1, slot, s, launches);
+        if (prof && j == 0) cudaEventRecordWithFlags(h->ev[3], s, cudaEventRecordExternal);
+        launch_lowrank<T>(D, P, 1, slot, false, s, launches);
+    }
+}
+
 template <typename T>
 void enqueue_cycle(mgmc_ctx* h, cudaStream_t s, int& launches)
 {
     if (h->is_batch() || h->fused) {
         enqueue_cycle_batch<T>(h, s, launches);
+        return;
+    }
+    if (h->recursive && !h->cfg.gibbs) {
+        std::vector<int> visit((size_t)h->L, 0);
+        enqueue_level<T>(h, h->L - 1, visit, s, launches);
+        launch_qoi<T>(levels_of<T>(h)[h->L - 1], h->n_qoi, h->q_site, h->q_w, h->P, s, launches);
         return;
     }
     auto& lv = levels_of<T>(h);
@@ -664,6 +715,17 @@ mgmc_status mgmc_create(const mgmc_config* cfg_in, const mgmc_allocator* alloc, 
     for (int nn = cfg.n; nn >= 3; nn = (nn - 1) / 2) ++max_levels;
     if (cfg.n_levels == 0) cfg.n_levels = max_levels;
     if (cfg.n_levels < 1 || cfg.n_levels > max_levels) return fail(MGMC_ERR_ARG, "n_levels out of range");
+    if (cfg.disc == MGMC_SSL && cfg.precision != MGMC_FP64)
+        return fail(MGMC_ERR_ARG, "the squared shifted Laplacian runs in FP64");
+    if (cfg.gamma < 0 || cfg.gamma > 2) return fail(MGMC_ERR_ARG, "gamma must be 0, 1 or 2");
+    if (cfg.gamma == 0) cfg.gamma = cfg.disc == MGMC_SSL ? 2 : 1;
+    {
+        // the noise slots of the last visit of the coarsest grid must fit 16 bits
+        double visits = 1.0;
+        for (int l = cfg.n_levels - 2; l >= 1; --l) visits *= cfg.gamma;
+        const int S = std::max(1, std::max(cfg.nu1, cfg.nu2));
+        if (2.0 * visits * S > 65536.0) return fail(MGMC_ERR_ARG, "too many grid visits per cycle for the noise slots");
+    }
     if (cfg.gibbs != 0 && cfg.gibbs != 1) return fail(MGMC_ERR_ARG, "gibbs must be 0 or 1");
     if (cfg.gibbs && cfg.n_levels < 2) return fail(MGMC_ERR_ARG, "the Gibbs sampler needs n_levels >= 2");
     for (int t = 0; t < n_qoi; ++t)
@@ -702,11 +764,14 @@ mgmc_status mgmc_create(const mgmc_config* cfg_in, const mgmc_allocator* alloc, 
             if (hp.lev[l].n <= cmax && bytes + 16384 <= budget) h->top = l;
         }
     }
-    // the Gibbs sampler sweeps the finest grid with the unfused kernels, outside the coarse kernel
-    if (cfg.gibbs) h->top = 0;
+    // the Gibbs sampler sweeps the finest grid with the unfused kernels, outside the coarse
+    // kernel; W-cycles and radius-2 grids run every grid above the coarsest on the general
+    // path, the cycle enqueued recursively
+    h->recursive = cfg.gamma == 2 || cfg.disc == MGMC_SSL;
+    if (cfg.gibbs || h->recursive) h->top = 0;
     h->n0 = hp.n0;
     h->f_norm = hp.f_norm;
-    h->fused = cfg.dim == 2 && cfg.nu1 == 1 && cfg.nu2 == 1 && !cfg.gibbs;
+    h->fused = cfg.dim == 2 && cfg.nu1 == 1 && cfg.nu2 == 1 && !cfg.gibbs && !h->recursive;
     auto cleanup = [&](mgmc_status s) {
         h->buf.release();
         delete h;
@@ -736,9 +801,9 @@ mgmc_status mgmc_create(const mgmc_config* cfg_in, const mgmc_allocator* alloc, 
     h->n_qoi = n_qoi;
     {
         const HostLevel& F = hp.lev[h->L - 1];
-        int pitch = (int)padded_pitch(F.n, h->fp32() ? 4 : 8);
-        long long plane = (long long)pitch * (F.n + 2);
-        long long base = 4 + pitch + (cfg.dim == 3 ? plane : 0);
+        const int pitch = h->fp32() ? h->lf[h->L - 1].pitch : h->ld[h->L - 1].pitch;
+        const long long plane = h->fp32() ? h->lf[h->L - 1].plane : h->ld[h->L - 1].plane;
+        const long long base = h->fp32() ? h->lf[h->L - 1].base : h->ld[h->L - 1].base;
         std::vector<long long> qs;
         std::vector<double> qw;
         for (int t = 0; t < n_qoi; ++t) {
@@ -786,7 +851,8 @@ mgmc_status mgmc_fine_operator(const mgmc_config* cfg, const double* kappa2, dou
     }
     HostProblem hp;
     hp.dim = cfg->dim;
-    hp.NS = cfg->dim == 2 ? 9 : 27;
+    hp.R = cfg->disc == MGMC_SSL ? 2 : 1;
+    hp.NS = cfg->dim == 2 ? (2 * hp.R + 1) * (2 * hp.R + 1) : 27;
     hp.C = (hp.NS - 1) / 2;
     hp.n_levels = 1;
     hp.scale_hd = cfg->scale_hd;
@@ -794,9 +860,12 @@ mgmc_status mgmc_fine_operator(const mgmc_config* cfg, const double* kappa2, dou
     hp.lev.assign(1, HostLevel());
     hp.lev[0].n = cfg->n;
     hp.lev[0].N = cfg->dim == 2 ? (long long)cfg->n * cfg->n : (long long)cfg->n * cfg->n * cfg->n;
-    if (cfg->disc != 0 && cfg->disc != 1) return fail(MGMC_ERR_ARG, "disc must be MGMC_FD or MGMC_Q1");
-    if (cfg->disc == 1 && kappa2)
-        return fail(MGMC_ERR_ARG, "the Q1 discretisation takes a constant kappa^2 (kappa2 = NULL)");
+    if (cfg->disc != MGMC_FD && cfg->disc != MGMC_Q1 && cfg->disc != MGMC_SSL)
+        return fail(MGMC_ERR_ARG, "disc must be MGMC_FD, MGMC_Q1 or MGMC_SSL");
+    if (cfg->disc != MGMC_FD && kappa2)
+        return fail(MGMC_ERR_ARG, "the Q1 and squared-operator discretisations take a constant kappa^2 (kappa2 = NULL)");
+    if (cfg->disc == MGMC_SSL && cfg->dim != 2)
+        return fail(MGMC_ERR_ARG, "the squared shifted Laplacian is two-dimensional");
     std::string err = fine_operator(hp, cfg->dim, cfg->n, cfg->scale_hd, cfg->disc, kappa2, kappa2_const);
     if (!err.empty()) return fail(MGMC_ERR_ARG, err);
     const std::vector<double>& st = hp.lev[0].st;
@@ -1257,6 +1326,9 @@ mgmc_status mgmc_create_batch(int n_chains, const mgmc_config* cfgs, const mgmc_
     for (int c = 0; c < n_chains; ++c) {
         mgmc_config cfg = cfgs[c];
         if (cfg.gibbs) return cleanup(fail(MGMC_ERR_ARG, "batches run the MGMC V-cycle only (gibbs = 0)"));
+        if (cfg.gamma > 1 || cfg.disc == MGMC_SSL)
+            return cleanup(fail(MGMC_ERR_ARG, "batches run the V-cycle of the 5/9-point grids only (gamma <= 1, "
+                                              "disc != MGMC_SSL)"));
         if (cfg.coarse_max_n == 0) cfg.coarse_max_n = 31;
         const mgmc_problem& p = problems[c];
         mgmc_handle sh = nullptr;

@@ -59,6 +59,10 @@ struct DevLevel {
     // for the t-th positive stencil offset o_t
     T* coef;
     int ncoef;
+    // stencil radius of the coefficient form: 1 (9/27-point) or 2 (2D 25-point grids of
+    // the squared shifted Laplacian: offsets o = (dx+2) + 5 (dy+2), centre 12, slot t >= 1
+    // = a(i, i + o_{12+t}); two halo rows and columns around the interior)
+    int rad;
     // B_l rows grouped by grid row (finest level; used by the residual norm)
     const int* brow_ptr;    // [n^(dim-1) + 1]
     const int* bent_i;      // x index of the entry

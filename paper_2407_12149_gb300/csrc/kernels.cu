@@ -26,6 +26,8 @@
 // second read of theta'.
 #include "kernels.cuh"
 
+#include <type_traits>
+
 namespace mgmc {
 
 // Map a work item of colour `colour` to (row j, k, x parity, x block q).
@@ -86,6 +88,83 @@ __global__ void k_sweep_colour(DevLevel<T> L, DevProblem P, int redblack, int co
     const CycleState cs = *P.cs;
     long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     sweep_item<T, DIM>(L, P, cs, redblack != 0, colour, slot, item);
+}
+
+// 25-point grids (squared shifted Laplacian, FP64 2D): colour c = cx + 3 cy is the class
+// (i mod 3, j mod 3) = (cx, cy); one thread per site of the class.  Site i of row j takes
+// the normal of its member of the row's 4-site noise block (the same draw as every
+// other sweep kernel: block j nq + (i >> 2), half i & 1, member (i >> 1) & 1).
+__global__ void k_sweep25(DevLevel<double> L, DevProblem P, int colour, unsigned slot)
+{
+    const CycleState cs = *P.cs;
+    const int n = L.n, cx = colour % 3, cy = colour / 3;
+    const int nx = (n - cx + 2) / 3, ny = (n - cy + 2) / 3;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (nx <= 0 || t >= (long long)nx * ny) return;
+    const int i = cx + 3 * (int)(t % nx), j = cy + 3 * (int)(t / nx);
+    double z = 0.0;
+    if (cs.noise) {
+        double z0, z1;
+        const int nq = (n + 3) >> 2;
+        draw_half_ctr<double>(noise_counter(cs, 0u, 0u, L.level, slot), (unsigned)(j * nq + (i >> 2)), i & 1,
+                              (unsigned)cs.seed, (unsigned)(cs.seed >> 32), z0, z1);
+        z = ((i >> 1) & 1) ? z1 : z0;
+    }
+    const long long e = site_offset(2, L.pitch, L.plane, L.base, i, j, 0);
+    L.x[e] = update25(L, e, z);
+}
+
+// Exact coarsest sample theta_0 = A~_0^-1 f_0 + L_0^-T z (Sec. 3.5) with the coarsest
+// grid's v-th visit slot (W-cycle), one CTA: f_0 = fdense_0 + B_0 Gamma^-1 d_0, the
+// forward solve with the Cholesky factor, + z (kind 2, pair s >> 1, member s & 1),
+// the backward solve.
+template <typename T>
+__global__ void k_coarsest_slot(DevLevel<T> L, DevProblem P, const double* __restrict__ chol, int n0,
+                                unsigned slot)
+{
+    __shared__ double r[MGMC_MAX_COARSEST];
+    __shared__ double g[kMaxObs];
+    const CycleState cs = *P.cs;
+    const int n = L.n;
+    for (int s = threadIdx.x; s < n0; s += blockDim.x) {
+        const int i = s % n, j = (s / n) % n, k = L.dim == 3 ? s / (n * n) : 0;
+        r[s] = L.f ? (double)L.f[site_offset(L.dim, L.pitch, L.plane, L.base, i, j, k)] : 0.0;
+    }
+    for (int kk = threadIdx.x; kk < P.m; kk += blockDim.x) {
+        double acc = 0.0;
+        for (int t = 0; t < P.m; ++t) acc += P.Gamma_inv[kk * P.m + t] * L.d[t];
+        g[kk] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int kk = 0; kk < P.m; ++kk)
+            for (int t = L.bcol_ptr[kk]; t < L.bcol_ptr[kk + 1]; ++t) r[L.bcol_dense[t]] += L.bcol_w[t] * g[kk];
+    __syncthreads();
+    for (int i = 0; i < n0; ++i) {
+        if (threadIdx.x == 0) r[i] = r[i] / chol[(long long)i * n0 + i];
+        __syncthreads();
+        const double yi = r[i];
+        for (int t = i + 1 + threadIdx.x; t < n0; t += blockDim.x) r[t] -= chol[(long long)t * n0 + i] * yi;
+        __syncthreads();
+    }
+    if (cs.noise)
+        for (int s = threadIdx.x; s < n0; s += blockDim.x) {
+            double z0, z1;
+            draw_pair<double>(cs, (unsigned)(s >> 1), 2u, 0, slot, z0, z1);
+            r[s] += (s & 1) ? z1 : z0;
+        }
+    __syncthreads();
+    for (int i = n0 - 1; i >= 0; --i) {
+        if (threadIdx.x == 0) r[i] = r[i] / chol[(long long)i * n0 + i];
+        __syncthreads();
+        const double xi = r[i];
+        for (int t = threadIdx.x; t < i; t += blockDim.x) r[t] -= chol[(long long)i * n0 + t] * xi;
+        __syncthreads();
+    }
+    for (int s = threadIdx.x; s < n0; s += blockDim.x) {
+        const int i = s % n, j = (s / n) % n, k = L.dim == 3 ? s / (n * n) : 0;
+        L.x[site_offset(L.dim, L.pitch, L.plane, L.base, i, j, k)] = (T)r[s];
+    }
 }
 
 template <typename T, int DIM>
@@ -379,6 +458,19 @@ void launch_sweep(const DevLevel<T>& L, const DevProblem& P, int dir, unsigned s
 {
     const int bs = 256;
     int nq = (L.n + 3) / 4;
+    if constexpr (std::is_same<T, double>::value) {
+        if (L.rad == 2) {
+            // the nine classes in code order forward, reversed backward
+            for (int ci = 0; ci < 9; ++ci) {
+                const int c = dir == 0 ? ci : 8 - ci;
+                const long long sites = (long long)((L.n - c % 3 + 2) / 3) * ((L.n - c / 3 + 2) / 3);
+                if (sites <= 0) continue;
+                k_sweep25<<<blocks_for(sites, bs), bs, 0, st>>>(L, P, c, slot);
+                ++launches;
+            }
+            return;
+        }
+    }
     if (L.fine) {
         long long rows = L.dim == 3 ? (long long)L.n * L.n : L.n;
         for (int g = 0; g < 2; ++g) {
@@ -450,6 +542,14 @@ void launch_prolong(const DevLevel<T>& C, const DevLevel<T>& F, cudaStream_t st,
 }
 
 template <typename T>
+void launch_coarsest_slot(const DevLevel<T>& L, const DevProblem& P, const double* chol, int n0, unsigned slot,
+                          cudaStream_t st, int& launches)
+{
+    k_coarsest_slot<T><<<1, 256, 0, st>>>(L, P, chol, n0, slot);
+    ++launches;
+}
+
+template <typename T>
 void launch_qoi(const DevLevel<T>& L, int n_qoi, const long long* q_site, const double* q_w, const DevProblem& P,
                 cudaStream_t st, int& launches)
 {
@@ -505,6 +605,8 @@ void launch_resid(const DevLevel<T>& L, const DevProblem& P, double* u, double* 
     template void launch_lowrank<T>(const DevLevel<T>&, const DevProblem&, int, unsigned, bool, cudaStream_t, int&); \
     template void launch_restrict<T>(const DevLevel<T>&, const DevLevel<T>&, cudaStream_t, int&);                \
     template void launch_prolong<T>(const DevLevel<T>&, const DevLevel<T>&, cudaStream_t, int&);                 \
+    template void launch_coarsest_slot<T>(const DevLevel<T>&, const DevProblem&, const double*, int, unsigned,     \
+                                          cudaStream_t, int&);                                                   \
     template void launch_qoi<T>(const DevLevel<T>&, int, const long long*, const double*, const DevProblem&,      \
                                 cudaStream_t, int&);                                                             \
     template void launch_pack<T>(const DevLevel<T>&, T*, bool, cudaStream_t);                               \

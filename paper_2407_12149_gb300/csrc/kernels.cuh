@@ -13,6 +13,10 @@ void launch_lowrank(const DevLevel<T>& L, const DevProblem& P, int dir, unsigned
                     int& launches);
 template <typename T>
 void launch_restrict(const DevLevel<T>& F, const DevLevel<T>& C, cudaStream_t st, int& launches);
+// exact coarsest sample of the general path with the noise slot of the grid's visit
+template <typename T>
+void launch_coarsest_slot(const DevLevel<T>& L, const DevProblem& P, const double* chol, int n0, unsigned slot,
+                          cudaStream_t st, int& launches);
 template <typename T>
 void launch_prolong(const DevLevel<T>& C, const DevLevel<T>& F, cudaStream_t st, int& launches);
 // one chain of a batched coarse-grid launch

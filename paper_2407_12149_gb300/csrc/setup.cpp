@@ -1,6 +1,9 @@
 // setup.cpp -- host-side (FP64) construction of the MGMC hierarchy (Sec. 2.3-2.5).
 //
-//  - finest operator A_L = s (kappa^2 I - Delta_h), s = h^d or 1;
+//  - finest operator A_L = s (kappa^2 I - Delta_h), s = h^d or 1, its Q1
+//    finite-element matrix, or the 13-point matrix of the squared shifted
+//    Laplacian s (kappa^2 - Delta_h)^2 with u = du/dn = 0 (2D; Sec. 5.1.1), whose
+//    grids all carry radius-2 (5 x 5) stencils;
 //  - Galerkin coarse operators A_{l-1} = P^T A_l P (Eq. A_ell_1_B_ell_1): entry
 //    (J, J+q) = (P e_J)^T A (P e_{J+q}), the product of the two coarse hat
 //    functions through A, summed over the fine sites where both are nonzero;
@@ -8,9 +11,9 @@
 //  - per level and direction the low-rank matrices of Alg. 3:
 //    C = M^-1 B (M = D + L or D + L^T in colour order), S = Gamma + B^T C,
 //    G = C S^-1.  Each column of C is a forward substitution started from
-//    zero; a colour pass can only extend the support by one ring of
-//    neighbours, so the substitution runs on the bounding box of supp(b_k)
-//    grown by the number of colours, which gives the full-grid result;
+//    zero; a colour pass can only extend the support by one stencil radius,
+//    so the substitution runs on the bounding box of supp(b_k) grown by the
+//    radius times (the number of colours + 1), which gives the full-grid result;
 //  - the coarsest posterior operator A~_0 = A_0 + B_0 Gamma^-1 B_0^T and its
 //    Cholesky factor (exact coarse sampler, Sec. 3.5);
 //  - the finest data vector d_L = y, so that f_L = B_L Gamma^-1 d_L (Eq. f_ell_definition).
@@ -41,7 +44,12 @@ struct Grid {
     }
 };
 
-inline int oidx(int d, int dx, int dy, int dz) { return (dx + 1) + 3 * (dy + 1) + (d == 3 ? 9 * (dz + 1) : 0); }
+// offset index of (dx, dy, dz) in a full stencil of radius R: width W = 2R + 1, dx fastest
+inline int oidx(int d, int R, int dx, int dy, int dz)
+{
+    const int W = 2 * R + 1;
+    return (dx + R) + W * (dy + R) + (d == 3 ? W * W * (dz + R) : 0);
+}
 
 // hat function of coarse vertex J (1D) at fine vertex i: 1 at i = 2J+1, 1/2 at 2J, 2J+2
 inline double hat(int J, int i)
@@ -50,14 +58,20 @@ inline double hat(int J, int i)
     return t == 0 ? 1.0 : (t == 1 || t == -1) ? 0.5 : 0.0;
 }
 
-// colour (parity class) order of the Gibbs sweep
-std::vector<int> colour_order(int d)
+// colour order of the Gibbs sweep: parity classes (radius 1); radius-2 stencils (2D)
+// the nine classes (i mod 3, j mod 3), code (i mod 3) + 3 (j mod 3), in code order
+std::vector<int> colour_order(int d, int R)
 {
+    if (R == 2) return {0, 1, 2, 3, 4, 5, 6, 7, 8};
     if (d == 2) return {0, 3, 2, 1};
     return {0, 6, 5, 3, 4, 2, 1, 7};
 }
 
-int parity(int d, int i, int j, int k) { return (i & 1) | ((j & 1) << 1) | (d == 3 ? ((k & 1) << 2) : 0); }
+int colour_of(int d, int R, int i, int j, int k)
+{
+    if (R == 2) return i % 3 + 3 * (j % 3);
+    return (i & 1) | ((j & 1) << 1) | (d == 3 ? ((k & 1) << 2) : 0);
+}
 
 bool lu_inverse(int k, std::vector<double> A, std::vector<double>& inv)
 {
@@ -111,10 +125,10 @@ bool cholesky_lower(int k, const std::vector<double>& A, std::vector<double>& L)
 
 void galerkin(const HostProblem& hp, const HostLevel& F, HostLevel& Cl)
 {
-    const int d = hp.dim, NS = hp.NS;
+    const int d = hp.dim, NS = hp.NS, R = hp.R;
     Grid gf{d, F.n}, gc{d, Cl.n};
     Cl.st.assign((size_t)Cl.N * NS, 0.0);
-    const int kz = d == 3 ? 1 : 0;
+    const int kz = d == 3 ? 1 : 0, rz = d == 3 ? R : 0;
     for (long long J = 0; J < Cl.N; ++J) {
         int I0, I1, I2;
         gc.coords(J, I0, I1, I2);
@@ -126,22 +140,22 @@ void galerkin(const HostProblem& hp, const HostLevel& F, HostLevel& Cl)
                     int fi = 2 * I0 + 1 + px, fj = 2 * I1 + 1 + py, fk = d == 3 ? 2 * I2 + 1 + pz : 0;
                     double wJ = hat(I0, fi) * hat(I1, fj) * (d == 3 ? hat(I2, fk) : 1.0);
                     const double* a = &F.st[(size_t)gf.idx(fi, fj, fk) * NS];
-                    for (int oz = -kz; oz <= kz; ++oz)
-                        for (int oy = -1; oy <= 1; ++oy)
-                            for (int ox = -1; ox <= 1; ++ox) {
-                                double aij = a[oidx(d, ox, oy, oz)];
+                    for (int oz = -rz; oz <= rz; ++oz)
+                        for (int oy = -R; oy <= R; ++oy)
+                            for (int ox = -R; ox <= R; ++ox) {
+                                double aij = a[oidx(d, R, ox, oy, oz)];
                                 if (aij == 0.0) continue;
                                 int gi = fi + ox, gj = fj + oy, gk = fk + oz;
                                 if (!gf.inside(gi, gj, gk)) continue;
                                 // coarse neighbours K = J + q whose hat covers (gi, gj, gk)
-                                for (int qz = -kz; qz <= kz; ++qz)
-                                    for (int qy = -1; qy <= 1; ++qy)
-                                        for (int qx = -1; qx <= 1; ++qx) {
+                                for (int qz = -rz; qz <= rz; ++qz)
+                                    for (int qy = -R; qy <= R; ++qy)
+                                        for (int qx = -R; qx <= R; ++qx) {
                                             int K0 = I0 + qx, K1 = I1 + qy, K2 = I2 + qz;
                                             if (!gc.inside(K0, K1, K2)) continue;
                                             double wK = hat(K0, gi) * hat(K1, gj) * (d == 3 ? hat(K2, gk) : 1.0);
                                             if (wK == 0.0) continue;
-                                            out[oidx(d, qx, qy, qz)] += wJ * aij * wK;
+                                            out[oidx(d, R, qx, qy, qz)] += wJ * aij * wK;
                                         }
                             }
                 }
@@ -182,9 +196,9 @@ void coarsen_B(const HostProblem& hp, const HostLevel& F, HostLevel& Cl)
 void lower_solve_column(const HostProblem& hp, const HostLevel& L, int dir, int k,
                         std::vector<std::pair<long long, double>>& out)
 {
-    const int d = hp.dim, NS = hp.NS, n = L.n;
+    const int d = hp.dim, NS = hp.NS, n = L.n, R = hp.R;
     Grid g{d, n};
-    std::vector<int> order = colour_order(d);
+    std::vector<int> order = colour_order(d, R);
     if (dir == 1) std::reverse(order.begin(), order.end());
     int lo[3] = {n, n, n}, hi[3] = {-1, -1, -1};
     std::map<long long, double> b;
@@ -199,7 +213,7 @@ void lower_solve_column(const HostProblem& hp, const HostLevel& L, int dir, int 
     }
     out.clear();
     if (b.empty()) return;
-    const int grow = (int)order.size() + 1;
+    const int grow = R * ((int)order.size() + 1);
     int blo[3] = {0, 0, 0}, bhi[3] = {0, 0, 0}, ext[3] = {1, 1, 1};
     for (int a = 0; a < d; ++a) {
         blo[a] = std::max(0, lo[a] - grow);
@@ -210,21 +224,21 @@ void lower_solve_column(const HostProblem& hp, const HostLevel& L, int dir, int 
     auto bidx = [&](int i, int j, int kk) {
         return (size_t)(i - blo[0]) + (size_t)ext[0] * ((j - blo[1]) + (size_t)ext[1] * (kk - blo[2]));
     };
-    const int kz = d == 3 ? 1 : 0;
+    const int rz = d == 3 ? R : 0;
     for (int colour : order) {
         for (int kk = blo[2]; kk <= bhi[2]; ++kk)
             for (int j = blo[1]; j <= bhi[1]; ++j)
                 for (int i = blo[0]; i <= bhi[0]; ++i) {
-                    if (parity(d, i, j, kk) != colour) continue;
+                    if (colour_of(d, R, i, j, kk) != colour) continue;
                     long long s = g.idx(i, j, kk);
                     const double* a = &L.st[(size_t)s * NS];
                     auto it = b.find(s);
                     double acc = it == b.end() ? 0.0 : it->second;
-                    for (int oz = -kz; oz <= kz; ++oz)
-                        for (int oy = -1; oy <= 1; ++oy)
-                            for (int ox = -1; ox <= 1; ++ox) {
+                    for (int oz = -rz; oz <= rz; ++oz)
+                        for (int oy = -R; oy <= R; ++oy)
+                            for (int ox = -R; ox <= R; ++ox) {
                                 if (ox == 0 && oy == 0 && oz == 0) continue;
-                                double aij = a[oidx(d, ox, oy, oz)];
+                                double aij = a[oidx(d, R, ox, oy, oz)];
                                 if (aij == 0.0) continue;
                                 int i2 = i + ox, j2 = j + oy, k2 = kk + oz;
                                 if (i2 < blo[0] || i2 > bhi[0] || j2 < blo[1] || j2 > bhi[1] || k2 < blo[2] ||
@@ -285,7 +299,7 @@ bool lowrank_setup(const HostProblem& hp, HostLevel& L, int dir)
 void fused_extras(HostLevel& L, const HostProblem& hp, int l)
 {
     const HostLevel& Cl = hp.lev[l - 1];
-    const int d = hp.dim, m = hp.m, kz = d == 3 ? 1 : 0;
+    const int d = hp.dim, m = hp.m, R = hp.R, rz = d == 3 ? R : 0;
     L.hsite.clear();
     L.hval.clear();
     L.BtG.assign((size_t)m * m, 0.0);
@@ -300,10 +314,10 @@ void fused_extras(HostLevel& L, const HostProblem& hp, int l)
         int i, j, k;
         g.coords(s, i, j, k);
         const double* a = &L.st[(size_t)s * hp.NS];
-        for (int oz = -kz; oz <= kz; ++oz)
-            for (int oy = -1; oy <= 1; ++oy)
-                for (int ox = -1; ox <= 1; ++ox) {
-                    double aso = a[oidx(d, ox, oy, oz)];
+        for (int oz = -rz; oz <= rz; ++oz)
+            for (int oy = -R; oy <= R; ++oy)
+                for (int ox = -R; ox <= R; ++ox) {
+                    double aso = a[oidx(d, R, ox, oy, oz)];
                     if (aso == 0.0 || !g.inside(i + ox, j + oy, k + oz)) continue;
                     auto& v = AG[g.idx(i + ox, j + oy, k + oz)];
                     if (v.empty()) v.assign(m, 0.0);
@@ -344,15 +358,16 @@ std::vector<double> row_sums(const HostProblem& hp, int l)
     const HostLevel& L = hp.lev[l];
     Grid g{hp.dim, L.n};
     std::vector<double> out((size_t)L.N, 0.0);
-    const int kz = hp.dim == 3 ? 1 : 0;
+    const int R = hp.R, rz = hp.dim == 3 ? R : 0;
     for (long long s = 0; s < L.N; ++s) {
         int i, j, k;
         g.coords(s, i, j, k);
         double acc = 0.0;
-        for (int oz = -kz; oz <= kz; ++oz)
-            for (int oy = -1; oy <= 1; ++oy)
-                for (int ox = -1; ox <= 1; ++ox)
-                    if (g.inside(i + ox, j + oy, k + oz)) acc += L.st[(size_t)s * hp.NS + oidx(hp.dim, ox, oy, oz)];
+        for (int oz = -rz; oz <= rz; ++oz)
+            for (int oy = -R; oy <= R; ++oy)
+                for (int ox = -R; ox <= R; ++ox)
+                    if (g.inside(i + ox, j + oy, k + oz))
+                        acc += L.st[(size_t)s * hp.NS + oidx(hp.dim, R, ox, oy, oz)];
         out[(size_t)s] = acc;
     }
     return out;
@@ -394,6 +409,34 @@ std::string fine_operator(HostProblem& hp, int dim, int n, int scale_hd, int dis
             q1[(size_t)o] = q1scale * (stiff + kappa2_const * mass);
         }
     }
+    if (disc == 2) {
+        // (kappa^2 - Delta_h)^2 with u = du/dn = 0 as the product K K of the shifted
+        // 5-point Dirichlet operator K = kappa^2 + L (L = -Delta_h) with itself, plus
+        // 2 h^-4 per boundary side a vertex is adjacent to: the 13-point stencil's
+        // mirror ghost behind the boundary adds h^-4 to such a row, where K K misses
+        // the h^-4 of the dropped boundary vertex (Sec. 5.1.1)
+        if (!std::isfinite(kappa2_const) || kappa2_const < 0.0) return "kappa^2 must be finite and non-negative";
+        const double kc = kappa2_const + 4.0 * inv_h2, ko = -inv_h2;
+        const int nb[5][2] = {{0, 0}, {-1, 0}, {1, 0}, {0, -1}, {0, 1}};
+        for (long long s = 0; s < Fl.N; ++s) {
+            int i, j, k;
+            gf.coords(s, i, j, k);
+            double* a = &Fl.st[(size_t)s * hp.NS];
+            for (int t = 0; t < 5; ++t) {
+                const int ti = i + nb[t][0], tj = j + nb[t][1];
+                if (!gf.inside(ti, tj, 0)) continue;
+                const double kst = t == 0 ? kc : ko;
+                for (int u = 0; u < 5; ++u) {
+                    const int ui = ti + nb[u][0], uj = tj + nb[u][1];
+                    if (!gf.inside(ui, uj, 0)) continue;
+                    a[oidx(2, 2, ui - i, uj - j, 0)] += scale * kst * (u == 0 ? kc : ko);
+                }
+            }
+            const int sides = (i == 0) + (i == n - 1) + (j == 0) + (j == n - 1);
+            a[hp.C] += scale * 2.0 * inv_h2 * inv_h2 * sides;
+        }
+        return std::string();
+    }
     for (long long s = 0; s < Fl.N; ++s) {
         double k2 = kappa2 ? kappa2[s] : kappa2_const;
         if (!std::isfinite(k2) || k2 < 0.0) return "kappa^2 must be finite and non-negative";
@@ -412,7 +455,7 @@ std::string fine_operator(HostProblem& hp, int dim, int n, int scale_hd, int dis
         const int dd[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
         for (int t = 0; t < 2 * dim; ++t)
             if (gf.inside(i + dd[t][0], j + dd[t][1], k + dd[t][2]))
-                a[oidx(dim, dd[t][0], dd[t][1], dd[t][2])] = -scale * inv_h2;
+                a[oidx(dim, 1, dd[t][0], dd[t][1], dd[t][2])] = -scale * inv_h2;
     }
     return std::string();
 }
@@ -423,13 +466,16 @@ std::string build_hierarchy(HostProblem& hp, int dim, int n, int n_levels, int s
 {
     *code = MGMC_ERR_ARG;
     hp.dim = dim;
-    hp.NS = dim == 2 ? 9 : 27;
+    hp.R = disc == 2 ? 2 : 1;
+    hp.NS = dim == 2 ? (2 * hp.R + 1) * (2 * hp.R + 1) : 27;
     hp.C = (hp.NS - 1) / 2;
     hp.m = m;
     hp.scale_hd = scale_hd;
     hp.disc = disc;
-    if (disc != 0 && disc != 1) return "disc must be MGMC_FD or MGMC_Q1";
+    if (disc != 0 && disc != 1 && disc != 2) return "disc must be MGMC_FD, MGMC_Q1 or MGMC_SSL";
     if (disc == 1 && kappa2) return "the Q1 discretisation takes a constant kappa^2 (kappa2 = NULL)";
+    if (disc == 2 && (kappa2 || dim != 2))
+        return "the squared shifted Laplacian is 2D with a constant kappa^2 (kappa2 = NULL)";
     hp.n_levels = n_levels;
     hp.lev.assign(n_levels, HostLevel());
     {
@@ -535,16 +581,16 @@ std::string build_hierarchy(HostProblem& hp, int dim, int n, int n_levels, int s
         hp.n0 = n0;
         Grid g0{dim, L0.n};
         std::vector<double> A0((size_t)n0 * n0, 0.0);
-        const int kz = dim == 3 ? 1 : 0;
+        const int R = hp.R, rz = dim == 3 ? R : 0;
         for (int s = 0; s < n0; ++s) {
             int i, j, k;
             g0.coords(s, i, j, k);
-            for (int oz = -kz; oz <= kz; ++oz)
-                for (int oy = -1; oy <= 1; ++oy)
-                    for (int ox = -1; ox <= 1; ++ox)
+            for (int oz = -rz; oz <= rz; ++oz)
+                for (int oy = -R; oy <= R; ++oy)
+                    for (int ox = -R; ox <= R; ++ox)
                         if (g0.inside(i + ox, j + oy, k + oz))
                             A0[(size_t)s * n0 + g0.idx(i + ox, j + oy, k + oz)] +=
-                                L0.st[(size_t)s * hp.NS + oidx(dim, ox, oy, oz)];
+                                L0.st[(size_t)s * hp.NS + oidx(dim, R, ox, oy, oz)];
         }
         if (m > 0) {
             // B_0 Gamma^-1 B_0^T

@@ -9,7 +9,7 @@ namespace mgmc {
 struct HostLevel {
     int n = 0;
     long long N = 0;
-    std::vector<double> st;          // [N * 3^d] full stencil, offset (dx+1) + 3(dy+1) [+ 9(dz+1)]
+    std::vector<double> st;          // [N * W^d] full stencil, W = 2R + 1, offset (dx+R) + W(dy+R) [+ W^2(dz+R)]
     // B_l by columns: entries bptr[k] .. bptr[k+1]-1 of (dense site, weight)
     std::vector<int> bptr;
     std::vector<long long> bsite;
@@ -27,10 +27,11 @@ struct HostLevel {
 
 struct HostProblem {
     int dim = 2, NS = 9, C = 4;
+    int R = 1;                        // stencil radius: 1, or 2 for the squared shifted Laplacian
     int n_levels = 1;
     int m = 0;
     int scale_hd = 1;
-    int disc = 0;                     // 0: finite differences on the finest grid, 1: Q1 elements
+    int disc = 0;                     // finest grid: 0 finite differences, 1 Q1 elements, 2 squared shifted Laplacian
     double woff_fine = 0.0;           // s / h^2 of the finest grid
     std::vector<double> kappa_part;  // s * kappa^2 at the fine sites
     std::vector<HostLevel> lev;      // 0 = coarsest

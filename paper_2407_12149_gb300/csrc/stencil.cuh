@@ -40,6 +40,35 @@ __device__ __forceinline__ T coef_at(const DevLevel<T>& L, long long e, int o)
     return L.coef[(long long)(NS - 1 - o - C) * L.alloc + en];
 }
 
+// radius-2 (25-point) 2D stencils: offset o = (dx+2) + 5 (dy+2), centre 12
+__device__ __forceinline__ long long off25(int o, int pitch)
+{
+    return (long long)(o % 5 - 2) + (long long)pitch * (o / 5 - 2);
+}
+
+// a(i, i + o) of a 25-point grid from the symmetric half storage (a(i, i + o) for
+// o < 12 is a(i + o, i), slot 12 - o at the neighbour)
+__device__ __forceinline__ double coef25_at(const DevLevel<double>& L, long long e, int o)
+{
+    if (o > 12) return L.coef[(long long)(o - 12) * L.alloc + e];
+    return L.coef[(long long)(12 - o) * L.alloc + e + off25(o, L.pitch)];
+}
+
+// one Gibbs update of a 25-point site, x_i <- (f_i + sqrt(a_ii) z - sum_{j != i} a_ij x_j) / a_ii
+// with the neighbours in lexicographic offset order
+__device__ __forceinline__ double update25(const DevLevel<double>& L, long long e, double z)
+{
+    const double aii = L.coef[e];
+    double acc = L.f ? L.f[e] : 0.0;
+    acc += sqrt(aii) * z;
+#pragma unroll
+    for (int o = 0; o < 25; ++o) {
+        if (o == 12) continue;
+        acc -= coef25_at(L, e, o) * L.x[e + off25(o, L.pitch)];
+    }
+    return acc / aii;
+}
+
 // ---------------------------------------------------------------------------
 // one site update of the Gibbs sweep with right-hand side fdense_i + sqrt(a_ii) z
 // ---------------------------------------------------------------------------
@@ -154,6 +183,15 @@ __device__ __forceinline__ double apply_A(const DevLevel<double>& L, long long e
         acc += w * x[e + 1];
         acc += w * x[e + L.pitch];
         if (DIM == 3) acc += w * x[e + L.plane];
+        return acc;
+    }
+    if (DIM == 2 && L.rad == 2) {
+        double acc = 0.0;
+#pragma unroll
+        for (int o = 0; o < 25; ++o) {
+            double a = (o == 12) ? L.coef[e] : coef25_at(L, e, o);
+            acc += a * x[e + off25(o, L.pitch)];
+        }
         return acc;
     }
     constexpr int NS = Offsets<DIM>::NS;

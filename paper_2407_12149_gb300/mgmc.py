@@ -21,6 +21,7 @@ MGMC_FP64 = 0
 MGMC_FP32 = 1
 MGMC_FD = 0
 MGMC_Q1 = 1
+MGMC_SSL = 2
 MGMC_MAX_OBS = 64
 MGMC_NOALLOC_MAX_SERIES = 65536
 
@@ -38,7 +39,7 @@ class mgmc_config(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("n_levels", ctypes.c_int), ("nu1", ctypes.c_int),
                 ("nu2", ctypes.c_int), ("precision", ctypes.c_int), ("scale_hd", ctypes.c_int),
                 ("coarse_max_n", ctypes.c_int), ("gibbs", ctypes.c_int), ("disc", ctypes.c_int),
-                ("band_min_n", ctypes.c_int)]
+                ("band_min_n", ctypes.c_int), ("gamma", ctypes.c_int)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -192,11 +193,12 @@ class TorchAllocator:
 
 def mgmc_fine_operator(problem) -> np.ndarray:
     """The finest grid's operator A_L of a problem as the library assembles it:
-    float64 [N, 3^dim] stencil (host only)."""
+    float64 [N, W^dim] stencil, W = 5 for the squared shifted Laplacian, else 3 (host only)."""
     p = problem
-    cfg = mgmc_config(p.dim, p.n, p.n_levels, 1, 1, MGMC_FP64, p.scale_hd, 0, 0, getattr(p, "disc", MGMC_FD))
+    disc = getattr(p, "disc", MGMC_FD)
+    cfg = mgmc_config(p.dim, p.n, p.n_levels, 1, 1, MGMC_FP64, p.scale_hd, 0, 0, disc)
     k2 = None if p.kappa2 is None else np.ascontiguousarray(p.kappa2, dtype=np.float64).ravel()
-    out = np.empty((p.N, 3 ** p.dim), dtype=np.float64)
+    out = np.empty((p.N, (5 if disc == MGMC_SSL else 3) ** p.dim), dtype=np.float64)
     _check(load().mgmc_fine_operator(ctypes.byref(cfg), _ptr(k2, ctypes.c_double), float(p.kappa2_const),
                                      _ptr(out, ctypes.c_double)))
     return out
@@ -223,9 +225,10 @@ def mgmc_point_obs_rows(dim: int, n: int, xyz: np.ndarray):
 def mgmc_create(dim, n, *, n_levels=0, nu1=1, nu2=1, precision=MGMC_FP64, scale_hd=1, coarse_max_n=0,
                 kappa2=None, kappa2_const=10.0, obs_site=None, obs_w=None, Gamma=None, y=None,
                 qoi_site=None, qoi_w=None, allocator: Optional[TorchAllocator] = None, stream=None, gibbs=0,
-                disc=MGMC_FD, band_min_n=0):
+                disc=MGMC_FD, band_min_n=0, gamma=0):
     L = load()
-    cfg = mgmc_config(dim, n, n_levels, nu1, nu2, precision, scale_hd, coarse_max_n, gibbs, disc, band_min_n)
+    cfg = mgmc_config(dim, n, n_levels, nu1, nu2, precision, scale_hd, coarse_max_n, gibbs, disc, band_min_n,
+                      gamma)
     k2 = None if kappa2 is None else np.ascontiguousarray(kappa2, dtype=np.float64).ravel()
     if obs_site is None:
         m, nnz, os_, ow_, G_, y_ = 0, 1, None, None, None, None
@@ -336,10 +339,12 @@ def mgmc_destroy(h):
 
 class Sampler:
     """MGMC sampler of one posterior problem (paper_2407_12149_gb300.inputs.Problem);
-    gibbs=True gives the plain Gibbs sampler of the same posterior (finest-grid sweeps only)."""
+    gibbs=True gives the plain Gibbs sampler of the same posterior (finest-grid sweeps only).
+    gamma: cycle index (1 V-cycle, 2 W-cycle; 0 = 2 for the squared shifted Laplacian, else 1)."""
 
     def __init__(self, problem, precision: str = "fp64", nu1: int = 1, nu2: int = 1, coarse_max_n: int = 0,
-                 device: int = 0, use_torch_allocator: bool = True, gibbs: bool = False, band_min_n: int = 0):
+                 device: int = 0, use_torch_allocator: bool = True, gibbs: bool = False, band_min_n: int = 0,
+                 gamma: int = 0):
         torch = _torch()
         if not torch.cuda.is_available():
             raise MGMCError(2, "no CUDA device available (the sampler has no CPU fallback)")
@@ -353,7 +358,8 @@ class Sampler:
                              scale_hd=p.scale_hd, coarse_max_n=coarse_max_n, kappa2=p.kappa2,
                              kappa2_const=p.kappa2_const, obs_site=p.obs_site, obs_w=p.obs_w, Gamma=p.Gamma,
                              y=p.y, qoi_site=p.qoi_site, qoi_w=p.qoi_w, allocator=self._alloc,
-                             gibbs=1 if gibbs else 0, disc=getattr(p, "disc", MGMC_FD), band_min_n=band_min_n)
+                             gibbs=1 if gibbs else 0, disc=getattr(p, "disc", MGMC_FD), band_min_n=band_min_n,
+                             gamma=gamma)
 
     def zeros(self):
         torch = _torch()

@@ -82,9 +82,11 @@ def test_stats_rejects_short_series(lib):
 
 
 @pytest.mark.parametrize("dim,n,disc,scale_hd,var", [(2, 15, 0, 1, True), (2, 7, 0, 0, False), (3, 7, 0, 1, True),
-                                                     (2, 15, 1, 1, False), (2, 7, 1, 0, False), (3, 7, 1, 1, False)])
+                                                     (2, 15, 1, 1, False), (2, 7, 1, 0, False), (3, 7, 1, 1, False),
+                                                     (2, 1, 2, 1, False), (2, 15, 2, 1, False), (2, 31, 2, 0, False)])
 def test_fine_operator_matches_oracle(lib, dim, n, disc, scale_hd, var):
-    """mgmc_fine_operator (host only) returns the oracle's finest stencil (FD and Q1)."""
+    """mgmc_fine_operator (host only) returns the oracle's finest stencil (FD, Q1 and the
+    13-point squared shifted Laplacian, assembled there as a stencil product)."""
     import oracle
     p = inputs.make_problem("op", dim, n, kappa2_seed=4 if var else None, kappa2_const=37.0, scale_hd=scale_hd,
                             disc=disc)
@@ -102,5 +104,9 @@ def test_fine_operator_rejects_bad_input(lib):
         mgmc.mgmc_fine_operator(p)
     p = inputs.make_problem("op", 2, 7)
     p.n = 8
+    with pytest.raises(mgmc.MGMCError):
+        mgmc.mgmc_fine_operator(p)
+    p = inputs.make_problem("op", 3, 7)
+    p.disc = 2
     with pytest.raises(mgmc.MGMCError):
         mgmc.mgmc_fine_operator(p)
