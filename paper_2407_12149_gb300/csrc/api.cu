@@ -109,6 +109,12 @@ struct mgmc_ctx {
     size_t coarse_smem = 0;   // dynamic shared memory of the coarse-grid kernel
     bool fused = false;   // 2D, nu1 = nu2 = 1: fused tile kernels on the grids above coarse_max_n
     bool recursive = false;   // W-cycle or radius-2 grids: general kernels, cycle enqueued recursively
+    // recursive path, 2D: grids 0..small_top run in one k_cycle_small launch per visit of
+    // grid small_top (-1: none); the phase lists of the cycle's visits, in cycle order
+    int small_top = -1;
+    int4* small_ops = nullptr;
+    std::vector<int> small_off, small_cnt;
+    int small_next = 0;
     DevProblem* P_dev = nullptr;   // device copy of P (batched launches)
     // batch handle: per-chain handles and the job tables of the batched launches
     std::vector<mgmc_ctx*> sub;
@@ -440,6 +446,50 @@ void enqueue_cycle_batch(mgmc_ctx* h, cudaStream_t s, int& launches)
     launch_qoi_batch<T>((const QoiJob<T>*)h->jobs_qoi, nc, s, launches);
 }
 
+// The phases of one visit of grid l <= small_top and everything below it, with the slots
+// of the per-launch path (enqueue_level).
+void small_phases(const mgmc_ctx* h, int l, std::vector<int>& visit, std::vector<int4>& ops)
+{
+    const int v = visit[(size_t)l]++;
+    if (l == 0) {
+        ops.push_back(make_int4(kOpCoarsest, 0, v, 0));
+        return;
+    }
+    const int S = std::max(1, std::max(h->cfg.nu1, h->cfg.nu2));
+    for (int j = 0; j < h->cfg.nu1; ++j) {
+        const int slot = 2 * (v * S + j);
+        ops.push_back(make_int4(kOpSweep, l, slot, 0));
+        ops.push_back(make_int4(kOpLowrank, l, slot, j == h->cfg.nu1 - 1 ? 4 : 0));
+    }
+    if (h->cfg.nu1 == 0) ops.push_back(make_int4(kOpLowrank, l, 0, 2 | 4));
+    ops.push_back(make_int4(kOpRestrict, l, 0, 0));
+    ops.push_back(make_int4(kOpZero, l - 1, 0, 0));
+    const int calls = l == h->L - 1 ? 1 : h->cfg.gamma;
+    for (int g = 0; g < calls; ++g) small_phases(h, l - 1, visit, ops);
+    ops.push_back(make_int4(kOpProlong, l, 0, 0));
+    for (int j = 0; j < h->cfg.nu2; ++j) {
+        const int slot = 2 * (v * S + j) + 1;
+        ops.push_back(make_int4(kOpSweep, l, slot, 1));
+        ops.push_back(make_int4(kOpLowrank, l, slot, 1));
+    }
+}
+
+// The visits of one cycle in the order enqueue_level makes them; every visit of grid
+// small_top gets its phase list.
+void plan_small(mgmc_ctx* h, int l, std::vector<int>& visit, std::vector<int4>& ops)
+{
+    if (l <= h->small_top) {
+        h->small_off.push_back((int)ops.size());
+        small_phases(h, l, visit, ops);
+        h->small_cnt.push_back((int)ops.size() - h->small_off.back());
+        return;
+    }
+    ++visit[(size_t)l];
+    if (l == 0) return;
+    const int calls = l == h->L - 1 ? 1 : h->cfg.gamma;
+    for (int g = 0; g < calls; ++g) plan_small(h, l - 1, visit, ops);
+}
+
 // Alg. 1 on grid l of the general path, recursively: the v-th visit of the grid uses the
 // noise slots 2 (v S + j) / 2 (v S + j) + 1, the coarsest grid's v-th sample slot v; the
 // finest grid calls grid l-1 once, every other grid cfg.gamma times from psi = 0.
@@ -449,6 +499,13 @@ void enqueue_level(mgmc_ctx* h, int l, std::vector<int>& visit, cudaStream_t s, 
     auto& lv = levels_of<T>(h);
     const DevProblem& P = h->P;
     const int Lf = h->L - 1;
+    if (l <= h->small_top) {
+        // this visit's phase list (built at creation in the same visit order)
+        const int k = h->small_next++;
+        launch_cycle_small<T>((const DevLevel<T>*)h->levels_dev, P, h->chol, h->n0, h->small_ops + h->small_off[k],
+                              h->small_cnt[k], s, launches);
+        return;
+    }
     const int v = visit[(size_t)l]++;
     if (l == 0) {
         launch_coarsest_slot<T>(lv[0], P, h->chol, h->n0, (unsigned)v, s, launches);
@@ -487,6 +544,7 @@ void enqueue_cycle(mgmc_ctx* h, cudaStream_t s, int& launches)
         return;
     }
     if (h->recursive && !h->cfg.gibbs) {
+        h->small_next = 0;
         std::vector<int> visit((size_t)h->L, 0);
         enqueue_level<T>(h, h->L - 1, visit, s, launches);
         launch_qoi<T>(levels_of<T>(h)[h->L - 1], h->n_qoi, h->q_site, h->q_w, h->P, s, launches);
@@ -793,6 +851,21 @@ mgmc_status mgmc_create(const mgmc_config* cfg_in, const mgmc_allocator* alloc, 
     if (st != MGMC_OK) return cleanup(fail(st, "device upload failed"));
     st = h->fp32() ? build_device_levels<float>(h, hp) : build_device_levels<double>(h, hp);
     if (st != MGMC_OK) return cleanup(st);
+    // recursive path (2D): the grids with n <= coarse_max_n (0: 63) in one CTA per visit
+    if (h->recursive && !cfg.gibbs && cfg.dim == 2) {
+        const int thr = cfg.coarse_max_n > 0 ? cfg.coarse_max_n : 63;
+        for (int l = 0; l < h->L; ++l)
+            if (hp.lev[l].n <= thr) h->small_top = l;
+        if (h->small_top >= 1) {
+            std::vector<int> visit((size_t)h->L, 0);
+            std::vector<int4> ops;
+            plan_small(h, h->L - 1, visit, ops);
+            h->small_ops = upload(h, ops, st);
+            if (st != MGMC_OK) return cleanup(fail(st, "device upload failed"));
+        } else {
+            h->small_top = -1;
+        }
+    }
     h->P_dev = (DevProblem*)h->buf.get(sizeof(DevProblem));
     if (!h->P_dev) return cleanup(fail(MGMC_ERR_OOM, "allocator returned NULL"));
     if (cudaMemcpyAsync(h->P_dev, &h->P, sizeof(DevProblem), cudaMemcpyHostToDevice, h->buf.stream) != cudaSuccess)

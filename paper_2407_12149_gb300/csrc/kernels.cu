@@ -94,13 +94,17 @@ __global__ void k_sweep_colour(DevLevel<T> L, DevProblem P, int redblack, int co
 // (i mod 3, j mod 3) = (cx, cy); one thread per site of the class.  Site i of row j takes
 // the normal of its member of the row's 4-site noise block (the same draw as every
 // other sweep kernel: block j nq + (i >> 2), half i & 1, member (i >> 1) & 1).
-__global__ void k_sweep25(DevLevel<double> L, DevProblem P, int colour, unsigned slot)
+__device__ __forceinline__ long long colour25_sites(int n, int colour)
 {
-    const CycleState cs = *P.cs;
+    const int nx = (n - colour % 3 + 2) / 3, ny = (n - colour / 3 + 2) / 3;
+    return nx > 0 && ny > 0 ? (long long)nx * ny : 0;
+}
+
+__device__ __forceinline__ void sweep25_site(const DevLevel<double>& L, const CycleState& cs, int colour,
+                                             unsigned slot, long long t)
+{
     const int n = L.n, cx = colour % 3, cy = colour / 3;
-    const int nx = (n - cx + 2) / 3, ny = (n - cy + 2) / 3;
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (nx <= 0 || t >= (long long)nx * ny) return;
+    const int nx = (n - cx + 2) / 3;
     const int i = cx + 3 * (int)(t % nx), j = cy + 3 * (int)(t / nx);
     double z = 0.0;
     if (cs.noise) {
@@ -114,17 +118,22 @@ __global__ void k_sweep25(DevLevel<double> L, DevProblem P, int colour, unsigned
     L.x[e] = update25(L, e, z);
 }
 
+__global__ void k_sweep25(DevLevel<double> L, DevProblem P, int colour, unsigned slot)
+{
+    const CycleState cs = *P.cs;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= colour25_sites(L.n, colour)) return;
+    sweep25_site(L, cs, colour, slot, t);
+}
+
 // Exact coarsest sample theta_0 = A~_0^-1 f_0 + L_0^-T z (Sec. 3.5) with the coarsest
 // grid's v-th visit slot (W-cycle), one CTA: f_0 = fdense_0 + B_0 Gamma^-1 d_0, the
 // forward solve with the Cholesky factor, + z (kind 2, pair s >> 1, member s & 1),
 // the backward solve.
 template <typename T>
-__global__ void k_coarsest_slot(DevLevel<T> L, DevProblem P, const double* __restrict__ chol, int n0,
-                                unsigned slot)
+__device__ void coarsest_slot_body(const DevLevel<T>& L, const DevProblem& P, const CycleState& cs,
+                                   const double* __restrict__ chol, int n0, unsigned slot, double* r, double* g)
 {
-    __shared__ double r[MGMC_MAX_COARSEST];
-    __shared__ double g[kMaxObs];
-    const CycleState cs = *P.cs;
     const int n = L.n;
     for (int s = threadIdx.x; s < n0; s += blockDim.x) {
         const int i = s % n, j = (s / n) % n, k = L.dim == 3 ? s / (n * n) : 0;
@@ -165,6 +174,16 @@ __global__ void k_coarsest_slot(DevLevel<T> L, DevProblem P, const double* __res
         const int i = s % n, j = (s / n) % n, k = L.dim == 3 ? s / (n * n) : 0;
         L.x[site_offset(L.dim, L.pitch, L.plane, L.base, i, j, k)] = (T)r[s];
     }
+}
+
+template <typename T>
+__global__ void k_coarsest_slot(DevLevel<T> L, DevProblem P, const double* __restrict__ chol, int n0,
+                                unsigned slot)
+{
+    __shared__ double r[MGMC_MAX_COARSEST];
+    __shared__ double g[kMaxObs];
+    const CycleState cs = *P.cs;
+    coarsest_slot_body<T>(L, P, cs, chol, n0, slot, r, g);
 }
 
 template <typename T, int DIM>
@@ -215,11 +234,9 @@ __device__ __forceinline__ T prolong_site(const DevLevel<T>& C, int fi, int fj, 
 // smoothing) only d_{l-1} = d_l - z.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void k_lowrank_v(DevLevel<T> L, DevProblem P, int dir, unsigned slot, int want_dnext)
+__device__ __forceinline__ void lowrank_v_body(const DevLevel<T>& L, const DevProblem& P, const CycleState& cs,
+                                               int dir, unsigned slot, int want_dnext, double* z, double* zp)
 {
-    __shared__ double z[kMaxObs];
-    __shared__ double zp[kMaxObs];
-    const CycleState cs = *P.cs;
     const int m = P.m;
     for (int k = threadIdx.x; k < m; k += blockDim.x) {
         double acc = 0.0;
@@ -245,6 +262,40 @@ __global__ void k_lowrank_v(DevLevel<T> L, DevProblem P, int dir, unsigned slot,
     }
 }
 
+template <typename T>
+__global__ void k_lowrank_v(DevLevel<T> L, DevProblem P, int dir, unsigned slot, int want_dnext)
+{
+    __shared__ double z[kMaxObs];
+    __shared__ double zp[kMaxObs];
+    const CycleState cs = *P.cs;
+    lowrank_v_body<T>(L, P, cs, dir, slot, want_dnext, z, zp);
+}
+
+// theta' = theta*_s - G v on G's rows r0, r0 + stride, ...
+template <typename T>
+__device__ __forceinline__ void lowrank_rows(const DevLevel<T>& L, int m, int dir, const double* v, int r0, int stride)
+{
+    const int rows = L.g_rows[dir];
+    const double* G = L.g_val[dir];
+    for (int r = r0; r < rows; r += stride) {
+        double acc = 0.0;
+        for (int kk = 0; kk < m; ++kk) acc += G[(long long)r * m + kk] * v[kk];
+        const long long s = L.g_site[dir][r];
+        L.x[s] = (T)((double)L.x[s] - acc);
+    }
+}
+
+// d_{l-1} = d_l - B^T theta' = d_l - z + (B^T G) v
+template <typename T>
+__device__ __forceinline__ void lowrank_dnext(const DevLevel<T>& L, int m, const double* v)
+{
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        double acc = 0.0;
+        for (int t = 0; t < m; ++t) acc += L.BtG[k * m + t] * v[t];
+        L.dnext[k] = L.d[k] - L.lrv[m + k] + acc;
+    }
+}
+
 // theta' = theta*_s - G v on G's rows, spread over the grid; with want_dnext block 0
 // also forms d_{l-1} = d_l - B^T theta' = d_l - z + (B^T G) v
 template <typename T>
@@ -254,41 +305,32 @@ __global__ void k_lowrank_apply(DevLevel<T> L, DevProblem P, int dir, int want_d
     const int m = P.m;
     for (int k = threadIdx.x; k < m; k += blockDim.x) v[k] = L.lrv[k];
     __syncthreads();
-    const int rows = L.g_rows[dir];
-    const double* G = L.g_val[dir];
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
-        double acc = 0.0;
-        for (int kk = 0; kk < m; ++kk) acc += G[(long long)r * m + kk] * v[kk];
-        const long long s = L.g_site[dir][r];
-        L.x[s] = (T)((double)L.x[s] - acc);
-    }
-    if (want_dnext && blockIdx.x == 0)
-        for (int k = threadIdx.x; k < m; k += blockDim.x) {
-            double acc = 0.0;
-            for (int t = 0; t < m; ++t) acc += L.BtG[k * m + t] * v[t];
-            L.dnext[k] = L.d[k] - L.lrv[m + k] + acc;
-        }
+    lowrank_rows<T>(L, m, dir, v, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+    if (want_dnext && blockIdx.x == 0) lowrank_dnext<T>(L, m, v);
 }
 
 // r = f_l - A_l theta at every interior site of the fine grid (the restriction's input)
+template <typename T, int DIM>
+__device__ __forceinline__ void residual_site(const DevLevel<T>& F, long long s)
+{
+    int i = (int)(s % F.n), j = (int)((s / F.n) % F.n), k = DIM == 3 ? (int)(s / ((long long)F.n * F.n)) : 0;
+    long long e = site_offset(DIM, F.pitch, F.plane, F.base, i, j, k);
+    F.res[e] = (F.f ? F.f[e] : T(0)) - apply_A<DIM>(F, e);
+}
+
 template <typename T, int DIM>
 __global__ void k_residual(DevLevel<T> F)
 {
     long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long N = (long long)F.n * F.n * (DIM == 3 ? F.n : 1);
     if (s >= N) return;
-    int i = (int)(s % F.n), j = (int)((s / F.n) % F.n), k = DIM == 3 ? (int)(s / ((long long)F.n * F.n)) : 0;
-    long long e = site_offset(DIM, F.pitch, F.plane, F.base, i, j, k);
-    F.res[e] = (F.f ? F.f[e] : T(0)) - apply_A<DIM>(F, e);
+    residual_site<T, DIM>(F, s);
 }
 
 // f_c(I) = sum_p w(p) r(2I + p) over the 3^d fine sites 2I + p, p in {0, 1, 2}^d, from the residual field
 template <typename T, int DIM>
-__global__ void k_restrict(DevLevel<T> F, DevLevel<T> C)
+__device__ __forceinline__ void restrict_site(const DevLevel<T>& F, const DevLevel<T>& C, long long s)
 {
-    long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    long long N = (long long)C.n * C.n * (DIM == 3 ? C.n : 1);
-    if (s >= N) return;
     int I = (int)(s % C.n), J = (int)((s / C.n) % C.n), K = DIM == 3 ? (int)(s / ((long long)C.n * C.n)) : 0;
     T acc = T(0);
     const int nz = DIM == 3 ? 3 : 1;
@@ -304,14 +346,131 @@ __global__ void k_restrict(DevLevel<T> F, DevLevel<T> C)
 }
 
 template <typename T, int DIM>
+__global__ void k_restrict(DevLevel<T> F, DevLevel<T> C)
+{
+    long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long N = (long long)C.n * C.n * (DIM == 3 ? C.n : 1);
+    if (s >= N) return;
+    restrict_site<T, DIM>(F, C, s);
+}
+
+template <typename T, int DIM>
+__device__ __forceinline__ void prolong_add_site(const DevLevel<T>& C, const DevLevel<T>& F, long long s)
+{
+    int i = (int)(s % F.n), j = (int)((s / F.n) % F.n), k = DIM == 3 ? (int)(s / ((long long)F.n * F.n)) : 0;
+    long long e = site_offset(DIM, F.pitch, F.plane, F.base, i, j, k);
+    F.x[e] = F.x[e] + prolong_site<T, DIM>(C, i, j, k);
+}
+
+template <typename T, int DIM>
 __global__ void k_prolong(DevLevel<T> C, DevLevel<T> F)
 {
     long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long N = (long long)F.n * F.n * (DIM == 3 ? F.n : 1);
     if (s >= N) return;
-    int i = (int)(s % F.n), j = (int)((s / F.n) % F.n), k = DIM == 3 ? (int)(s / ((long long)F.n * F.n)) : 0;
-    long long e = site_offset(DIM, F.pitch, F.plane, F.base, i, j, k);
-    F.x[e] = F.x[e] + prolong_site<T, DIM>(C, i, j, k);
+    prolong_add_site<T, DIM>(C, F, s);
+}
+
+// ---------------------------------------------------------------------------
+// Grids 0..top of the general path in one CTA (2D).  The host lists the phases of one
+// visit of grid `top` -- with the V- or W-cycle recursion below it, in the order and
+// with the noise slots of the per-launch path -- and the CTA runs them one after the
+// other, a barrier after each phase (and between colours).  Every phase evaluates the
+// per-site functions of the per-launch kernels, so both give identical states; one
+// launch replaces the hundreds of small launches the coarse visits of a W-cycle need.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kSmallCycleThreads)
+    k_cycle_small(const DevLevel<T>* __restrict__ lv, DevProblem P, const double* __restrict__ chol, int n0,
+                  const int4* __restrict__ ops, int n_ops)
+{
+    __shared__ double r[MGMC_MAX_COARSEST];
+    __shared__ double g[kMaxObs];
+    __shared__ double z[kMaxObs];
+    __shared__ double zp[kMaxObs];
+    const CycleState cs = *P.cs;
+    const int m = P.m;
+    for (int q = 0; q < n_ops; ++q) {
+        const int4 op = ops[q];
+        const DevLevel<T>& L = lv[op.y];
+        const long long N = (long long)L.n * L.n;
+        switch (op.x) {
+        case kOpSweep: {
+            const unsigned slot = (unsigned)op.z;
+            const int dir = op.w;
+            const int nq = (L.n + 3) >> 2;
+            bool done = false;
+            if constexpr (std::is_same<T, double>::value) {
+                if (L.rad == 2) {
+                    for (int ci = 0; ci < 9; ++ci) {
+                        const int c = dir == 0 ? ci : 8 - ci;
+                        const long long sites = colour25_sites(L.n, c);
+                        for (long long t = threadIdx.x; t < sites; t += blockDim.x) sweep25_site(L, cs, c, slot, t);
+                        __syncthreads();
+                    }
+                    done = true;
+                }
+            }
+            if (done) break;
+            if (L.fine) {
+                for (int g2 = 0; g2 < 2; ++g2) {
+                    const int colour = dir == 0 ? g2 : 1 - g2;
+                    const long long items = (long long)L.n * nq;
+                    for (long long it = threadIdx.x; it < items; it += blockDim.x)
+                        sweep_item<T, 2>(L, P, cs, true, colour, slot, it);
+                    __syncthreads();
+                }
+            } else {
+                const int seq2[4] = {0, 3, 2, 1};
+                for (int ci = 0; ci < 4; ++ci) {
+                    const int c = seq2[dir == 0 ? ci : 3 - ci];
+                    const int py = (c >> 1) & 1;
+                    const long long items = (long long)((L.n - py + 1) / 2) * nq;
+                    for (long long it = threadIdx.x; it < items; it += blockDim.x)
+                        sweep_item<T, 2>(L, P, cs, false, c, slot, it);
+                    __syncthreads();
+                }
+            }
+            break;
+        }
+        case kOpLowrank: {
+            if (m == 0) break;
+            const int dir = (op.w & 3) == 2 ? -1 : (op.w & 3);
+            const int dn = (op.w >> 2) & 1;
+            lowrank_v_body<T>(L, P, cs, dir, (unsigned)op.z, dn, z, zp);
+            __syncthreads();
+            if (dir >= 0) {
+                for (int k = threadIdx.x; k < m; k += blockDim.x) zp[k] = L.lrv[k];
+                __syncthreads();
+                lowrank_rows<T>(L, m, dir, zp, threadIdx.x, blockDim.x);
+                if (dn) lowrank_dnext<T>(L, m, zp);
+            }
+            break;
+        }
+        case kOpRestrict: {
+            for (long long s2 = threadIdx.x; s2 < N; s2 += blockDim.x) residual_site<T, 2>(L, s2);
+            __syncthreads();
+            const DevLevel<T>& C = lv[op.y - 1];
+            const long long Nc = (long long)C.n * C.n;
+            for (long long s2 = threadIdx.x; s2 < Nc; s2 += blockDim.x) restrict_site<T, 2>(L, C, s2);
+            break;
+        }
+        case kOpZero:
+            for (long long e = threadIdx.x; e < L.alloc; e += blockDim.x) L.x[e] = T(0);
+            break;
+        case kOpCoarsest:
+            coarsest_slot_body<T>(lv[0], P, cs, chol, n0, (unsigned)op.z, r, g);
+            break;
+        case kOpProlong: {
+            const DevLevel<T>& C = lv[op.y - 1];
+            for (long long s2 = threadIdx.x; s2 < N; s2 += blockDim.x) prolong_add_site<T, 2>(C, L, s2);
+            break;
+        }
+        default:
+            break;
+        }
+        __syncthreads();
+    }
 }
 
 // The whole V-cycle below (and including) level `top`, one CTA.
@@ -550,6 +709,14 @@ void launch_coarsest_slot(const DevLevel<T>& L, const DevProblem& P, const doubl
 }
 
 template <typename T>
+void launch_cycle_small(const DevLevel<T>* levels_dev, const DevProblem& P, const double* chol, int n0,
+                        const int4* ops, int n_ops, cudaStream_t st, int& launches)
+{
+    k_cycle_small<T><<<1, kSmallCycleThreads, 0, st>>>(levels_dev, P, chol, n0, ops, n_ops);
+    ++launches;
+}
+
+template <typename T>
 void launch_qoi(const DevLevel<T>& L, int n_qoi, const long long* q_site, const double* q_w, const DevProblem& P,
                 cudaStream_t st, int& launches)
 {
@@ -607,6 +774,8 @@ void launch_resid(const DevLevel<T>& L, const DevProblem& P, double* u, double* 
     template void launch_prolong<T>(const DevLevel<T>&, const DevLevel<T>&, cudaStream_t, int&);                 \
     template void launch_coarsest_slot<T>(const DevLevel<T>&, const DevProblem&, const double*, int, unsigned,     \
                                           cudaStream_t, int&);                                                   \
+    template void launch_cycle_small<T>(const DevLevel<T>*, const DevProblem&, const double*, int, const int4*,    \
+                                        int, cudaStream_t, int&);                                                \
     template void launch_qoi<T>(const DevLevel<T>&, int, const long long*, const double*, const DevProblem&,      \
                                 cudaStream_t, int&);                                                             \
     template void launch_pack<T>(const DevLevel<T>&, T*, bool, cudaStream_t);                               \

@@ -17,6 +17,13 @@ void launch_restrict(const DevLevel<T>& F, const DevLevel<T>& C, cudaStream_t st
 template <typename T>
 void launch_coarsest_slot(const DevLevel<T>& L, const DevProblem& P, const double* chol, int n0, unsigned slot,
                           cudaStream_t st, int& launches);
+// the small grids of the general path (2D) in one CTA: a list of phases {code, level, slot,
+// flags} the host builds from the cycle's recursion (kernels.cu, k_cycle_small)
+enum { kOpSweep = 0, kOpLowrank = 1, kOpRestrict = 2, kOpZero = 3, kOpCoarsest = 4, kOpProlong = 5 };
+constexpr int kSmallCycleThreads = 512;
+template <typename T>
+void launch_cycle_small(const DevLevel<T>* levels_dev, const DevProblem& P, const double* chol, int n0,
+                        const int4* ops, int n_ops, cudaStream_t st, int& launches);
 template <typename T>
 void launch_prolong(const DevLevel<T>& C, const DevLevel<T>& F, cudaStream_t st, int& launches);
 // one chain of a batched coarse-grid launch

@@ -51,13 +51,14 @@ def _gpu(p, gamma, **kw):
     return Sampler(p, precision="fp64", gamma=gamma, **kw)
 
 
-@pytest.mark.parametrize("n,gamma", [(31, 2), (63, 2), (63, 1), (127, 2)])
-def test_ssl_parity(torch_mod, n, gamma):
+@pytest.mark.parametrize("n,gamma,cmax", [(31, 2, 0), (63, 2, 0), (63, 1, 0), (127, 2, 0), (127, 2, 1)])
+def test_ssl_parity(torch_mod, n, gamma, cmax):
     """The Table 1c posterior (squared shifted Laplacian, 8 ball observations), per site
-    after 1, 5 and 40 cycles, QoI series included; 63^2 also as a V-cycle."""
+    after 1, 5 and 40 cycles, QoI series included; 63^2 also as a V-cycle.  cmax = 0: the
+    grids up to 63^2 in the one-CTA kernel; 1: every grid on its own launches."""
     p = inputs.table1c(n)
     o = _orc(p, gamma)
-    s = _gpu(p, gamma)
+    s = _gpu(p, gamma, coarse_max_n=cmax)
     tol = _tol(p)
     for n_steps in (1, 5, 40):
         xo, qo = o.sample(n_steps, 77)
@@ -82,6 +83,24 @@ def test_sl_w_cycle_parity(torch_mod, n, m, nu):
         _check64(xg, xo)
         _check64(qg, qo)
     s.close()
+
+
+@pytest.mark.parametrize("disc,n,gamma", [(2, 127, 2), (2, 63, 1), (0, 127, 2), (0, 63, 2)])
+def test_small_grid_kernel_is_bitwise_per_launch_path(torch_mod, disc, n, gamma):
+    """The one-CTA kernel of the small grids gives the same bits as one launch per phase
+    (coarse_max_n = 1), with far fewer launches; 63^2 runs the whole cycle in it."""
+    if disc == 2:
+        p = inputs.table1c(n)
+    else:
+        p = inputs.make_problem("w", 2, n, kappa2_seed=3, m=6, obs_seed=2, qoi_cells=(n + 1) // 4)
+    a = _gpu(p, gamma, coarse_max_n=1)
+    b = _gpu(p, gamma)
+    xa, qa = _run_gpu(torch_mod, a, p, 12, 31, step_offset=5)
+    xb, qb = _run_gpu(torch_mod, b, p, 12, 31, step_offset=5)
+    assert np.array_equal(xa, xb) and np.array_equal(qa, qb)
+    assert b.launches_per_cycle() < a.launches_per_cycle()
+    a.close()
+    b.close()
 
 
 def test_ssl_gibbs_and_mean_solve(torch_mod):
