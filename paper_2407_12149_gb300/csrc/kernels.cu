@@ -376,8 +376,9 @@ __global__ void k_prolong(DevLevel<T> C, DevLevel<T> F)
 // visit of grid `top` -- with the V- or W-cycle recursion below it, in the order and
 // with the noise slots of the per-launch path -- and the CTA runs them one after the
 // other, a barrier after each phase (and between colours).  Every phase evaluates the
-// per-site functions of the per-launch kernels, so both give identical states; one
-// launch replaces the hundreds of small launches the coarse visits of a W-cycle need.
+// per-site functions of the per-launch kernels (the two agree to rounding: the compiler
+// may contract their multiply-adds differently); one launch replaces the hundreds of
+// small launches the coarse visits of a W-cycle need.
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kSmallCycleThreads)
