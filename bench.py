@@ -218,6 +218,8 @@ WORKLOADS = {
     "gibbs-vs-mgmc-2d-q1": {"n": 511, "chains": 1, "table": True, "q1": True},   # Table 1a setting (Q1 elements)
     # Table 1c setting: squared shifted Laplacian (13-point FD), W-cycle, FP64
     "gibbs-vs-mgmc-2d-ssl": {"n": 511, "chains": 1, "table": True, "ssl": True},
+    # time per W-cycle of the Table 1c setting, 31^2 .. 511^2 (no IACT): the cost side alone
+    "wcycle-ssl-steps": {"n": 511, "chains": 1, "wsteps": True},
     "convergence-2d": {"n": 255, "chains": 512, "conv": True},   # Sec. 5.3: R, Z, rates, RMSE (Q1, 31^2..255^2)
     "tc-gemm-8192": {"n": 8192, "chains": 1, "gemm": True},      # the U-Net's tensor-core GEMM, 8192^3 BF16
 }
@@ -881,6 +883,53 @@ def run_gibbs_table(args):
     print(json.dumps(line), flush=True)
 
 
+def run_wcycle_steps(args):
+    """Time per MGMC W(1,1)-cycle of the Table 1c setting (squared shifted Laplacian,
+    13-point finite differences, FP64, one chain) on 31^2 .. 511^2: CUDA events over
+    --steps back-to-back cycles after --warmup, state resident, the small grids in the
+    one-CTA kernel (default) and with one launch per phase (coarse_max_n = 1)."""
+    import torch
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    from paper_2407_12149_gb300 import build, inputs
+    from paper_2407_12149_gb300 import mgmc as M
+    build.build()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(gpu_id_for_smi(torch, local))
+    rows = []
+    for n in (31, 63, 127, 255, 511):
+        p = inputs.table1c(n)
+        row = {"n": n}
+        for key, cmax in (("small_kernel", 0), ("per_phase_launches", 1)):
+            s = M.Sampler(p, precision="fp64", coarse_max_n=cmax, device=local)
+            x = s.zeros()
+            s.sample(x, args.warmup, 7)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.sample(None, args.steps, 7, step_offset=args.warmup)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            row[f"ms_per_cycle_{key}"] = e0.elapsed_time(e1) / args.steps
+            row[f"launches_{key}"] = s.launches_per_cycle()
+            s.close()
+        rows.append(row)
+    clk = clocks.stop()
+    big = rows[-1]
+    line = {
+        "metric": "ms per W-cycle step (Table 1c setting, 511^2)", "value": big["ms_per_cycle_small_kernel"],
+        "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": big["ms_per_cycle_small_kernel"], "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "wcycle-ssl-steps: squared shifted Laplacian (13-point FD, u = du/dn = 0), "
+                               "kappa^-1 = 0.1, 8 ball obs, W(1,1)-cycle, FP64, one chain, 31^2 .. 511^2",
+                   "table": rows, "timing": "CUDA events over back-to-back cycles, state resident (L2)"},
+        "roofline": None, "cpu_baseline": None, "e2e": None, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_convergence(args):
     """The experiments of Sec. 5.3 on the Table 1a posterior (Q1 elements, kappa^-1 = 0.1,
     8 point observations), FP32: many independent chains from theta^(0) = 0 -- MGMC as
@@ -993,6 +1042,8 @@ def main():
         run_warmstart(args)
     elif WORKLOADS[args.workload].get("table"):
         run_gibbs_table(args)
+    elif WORKLOADS[args.workload].get("wsteps"):
+        run_wcycle_steps(args)
     elif WORKLOADS[args.workload].get("conv"):
         run_convergence(args)
     elif WORKLOADS[args.workload].get("gemm"):

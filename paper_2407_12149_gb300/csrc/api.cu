@@ -502,8 +502,8 @@ void enqueue_level(mgmc_ctx* h, int l, std::vector<int>& visit, cudaStream_t s, 
     if (l <= h->small_top) {
         // this visit's phase list (built at creation in the same visit order)
         const int k = h->small_next++;
-        launch_cycle_small<T>((const DevLevel<T>*)h->levels_dev, P, h->chol, h->n0, h->small_ops + h->small_off[k],
-                              h->small_cnt[k], s, launches);
+        launch_cycle_small<T>((const DevLevel<T>*)h->levels_dev, h->small_top, P, h->chol, h->n0,
+                              h->small_ops + h->small_off[k], h->small_cnt[k], s, launches);
         return;
     }
     const int v = visit[(size_t)l]++;
@@ -854,7 +854,7 @@ mgmc_status mgmc_create(const mgmc_config* cfg_in, const mgmc_allocator* alloc, 
     // recursive path (2D): the grids with n <= coarse_max_n (0: 63) in one CTA per visit
     if (h->recursive && !cfg.gibbs && cfg.dim == 2) {
         const int thr = cfg.coarse_max_n > 0 ? cfg.coarse_max_n : 63;
-        for (int l = 0; l < h->L; ++l)
+        for (int l = 0; l < h->L && l < kSmallMaxLevels; ++l)
             if (hp.lev[l].n <= thr) h->small_top = l;
         if (h->small_top >= 1) {
             std::vector<int> visit((size_t)h->L, 0);

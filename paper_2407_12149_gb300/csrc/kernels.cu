@@ -380,19 +380,33 @@ __global__ void k_prolong(DevLevel<T> C, DevLevel<T> F)
 // may contract their multiply-adds differently); one launch replaces the hundreds of
 // small launches the coarse visits of a W-cycle need.
 // ---------------------------------------------------------------------------
+// The descriptors of grids 0..top and (up to kSmallMaxOps) the phase list are staged in
+// shared memory first, so that a phase's data loads do not wait on two dependent global
+// loads (the phase, then the descriptor fields) each time.
 template <typename T>
 __global__ void __launch_bounds__(kSmallCycleThreads)
-    k_cycle_small(const DevLevel<T>* __restrict__ lv, DevProblem P, const double* __restrict__ chol, int n0,
-                  const int4* __restrict__ ops, int n_ops)
+    k_cycle_small(const DevLevel<T>* __restrict__ lv_g, int top, DevProblem P, const double* __restrict__ chol,
+                  int n0, const int4* __restrict__ ops_g, int n_ops)
 {
     __shared__ double r[MGMC_MAX_COARSEST];
     __shared__ double g[kMaxObs];
     __shared__ double z[kMaxObs];
     __shared__ double zp[kMaxObs];
+    __shared__ DevLevel<T> lv[kSmallMaxLevels];
+    __shared__ int4 ops_s[kSmallMaxOps];
+    {
+        const int words = (top + 1) * (int)(sizeof(DevLevel<T>) / sizeof(unsigned long long));
+        const unsigned long long* src = reinterpret_cast<const unsigned long long*>(lv_g);
+        unsigned long long* dst = reinterpret_cast<unsigned long long*>(lv);
+        for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = src[w];
+        const int ns = n_ops < kSmallMaxOps ? n_ops : kSmallMaxOps;
+        for (int q = threadIdx.x; q < ns; q += blockDim.x) ops_s[q] = ops_g[q];
+    }
+    __syncthreads();
     const CycleState cs = *P.cs;
     const int m = P.m;
     for (int q = 0; q < n_ops; ++q) {
-        const int4 op = ops[q];
+        const int4 op = q < kSmallMaxOps ? ops_s[q] : ops_g[q];
         const DevLevel<T>& L = lv[op.y];
         const long long N = (long long)L.n * L.n;
         switch (op.x) {
@@ -710,10 +724,10 @@ void launch_coarsest_slot(const DevLevel<T>& L, const DevProblem& P, const doubl
 }
 
 template <typename T>
-void launch_cycle_small(const DevLevel<T>* levels_dev, const DevProblem& P, const double* chol, int n0,
+void launch_cycle_small(const DevLevel<T>* levels_dev, int top, const DevProblem& P, const double* chol, int n0,
                         const int4* ops, int n_ops, cudaStream_t st, int& launches)
 {
-    k_cycle_small<T><<<1, kSmallCycleThreads, 0, st>>>(levels_dev, P, chol, n0, ops, n_ops);
+    k_cycle_small<T><<<1, kSmallCycleThreads, 0, st>>>(levels_dev, top, P, chol, n0, ops, n_ops);
     ++launches;
 }
 
@@ -775,8 +789,8 @@ void launch_resid(const DevLevel<T>& L, const DevProblem& P, double* u, double* 
     template void launch_prolong<T>(const DevLevel<T>&, const DevLevel<T>&, cudaStream_t, int&);                 \
     template void launch_coarsest_slot<T>(const DevLevel<T>&, const DevProblem&, const double*, int, unsigned,     \
                                           cudaStream_t, int&);                                                   \
-    template void launch_cycle_small<T>(const DevLevel<T>*, const DevProblem&, const double*, int, const int4*,    \
-                                        int, cudaStream_t, int&);                                                \
+    template void launch_cycle_small<T>(const DevLevel<T>*, int, const DevProblem&, const double*, int,            \
+                                        const int4*, int, cudaStream_t, int&);                                   \
     template void launch_qoi<T>(const DevLevel<T>&, int, const long long*, const double*, const DevProblem&,      \
                                 cudaStream_t, int&);                                                             \
     template void launch_pack<T>(const DevLevel<T>&, T*, bool, cudaStream_t);                               \

@@ -21,8 +21,10 @@ void launch_coarsest_slot(const DevLevel<T>& L, const DevProblem& P, const doubl
 // flags} the host builds from the cycle's recursion (kernels.cu, k_cycle_small)
 enum { kOpSweep = 0, kOpLowrank = 1, kOpRestrict = 2, kOpZero = 3, kOpCoarsest = 4, kOpProlong = 5 };
 constexpr int kSmallCycleThreads = 512;
+constexpr int kSmallMaxLevels = 16;   // grids 0..top held by the kernel (top < 16)
+constexpr int kSmallMaxOps = 1024;    // phases staged in shared memory (later ones read from global)
 template <typename T>
-void launch_cycle_small(const DevLevel<T>* levels_dev, const DevProblem& P, const double* chol, int n0,
+void launch_cycle_small(const DevLevel<T>* levels_dev, int top, const DevProblem& P, const double* chol, int n0,
                         const int4* ops, int n_ops, cudaStream_t st, int& launches);
 template <typename T>
 void launch_prolong(const DevLevel<T>& C, const DevLevel<T>& F, cudaStream_t st, int& launches);
