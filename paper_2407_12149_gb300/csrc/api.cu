@@ -113,6 +113,7 @@ struct mgmc_ctx {
     // grid small_top (-1: none); the phase lists of the cycle's visits, in cycle order
     int small_top = -1;
     int4* small_ops = nullptr;
+    double* small_z = nullptr;   // normals of one sweep of the largest 25-point grid held
     std::vector<int> small_off, small_cnt;
     int small_next = 0;
     DevProblem* P_dev = nullptr;   // device copy of P (batched launches)
@@ -503,7 +504,7 @@ void enqueue_level(mgmc_ctx* h, int l, std::vector<int>& visit, cudaStream_t s, 
         // this visit's phase list (built at creation in the same visit order)
         const int k = h->small_next++;
         launch_cycle_small<T>((const DevLevel<T>*)h->levels_dev, h->small_top, P, h->chol, h->n0,
-                              h->small_ops + h->small_off[k], h->small_cnt[k], s, launches);
+                              h->small_ops + h->small_off[k], h->small_cnt[k], h->small_z, s, launches);
         return;
     }
     const int v = visit[(size_t)l]++;
@@ -861,6 +862,10 @@ mgmc_status mgmc_create(const mgmc_config* cfg_in, const mgmc_allocator* alloc, 
             std::vector<int4> ops;
             plan_small(h, h->L - 1, visit, ops);
             h->small_ops = upload(h, ops, st);
+            long long zmax = 1;
+            for (int l = 0; l <= h->small_top; ++l) zmax = std::max(zmax, (long long)hp.lev[l].n * hp.lev[l].n);
+            h->small_z = (double*)h->buf.get((size_t)zmax * sizeof(double));
+            if (!h->small_z) return cleanup(fail(MGMC_ERR_OOM, "allocator returned NULL"));
             if (st != MGMC_OK) return cleanup(fail(st, "device upload failed"));
         } else {
             h->small_top = -1;

@@ -100,12 +100,40 @@ __device__ __forceinline__ long long colour25_sites(int n, int colour)
     return nx > 0 && ny > 0 ? (long long)nx * ny : 0;
 }
 
+// the t-th site (i, j) of class `colour` = cx + 3 cy
+__device__ __forceinline__ void colour25_site(int n, int colour, long long t, int& i, int& j)
+{
+    const int cx = colour % 3, cy = colour / 3;
+    const int nx = (n - cx + 2) / 3;
+    i = cx + 3 * (int)(t % nx);
+    j = cy + 3 * (int)(t / nx);
+}
+
+// the site normals of one sweep of a 25-point grid into zb[j n + i], the draws of
+// sweep25_site: item (j, q, px) gives the pair of sites 4q + px and 4q + px + 2 (z0, z1
+// of the half block px of row j's block q)
+__device__ __forceinline__ void draw25_pair(const DevLevel<double>& L, const CycleState& cs, unsigned slot,
+                                            double* zb, long long item)
+{
+    const int n = L.n, nq = (n + 3) >> 2;
+    const int px = (int)(item & 1);
+    const long long rq = item >> 1;
+    const int q = (int)(rq % nq), j = (int)(rq / nq);
+    const int i0 = 4 * q + px;
+    if (i0 >= n) return;
+    double z0, z1;
+    draw_half_ctr<double>(noise_counter(cs, 0u, 0u, L.level, slot), (unsigned)(j * nq + q), px, (unsigned)cs.seed,
+                          (unsigned)(cs.seed >> 32), z0, z1);
+    zb[(long long)j * n + i0] = z0;
+    if (i0 + 2 < n) zb[(long long)j * n + i0 + 2] = z1;
+}
+
 __device__ __forceinline__ void sweep25_site(const DevLevel<double>& L, const CycleState& cs, int colour,
                                              unsigned slot, long long t)
 {
-    const int n = L.n, cx = colour % 3, cy = colour / 3;
-    const int nx = (n - cx + 2) / 3;
-    const int i = cx + 3 * (int)(t % nx), j = cy + 3 * (int)(t / nx);
+    const int n = L.n;
+    int i, j;
+    colour25_site(n, colour, t, i, j);
     double z = 0.0;
     if (cs.noise) {
         double z0, z1;
@@ -386,7 +414,7 @@ __global__ void k_prolong(DevLevel<T> C, DevLevel<T> F)
 template <typename T>
 __global__ void __launch_bounds__(kSmallCycleThreads)
     k_cycle_small(const DevLevel<T>* __restrict__ lv_g, int top, DevProblem P, const double* __restrict__ chol,
-                  int n0, const int4* __restrict__ ops_g, int n_ops)
+                  int n0, const int4* __restrict__ ops_g, int n_ops, double* __restrict__ zb)
 {
     __shared__ double r[MGMC_MAX_COARSEST];
     __shared__ double g[kMaxObs];
@@ -417,10 +445,23 @@ __global__ void __launch_bounds__(kSmallCycleThreads)
             bool done = false;
             if constexpr (std::is_same<T, double>::value) {
                 if (L.rad == 2) {
+                    // the sweep's normals first, for all sites at once (one draw per pair), then
+                    // the nine classes read them: the colour phases carry no Box-Muller transform
+                    if (cs.noise) {
+                        const long long items = (long long)L.n * nq * 2;
+                        for (long long it = threadIdx.x; it < items; it += blockDim.x) draw25_pair(L, cs, slot, zb, it);
+                        __syncthreads();
+                    }
                     for (int ci = 0; ci < 9; ++ci) {
                         const int c = dir == 0 ? ci : 8 - ci;
                         const long long sites = colour25_sites(L.n, c);
-                        for (long long t = threadIdx.x; t < sites; t += blockDim.x) sweep25_site(L, cs, c, slot, t);
+                        for (long long t = threadIdx.x; t < sites; t += blockDim.x) {
+                            int i, j;
+                            colour25_site(L.n, c, t, i, j);
+                            const double zz = cs.noise ? zb[(long long)j * L.n + i] : 0.0;
+                            const long long e = site_offset(2, L.pitch, L.plane, L.base, i, j, 0);
+                            L.x[e] = update25(L, e, zz);
+                        }
                         __syncthreads();
                     }
                     done = true;
@@ -725,9 +766,9 @@ void launch_coarsest_slot(const DevLevel<T>& L, const DevProblem& P, const doubl
 
 template <typename T>
 void launch_cycle_small(const DevLevel<T>* levels_dev, int top, const DevProblem& P, const double* chol, int n0,
-                        const int4* ops, int n_ops, cudaStream_t st, int& launches)
+                        const int4* ops, int n_ops, double* zb, cudaStream_t st, int& launches)
 {
-    k_cycle_small<T><<<1, kSmallCycleThreads, 0, st>>>(levels_dev, top, P, chol, n0, ops, n_ops);
+    k_cycle_small<T><<<1, kSmallCycleThreads, 0, st>>>(levels_dev, top, P, chol, n0, ops, n_ops, zb);
     ++launches;
 }
 
@@ -790,7 +831,7 @@ void launch_resid(const DevLevel<T>& L, const DevProblem& P, double* u, double* 
     template void launch_coarsest_slot<T>(const DevLevel<T>&, const DevProblem&, const double*, int, unsigned,     \
                                           cudaStream_t, int&);                                                   \
     template void launch_cycle_small<T>(const DevLevel<T>*, int, const DevProblem&, const double*, int,            \
-                                        const int4*, int, cudaStream_t, int&);                                   \
+                                        const int4*, int, double*, cudaStream_t, int&);                          \
     template void launch_qoi<T>(const DevLevel<T>&, int, const long long*, const double*, const DevProblem&,      \
                                 cudaStream_t, int&);                                                             \
     template void launch_pack<T>(const DevLevel<T>&, T*, bool, cudaStream_t);                               \

@@ -23,9 +23,10 @@ enum { kOpSweep = 0, kOpLowrank = 1, kOpRestrict = 2, kOpZero = 3, kOpCoarsest =
 constexpr int kSmallCycleThreads = 512;
 constexpr int kSmallMaxLevels = 16;   // grids 0..top held by the kernel (top < 16)
 constexpr int kSmallMaxOps = 1024;    // phases staged in shared memory (later ones read from global)
+// zb: scratch of n^2 doubles for the largest 25-point grid held (the normals of a sweep)
 template <typename T>
 void launch_cycle_small(const DevLevel<T>* levels_dev, int top, const DevProblem& P, const double* chol, int n0,
-                        const int4* ops, int n_ops, cudaStream_t st, int& launches);
+                        const int4* ops, int n_ops, double* zb, cudaStream_t st, int& launches);
 template <typename T>
 void launch_prolong(const DevLevel<T>& C, const DevLevel<T>& F, cudaStream_t st, int& launches);
 // one chain of a batched coarse-grid launch
