@@ -238,6 +238,16 @@ mgmc_status build_device_levels(mgmc_ctx* h, const HostProblem& hp)
                 for (int t = 1; t < D.ncoef; ++t) coef[(size_t)t * D.alloc + e] = (T)a[hp.C + t];
             }
             D.coef = upload(h, coef, st);
+            if (R == 2 && sizeof(T) == 8) {
+                std::vector<double> aux((size_t)D.alloc * 2, 0.0);
+                for (long long s2 = 0; s2 < HL.N; ++s2) {
+                    const long long e = off(s2);
+                    const double aii = HL.st[(size_t)s2 * hp.NS + hp.C];
+                    aux[(size_t)e] = 1.0 / aii;
+                    aux[(size_t)D.alloc + (size_t)e] = std::sqrt(aii);
+                }
+                D.inv_sqrt25 = upload(h, aux, st);
+            }
         }
         if (hp.m > 0) {
             // rows of B grouped by grid row, sorted by x index

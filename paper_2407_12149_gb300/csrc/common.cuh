@@ -63,6 +63,9 @@ struct DevLevel {
     // the squared shifted Laplacian: offsets o = (dx+2) + 5 (dy+2), centre 12, slot t >= 1
     // = a(i, i + o_{12+t}); two halo rows and columns around the interior)
     int rad;
+    // FP64 25-point grids: 1 / a_ii at [e] and sqrt(a_ii) at [alloc + e] (correctly rounded on
+    // the host), so that a site update needs neither a division nor a square root
+    const double* inv_sqrt25;
     // B_l rows grouped by grid row (finest level; used by the residual norm)
     const int* brow_ptr;    // [n^(dim-1) + 1]
     const int* bent_i;      // x index of the entry

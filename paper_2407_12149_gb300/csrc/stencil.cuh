@@ -55,18 +55,18 @@ __device__ __forceinline__ double coef25_at(const DevLevel<double>& L, long long
 }
 
 // one Gibbs update of a 25-point site, x_i <- (f_i + sqrt(a_ii) z - sum_{j != i} a_ij x_j) / a_ii
-// with the neighbours in lexicographic offset order
+// with the neighbours in lexicographic offset order; 1 / a_ii and sqrt(a_ii) come from the
+// host (FP64 division and square root are long instruction sequences on this GPU)
 __device__ __forceinline__ double update25(const DevLevel<double>& L, long long e, double z)
 {
-    const double aii = L.coef[e];
     double acc = L.f ? L.f[e] : 0.0;
-    acc += sqrt(aii) * z;
+    acc += L.inv_sqrt25[L.alloc + e] * z;
 #pragma unroll
     for (int o = 0; o < 25; ++o) {
         if (o == 12) continue;
         acc -= coef25_at(L, e, o) * L.x[e + off25(o, L.pitch)];
     }
-    return acc / aii;
+    return acc * L.inv_sqrt25[e];
 }
 
 // ---------------------------------------------------------------------------
