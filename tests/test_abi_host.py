@@ -51,10 +51,17 @@ def test_point_obs_rows_rejects_outside_points(lib):
 @pytest.mark.parametrize("kw,msg", [(dict(dim=4, n=7), "dim"), (dict(dim=2, n=30), "2^k - 1"),
                                     (dict(dim=2, n=7, n_levels=9), "n_levels"),
                                     (dict(dim=2, n=7, precision=5), "precision"),
-                                    (dict(dim=2, n=7, band_min_n=-1), "band_min_n")])
+                                    (dict(dim=2, n=7, band_min_n=-1), "band_min_n"),
+                                    (dict(dim=2, n=7, disc=2, precision=1), "FP64"),
+                                    (dict(dim=2, n=7, gamma=3), "gamma"),
+                                    (dict(dim=2, n=16383, gamma=2, nu=16), "noise slots")])
 def test_create_rejects_bad_config(lib, kw, msg):
-    cfg = mgmc.mgmc_config(kw.get("dim", 2), kw.get("n", 7), kw.get("n_levels", 0), 1, 1, kw.get("precision", 0), 1, 0)
+    nu = kw.get("nu", 1)
+    cfg = mgmc.mgmc_config(kw.get("dim", 2), kw.get("n", 7), kw.get("n_levels", 0), nu, nu, kw.get("precision", 0), 1,
+                           0)
     cfg.band_min_n = kw.get("band_min_n", 0)
+    cfg.disc = kw.get("disc", 0)
+    cfg.gamma = kw.get("gamma", 0)
     h = ctypes.c_void_p()
     rc = lib.mgmc_create(ctypes.byref(cfg), None, None, None, 10.0, 0, None, None, 1, None, None, 0, None, None,
                          ctypes.byref(h))
