@@ -85,6 +85,20 @@ def test_sl_w_cycle_parity(torch_mod, n, m, nu):
     s.close()
 
 
+def test_w_cycle_parity_3d(torch_mod):
+    """The W-cycle in 3D (15^3, four grids, non-stationary kappa^2, observations): the
+    general kernels with the recursion, every grid on its own launches."""
+    p = inputs.make_problem("w3", 3, 15, kappa2_seed=4, m=4, obs_seed=3, qoi_cells=4)
+    o = _orc(p, 2)
+    s = _gpu(p, 2)
+    for n_steps in (1, 10):
+        xo, qo = o.sample(n_steps, 13)
+        xg, qg = _run_gpu(torch_mod, s, p, n_steps, 13)
+        _check64(xg, xo)
+        _check64(qg, qo)
+    s.close()
+
+
 @pytest.mark.parametrize("disc,n,gamma", [(2, 127, 2), (2, 63, 1), (0, 127, 2), (0, 63, 2)])
 def test_small_grid_kernel_is_bitwise_per_launch_path(torch_mod, disc, n, gamma):
     """The one-CTA kernel of the small grids evaluates the per-site functions of the
